@@ -1,0 +1,258 @@
+/*
+ * ddnm.h -- C ABI of the GB300 (sm_103a) library for the online solve of the
+ * domain-decomposition nonlinear-manifold ROM with hyper-reduction of
+ * Diaz, Choi & Heinkenschloss, arXiv 2305.15163 ("the paper").
+ *
+ * The library solves, for a batch of parameters mu = (a, lambda), the WFPC
+ * DD-LSPG-ROM of Sec. 3.1, Eq. (dd_lspg_NLP):
+ *
+ *     min  1/2 sum_i || Z_i r_i( g_i^O(xh_i^O), g_i^G(xh_i^G) ) ||^2
+ *     s.t. sum_i C A_i g_i^G(xh_i^G) = 0
+ *
+ * on the steady 2D Burgers problem of Sec. 7.1 (centred finite differences,
+ * Dirichlet data from the exact solution Eq. (burgers_pde_exact_solution)),
+ * with the Lagrange-Gauss-Newton SQP of Sec. 4.1 (KKT system Eq. (sqp_system),
+ * Gauss-Newton Hessian Eq. (gauss_newton_hessian), update Eq. (sqp_update)).
+ *
+ * Conventions shared by every call:
+ *  - Grid: nx x ny interior nodes of the box [box0,box1] x [box2,box3],
+ *    x_i = box0 + i h_x, h_x = (box1-box0)/(nx+1), i = 1..nx (same in y).
+ *  - State ordering x = [u; v], each block x-fastest: u at node (i,j) has
+ *    global id (j-1)*nx + (i-1), v at that node has id nx*ny + that.
+ *  - Subdomains are boxes of nodes cut at breakpoints xb[0..kx], yb[0..ky]
+ *    (0 = xb[0] < ... < xb[kx] = nx); subdomain s = sy*kx + sx.
+ *  - Residual rows of subdomain s (Sec. 2, P_s^r): u rows of its owned nodes in
+ *    ascending node order, then the v rows; HR rows are indices into that list.
+ *  - Interior / interface states of s (Sec. 2, P_s^O, P_s^G): global variable
+ *    ids in ascending order.  Interface = variables entering the residual rows
+ *    of s and of at least one other subdomain; interior = the rest.
+ *  - Compatibility rows (Eq. compatibility_conditions_mat): for every shared
+ *    variable (ascending id), with S = sorted subdomains sharing it, the rows
+ *    x_{S0} - x_{S1} = 0, x_{S1} - x_{S2} = 0, ...; N_A rows in total.
+ *  - Latent vector xh = [xh_0^O; xh_0^G; xh_1^O; ...] (Eq. sqp_notation), n_D
+ *    entries; multipliers lambda have n_C entries; the KKT right-hand side is
+ *    F = [rho_0; ...; rho_{n-1}; Atil] (n_D + n_C), rho_i of
+ *    Eq. (optimality_residuals_GN), Atil = sum_i C A_i g_i^G.
+ *  - All arrays are dense, row-major, FP64 unless stated.
+ *
+ * Ownership: every call copies what it needs from the caller's arrays; the
+ * caller keeps ownership and may free them on return (for mem_kind
+ * DDNM_MEM_DEVICE, once the stream has passed the call).
+ *
+ * Errors: every int-returning call returns DDNM_OK (0) or a negative DDNM_E_*
+ * code; ddnm_last_error(ctx) then holds a one-line message.  A solve that does
+ * not converge is not an error: it is a per-instance status in ddnm_stats.
+ * No call falls back to a CPU implementation.  ddnm_setup and the query calls
+ * are host bookkeeping and work without a GPU; the first call that computes
+ * (solve, residual, linearize) uploads the tables to the device and fails with
+ * DDNM_E_CUDA when no usable CUDA device is present.
+ *
+ * Threading: one context per host thread at a time; calls on one context are
+ * not thread-safe.  Work is queued on the caller's stream (NULL = legacy
+ * default stream).  With DDNM_MEM_HOST the call returns after the results are
+ * in the caller's host arrays; with DDNM_MEM_DEVICE it returns once the work is
+ * queued and the output pointers are device pointers written by that stream.
+ */
+#ifndef DDNM_H
+#define DDNM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDNM_OK 0
+#define DDNM_E_INVALID (-1)      /* bad argument or size mismatch */
+#define DDNM_E_STATE (-2)        /* call made in the wrong order (e.g. solve before all decoders are loaded) */
+#define DDNM_E_CUDA (-3)         /* CUDA runtime error, or no usable device */
+#define DDNM_E_NOMEM (-4)        /* device or host allocation failed */
+#define DDNM_E_UNSUPPORTED (-5)  /* sizes beyond what the kernels are built for */
+
+enum { DDNM_FP64 = 0, DDNM_MIXED = 1 };                       /* evaluation precision */
+enum { DDNM_ACT_SWISH = 0, DDNM_ACT_SIGMOID = 1, DDNM_ACT_IDENTITY = 2 };
+enum { DDNM_MEM_HOST = 0, DDNM_MEM_DEVICE = 1 };
+enum { DDNM_DECODER_INTERIOR = 0, DDNM_DECODER_INTERFACE = 1 };
+
+/* per-instance termination status (ddnm_stats.status) */
+enum {
+    DDNM_CONVERGED = 0,  /* ||F||_2 < tol at an accepted iterate */
+    DDNM_MAX_ITER = 1,   /* max_iter accepted steps taken without convergence */
+    DDNM_NONFINITE = 2,  /* the merit became NaN or Inf at an accepted iterate */
+    DDNM_KKT_FAIL = 3    /* KKT system not solvable by the Schur route (Lemma 1 fails) */
+};
+/* per-instance flags (ddnm_stats.flags, bit mask) */
+#define DDNM_FLAG_LS_FAIL 1   /* some line search took its last trial without passing Armijo */
+
+/* Problem statement (Sec. 2, 3.1, 7.1). */
+typedef struct ddnm_problem {
+    int nx, ny;             /* interior grid nodes */
+    double nu;              /* viscosity */
+    double box[4];          /* x0, x1, y0, y1 of the domain */
+    int kx, ky;             /* subdomains in x and y */
+    const int* xb;          /* kx+1 node breakpoints, 0 .. nx */
+    const int* yb;          /* ky+1 node breakpoints, 0 .. ny */
+    const int* n_omega;     /* kx*ky interior latent dims n_i^O (1..16) */
+    const int* n_gamma;     /* kx*ky interface latent dims n_i^G (1..8, n_i^O + n_i^G <= 16) */
+    const int* hr_count;    /* kx*ky collocation row counts N_i^B (>= n_i^O + n_i^G) */
+    const int* hr_rows;     /* sum(hr_count) local residual-row ids, sorted ascending per subdomain */
+    int n_c;                /* rows of the test matrix C (weak constraints), 1..128 */
+    int precision;          /* DDNM_FP64 or DDNM_MIXED (FP32 evaluation, FP64 KKT/merit) */
+    int device;             /* CUDA device ordinal */
+} ddnm_problem;
+
+/* SQP options (Sec. 4.1, 7.1).  Defaults: tol 1e-4, max_iter 15, c1 1e-4, beta 0.5, 20 backtracks. */
+typedef struct ddnm_options {
+    double tol;             /* stop when ||F||_2 < tol */
+    int max_iter;           /* accepted SQP steps */
+    double armijo_c1;       /* accept alpha when phi(alpha)^2 <= (1 - 2 c1 alpha) phi(0)^2 */
+    double beta;            /* backtracking factor */
+    int max_backtracks;     /* after this many halvings the last trial is taken (flag LS_FAIL) */
+} ddnm_options;
+
+/* One sparse-masked shallow decoder g(x) = offset + scale o (W2 sigma(W1 x + b1))
+ * (Sec. 5.1 Eq. autoencoder_architecture b/d, de-normalisation layer Sec. 7.3).
+ * W2 in ELL form: row r has its nonzero columns cols[r*K .. r*K+K-1] (ascending,
+ * -1 padding at the end) with values vals[...].  Host FP64 arrays, copied. */
+typedef struct ddnm_decoder {
+    int N;                  /* outputs (must equal N_i^O or N_i^G) */
+    int w;                  /* width (hidden units) */
+    int n;                  /* latent dim (must equal n_i^O or n_i^G) */
+    int act;                /* DDNM_ACT_* */
+    int K;                  /* ELL slots per row (<= 64) */
+    const double* W1;       /* w x n */
+    const double* b1;       /* w */
+    const int* cols;        /* N x K */
+    const double* vals;     /* N x K */
+    const double* scale;    /* N (NULL = ones) */
+    const double* offset;   /* N (NULL = zeros) */
+} ddnm_decoder;
+
+typedef struct ddnm_sizes {
+    int n_sub;              /* kx*ky */
+    int N_x;                /* 2 nx ny */
+    int n_D;                /* sum_i n_i^O + n_i^G */
+    int n_C;                /* weak constraints */
+    int N_A;                /* compatibility rows */
+    int sum_hr;             /* sum_i N_i^B */
+    int sum_gamma;          /* sum_i N_i^G */
+} ddnm_sizes;
+
+typedef struct ddnm_stats {
+    int iters;              /* accepted SQP steps */
+    int status;             /* DDNM_CONVERGED .. DDNM_KKT_FAIL */
+    int flags;              /* DDNM_FLAG_* */
+    int n_evals;            /* residual/Jacobian evaluations, line-search trials included */
+    double merit;           /* ||F||_2 at the returned iterate */
+    double alpha_last;      /* step length of the last accepted step (0 if none) */
+} ddnm_stats;
+
+/* Per-kernel device time and launch counts, accumulated while timing is on
+ * (ddnm_timing_enable).  Times come from CUDA events recorded on the caller's
+ * stream around every launch of that kernel. */
+typedef struct ddnm_timing {
+    double eval_ms;             /* k_eval: fused decoder / residual / Gauss-Newton blocks */
+    double constraint_ms;       /* k_constraint: FP64 weak-constraint residual */
+    double step_ms;             /* k_step: FP64 Schur KKT solve, Armijo, update */
+    long long eval_launches;
+    long long constraint_launches;
+    long long step_launches;
+    long long other_launches;   /* set-up, statistics, reconstruction kernels */
+} ddnm_timing;
+
+/* Algorithmic work of ONE evaluation of ONE instance (all subdomains), counted
+ * from the sizes of the set-up (subnets, HR rows, constraint rows): what the
+ * method must compute, independent of how the kernels do it. */
+typedef struct ddnm_work {
+    double eval_flops;          /* value-type flops of k_eval: hidden layers, decoder outputs and
+                                   Jacobian rows, residual rows and chain rule, H_i and R_i^T r_i, D_i */
+    double eval_fp64_flops;     /* FP64 flops of k_eval: per-subdomain Cholesky and Schur pieces */
+    double eval_bytes;          /* unique global bytes one instance-evaluation must touch
+                                   (weights and tables counted once, latents, outputs) */
+    double constraint_fp64_flops;  /* 2 n_C N_A */
+    double step_fp64_flops;     /* Schur assembly + n_C Cholesky + back-substitution, per accepted step */
+} ddnm_work;
+
+typedef struct ddnm_ctx ddnm_ctx;
+
+/* Build the algebraic DD (Sec. 2: residual/interior/interface sampling, ports,
+ * compatibility rows) and the HR stencil tables (Sec. 5.3) on the host.
+ * Copies every array of p.  Returns DDNM_E_INVALID for inconsistent sizes,
+ * DDNM_E_UNSUPPORTED beyond the limits stated above (or with a single
+ * subdomain).  *out is NULL on failure.  Device memory is allocated by the
+ * first solve / residual / linearize call on p->device. */
+int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out);
+
+/* Free all host and device memory of ctx (NULL is a no-op). */
+void ddnm_destroy(ddnm_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call.
+ * ddnm_last_error(NULL) gives the message of the last failed ddnm_setup on this thread. */
+const char* ddnm_last_error(const ddnm_ctx* ctx);
+
+/* Sizes of the decomposition. */
+int ddnm_get_sizes(const ddnm_ctx* ctx, ddnm_sizes* out);
+
+/* Subdomain sub: info[6] = {N_r, N^O, N^G, n^O, n^G, N^B}; interior_ids (N^O) and
+ * interface_ids (N^G) receive global variable ids if non-NULL. */
+int ddnm_get_subdomain(const ddnm_ctx* ctx, int sub, int* info, int* interior_ids, int* interface_ids);
+
+/* Compatibility rows (Eq. compatibility_conditions_mat): for row k, the shared
+ * variable row_var[k] and the two subdomains it equates, row_lo[k] (+1) and
+ * row_hi[k] (-1).  Arrays of N_A entries; any may be NULL. */
+int ddnm_get_constraints(const ddnm_ctx* ctx, int* row_var, int* row_lo, int* row_hi);
+
+/* Gaussian test matrix C of the weak constraint (Sec. 3.1), n_C x N_A, FP64. */
+int ddnm_set_test_matrix(ddnm_ctx* ctx, const double* C);
+
+/* Load decoder `kind` (DDNM_DECODER_INTERIOR / _INTERFACE) of subdomain `sub`
+ * and build its HR subnet (Sec. 5.4, Eq. subnet) for the outputs the HR
+ * stencils (interior) or the constraint (interface, all rows; Sec. 5.3 remark)
+ * need.  DDNM_E_INVALID on size mismatch or a column outside [-1, w). */
+int ddnm_load_decoders(ddnm_ctx* ctx, int sub, int kind, const ddnm_decoder* d);
+
+/* Replace the SQP options. */
+int ddnm_set_options(ddnm_ctx* ctx, const ddnm_options* opt);
+
+/* Batched SQP solve (Sec. 4.1) of B instances.
+ *   mu      B x 2 (a, lambda)
+ *   x0      B x n_D start, or NULL for xh0 = 0
+ *   lam0    B x n_C start, or NULL for the least-squares multiplier of
+ *           Eq. (optimality_residuals b) at x0 (Sec. 7.2)
+ *   x_out   B x n_D, lam_out B x n_C  (either may be NULL)
+ *   state_out B x N_x reconstructed state g(xh) taking every variable from its
+ *           owning subdomain, or NULL
+ *   stats   B entries, or NULL
+ * Pointers are host (DDNM_MEM_HOST) or device (DDNM_MEM_DEVICE) memory;
+ * stream is a cudaStream_t (NULL = default stream). */
+int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const double* x0, const double* lam0,
+                     double* x_out, double* lam_out, double* state_out, ddnm_stats* stats,
+                     int mem_kind, void* stream);
+
+/* One evaluation at (x, lam) without iterating.
+ *   F_out      B x (n_D + n_C) KKT right-hand side F (NULL to skip)
+ *   r_hr_out   B x sum(N_i^B) collocation residuals Z_i r_i (NULL to skip)
+ *   r_full_out B x N_x FOM residual r(g(xh); mu) of the reconstructed state (NULL to skip) */
+int ddnm_residual(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam,
+                  double* F_out, double* r_hr_out, double* r_full_out, int mem_kind, void* stream);
+
+/* The blocks one evaluation builds (for checking them): per instance and
+ * subdomain H_i = R_i^T R_i (n_i x n_i, Eq. gauss_newton_hessian) and
+ * D_i = C A_i dg_i^G/dxh (n_C x n_i^G), concatenated over subdomains;
+ * Atil (n_C).  Any output may be NULL. */
+int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam,
+                   double* H_out, double* D_out, double* Atil_out, int mem_kind, void* stream);
+
+/* Turn per-kernel timing on (resets the counters) or off.  While on, every
+ * compute call synchronises its stream before returning. */
+int ddnm_timing_enable(ddnm_ctx* ctx, int on);
+
+/* Read the accumulated per-kernel timing (launch counts are kept even when timing is off). */
+int ddnm_get_timing(const ddnm_ctx* ctx, ddnm_timing* out);
+
+/* Algorithmic work per instance-evaluation (valid once decoders and C are loaded;
+ * DDNM_E_STATE before). */
+int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDNM_H */

@@ -1,0 +1,319 @@
+"""Python binding of libddnm.so, the GB300 (sm_103a) library for the online solve of the
+DD NM-ROM with hyper-reduction (arXiv 2305.15163, Sec. 3.1 / 4.1 / 7.1).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.
+The functions keep the C names of ``include/ddnm.h``; ``Solver`` bundles them.
+Arrays may be numpy (host memory) or torch CUDA tensors (device memory, queued on
+the current torch stream).  There is no CPU path: if the library cannot be loaded,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddnm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2305_15163_gb300.build` "
+                      "(or __graft_entry__.build()); there is no fallback implementation")
+_lib = C.CDLL(LIB_PATH)
+
+DDNM_OK, DDNM_E_INVALID, DDNM_E_STATE, DDNM_E_CUDA, DDNM_E_NOMEM, DDNM_E_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+DDNM_FP64, DDNM_MIXED = 0, 1
+DDNM_ACT = {"swish": 0, "sigmoid": 1, "identity": 2}
+DDNM_MEM_HOST, DDNM_MEM_DEVICE = 0, 1
+DDNM_DECODER_INTERIOR, DDNM_DECODER_INTERFACE = 0, 1
+DDNM_CONVERGED, DDNM_MAX_ITER, DDNM_NONFINITE, DDNM_KKT_FAIL = 0, 1, 2, 3
+DDNM_FLAG_LS_FAIL = 1
+
+_ip = C.POINTER(C.c_int)
+_dp = C.POINTER(C.c_double)
+
+
+class ddnm_problem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nu", C.c_double), ("box", C.c_double * 4),
+                ("kx", C.c_int), ("ky", C.c_int), ("xb", _ip), ("yb", _ip), ("n_omega", _ip),
+                ("n_gamma", _ip), ("hr_count", _ip), ("hr_rows", _ip), ("n_c", C.c_int),
+                ("precision", C.c_int), ("device", C.c_int)]
+
+
+class ddnm_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("armijo_c1", C.c_double),
+                ("beta", C.c_double), ("max_backtracks", C.c_int)]
+
+
+class ddnm_decoder(C.Structure):
+    _fields_ = [("N", C.c_int), ("w", C.c_int), ("n", C.c_int), ("act", C.c_int), ("K", C.c_int),
+                ("W1", _dp), ("b1", _dp), ("cols", _ip), ("vals", _dp), ("scale", _dp), ("offset", _dp)]
+
+
+class ddnm_sizes(C.Structure):
+    _fields_ = [("n_sub", C.c_int), ("N_x", C.c_int), ("n_D", C.c_int), ("n_C", C.c_int),
+                ("N_A", C.c_int), ("sum_hr", C.c_int), ("sum_gamma", C.c_int)]
+
+
+class ddnm_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("flags", C.c_int), ("n_evals", C.c_int),
+                ("merit", C.c_double), ("alpha_last", C.c_double)]
+
+
+class ddnm_timing(C.Structure):
+    _fields_ = [("eval_ms", C.c_double), ("constraint_ms", C.c_double), ("step_ms", C.c_double),
+                ("eval_launches", C.c_longlong), ("constraint_launches", C.c_longlong),
+                ("step_launches", C.c_longlong), ("other_launches", C.c_longlong)]
+
+
+class ddnm_work(C.Structure):
+    _fields_ = [("eval_flops", C.c_double), ("eval_fp64_flops", C.c_double), ("eval_bytes", C.c_double),
+                ("constraint_fp64_flops", C.c_double), ("step_fp64_flops", C.c_double)]
+
+
+STATS_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("flags", np.int32),
+                        ("n_evals", np.int32), ("merit", np.float64), ("alpha_last", np.float64)])
+
+_vp = C.c_void_p
+_sig = {
+    "ddnm_setup": (C.c_int, [C.POINTER(ddnm_problem), C.POINTER(_vp)]),
+    "ddnm_destroy": (None, [_vp]),
+    "ddnm_last_error": (C.c_char_p, [_vp]),
+    "ddnm_get_sizes": (C.c_int, [_vp, C.POINTER(ddnm_sizes)]),
+    "ddnm_get_subdomain": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "ddnm_get_constraints": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "ddnm_set_test_matrix": (C.c_int, [_vp, _vp]),
+    "ddnm_load_decoders": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(ddnm_decoder)]),
+    "ddnm_set_options": (C.c_int, [_vp, C.POINTER(ddnm_options)]),
+    "ddnm_solve_batch": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
+    "ddnm_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
+    "ddnm_linearize": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
+    "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
+    "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
+    "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
+}
+for _n, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _n)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class DDNMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ddnm error {code}: {msg}")
+        self.code = code
+
+
+def ddnm_last_error(ctx) -> str:
+    return (_lib.ddnm_last_error(ctx) or b"").decode()
+
+
+def _check(ctx, rc):
+    if rc != DDNM_OK:
+        raise DDNMError(rc, ddnm_last_error(ctx))
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()   # torch tensor
+
+
+# ------------------------------------------------------------------ C entry points
+
+def ddnm_setup(nx, ny, xb, yb, n_omega, n_gamma, hr_count, hr_rows, n_c, precision=DDNM_MIXED,
+               nu=0.1, box=(-1.0, 1.0, -1.0, 1.0), device=0):
+    keep = [_i32(xb), _i32(yb), _i32(n_omega), _i32(n_gamma), _i32(hr_count), _i32(hr_rows)]
+    p = ddnm_problem(nx, ny, nu, (C.c_double * 4)(*box), len(keep[0]) - 1, len(keep[1]) - 1,
+                     *[k.ctypes.data_as(_ip) for k in keep], n_c, precision, device)
+    ctx = _vp()
+    _check(None, _lib.ddnm_setup(C.byref(p), C.byref(ctx)))
+    return ctx
+
+
+def ddnm_destroy(ctx):
+    _lib.ddnm_destroy(ctx)
+
+
+def ddnm_get_sizes(ctx) -> ddnm_sizes:
+    s = ddnm_sizes()
+    _check(ctx, _lib.ddnm_get_sizes(ctx, C.byref(s)))
+    return s
+
+
+def ddnm_get_subdomain(ctx, sub):
+    info = np.zeros(6, dtype=np.int32)
+    _check(ctx, _lib.ddnm_get_subdomain(ctx, sub, info.ctypes.data, None, None))
+    inter = np.zeros(info[1], dtype=np.int32)
+    face = np.zeros(info[2], dtype=np.int32)
+    _check(ctx, _lib.ddnm_get_subdomain(ctx, sub, info.ctypes.data, inter.ctypes.data, face.ctypes.data))
+    return dict(N_r=int(info[0]), N_omega=int(info[1]), N_gamma=int(info[2]), n_omega=int(info[3]),
+                n_gamma=int(info[4]), N_B=int(info[5]), interior=inter, interface=face)
+
+
+def ddnm_get_constraints(ctx):
+    n = ddnm_get_sizes(ctx).N_A
+    var, lo, hi = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    _check(ctx, _lib.ddnm_get_constraints(ctx, var.ctypes.data, lo.ctypes.data, hi.ctypes.data))
+    return var, lo, hi
+
+
+def ddnm_set_test_matrix(ctx, Cmat):
+    Cm = _f64(Cmat)
+    _check(ctx, _lib.ddnm_set_test_matrix(ctx, Cm.ctypes.data))
+
+
+def ddnm_set_options(ctx, tol=1e-4, max_iter=15, armijo_c1=1e-4, beta=0.5, max_backtracks=20):
+    o = ddnm_options(tol, max_iter, armijo_c1, beta, max_backtracks)
+    _check(ctx, _lib.ddnm_set_options(ctx, C.byref(o)))
+
+
+def ddnm_load_decoders(ctx, sub, kind, spec: dict):
+    """spec: the decoder dict of ``inputs.decoder`` (N, w, n, act, W1, b1, cols, vals, scale, offset)."""
+    W1, b1, vals = _f64(spec["W1"]), _f64(spec["b1"]), _f64(spec["vals"])
+    cols = _i32(spec["cols"])
+    sc, off = _f64(spec["scale"]), _f64(spec["offset"])
+    d = ddnm_decoder(spec["N"], spec["w"], spec["n"], DDNM_ACT[spec.get("act", "swish")], cols.shape[1],
+                     W1.ctypes.data_as(_dp), b1.ctypes.data_as(_dp), cols.ctypes.data_as(_ip),
+                     vals.ctypes.data_as(_dp), sc.ctypes.data_as(_dp), off.ctypes.data_as(_dp))
+    _check(ctx, _lib.ddnm_load_decoders(ctx, sub, kind, C.byref(d)))
+
+
+def _mem_kind(*arrays):
+    kinds = {isinstance(a, np.ndarray) for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise TypeError("mix of host (numpy) and device (torch) arrays")
+    return DDNM_MEM_HOST if (not kinds or kinds == {True}) else DDNM_MEM_DEVICE
+
+
+def _stream(kind):
+    if kind != DDNM_MEM_DEVICE:
+        return None
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def ddnm_solve_batch(ctx, B, mu, x0, lam0, x_out, lam_out, state_out, stats):
+    """Raw call: arrays are numpy (host) or torch CUDA tensors (device); stats is a numpy
+    STATS_DTYPE array (host) or a torch uint8 tensor of B*32 bytes (device)."""
+    kind = _mem_kind(mu, x0, lam0, x_out, lam_out, state_out, stats)
+    _check(ctx, _lib.ddnm_solve_batch(ctx, B, _ptr(mu), _ptr(x0), _ptr(lam0), _ptr(x_out), _ptr(lam_out),
+                                      _ptr(state_out), _ptr(stats), kind, _stream(kind)))
+
+
+def ddnm_residual(ctx, B, mu, x, lam, F_out, r_hr_out, r_full_out):
+    kind = _mem_kind(mu, x, lam, F_out, r_hr_out, r_full_out)
+    _check(ctx, _lib.ddnm_residual(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(F_out), _ptr(r_hr_out),
+                                   _ptr(r_full_out), kind, _stream(kind)))
+
+
+def ddnm_linearize(ctx, B, mu, x, lam, H_out, D_out, Atil_out):
+    kind = _mem_kind(mu, x, lam, H_out, D_out, Atil_out)
+    _check(ctx, _lib.ddnm_linearize(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(H_out), _ptr(D_out),
+                                    _ptr(Atil_out), kind, _stream(kind)))
+
+
+def ddnm_timing_enable(ctx, on=True):
+    _check(ctx, _lib.ddnm_timing_enable(ctx, int(bool(on))))
+
+
+def ddnm_get_timing(ctx) -> dict:
+    t = ddnm_timing()
+    _check(ctx, _lib.ddnm_get_timing(ctx, C.byref(t)))
+    return {k: getattr(t, k) for k, _ in ddnm_timing._fields_}
+
+
+def ddnm_get_work(ctx) -> dict:
+    w = ddnm_work()
+    _check(ctx, _lib.ddnm_get_work(ctx, C.byref(w)))
+    return {k: getattr(w, k) for k, _ in ddnm_work._fields_}
+
+
+# ------------------------------------------------------------------ convenience wrapper
+
+class Solver:
+    """One library context for a workload (``inputs.Workload``-like object)."""
+
+    def __init__(self, wl, precision=None, device=0):
+        prec = precision if precision is not None else (DDNM_MIXED if wl.mixed else DDNM_FP64)
+        self.wl = wl
+        hr = getattr(wl, "hr_override", None)
+        if hr is None:
+            import inputs   # seeded generator (not method code)
+            hr = inputs.hr_sets(wl)
+        self.hr = hr
+        self.ctx = ddnm_setup(wl.nx, wl.ny, wl.xb, wl.yb, wl.n_omega, wl.n_gamma, [len(h) for h in hr],
+                              np.concatenate(hr), wl.n_c(), prec, wl.nu, device=device)
+        self.sizes = ddnm_get_sizes(self.ctx)
+        self.subs = [ddnm_get_subdomain(self.ctx, i) for i in range(self.sizes.n_sub)]
+
+    def close(self):
+        if self.ctx:
+            ddnm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, dec_o, dec_g, Cmat):
+        for i, (a, b) in enumerate(zip(dec_o, dec_g)):
+            ddnm_load_decoders(self.ctx, i, DDNM_DECODER_INTERIOR, a)
+            ddnm_load_decoders(self.ctx, i, DDNM_DECODER_INTERFACE, b)
+        ddnm_set_test_matrix(self.ctx, Cmat)
+
+    def options(self, **kw):
+        ddnm_set_options(self.ctx, **kw)
+
+    def solve(self, mu, x0=None, lam0=None, state=False):
+        """Host (numpy) solve: returns (x, lam, stats[, state])."""
+        mu = _f64(mu).reshape(-1, 2)
+        B = mu.shape[0]
+        s = self.sizes
+        x = np.zeros((B, s.n_D))
+        lam = np.zeros((B, s.n_C))
+        st = np.zeros(B, dtype=STATS_DTYPE)
+        stt = np.zeros((B, s.N_x)) if state else None
+        ddnm_solve_batch(self.ctx, B, mu, None if x0 is None else _f64(x0), None if lam0 is None else _f64(lam0),
+                         x, lam, stt, st)
+        return (x, lam, st, stt) if state else (x, lam, st)
+
+    def residual(self, mu, x, lam=None, full=False):
+        mu = _f64(mu).reshape(-1, 2)
+        B = mu.shape[0]
+        s = self.sizes
+        F = np.zeros((B, s.n_D + s.n_C))
+        r = np.zeros((B, s.sum_hr))
+        rf = np.zeros((B, s.N_x)) if full else None
+        ddnm_residual(self.ctx, B, mu, _f64(x).reshape(B, -1), None if lam is None else _f64(lam).reshape(B, -1),
+                      F, r, rf)
+        return (F, r, rf) if full else (F, r)
+
+    def linearize(self, mu, x, lam=None):
+        mu = _f64(mu).reshape(-1, 2)
+        B = mu.shape[0]
+        s = self.sizes
+        hs = sum((d["n_omega"] + d["n_gamma"]) ** 2 for d in self.subs)
+        ds = sum(s.n_C * d["n_gamma"] for d in self.subs)
+        H = np.zeros((B, hs))
+        D = np.zeros((B, ds))
+        A = np.zeros((B, s.n_C))
+        ddnm_linearize(self.ctx, B, mu, _f64(x).reshape(B, -1), None if lam is None else _f64(lam).reshape(B, -1),
+                       H, D, A)
+        return H, D, A

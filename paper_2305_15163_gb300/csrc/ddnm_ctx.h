@@ -1,0 +1,78 @@
+// Library context: host copy of the problem and device handles.  Internal.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ddnm.h"
+#include "ddnm_internal.h"
+
+struct DecoderHost {
+    bool loaded = false;
+    int N = 0, w = 0, n = 0, act = 0, K = 0;
+    std::vector<double> W1, b1, vals, scale, offset;
+    std::vector<int> cols;
+};
+
+struct SubHost {
+    std::vector<int> owned;      // owned node ids, ascending
+    std::vector<int> interior;   // global variable ids, ascending
+    std::vector<int> interface;  // global variable ids, ascending
+    std::vector<int> hr_rows;    // local residual-row ids
+    std::vector<int> hr_ops;     // HR_INTS per row
+    std::vector<int> need;       // interior outputs the stencils use (I_o), ascending local indices
+    int nO = 0, nG = 0;
+};
+
+struct ddnm_ctx {
+    // problem
+    int nx = 0, ny = 0, kx = 0, ky = 0, n_sub = 0, N = 0, n_C = 0, N_A = 0;
+    int precision = DDNM_MIXED, device = 0;
+    double nu = 0.1, box[4] = {-1, 1, -1, 1}, hx = 0, hy = 0;
+    ddnm_options opt{1e-4, 15, 1e-4, 0.5, 20};
+    std::vector<int> xb, yb;
+    std::vector<SubHost> subs;
+    std::vector<int> con_var, con_lo, con_hi, con_lo_flat, con_hi_flat;
+    std::vector<int> bnd_ij;     // 2 per Dirichlet point (I, J), 0 <= I <= nx+1
+    std::vector<int> goff;       // offset of each subdomain's interface outputs
+    std::vector<double> C;
+    bool have_C = false;
+    std::vector<DecoderHost> decO, decG;
+    int n_D = 0, sum_NG = 0, sum_NB = 0;
+
+    // device side (valid once finalized)
+    bool finalized = false;
+    std::vector<ddnm::SubDev> hsub;
+    ddnm::ProbDev pd{};
+    int eval_smem = 0, step_smem = 0, rec_smem = 0;
+    void* d_vpool = nullptr;
+    int* d_ipool = nullptr;
+    int* d_hr = nullptr;
+    int* d_con = nullptr;
+    double* d_C = nullptr;
+    int* d_bnd_ij = nullptr;
+    ddnm::SubDev* d_sub = nullptr;
+
+    // workspace for up to cap_B instances
+    int cap_B = 0;
+    void* d_ws = nullptr;
+    int* h_active = nullptr;     // pinned
+
+    std::vector<long long> nnzO, nnzG;   // mask nonzeros of the interior subnet rows / all interface rows
+
+    // per-kernel timing (ddnm_timing_enable)
+    bool timing = false;
+    ddnm_timing tm{};
+    std::vector<cudaEvent_t> events;   // pool, pairs (start, stop)
+    std::vector<int> event_kind;       // 0 eval, 1 constraint, 2 step for each recorded pair
+    size_t n_events = 0;               // pairs in use for the current call
+
+    std::string err;
+};
+
+// set-up helpers implemented in ddnm_host.cpp
+int ddnm_fail(ddnm_ctx* ctx, int code, const std::string& msg);
+int ddnm_finalize(ddnm_ctx* ctx);
+int ddnm_reserve(ddnm_ctx* ctx, int B);
+void ddnm_release_events(ddnm_ctx* ctx);

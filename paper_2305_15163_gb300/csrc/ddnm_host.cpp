@@ -1,0 +1,630 @@
+// Host set-up of the DD NM-ROM-HR solve: algebraic domain decomposition (Sec. 2),
+// HR stencil tables (Sec. 5.3), HR subnets (Sec. 5.4), device upload.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "ddnm_ctx.h"
+
+using namespace ddnm;
+
+// message of the last failed ddnm_setup on this thread (there is no context to hold it)
+static thread_local std::string g_setup_err;
+
+int ddnm_fail(ddnm_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+static int cuda_fail(ddnm_ctx* ctx, cudaError_t e, const char* what) {
+    return ddnm_fail(ctx, DDNM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+    } while (0)
+
+static int find_sorted(const std::vector<int>& v, int key) {
+    auto it = std::lower_bound(v.begin(), v.end(), key);
+    return (it != v.end() && *it == key) ? int(it - v.begin()) : -1;
+}
+
+// ------------------------------------------------------------------------------- set-up
+
+extern "C" int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out) {
+    if (!out) return DDNM_E_INVALID;
+    *out = nullptr;
+    if (!p) {
+        g_setup_err = "ddnm_setup: problem is NULL";
+        return DDNM_E_INVALID;
+    }
+    ddnm_ctx* ctx = new (std::nothrow) ddnm_ctx();
+    if (!ctx) return DDNM_E_NOMEM;
+    auto bail = [&](int code, const std::string& msg) {
+        g_setup_err = "ddnm_setup: " + msg;
+        delete ctx;
+        return code;
+    };
+    g_setup_err.clear();
+    if (p->nx < 2 || p->ny < 2 || p->kx < 1 || p->ky < 1 || !p->xb || !p->yb || !p->n_omega || !p->n_gamma ||
+        !p->hr_count || !p->hr_rows)
+        return bail(DDNM_E_INVALID, "missing or non-positive problem fields");
+    if (p->kx * p->ky < 2) return bail(DDNM_E_UNSUPPORTED, "at least two subdomains are needed (WFPC constraints)");
+    if (p->device < 0) return bail(DDNM_E_INVALID, "negative device ordinal");
+    if (!(p->nu > 0) || !(p->box[1] > p->box[0]) || !(p->box[3] > p->box[2]))
+        return bail(DDNM_E_INVALID, "nu and the box must be positive");
+    if (p->precision != DDNM_FP64 && p->precision != DDNM_MIXED) return bail(DDNM_E_INVALID, "unknown precision");
+    if (p->n_c < 1 || p->n_c > MAX_NC) return bail(DDNM_E_UNSUPPORTED, "n_c must be in 1..128");
+    if ((long long)p->nx * p->ny * 2 >= (1LL << OP_SHIFT)) return bail(DDNM_E_UNSUPPORTED, "grid too large");
+
+    ctx->nx = p->nx; ctx->ny = p->ny; ctx->kx = p->kx; ctx->ky = p->ky;
+    ctx->n_sub = p->kx * p->ky;
+    ctx->N = p->nx * p->ny;
+    ctx->nu = p->nu;
+    std::memcpy(ctx->box, p->box, sizeof(ctx->box));
+    ctx->hx = (p->box[1] - p->box[0]) / (p->nx + 1);
+    ctx->hy = (p->box[3] - p->box[2]) / (p->ny + 1);
+    ctx->precision = p->precision;
+    ctx->device = p->device;
+    ctx->n_C = p->n_c;
+    ctx->xb.assign(p->xb, p->xb + p->kx + 1);
+    ctx->yb.assign(p->yb, p->yb + p->ky + 1);
+    if (ctx->xb.front() != 0 || ctx->xb.back() != p->nx || ctx->yb.front() != 0 || ctx->yb.back() != p->ny)
+        return bail(DDNM_E_INVALID, "breakpoints must start at 0 and end at nx / ny");
+    for (int k = 0; k < p->kx; ++k)
+        if (ctx->xb[k + 1] <= ctx->xb[k]) return bail(DDNM_E_INVALID, "x breakpoints must increase");
+    for (int k = 0; k < p->ky; ++k)
+        if (ctx->yb[k + 1] <= ctx->yb[k]) return bail(DDNM_E_INVALID, "y breakpoints must increase");
+
+    // the set-up is host bookkeeping only; the device is first touched when the first
+    // solve / evaluation uploads the tables (ddnm_finalize)
+    const int nx = p->nx, ny = p->ny, N = ctx->N, ns = ctx->n_sub;
+    // owner of each node
+    std::vector<int> owner(N);
+    ctx->subs.resize(ns);
+    for (int sy = 0; sy < p->ky; ++sy)
+        for (int sx = 0; sx < p->kx; ++sx) {
+            int s = sy * p->kx + sx;
+            for (int j = ctx->yb[sy]; j < ctx->yb[sy + 1]; ++j)
+                for (int i = ctx->xb[sx]; i < ctx->xb[sx + 1]; ++i) {
+                    owner[j * nx + i] = s;
+                    ctx->subs[s].owned.push_back(j * nx + i);
+                }
+        }
+    for (auto& sd : ctx->subs) std::sort(sd.owned.begin(), sd.owned.end());
+
+    // sharing set of each node: the owners of the node and of its in-grid 5-point neighbours
+    // (node q enters the residual of subdomain s iff s owns q or a neighbour of q)
+    std::vector<unsigned char> nshare(N);
+    std::vector<int> share(5 * (size_t)N);
+    for (int q = 0; q < N; ++q) {
+        int i = q % nx, j = q / nx, c = 0;
+        int tmp[5];
+        tmp[c++] = owner[q];
+        if (i > 0) tmp[c++] = owner[q - 1];
+        if (i < nx - 1) tmp[c++] = owner[q + 1];
+        if (j > 0) tmp[c++] = owner[q - nx];
+        if (j < ny - 1) tmp[c++] = owner[q + nx];
+        std::sort(tmp, tmp + c);
+        int m = int(std::unique(tmp, tmp + c) - tmp);
+        nshare[q] = (unsigned char)m;
+        for (int k = 0; k < m; ++k) share[5 * (size_t)q + k] = tmp[k];
+    }
+    // interior and interface variables of each subdomain
+    std::vector<int> stamp(N, -1);
+    for (int s = 0; s < ns; ++s) {
+        SubHost& sd = ctx->subs[s];
+        std::vector<int> dep;
+        for (int q : sd.owned) {
+            int i = q % nx, j = q / nx;
+            int nb[5] = {q, i > 0 ? q - 1 : -1, i < nx - 1 ? q + 1 : -1, j > 0 ? q - nx : -1, j < ny - 1 ? q + nx : -1};
+            for (int v : nb)
+                if (v >= 0 && stamp[v] != s) {
+                    stamp[v] = s;
+                    dep.push_back(v);
+                }
+        }
+        std::sort(dep.begin(), dep.end());
+        std::vector<int> in_n, face_n;
+        for (int q : dep) (nshare[q] > 1 ? face_n : in_n).push_back(q);
+        for (int comp = 0; comp < 2; ++comp) {
+            for (int q : in_n) sd.interior.push_back(comp * N + q);
+            for (int q : face_n) sd.interface.push_back(comp * N + q);
+        }
+        sd.nO = p->n_omega[s];
+        sd.nG = p->n_gamma[s];
+        if (sd.nO < 1 || sd.nG < 0 || sd.nO + sd.nG > MAX_NI || sd.nG > MAX_NG)
+            return bail(DDNM_E_UNSUPPORTED, "latent dims must satisfy 1 <= n^O, n^G <= 8, n^O + n^G <= 16");
+        if (ns > 1 && sd.nG < 1) return bail(DDNM_E_INVALID, "n^G must be >= 1 with more than one subdomain");
+    }
+    // compatibility rows
+    ctx->goff.assign(ns + 1, 0);
+    for (int s = 0; s < ns; ++s) ctx->goff[s + 1] = ctx->goff[s] + (int)ctx->subs[s].interface.size();
+    ctx->sum_NG = ctx->goff[ns];
+    for (int var = 0; var < 2 * N; ++var) {
+        int q = var % N, m = nshare[q];
+        for (int k = 0; k + 1 < m; ++k) {
+            int lo = share[5 * (size_t)q + k], hi = share[5 * (size_t)q + k + 1];
+            int li = find_sorted(ctx->subs[lo].interface, var), hj = find_sorted(ctx->subs[hi].interface, var);
+            if (li < 0 || hj < 0) return bail(DDNM_E_INVALID, "internal: shared variable missing from an interface");
+            ctx->con_var.push_back(var);
+            ctx->con_lo.push_back(lo);
+            ctx->con_hi.push_back(hi);
+            ctx->con_lo_flat.push_back(ctx->goff[lo] + li);
+            ctx->con_hi_flat.push_back(ctx->goff[hi] + hj);
+        }
+    }
+    ctx->N_A = (int)ctx->con_var.size();
+    if (ns > 1 && ctx->N_A == 0) return bail(DDNM_E_INVALID, "internal: no compatibility rows");
+
+    // HR rows and their stencil operands
+    std::map<long long, int> bnd_id;
+    int hr_pos = 0;
+    for (int s = 0; s < ns; ++s) {
+        SubHost& sd = ctx->subs[s];
+        int nb = p->hr_count[s];
+        int nown = (int)sd.owned.size();
+        if (nb < sd.nO + sd.nG || nb > 2 * nown)
+            return bail(DDNM_E_INVALID, "hr_count must be in [n^O + n^G, N_r]");
+        sd.hr_rows.assign(p->hr_rows + hr_pos, p->hr_rows + hr_pos + nb);
+        hr_pos += nb;
+        for (int k = 0; k < nb; ++k) {
+            if (sd.hr_rows[k] < 0 || sd.hr_rows[k] >= 2 * nown || (k && sd.hr_rows[k] <= sd.hr_rows[k - 1]))
+                return bail(DDNM_E_INVALID, "hr_rows must be ascending local residual-row ids");
+        }
+        // first pass: interior outputs the stencils need (I_o)
+        std::vector<int> raw;   // (comp, var or -(boundary key)-1) per operand
+        for (int l : sd.hr_rows) {
+            int comp = l / nown, q = sd.owned[l % nown];
+            int i = q % nx, j = q / nx;
+            // operands: centre, E, W, N, S of component comp, then the other component at the centre
+            int I[6] = {i, i + 1, i - 1, i, i, i}, J[6] = {j, j, j, j + 1, j - 1, j};
+            int cmp[6] = {comp, comp, comp, comp, comp, 1 - comp};
+            raw.push_back(comp);
+            for (int o = 0; o < 6; ++o) {
+                if (I[o] >= 0 && I[o] < nx && J[o] >= 0 && J[o] < ny) {
+                    raw.push_back(cmp[o] * N + J[o] * nx + I[o]);
+                } else {
+                    long long key = (long long)(J[o] + 1) * (nx + 2) + (I[o] + 1);   // 1-based grid point
+                    auto it = bnd_id.find(key);
+                    int id;
+                    if (it == bnd_id.end()) {
+                        id = (int)bnd_id.size();
+                        bnd_id[key] = id;
+                        ctx->bnd_ij.push_back(I[o] + 1);
+                        ctx->bnd_ij.push_back(J[o] + 1);
+                    } else {
+                        id = it->second;
+                    }
+                    raw.push_back(-(2 * id + cmp[o]) - 1);
+                }
+            }
+        }
+        for (int k = 0; k < nb; ++k)
+            for (int o = 0; o < 6; ++o) {
+                int v = raw[k * HR_INTS + 1 + o];
+                if (v >= 0) {
+                    int li = find_sorted(sd.interior, v);
+                    if (li >= 0) sd.need.push_back(li);
+                }
+            }
+        std::sort(sd.need.begin(), sd.need.end());
+        sd.need.erase(std::unique(sd.need.begin(), sd.need.end()), sd.need.end());
+        // second pass: operand codes
+        for (int k = 0; k < nb; ++k) {
+            sd.hr_ops.push_back(raw[k * HR_INTS]);
+            for (int o = 0; o < 6; ++o) {
+                int v = raw[k * HR_INTS + 1 + o];
+                int code;
+                if (v >= 0) {
+                    int li = find_sorted(sd.interior, v);
+                    if (li >= 0) {
+                        code = (OP_INTERIOR << OP_SHIFT) | find_sorted(sd.need, li);
+                    } else {
+                        int gi = find_sorted(sd.interface, v);
+                        if (gi < 0) return bail(DDNM_E_INVALID, "internal: stencil operand outside the subdomain");
+                        code = (OP_INTERFACE << OP_SHIFT) | gi;
+                    }
+                } else {
+                    code = (OP_BOUNDARY << OP_SHIFT) | (-v - 1);
+                }
+                sd.hr_ops.push_back(code);
+            }
+        }
+        ctx->sum_NB += nb;
+        ctx->n_D += sd.nO + sd.nG;
+    }
+    ctx->decO.resize(ns);
+    ctx->decG.resize(ns);
+    *out = ctx;
+    return DDNM_OK;
+}
+
+extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_vpool);
+    cudaFree(ctx->d_ipool);
+    cudaFree(ctx->d_hr);
+    cudaFree(ctx->d_con);
+    cudaFree(ctx->d_C);
+    cudaFree(ctx->d_bnd_ij);
+    cudaFree(ctx->d_sub);
+    cudaFree(ctx->d_ws);
+    if (ctx->h_active) cudaFreeHost(ctx->h_active);
+    ddnm_release_events(ctx);
+    delete ctx;
+}
+
+extern "C" const char* ddnm_last_error(const ddnm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_err.c_str(); }
+
+extern "C" int ddnm_get_sizes(const ddnm_ctx* ctx, ddnm_sizes* out) {
+    if (!ctx || !out) return DDNM_E_INVALID;
+    out->n_sub = ctx->n_sub;
+    out->N_x = 2 * ctx->N;
+    out->n_D = ctx->n_D;
+    out->n_C = ctx->n_C;
+    out->N_A = ctx->N_A;
+    out->sum_hr = ctx->sum_NB;
+    out->sum_gamma = ctx->sum_NG;
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_get_subdomain(const ddnm_ctx* ctx, int sub, int* info, int* interior_ids, int* interface_ids) {
+    if (!ctx || sub < 0 || sub >= ctx->n_sub) return DDNM_E_INVALID;
+    const SubHost& sd = ctx->subs[sub];
+    if (info) {
+        info[0] = 2 * (int)sd.owned.size();
+        info[1] = (int)sd.interior.size();
+        info[2] = (int)sd.interface.size();
+        info[3] = sd.nO;
+        info[4] = sd.nG;
+        info[5] = (int)sd.hr_rows.size();
+    }
+    if (interior_ids) std::copy(sd.interior.begin(), sd.interior.end(), interior_ids);
+    if (interface_ids) std::copy(sd.interface.begin(), sd.interface.end(), interface_ids);
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_get_constraints(const ddnm_ctx* ctx, int* row_var, int* row_lo, int* row_hi) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (row_var) std::copy(ctx->con_var.begin(), ctx->con_var.end(), row_var);
+    if (row_lo) std::copy(ctx->con_lo.begin(), ctx->con_lo.end(), row_lo);
+    if (row_hi) std::copy(ctx->con_hi.begin(), ctx->con_hi.end(), row_hi);
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_set_test_matrix(ddnm_ctx* ctx, const double* C) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (!C) return ddnm_fail(ctx, DDNM_E_INVALID, "C is NULL");
+    size_t n = (size_t)ctx->n_C * ctx->N_A;
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(C[k])) return ddnm_fail(ctx, DDNM_E_INVALID, "C has a non-finite entry");
+    ctx->C.assign(C, C + n);
+    ctx->have_C = true;
+    ctx->finalized = false;
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_set_options(ddnm_ctx* ctx, const ddnm_options* o) {
+    if (!ctx || !o) return DDNM_E_INVALID;
+    if (!(o->tol >= 0) || o->max_iter < 0 || !(o->armijo_c1 >= 0 && o->armijo_c1 < 0.5) || !(o->beta > 0 && o->beta < 1) ||
+        o->max_backtracks < 0 || o->max_iter > 100000 || o->max_backtracks > 60)
+        return ddnm_fail(ctx, DDNM_E_INVALID, "options out of range");
+    ctx->opt = *o;
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_load_decoders(ddnm_ctx* ctx, int sub, int kind, const ddnm_decoder* d) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (!d || sub < 0 || sub >= ctx->n_sub || (kind != DDNM_DECODER_INTERIOR && kind != DDNM_DECODER_INTERFACE))
+        return ddnm_fail(ctx, DDNM_E_INVALID, "bad decoder arguments");
+    const SubHost& sd = ctx->subs[sub];
+    int N = kind == DDNM_DECODER_INTERIOR ? (int)sd.interior.size() : (int)sd.interface.size();
+    int n = kind == DDNM_DECODER_INTERIOR ? sd.nO : sd.nG;
+    if (d->N != N || d->n != n) return ddnm_fail(ctx, DDNM_E_INVALID, "decoder size does not match the decomposition");
+    if (d->w < 1 || d->K < 1 || d->K > MAX_K) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "decoder width or K out of range");
+    if (d->act < DDNM_ACT_SWISH || d->act > DDNM_ACT_IDENTITY) return ddnm_fail(ctx, DDNM_E_INVALID, "unknown activation");
+    if (!d->W1 || !d->b1 || !d->cols || !d->vals) return ddnm_fail(ctx, DDNM_E_INVALID, "decoder array is NULL");
+    DecoderHost h;
+    h.N = N; h.w = d->w; h.n = n; h.act = d->act; h.K = d->K;
+    h.W1.assign(d->W1, d->W1 + (size_t)d->w * n);
+    h.b1.assign(d->b1, d->b1 + d->w);
+    h.cols.assign(d->cols, d->cols + (size_t)N * d->K);
+    h.vals.assign(d->vals, d->vals + (size_t)N * d->K);
+    for (int r = 0; r < N; ++r) {
+        bool pad = false;
+        for (int t = 0; t < d->K; ++t) {
+            int c = h.cols[(size_t)r * d->K + t];
+            if (c < -1 || c >= d->w) return ddnm_fail(ctx, DDNM_E_INVALID, "decoder column outside [-1, w)");
+            if (c < 0) pad = true;
+            else if (pad) return ddnm_fail(ctx, DDNM_E_INVALID, "decoder row has a column after -1 padding");
+        }
+    }
+    h.scale = d->scale ? std::vector<double>(d->scale, d->scale + N) : std::vector<double>(N, 1.0);
+    h.offset = d->offset ? std::vector<double>(d->offset, d->offset + N) : std::vector<double>(N, 0.0);
+    for (double v : h.W1) if (!std::isfinite(v)) return ddnm_fail(ctx, DDNM_E_INVALID, "non-finite W1");
+    h.loaded = true;
+    (kind == DDNM_DECODER_INTERIOR ? ctx->decO : ctx->decG)[sub] = std::move(h);
+    ctx->finalized = false;
+    return DDNM_OK;
+}
+
+// ------------------------------------------------------------------- finalize (upload)
+
+namespace {
+struct Pools {
+    std::vector<double> v;
+    std::vector<int> i;
+    long long addv(const double* p, size_t n) {
+        long long o = (long long)v.size();
+        v.insert(v.end(), p, p + n);
+        while (v.size() % 4) v.push_back(0.0);   // keep 16-byte alignment for float and double views
+        return o;
+    }
+    long long addi(const int* p, size_t n) {
+        long long o = (long long)i.size();
+        i.insert(i.end(), p, p + n);
+        while (i.size() % 4) i.push_back(-1);
+        return o;
+    }
+};
+
+// HR subnet of Sec. 5.4: hidden set I_h = union of the mask columns of the rows I_o (ascending);
+// W1~ = W1[I_h], b1~ = b1[I_h], W2~ = W2[I_o, I_h] with columns renumbered into I_h.
+void build_subnet(const DecoderHost& d, const std::vector<int>& Io, Pools& P, long long& w1, long long& b1,
+                  long long& w2, long long& out, long long& col, int& h) {
+    std::vector<int> Ih;
+    for (int r : Io)
+        for (int t = 0; t < d.K; ++t) {
+            int c = d.cols[(size_t)r * d.K + t];
+            if (c >= 0) Ih.push_back(c);
+        }
+    std::sort(Ih.begin(), Ih.end());
+    Ih.erase(std::unique(Ih.begin(), Ih.end()), Ih.end());
+    std::vector<int> pos(d.w, -1);
+    for (size_t k = 0; k < Ih.size(); ++k) pos[Ih[k]] = (int)k;
+    std::vector<double> W1s, b1s, w2s, sc;
+    std::vector<int> cs;
+    for (int c : Ih) {
+        for (int k = 0; k < d.n; ++k) W1s.push_back(d.W1[(size_t)c * d.n + k]);
+        b1s.push_back(d.b1[c]);
+    }
+    for (int r : Io) {
+        for (int t = 0; t < d.K; ++t) {
+            int c = d.cols[(size_t)r * d.K + t];
+            cs.push_back(c >= 0 ? pos[c] : -1);
+            w2s.push_back(c >= 0 ? d.vals[(size_t)r * d.K + t] : 0.0);
+        }
+    }
+    for (int r : Io) sc.push_back(d.scale[r]);
+    for (int r : Io) sc.push_back(d.offset[r]);
+    h = (int)Ih.size();
+    w1 = P.addv(W1s.data(), W1s.size());
+    b1 = P.addv(b1s.data(), b1s.size());
+    w2 = P.addv(w2s.data(), w2s.size());
+    out = P.addv(sc.data(), sc.size());
+    col = P.addi(cs.data(), cs.size());
+}
+}  // namespace
+
+int ddnm_finalize(ddnm_ctx* ctx) {
+    if (ctx->finalized) return DDNM_OK;
+    if (!ctx->have_C) return ddnm_fail(ctx, DDNM_E_STATE, "test matrix C not set");
+    for (int s = 0; s < ctx->n_sub; ++s)
+        if (!ctx->decO[s].loaded || !ctx->decG[s].loaded)
+            return ddnm_fail(ctx, DDNM_E_STATE, "decoder of subdomain " + std::to_string(s) + " not loaded");
+    CK(cudaSetDevice(ctx->device));
+    const int ns = ctx->n_sub, nC = ctx->n_C;
+    Pools P;
+    std::vector<int> hr_all;
+    ctx->hsub.assign(ns, SubDev{});
+    int xoff = 0, hr_off = 0, blk = 0;
+    const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
+    ctx->eval_smem = 0;
+    ctx->rec_smem = 0;
+    ctx->nnzO.assign(ns, 0);
+    ctx->nnzG.assign(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+        const SubHost& sd = ctx->subs[s];
+        const DecoderHost &dO = ctx->decO[s], &dG = ctx->decG[s];
+        if (dO.K != dG.K) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "interior and interface decoders must share K");
+        SubDev& S = ctx->hsub[s];
+        S.nO = sd.nO; S.nG = sd.nG; S.ni = sd.nO + sd.nG; S.xoff = xoff; xoff += S.ni;
+        S.NB = (int)sd.hr_rows.size(); S.hr_off = hr_off; hr_off += S.NB;
+        S.K = dO.K; S.actO = dO.act; S.actG = dG.act;
+        S.goff = ctx->goff[s];
+        S.mO = (int)sd.need.size();
+        S.NG = (int)sd.interface.size();
+        build_subnet(dO, sd.need, P, S.w1O, S.b1O, S.w2O, S.outO, S.colO, S.hO);
+        for (int r : sd.need)
+            for (int t = 0; t < dO.K; ++t) ctx->nnzO[s] += dO.cols[(size_t)r * dO.K + t] >= 0;
+        for (int c : dG.cols) ctx->nnzG[s] += c >= 0;
+        std::vector<int> allG(S.NG);
+        for (int r = 0; r < S.NG; ++r) allG[r] = r;
+        build_subnet(dG, allG, P, S.w1G, S.b1G, S.w2G, S.outG, S.colG, S.hG);
+        // M_i = C A_i, stored N^G x n_C
+        std::vector<double> M((size_t)S.NG * nC, 0.0);
+        for (int r = 0; r < ctx->N_A; ++r) {
+            if (ctx->con_lo[r] == s) {
+                int li = ctx->con_lo_flat[r] - S.goff;
+                for (int c = 0; c < nC; ++c) M[(size_t)li * nC + c] += ctx->C[(size_t)c * ctx->N_A + r];
+            }
+            if (ctx->con_hi[r] == s) {
+                int li = ctx->con_hi_flat[r] - S.goff;
+                for (int c = 0; c < nC; ++c) M[(size_t)li * nC + c] -= ctx->C[(size_t)c * ctx->N_A + r];
+            }
+        }
+        S.M = P.addv(M.data(), M.size());
+        // full decoders and ownership for reconstruction
+        S.NO_full = dO.N; S.wO_full = dO.w; S.wG_full = dG.w;
+        std::vector<double> so(dO.scale);
+        so.insert(so.end(), dO.offset.begin(), dO.offset.end());
+        S.fw1O = P.addv(dO.W1.data(), dO.W1.size());
+        S.fb1O = P.addv(dO.b1.data(), dO.b1.size());
+        S.fw2O = P.addv(dO.vals.data(), dO.vals.size());
+        S.foutO = P.addv(so.data(), so.size());
+        S.fcolO = P.addi(dO.cols.data(), dO.cols.size());
+        std::vector<double> sg(dG.scale);
+        sg.insert(sg.end(), dG.offset.begin(), dG.offset.end());
+        S.fw1G = P.addv(dG.W1.data(), dG.W1.size());
+        S.fb1G = P.addv(dG.b1.data(), dG.b1.size());
+        S.fw2G = P.addv(dG.vals.data(), dG.vals.size());
+        S.foutG = P.addv(sg.data(), sg.size());
+        S.fcolG = P.addi(dG.cols.data(), dG.cols.size());
+        std::vector<int> own, ids;
+        for (int v : sd.interior) { own.push_back(std::binary_search(sd.owned.begin(), sd.owned.end(), v % ctx->N) ? 1 : 0); ids.push_back(v); }
+        for (int v : sd.interface) { own.push_back(std::binary_search(sd.owned.begin(), sd.owned.end(), v % ctx->N) ? 1 : 0); ids.push_back(v); }
+        S.own = P.addi(own.data(), own.size());
+        S.ids = P.addi(ids.data(), ids.size());
+        S.blk = blk;
+        blk += blk_layout(S.ni, S.nG, nC).size;
+        hr_all.insert(hr_all.end(), sd.hr_ops.begin(), sd.hr_ops.end());
+        S.smem_bytes = eval_smem(S, nC, (int)tsize).bytes;
+        ctx->eval_smem = std::max(ctx->eval_smem, S.smem_bytes);
+        ctx->rec_smem = std::max(ctx->rec_smem, (int)(std::max(dO.w, dG.w) * tsize));
+    }
+    int dev_max = 0;
+    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (ctx->eval_smem > dev_max)
+        return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain needs " + std::to_string(ctx->eval_smem) +
+                                                      " bytes of shared memory (device limit " + std::to_string(dev_max) + ")");
+    if (ctx->rec_smem > dev_max) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "decoder too wide for reconstruction");
+    ctx->step_smem = (int)((size_t)nC * nC + 4 * nC + 2 * MAX_NI * 4) * 8;
+    // upload
+    cudaFree(ctx->d_vpool); cudaFree(ctx->d_ipool); cudaFree(ctx->d_hr); cudaFree(ctx->d_con);
+    cudaFree(ctx->d_C); cudaFree(ctx->d_bnd_ij); cudaFree(ctx->d_sub);
+    ctx->d_vpool = nullptr; ctx->d_ipool = nullptr; ctx->d_hr = nullptr; ctx->d_con = nullptr;
+    ctx->d_C = nullptr; ctx->d_bnd_ij = nullptr; ctx->d_sub = nullptr;
+    if (tsize == 8) {
+        CK(cudaMalloc(&ctx->d_vpool, P.v.size() * 8));
+        CK(cudaMemcpy(ctx->d_vpool, P.v.data(), P.v.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(P.v.begin(), P.v.end());
+        CK(cudaMalloc(&ctx->d_vpool, f.size() * 4));
+        CK(cudaMemcpy(ctx->d_vpool, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMalloc(&ctx->d_ipool, std::max<size_t>(P.i.size(), 1) * 4));
+    CK(cudaMemcpy(ctx->d_ipool, P.i.data(), P.i.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_hr, hr_all.size() * 4));
+    CK(cudaMemcpy(ctx->d_hr, hr_all.data(), hr_all.size() * 4, cudaMemcpyHostToDevice));
+    std::vector<int> con(ctx->con_lo_flat);
+    con.insert(con.end(), ctx->con_hi_flat.begin(), ctx->con_hi_flat.end());
+    CK(cudaMalloc(&ctx->d_con, std::max<size_t>(con.size(), 1) * 4));
+    CK(cudaMemcpy(ctx->d_con, con.data(), con.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_C, std::max<size_t>(ctx->C.size(), 1) * 8));
+    CK(cudaMemcpy(ctx->d_C, ctx->C.data(), ctx->C.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_bnd_ij, std::max<size_t>(ctx->bnd_ij.size(), 1) * 4));
+    CK(cudaMemcpy(ctx->d_bnd_ij, ctx->bnd_ij.data(), ctx->bnd_ij.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_sub, ns * sizeof(SubDev)));
+    CK(cudaMemcpy(ctx->d_sub, ctx->hsub.data(), ns * sizeof(SubDev), cudaMemcpyHostToDevice));
+
+    ProbDev& pd = ctx->pd;
+    pd = ProbDev{};
+    pd.n_sub = ns; pd.n_D = ctx->n_D; pd.n_C = nC; pd.N_A = ctx->N_A;
+    pd.sum_NG = ctx->sum_NG; pd.sum_NB = ctx->sum_NB; pd.n_bnd = (int)ctx->bnd_ij.size() / 2;
+    pd.N_x = 2 * ctx->N; pd.nx = ctx->nx; pd.ny = ctx->ny;
+    pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
+    pd.blk_stride = blk;
+    pd.sub = ctx->d_sub; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool; pd.hr = ctx->d_hr;
+    pd.con_lo = ctx->d_con; pd.con_hi = ctx->d_con + ctx->N_A; pd.C = ctx->d_C; pd.bnd_ij = ctx->d_bnd_ij;
+    ctx->cap_B = 0;   // workspace pointers are re-carved on the next reserve
+    ctx->finalized = true;
+    return DDNM_OK;
+}
+
+// Workspace for B instances: one allocation, carved into the per-instance arrays.
+int ddnm_reserve(ddnm_ctx* ctx, int B) {
+    ProbDev& pd = ctx->pd;
+    if (B <= ctx->cap_B && ctx->d_ws) return DDNM_OK;
+    int cap = std::max(B, 2 * ctx->cap_B);
+    const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t o = 0;
+    size_t o_mu = o; o = al(o + (size_t)cap * 2 * 8);
+    size_t o_x = o; o = al(o + (size_t)cap * pd.n_D * 8);
+    size_t o_lam = o; o = al(o + (size_t)cap * pd.n_C * 8);
+    size_t o_xt = o; o = al(o + (size_t)cap * pd.n_D * 8);
+    size_t o_lamt = o; o = al(o + (size_t)cap * pd.n_C * 8);
+    size_t o_s = o; o = al(o + (size_t)cap * pd.n_D * 8);
+    size_t o_slam = o; o = al(o + (size_t)cap * pd.n_C * 8);
+    size_t o_At = o; o = al(o + (size_t)cap * pd.n_C * 8);
+    size_t o_dst = o; o = al(o + (size_t)cap * INST_DBLS * 8);
+    size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
+    size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * 8);
+    size_t o_gG = o; o = al(o + (size_t)cap * pd.sum_NG * tsize);
+    size_t o_blk = o; o = al(o + (size_t)cap * pd.blk_stride * 8);
+    size_t o_act = o; o = al(o + 64);
+    cudaFree(ctx->d_ws);
+    ctx->d_ws = nullptr;
+    ctx->cap_B = 0;
+    CK(cudaSetDevice(ctx->device));
+    cudaError_t e = cudaMalloc(&ctx->d_ws, o);
+    if (e != cudaSuccess) return ddnm_fail(ctx, DDNM_E_NOMEM, std::string("workspace: ") + cudaGetErrorString(e));
+    if (!ctx->h_active) CK(cudaMallocHost(&ctx->h_active, 64));
+    char* base = (char*)ctx->d_ws;
+    pd.mu = (double*)(base + o_mu);
+    pd.x = (double*)(base + o_x);
+    pd.lam = (double*)(base + o_lam);
+    pd.xt = (double*)(base + o_xt);
+    pd.lamt = (double*)(base + o_lamt);
+    pd.s = (double*)(base + o_s);
+    pd.slam = (double*)(base + o_slam);
+    pd.Atil = (double*)(base + o_At);
+    pd.dst = (double*)(base + o_dst);
+    pd.ist = (int*)(base + o_ist);
+    pd.bnd = (double*)(base + o_bnd);
+    pd.gG = (void*)(base + o_gG);
+    pd.blk = (double*)(base + o_blk);
+    pd.active = (int*)(base + o_act);
+    ctx->cap_B = cap;
+    return DDNM_OK;
+}
+
+// ------------------------------------------------------------------- work counts
+
+extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
+    if (!ctx || !out) return DDNM_E_INVALID;
+    if (!ctx->finalized) {
+        int rc = ddnm_finalize(ctx);
+        if (rc) return rc;
+    }
+    const double nC = ctx->n_C, tsz = ctx->precision == DDNM_FP64 ? 8.0 : 4.0;
+    double f = 0, f64 = 0, bytes = 0, step = 0;
+    for (int s = 0; s < ctx->n_sub; ++s) {
+        const SubDev& S = ctx->hsub[s];
+        const double ni = S.ni, nO = S.nO, nG = S.nG;
+        // hidden layers: z = W1 x + b1 (2 h n), P = sigma'(z) W1 (h n)
+        f += 3.0 * (S.hO * nO + S.hG * nG);
+        // outputs and Jacobian rows over the mask nonzeros, then de-normalisation
+        f += 2.0 * ctx->nnzO[s] * (nO + 1) + 2.0 * ctx->nnzG[s] * (nG + 1) + S.mO * (nO + 2) + S.NG * (nG + 2);
+        // residual row, 6 partials, chain rule R = sum_o d_o J_o
+        f += S.NB * (30.0 + 12.0 * ni);
+        // H = R^T R (upper triangle) and R^T r
+        f += 2.0 * S.NB * (ni * (ni + 1) / 2 + ni);
+        // D_i = (C A_i) dg^G/dxh
+        f += 2.0 * nC * S.NG * nG;
+        // FP64: rho += D^T lambda, Cholesky, t, W = L_GG^{-1} D^T, u, S_i = W^T W
+        f64 += 2 * nC * nG + ni * ni * ni / 3.0 + ni * ni + nC * nG * nG + 2 * nC * nG + 2.0 * nC * nC * nG;
+        // bytes: subnet weights, tables and M_i once; per instance latents, multipliers, block outputs
+        bytes += tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] + 2.0 * (S.mO + S.NG) +
+                        S.NG * nC) +
+                 4.0 * ((double)S.mO * S.K + (double)S.NG * S.K + 7.0 * S.NB) +
+                 8.0 * (blk_layout(S.ni, S.nG, ctx->n_C).size) + tsz * S.NG;
+        // step: sum of S_i and u_i, back-substitution per subdomain
+        step += nC * nC + nC + 2.0 * nG * nC + ni * ni;
+    }
+    bytes += 8.0 * (ctx->n_D + nC + 2);
+    step += nC * nC * nC / 3.0 + 2.0 * nC * nC;
+    out->eval_flops = f;
+    out->eval_fp64_flops = f64;
+    out->eval_bytes = bytes;
+    out->constraint_fp64_flops = 2.0 * nC * ctx->N_A + ctx->N_A;
+    out->step_fp64_flops = step;
+    return DDNM_OK;
+}

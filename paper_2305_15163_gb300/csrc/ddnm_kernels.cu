@@ -1,0 +1,1074 @@
+// sm_103a kernels of the batched Lagrange-Gauss-Newton SQP (Sec. 4.1) for the WFPC
+// DD-LSPG-ROM with collocation HR (Sec. 3.1, 5.3) on steady 2D Burgers (Sec. 7.1).
+//
+// One SQP "pass" over the batch is three launches:
+//   k_eval<T>       one CTA per (instance, subdomain): HR subnets of both decoders
+//                   (Eq. subnet) with Jacobians, the collocated Burgers residual and its
+//                   stencil partials (Eq. burgers_discretized), the chain rule
+//                   R_i = dr/dx dg/dxh (Eq. gauss_newton_hessian b), H_i = R_i^T R_i,
+//                   R_i^T r_i, D_i = C A_i dg^G/dxh, rho_i (Eq. optimality_residuals_GN),
+//                   and the subdomain's share of the Schur complement of the
+//                   block-arrowhead KKT matrix Eq. (sqp_system) in FP64.
+//   k_constraint<T> one CTA per (instance, row of C): Atil = C (sum_i A_i g_i^G) in FP64.
+//   k_step          one CTA per instance: merit ||F||_2, Armijo backtracking (Sec. 4.1),
+//                   least-squares multiplier start (Sec. 7.2), FP64 Schur solve of the KKT
+//                   system and the update Eq. (sqp_update).
+// T is float (MIXED) or double (FP64).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "ddnm_ctx.h"
+
+using namespace ddnm;
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void activation(int act, T z, T& s, T& ds) {
+    if (act == DDNM_ACT_SWISH) {
+        const T g = T(1) / (T(1) + exp(-z));
+        s = z * g;
+        ds = g + z * g * (T(1) - g);
+    } else if (act == DDNM_ACT_SIGMOID) {
+        const T g = T(1) / (T(1) + exp(-z));
+        s = g;
+        ds = g * (T(1) - g);
+    } else {
+        s = z;
+        ds = T(1);
+    }
+}
+
+// exact solution of the steady Burgers problem (Eq. burgers_pde_exact_solution), the Dirichlet data
+__device__ void exact_uv(double x, double y, double a, double lam, double nu, double& u, double& v) {
+    const double ep = exp(lam * (x - 1.0)), em = exp(-lam * (x - 1.0));
+    const double cy = cos(lam * y), sy = sin(lam * y);
+    const double psi = a * (1.0 + x) + (ep + em) * cy;
+    u = -2.0 * nu * (a + lam * (ep - em) * cy) / psi;
+    v = 2.0 * nu * lam * (ep + em) * sy / psi;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the CTA; every thread gets the result
+__device__ double block_sum(double v, double* scratch /* >= 32 */) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0) scratch[w] = v;
+    __syncthreads();
+    double t = (l < nw) ? scratch[l] : 0.0;
+    t = warp_sum(t);
+    return t;
+}
+
+// In-place lower Cholesky of the n x n row-major matrix A in shared memory, whole CTA.
+// Returns false (uniformly) when a pivot is not positive and finite (H not PD, Lemma 1).
+__device__ bool block_cholesky(double* A, int n, int* s_ok) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int j = 0; j < n; ++j) {
+        __syncthreads();
+        if (tid == 0) {
+            const double d = A[j * n + j];
+            const int ok = (d > 0.0) && isfinite(d);
+            *s_ok = ok;
+            if (ok) A[j * n + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (!*s_ok) return false;
+        const double djj = A[j * n + j];
+        for (int i = j + 1 + tid; i < n; i += nth) A[i * n + j] /= djj;
+        __syncthreads();
+        const int m = n - j - 1;
+        for (int e = tid; e < m * m; e += nth) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Solve L L^T x = x in place (L from block_cholesky), whole CTA.
+__device__ void block_chol_solve(const double* L, int n, double* x) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int j = 0; j < n; ++j) {
+        __syncthreads();
+        if (tid == 0) x[j] /= L[j * n + j];
+        __syncthreads();
+        const double xj = x[j];
+        for (int i = j + 1 + tid; i < n; i += nth) x[i] -= L[i * n + j] * xj;
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        __syncthreads();
+        if (tid == 0) x[j] /= L[j * n + j];
+        __syncthreads();
+        const double xj = x[j];
+        for (int i = tid; i < j; i += nth) x[i] -= L[j * n + i] * xj;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------ evaluation
+
+template <typename T>
+__device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned char* smem) {
+    const EvalSmem L = eval_smem(S, P.n_C, (int)sizeof(T));
+    T* sx = (T*)(smem + L.sx);
+    T* sO = (T*)(smem + L.sO);
+    T* PO = (T*)(smem + L.PO);
+    T* sG = (T*)(smem + L.sG);
+    T* PG = (T*)(smem + L.PG);
+    T* yO = (T*)(smem + L.yO);
+    T* JO = (T*)(smem + L.JO);
+    T* yG = (T*)(smem + L.yG);
+    T* JG = (T*)(smem + L.JG);
+    T* Rr = (T*)(smem + L.Rr);
+    T* red = (T*)(smem + L.red);
+    double* dH = (double*)(smem + L.dH);
+    double* drho = (double*)(smem + L.drho);
+    double* dD = (double*)(smem + L.dD);
+    double* dL = (double*)(smem + L.dL);
+    double* dt = (double*)(smem + L.dt);
+    double* dW = (double*)(smem + L.dW);
+    double* dlam = (double*)(smem + L.dlam);
+
+    const T* V = (const T*)P.vpool;
+    const int* IP = P.ipool;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C;
+    const int ld = ni + 1;
+
+    // latent coordinates and multipliers of the trial point
+    if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
+    for (int c = tid; c < nC; c += nth) dlam[c] = P.lamt[(size_t)b * nC + c];
+    __syncthreads();
+
+    // hidden layers of both subnets: sigma(z) and P = sigma'(z) W1 (rows of I_h)
+    for (int c = tid; c < S.hO + S.hG; c += nth) {
+        const bool g = c >= S.hO;
+        const int cc = g ? c - S.hO : c;
+        const int n = g ? nG : nO;
+        const T* W1 = V + (g ? S.w1G : S.w1O) + (size_t)cc * n;
+        const T* xs = sx + (g ? nO : 0);
+        T z = V[(g ? S.b1G : S.b1O) + cc];
+        for (int k = 0; k < n; ++k) z += W1[k] * xs[k];
+        T s, ds;
+        activation<T>(g ? S.actG : S.actO, z, s, ds);
+        (g ? sG : sO)[cc] = s;
+        T* Pr = (g ? PG : PO) + (size_t)cc * n;
+        for (int k = 0; k < n; ++k) Pr[k] = ds * W1[k];
+    }
+    __syncthreads();
+
+    // decoder outputs and Jacobian rows: needed interior rows (I_o) and all interface rows
+    T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
+    for (int r = tid; r < S.mO + S.NG; r += nth) {
+        const bool g = r >= S.mO;
+        const int rr = g ? r - S.mO : r;
+        const int n = g ? nG : nO;
+        const int* cols = IP + (g ? S.colG : S.colO) + (size_t)rr * S.K;
+        const T* vals = V + (g ? S.w2G : S.w2O) + (size_t)rr * S.K;
+        const T* sv = g ? sG : sO;
+        const T* Pm = g ? PG : PO;
+        T y = T(0);
+        T J[MAX_NI];
+#pragma unroll
+        for (int k = 0; k < MAX_NI; ++k) J[k] = T(0);
+        for (int t = 0; t < S.K; ++t) {
+            const int c = cols[t];
+            if (c < 0) break;
+            const T v = vals[t];
+            y += v * sv[c];
+            const T* pc = Pm + (size_t)c * n;
+#pragma unroll
+            for (int k = 0; k < MAX_NI; ++k)
+                if (k < n) J[k] += v * pc[k];
+        }
+        const long long ob = g ? S.outG : S.outO;
+        const int cnt = g ? S.NG : S.mO;
+        const T sc = V[ob + rr], off = V[ob + cnt + rr];
+        y = off + sc * y;
+        T* yv = g ? yG : yO;
+        T* Jv = (g ? JG : JO) + (size_t)rr * n;
+        yv[rr] = y;
+#pragma unroll
+        for (int k = 0; k < MAX_NI; ++k)
+            if (k < n) Jv[k] = sc * J[k];
+        if (g) gout[rr] = y;
+    }
+    __syncthreads();
+
+    // collocated residual rows, stencil partials, chain rule
+    {
+        const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
+        const double* bnd = P.bnd + (size_t)b * P.n_bnd * 2;
+        const T ax = T(0.5 / P.hx), ay = T(0.5 / P.hy);
+        const T cx = T(P.nu / (P.hx * P.hx)), cy = T(P.nu / (P.hy * P.hy));
+        for (int q = tid; q < S.NB; q += nth) {
+            const int* op = hr + (size_t)q * HR_INTS;
+            const int comp = op[0];
+            T f[6];
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
+                f[o] = kind == OP_INTERIOR ? yO[idx] : (kind == OP_INTERFACE ? yG[idx] : (T)bnd[idx]);
+            }
+            const T up = comp == 0 ? f[0] : f[5];
+            const T vp = comp == 0 ? f[5] : f[0];
+            const T dxf = f[1] - f[2], dyf = f[3] - f[4];
+            const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
+                        cy * (f[3] - T(2) * f[0] + f[4]);
+            T d[6];
+            d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
+            d[1] = -up * ax + cx;
+            d[2] = up * ax + cx;
+            d[3] = -vp * ay + cy;
+            d[4] = vp * ay + cy;
+            d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
+            T R[MAX_NI];
+#pragma unroll
+            for (int k = 0; k < MAX_NI; ++k) R[k] = T(0);
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
+                if (kind == OP_INTERIOR) {
+                    const T* j = JO + (size_t)idx * nO;
+#pragma unroll
+                    for (int k = 0; k < MAX_NI; ++k)
+                        if (k < nO) R[k] += d[o] * j[k];
+                } else if (kind == OP_INTERFACE) {
+                    const T* j = JG + (size_t)idx * nG - nO;
+#pragma unroll
+                    for (int k = 0; k < MAX_NI; ++k)
+                        if (k >= nO && k < ni) R[k] += d[o] * j[k];
+                }
+            }
+            T* row = Rr + (size_t)q * ld;
+#pragma unroll
+            for (int k = 0; k < MAX_NI; ++k)
+                if (k < ni) row[k] = R[k];
+            row[ni] = r;
+            if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + q] = (double)r;
+        }
+    }
+    __syncthreads();
+
+    // H_i = R^T R (symmetric) and R^T r
+    {
+        const int npair = ni * (ni + 1) / 2;
+        for (int p = tid; p < npair + ni; p += nth) {
+            int a, c;
+            if (p < npair) {
+                int rem = p;
+                a = 0;
+                while (rem >= ni - a) {
+                    rem -= ni - a;
+                    ++a;
+                }
+                c = a + rem;
+            } else {
+                a = p - npair;
+                c = ni;
+            }
+            T acc = T(0);
+            for (int q = 0; q < S.NB; ++q) acc += Rr[(size_t)q * ld + a] * Rr[(size_t)q * ld + c];
+            if (p < npair) {
+                dH[a * ni + c] = (double)acc;
+                dH[c * ni + a] = (double)acc;
+            } else {
+                drho[a] = (double)acc;
+            }
+        }
+    }
+    // D_i = M_i^T-contraction: D[c][k] = sum_rows M[row][c] JG[row][k], M = C A_i
+    {
+        const int nout = nC * nG;
+        const T* M = V + S.M;
+        if (nout <= nth) {
+            const int groups = nth / nout;
+            if (tid < groups * nout) {
+                const int o = tid % nout, g = tid / nout;
+                const int c = o % nC, k = o / nC;
+                T acc = T(0);
+                for (int row = g; row < S.NG; row += groups) acc += M[(size_t)row * nC + c] * JG[(size_t)row * nG + k];
+                red[tid] = acc;
+            }
+            __syncthreads();
+            if (tid < nout) {
+                T acc = T(0);
+                for (int g = 0; g < groups; ++g) acc += red[g * nout + tid];
+                const int c = tid % nC, k = tid / nC;
+                dD[c * nG + k] = (double)acc;
+            }
+        } else {
+            for (int o = tid; o < nout; o += nth) {
+                const int c = o % nC, k = o / nC;
+                T acc = T(0);
+                for (int row = 0; row < S.NG; ++row) acc += M[(size_t)row * nC + c] * JG[(size_t)row * nG + k];
+                dD[c * nG + k] = (double)acc;
+            }
+        }
+    }
+    __syncthreads();
+
+    // rho_i = R^T r + E_i^T lambda (E_i = [0, D_i])
+    if (tid < ni) {
+        double v = drho[tid];
+        if (tid >= nO) {
+            const int k = tid - nO;
+            for (int c = 0; c < nC; ++c) v += dD[c * nG + k] * dlam[c];
+        }
+        drho[tid] = v;
+    }
+    __syncthreads();
+
+    double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
+    const BlkLayout BL = blk_layout(ni, nG, nC);
+    for (int e = tid; e < ni * ni; e += nth) blk[BL.H + e] = dH[e];
+    if (tid < ni) blk[BL.rho + tid] = drho[tid];
+    for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
+
+    // FP64 per-subdomain Schur pieces (warp 0): H = L L^T, t = L^{-1} rho,
+    // W = L_GG^{-1} D^T (the Omega rows of L^{-1} E^T vanish), u = W^T t_G
+    __shared__ int s_ok;
+    if (tid < 32) {
+        const int lane = tid;
+        for (int e = lane; e < ni * ni; e += 32) dL[e] = dH[e];
+        __syncwarp();
+        bool ok = true;
+        for (int j = 0; j < ni; ++j) {
+            const double d = dL[j * ni + j];
+            ok = (d > 0.0) && isfinite(d);
+            if (!ok) break;
+            const double sd = sqrt(d);
+            __syncwarp();
+            if (lane == 0) dL[j * ni + j] = sd;
+            for (int i = j + 1 + lane; i < ni; i += 32) dL[i * ni + j] /= sd;
+            __syncwarp();
+            const int m = ni - j - 1;
+            for (int e = lane; e < m * m; e += 32) {
+                const int i = j + 1 + e / m, k = j + 1 + e % m;
+                if (k <= i) dL[i * ni + k] -= dL[i * ni + j] * dL[k * ni + j];
+            }
+            __syncwarp();
+        }
+        if (ok) {
+            if (lane == 0) {
+                for (int i = 0; i < ni; ++i) {
+                    double v = drho[i];
+                    for (int k = 0; k < i; ++k) v -= dL[i * ni + k] * dt[k];
+                    dt[i] = v / dL[i * ni + i];
+                }
+            }
+            __syncwarp();
+            for (int c = lane; c < nC; c += 32) {
+                double uc = 0.0;
+                for (int k = 0; k < nG; ++k) {
+                    double v = dD[c * nG + k];
+                    for (int m = 0; m < k; ++m) v -= dL[(nO + k) * ni + nO + m] * dW[m * nC + c];
+                    v /= dL[(nO + k) * ni + nO + k];
+                    dW[k * nC + c] = v;
+                    uc += v * dt[nO + k];
+                }
+                blk[BL.u + c] = uc;
+            }
+        }
+        if (lane == 0) {
+            double ph = 0.0;
+            for (int i = 0; i < ni; ++i) ph += drho[i] * drho[i];
+            blk[BL.phi] = ph;
+            blk[BL.flag] = ok ? 0.0 : 1.0;
+            s_ok = ok;
+        }
+    }
+    __syncthreads();
+    if (s_ok) {
+        for (int e = tid; e < ni * ni; e += nth) blk[BL.L + e] = dL[e];
+        if (tid < ni) blk[BL.t + tid] = dt[tid];
+        for (int e = tid; e < nG * nC; e += nth) blk[BL.W + e] = dW[e];
+        // S_i = W^T W  (n_C x n_C)
+        for (int e = tid; e < nC * nC; e += nth) {
+            const int c1 = e / nC, c2 = e % nC;
+            double v = 0.0;
+            for (int k = 0; k < nG; ++k) v += dW[k * nC + c1] * dW[k * nC + c2];
+            blk[BL.S + e] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b = blockIdx.x / P.n_sub, si = blockIdx.x - (blockIdx.x / P.n_sub) * P.n_sub;
+    if (b >= B) return;
+    if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
+    eval_item<T>(P, P.sub[si], b, smem);
+}
+
+// Atil = C * jump with jump = sum_i A_i g_i^G (each row: g_lo - g_hi), FP64
+template <typename T>
+__global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
+    __shared__ double scratch[32];
+    const int c = blockIdx.x, b = blockIdx.y;
+    if (b >= B) return;
+    if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
+    const T* g = (const T*)P.gG + (size_t)b * P.sum_NG;
+    const double* Cr = P.C + (size_t)c * P.N_A;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < P.N_A; r += blockDim.x)
+        acc += Cr[r] * ((double)g[P.con_lo[r]] - (double)g[P.con_hi[r]]);
+    acc = block_sum(acc, scratch);
+    if (threadIdx.x == 0) P.Atil[(size_t)b * P.n_C + c] = acc;
+}
+
+// ------------------------------------------------------------------------ SQP step
+
+__global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
+    extern __shared__ __align__(16) double sm[];
+    __shared__ double scratch[32];
+    __shared__ int s_ok;
+    const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    if (b >= B) return;
+    int* ist = P.ist + (size_t)b * INST_INTS;
+    double* dst = P.dst + (size_t)b * INST_DBLS;
+    if (ist[I_STATUS] != ST_RUNNING) return;
+    const int nC = P.n_C, ns = P.n_sub, nD = P.n_D;
+    double* blk = P.blk + (size_t)b * P.blk_stride;
+    double* Sm = sm;                  // nC x nC
+    double* rhs = Sm + nC * nC;       // nC
+    double* x_ = P.x + (size_t)b * nD;
+    double* xt = P.xt + (size_t)b * nD;
+    double* s_ = P.s + (size_t)b * nD;
+    double* lam = P.lam + (size_t)b * nC;
+    double* lamt = P.lamt + (size_t)b * nC;
+    double* slam = P.slam + (size_t)b * nC;
+    const double* At = P.Atil + (size_t)b * nC;
+
+    // merit phi^2 = sum_i ||rho_i||^2 + ||Atil||^2, and whether any H_i was not PD
+    double acc = 0.0, fl = 0.0;
+    for (int i = tid; i < ns; i += nth) {
+        const SubDev& S = P.sub[i];
+        const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+        acc += blk[S.blk + BL.phi];
+        fl += blk[S.blk + BL.flag];
+    }
+    for (int c = tid; c < nC; c += nth) acc += At[c] * At[c];
+    const double phi2 = block_sum(acc, scratch);
+    const bool fail = block_sum(fl, scratch) != 0.0;
+    const double phi = sqrt(phi2);
+    const int mode = ist[I_MODE];
+    const int iters0 = ist[I_ITERS], nbt = ist[I_NBT];
+    const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
+    __syncthreads();
+    if (tid == 0) ist[I_NEVALS] += 1;
+
+    if (mode == MODE_INIT0) {
+        // least-squares multiplier (Sec. 7.2): min_l sum_i ||rho_i^G + D_i^T l||^2 at lambda = 0,
+        // normal equations (sum_i D_i D_i^T) l = -sum_i D_i rho_i^G
+        for (int e = tid; e < nC * nC; e += nth) {
+            const int c1 = e / nC, c2 = e % nC;
+            double v = 0.0;
+            for (int i = 0; i < ns; ++i) {
+                const SubDev& S = P.sub[i];
+                const double* D = blk + S.blk + blk_layout(S.ni, S.nG, nC).D;
+                for (int k = 0; k < S.nG; ++k) v += D[c1 * S.nG + k] * D[c2 * S.nG + k];
+            }
+            Sm[e] = v;
+        }
+        for (int c = tid; c < nC; c += nth) {
+            double v = 0.0;
+            for (int i = 0; i < ns; ++i) {
+                const SubDev& S = P.sub[i];
+                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+                const double* D = blk + S.blk + BL.D;
+                const double* rho = blk + S.blk + BL.rho;
+                for (int k = 0; k < S.nG; ++k) v -= D[c * S.nG + k] * rho[S.nO + k];
+            }
+            rhs[c] = v;
+        }
+        __syncthreads();
+        if (!block_cholesky(Sm, nC, &s_ok)) {
+            if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
+            return;
+        }
+        block_chol_solve(Sm, nC, rhs);
+        for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
+        if (tid == 0) {
+            ist[I_MODE] = MODE_INIT1;
+            atomicAdd(P.active, 1);
+        }
+        return;
+    }
+
+    bool accept = true;
+    bool lsfail = false;
+    if (mode == MODE_LS) {
+        const bool armijo = phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0;
+        if (!armijo) {
+            if (nbt < P.max_bt) accept = false;
+            else lsfail = true;
+        }
+    }
+    if (!accept) {
+        const double a = alpha * P.beta;
+        for (int k = tid; k < nD; k += nth) xt[k] = x_[k] + a * s_[k];
+        for (int c = tid; c < nC; c += nth) lamt[c] = lam[c] + a * slam[c];
+        if (tid == 0) {
+            dst[D_ALPHA] = a;
+            ist[I_NBT] = nbt + 1;
+            atomicAdd(P.active, 1);
+        }
+        return;
+    }
+    // accept the trial point
+    for (int k = tid; k < nD; k += nth) x_[k] = xt[k];
+    for (int c = tid; c < nC; c += nth) lam[c] = lamt[c];
+    const int iters = iters0 + (mode == MODE_LS ? 1 : 0);
+    int status = ST_RUNNING;
+    if (!isfinite(phi)) status = DDNM_NONFINITE;
+    else if (phi < P.tol) status = DDNM_CONVERGED;
+    else if (iters >= P.max_iter) status = DDNM_MAX_ITER;
+    else if (fail) status = DDNM_KKT_FAIL;
+    if (tid == 0) {
+        ist[I_ITERS] = iters;
+        dst[D_PHI0] = phi;
+        dst[D_PHI] = phi;
+        if (mode == MODE_LS) dst[D_ALPHA_LAST] = alpha;
+        if (lsfail) ist[I_FLAGS] |= DDNM_FLAG_LS_FAIL;
+    }
+    if (status != ST_RUNNING) {
+        __syncthreads();
+        if (tid == 0) ist[I_STATUS] = status;
+        return;
+    }
+
+    // Schur complement of Eq. (sqp_system): S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T W_i,
+    // S s_lambda = Atil - sum_i E_i H_i^{-1} rho_i = Atil - sum_i u_i
+    for (int e = tid; e < nC * nC; e += nth) {
+        double v = 0.0;
+        for (int i = 0; i < ns; ++i) {
+            const SubDev& S = P.sub[i];
+            v += blk[S.blk + blk_layout(S.ni, S.nG, nC).S + e];
+        }
+        Sm[e] = v;
+    }
+    for (int c = tid; c < nC; c += nth) {
+        double v = At[c];
+        for (int i = 0; i < ns; ++i) {
+            const SubDev& S = P.sub[i];
+            v -= blk[S.blk + blk_layout(S.ni, S.nG, nC).u + c];
+        }
+        rhs[c] = v;
+    }
+    __syncthreads();
+    if (!block_cholesky(Sm, nC, &s_ok)) {
+        if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
+        return;
+    }
+    block_chol_solve(Sm, nC, rhs);
+    // s_i = -L_i^{-T} (t_i + W_i s_lambda), one warp per subdomain
+    {
+        const int w = tid >> 5, lane = tid & 31, nw = nth >> 5;
+        for (int i = w; i < ns; i += nw) {
+            const SubDev& S = P.sub[i];
+            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+            const double* Li = blk + S.blk + BL.L;
+            const double* ti = blk + S.blk + BL.t;
+            const double* Wi = blk + S.blk + BL.W;
+            if (lane == 0) {
+                double z[MAX_NI];
+                for (int k = 0; k < S.ni; ++k) z[k] = ti[k];
+                for (int k = 0; k < S.nG; ++k) {
+                    double v = 0.0;
+                    for (int c = 0; c < nC; ++c) v += Wi[k * nC + c] * rhs[c];
+                    z[S.nO + k] += v;
+                }
+                for (int k = S.ni - 1; k >= 0; --k) {
+                    double v = z[k];
+                    for (int m = k + 1; m < S.ni; ++m) v -= Li[m * S.ni + k] * z[m];
+                    z[k] = v / Li[k * S.ni + k];
+                }
+                for (int k = 0; k < S.ni; ++k) s_[S.xoff + k] = -z[k];
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < nD; k += nth) xt[k] = x_[k] + s_[k];
+    for (int c = tid; c < nC; c += nth) {
+        slam[c] = rhs[c];
+        lamt[c] = lam[c] + rhs[c];
+    }
+    if (tid == 0) {
+        dst[D_ALPHA] = 1.0;
+        ist[I_NBT] = 0;
+        ist[I_MODE] = MODE_LS;
+        atomicAdd(P.active, 1);
+    }
+}
+
+// ------------------------------------------------------------------------ set-up / outputs
+
+// start state of every instance and its Dirichlet data
+__global__ void k_init(ProbDev P, int B, int has_x0, int has_lam0, int mode) {
+    const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    if (b >= B) return;
+    for (int k = tid; k < P.n_D; k += nth) {
+        const double v = has_x0 ? P.x[(size_t)b * P.n_D + k] : 0.0;
+        P.x[(size_t)b * P.n_D + k] = v;
+        P.xt[(size_t)b * P.n_D + k] = v;
+        P.s[(size_t)b * P.n_D + k] = 0.0;
+    }
+    for (int c = tid; c < P.n_C; c += nth) {
+        const double v = has_lam0 ? P.lam[(size_t)b * P.n_C + c] : 0.0;
+        P.lam[(size_t)b * P.n_C + c] = v;
+        P.lamt[(size_t)b * P.n_C + c] = v;
+        P.slam[(size_t)b * P.n_C + c] = 0.0;
+    }
+    const double a = P.mu[2 * b], lm = P.mu[2 * b + 1];
+    for (int p = tid; p < P.n_bnd; p += nth) {
+        const double x = P.bx0 + P.bnd_ij[2 * p] * P.hx, y = P.by0 + P.bnd_ij[2 * p + 1] * P.hy;
+        double u, v;
+        exact_uv(x, y, a, lm, P.nu, u, v);
+        P.bnd[((size_t)b * P.n_bnd + p) * 2] = u;
+        P.bnd[((size_t)b * P.n_bnd + p) * 2 + 1] = v;
+    }
+    if (tid == 0) {
+        int* ist = P.ist + (size_t)b * INST_INTS;
+        ist[I_STATUS] = ST_RUNNING;
+        ist[I_MODE] = mode;
+        ist[I_ITERS] = 0;
+        ist[I_NBT] = 0;
+        ist[I_FLAGS] = 0;
+        ist[I_NEVALS] = 0;
+        double* dst = P.dst + (size_t)b * INST_DBLS;
+        dst[D_PHI0] = 0.0;
+        dst[D_ALPHA] = 1.0;
+        dst[D_PHI] = 0.0;
+        dst[D_ALPHA_LAST] = 0.0;
+    }
+}
+
+__global__ void k_stats(ProbDev P, int B, ddnm_stats* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int* ist = P.ist + (size_t)b * INST_INTS;
+    const double* dst = P.dst + (size_t)b * INST_DBLS;
+    ddnm_stats s;
+    s.iters = ist[I_ITERS];
+    s.status = ist[I_STATUS];
+    s.flags = ist[I_FLAGS];
+    s.n_evals = ist[I_NEVALS];
+    s.merit = dst[D_PHI];
+    s.alpha_last = dst[D_ALPHA_LAST];
+    out[b] = s;
+}
+
+// F = [rho_0; ...; rho_{n-1}; Atil] of the last evaluation, plus the blocks for ddnm_linearize
+__global__ void k_gather(ProbDev P, int B, double* F, double* H, double* D, double* At) {
+    const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    if (b >= B) return;
+    const int nC = P.n_C;
+    const double* blk = P.blk + (size_t)b * P.blk_stride;
+    int hoff = 0, doff = 0, hsum = 0, dsum = 0;
+    for (int i = 0; i < P.n_sub; ++i) {
+        hsum += P.sub[i].ni * P.sub[i].ni;
+        dsum += nC * P.sub[i].nG;
+    }
+    for (int i = 0; i < P.n_sub; ++i) {
+        const SubDev& S = P.sub[i];
+        const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+        if (F)
+            for (int k = tid; k < S.ni; k += nth) F[(size_t)b * (P.n_D + nC) + S.xoff + k] = blk[S.blk + BL.rho + k];
+        if (H)
+            for (int e = tid; e < S.ni * S.ni; e += nth) H[(size_t)b * hsum + hoff + e] = blk[S.blk + BL.H + e];
+        if (D)
+            for (int e = tid; e < nC * S.nG; e += nth) D[(size_t)b * dsum + doff + e] = blk[S.blk + BL.D + e];
+        hoff += S.ni * S.ni;
+        doff += nC * S.nG;
+    }
+    for (int c = tid; c < nC; c += nth) {
+        const double a = P.Atil[(size_t)b * nC + c];
+        if (F) F[(size_t)b * (P.n_D + nC) + P.n_D + c] = a;
+        if (At) At[(size_t)b * nC + c] = a;
+    }
+}
+
+// full decoders (all outputs) for the reconstructed state; each variable from its owner
+template <typename T>
+__global__ void k_reconstruct(ProbDev P, int B, const double* xh, double* state) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* hid = (T*)smem;
+    const int b = blockIdx.x / P.n_sub, si = blockIdx.x % P.n_sub;
+    if (b >= B) return;
+    const SubDev& S = P.sub[si];
+    const T* V = (const T*)P.vpool;
+    const int* IP = P.ipool;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool g = pass == 1;
+        const int n = g ? S.nG : S.nO, w = g ? S.wG_full : S.wO_full, N = g ? S.NG : S.NO_full;
+        const double* x = xh + (size_t)b * P.n_D + S.xoff + (g ? S.nO : 0);
+        const T* W1 = V + (g ? S.fw1G : S.fw1O);
+        const T* b1 = V + (g ? S.fb1G : S.fb1O);
+        __syncthreads();
+        for (int c = tid; c < w; c += nth) {
+            T z = b1[c];
+            for (int k = 0; k < n; ++k) z += W1[(size_t)c * n + k] * (T)x[k];
+            T s, ds;
+            activation<T>(g ? S.actG : S.actO, z, s, ds);
+            hid[c] = s;
+        }
+        __syncthreads();
+        const int* cols = IP + (g ? S.fcolG : S.fcolO);
+        const T* vals = V + (g ? S.fw2G : S.fw2O);
+        const T* so = V + (g ? S.foutG : S.foutO);
+        const int* own = IP + S.own + (g ? S.NO_full : 0);
+        const int* ids = IP + S.ids + (g ? S.NO_full : 0);
+        for (int r = tid; r < N; r += nth) {
+            if (!own[r]) continue;
+            T y = T(0);
+            for (int t = 0; t < S.K; ++t) {
+                const int c = cols[(size_t)r * S.K + t];
+                if (c < 0) break;
+                y += vals[(size_t)r * S.K + t] * hid[c];
+            }
+            state[(size_t)b * P.N_x + ids[r]] = (double)(so[N + r] + so[r] * y);
+        }
+    }
+}
+
+// FOM residual r(x; mu) of Eq. (burgers_discretized) at every node, Dirichlet data from mu
+__global__ void k_fom_residual(ProbDev P, int B, const double* state, double* res) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = P.nx * P.ny;
+    if (gid >= (long long)B * N) return;
+    const int b = (int)(gid / N), p = (int)(gid % N);
+    const int i = p % P.nx, j = p / P.nx;
+    const double* u = state + (size_t)b * P.N_x;
+    const double* v = u + N;
+    const double a = P.mu[2 * b], lm = P.mu[2 * b + 1];
+    double U[5], Vv[5];   // centre, E, W, N, S
+    const int I[5] = {i, i + 1, i - 1, i, i}, J[5] = {j, j, j, j + 1, j - 1};
+    for (int o = 0; o < 5; ++o) {
+        if (I[o] >= 0 && I[o] < P.nx && J[o] >= 0 && J[o] < P.ny) {
+            U[o] = u[J[o] * P.nx + I[o]];
+            Vv[o] = v[J[o] * P.nx + I[o]];
+        } else {
+            exact_uv(P.bx0 + (I[o] + 1) * P.hx, P.by0 + (J[o] + 1) * P.hy, a, lm, P.nu, U[o], Vv[o]);
+        }
+    }
+    const double ax = 0.5 / P.hx, ay = 0.5 / P.hy, cx = P.nu / (P.hx * P.hx), cy = P.nu / (P.hy * P.hy);
+    const double ru = -U[0] * (U[1] - U[2]) * ax - Vv[0] * (U[3] - U[4]) * ay + cx * (U[1] - 2 * U[0] + U[2]) +
+                      cy * (U[3] - 2 * U[0] + U[4]);
+    const double rv = -U[0] * (Vv[1] - Vv[2]) * ax - Vv[0] * (Vv[3] - Vv[4]) * ay + cx * (Vv[1] - 2 * Vv[0] + Vv[2]) +
+                      cy * (Vv[3] - 2 * Vv[0] + Vv[4]);
+    res[(size_t)b * P.N_x + p] = ru;
+    res[(size_t)b * P.N_x + N + p] = rv;
+}
+
+// ------------------------------------------------------------------------ host drivers
+
+struct Launch {
+    ddnm_ctx* ctx;
+    cudaStream_t st;
+};
+
+int cfail(ddnm_ctx* ctx, cudaError_t e, const char* what) {
+    return ddnm_fail(ctx, DDNM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cfail(ctx, e_, #call);       \
+    } while (0)
+
+// per-kernel timing: a pair of events around a launch when timing is on
+int tstart(ddnm_ctx* ctx, int kind, cudaStream_t st) {
+    if (!ctx->timing) return -1;
+    const size_t k = ctx->n_events;
+    while (ctx->events.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ctx->events.push_back(e);
+    }
+    if (ctx->event_kind.size() < k + 1) ctx->event_kind.resize(k + 1);
+    ctx->event_kind[k] = kind;
+    cudaEventRecord(ctx->events[2 * k], st);
+    ctx->n_events = k + 1;
+    return (int)k;
+}
+
+void tstop(ddnm_ctx* ctx, int k, cudaStream_t st) {
+    if (k >= 0) cudaEventRecord(ctx->events[2 * k + 1], st);
+}
+
+int tflush(ddnm_ctx* ctx, cudaStream_t st) {
+    if (!ctx->timing || ctx->n_events == 0) return DDNM_OK;
+    CK(cudaStreamSynchronize(st));
+    for (size_t k = 0; k < ctx->n_events; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[2 * k], ctx->events[2 * k + 1]));
+        if (ctx->event_kind[k] == 0) ctx->tm.eval_ms += ms;
+        else if (ctx->event_kind[k] == 1) ctx->tm.constraint_ms += ms;
+        else ctx->tm.step_ms += ms;
+    }
+    ctx->n_events = 0;
+    return DDNM_OK;
+}
+
+template <typename T>
+int set_smem_attrs(ddnm_ctx* ctx) {
+    CK(cudaFuncSetAttribute(k_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->eval_smem));
+    CK(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->step_smem));
+    CK(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(ctx->rec_smem, 16)));
+    return DDNM_OK;
+}
+
+template <typename T>
+int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st) {
+    int k = tstart(ctx, 0, st);
+    k_eval<T><<<B * P.n_sub, EVAL_THREADS, ctx->eval_smem, st>>>(P, B);
+    CK(cudaGetLastError());
+    tstop(ctx, k, st);
+    ctx->tm.eval_launches++;
+    k = tstart(ctx, 1, st);
+    k_constraint<T><<<dim3(P.n_C, B), CON_THREADS, 0, st>>>(P, B);
+    CK(cudaGetLastError());
+    tstop(ctx, k, st);
+    ctx->tm.constraint_launches++;
+    return DDNM_OK;
+}
+
+// copy n doubles from the caller (host or device memory) into device memory
+int copy_in(ddnm_ctx* ctx, double* dst, const double* src, size_t n, int mem_kind, cudaStream_t st) {
+    if (!n) return DDNM_OK;
+    CK(cudaMemcpyAsync(dst, src, n * 8, mem_kind == DDNM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    return DDNM_OK;
+}
+
+int copy_out(ddnm_ctx* ctx, void* dst, const void* src, size_t bytes, int mem_kind, cudaStream_t st) {
+    if (!bytes) return DDNM_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, mem_kind == DDNM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    return DDNM_OK;
+}
+
+int prepare(ddnm_ctx* ctx, int B, int mem_kind) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (B < 1) return ddnm_fail(ctx, DDNM_E_INVALID, "B must be >= 1");
+    if (mem_kind != DDNM_MEM_HOST && mem_kind != DDNM_MEM_DEVICE) return ddnm_fail(ctx, DDNM_E_INVALID, "bad mem_kind");
+    int rc = ddnm_finalize(ctx);   // checks the call order first, then touches the device
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    rc = ddnm_reserve(ctx, B);
+    if (rc) return rc;
+    rc = ctx->precision == DDNM_FP64 ? set_smem_attrs<double>(ctx) : set_smem_attrs<float>(ctx);
+    return rc;
+}
+
+template <typename T>
+int reconstruct(ddnm_ctx* ctx, const ProbDev& P, int B, const double* xh_dev, double* state_dev, cudaStream_t st) {
+    CK(cudaMemsetAsync(state_dev, 0, (size_t)B * P.N_x * 8, st));
+    k_reconstruct<T><<<B * P.n_sub, 256, std::max(ctx->rec_smem, 16), st>>>(P, B, xh_dev, state_dev);
+    CK(cudaGetLastError());
+    ctx->tm.other_launches++;
+    return DDNM_OK;
+}
+
+// Temporary device buffer for outputs whose caller pointer is host memory.
+struct Tmp {
+    void* p = nullptr;
+    ~Tmp() { cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const double* x0, const double* lam0,
+                                double* x_out, double* lam_out, double* state_out, ddnm_stats* stats, int mem_kind,
+                                void* stream) {
+    int rc = prepare(ctx, B, mem_kind);
+    if (rc) return rc;
+    if (!mu) return ddnm_fail(ctx, DDNM_E_INVALID, "mu is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProbDev P = ctx->pd;
+    P.r_hr = nullptr;
+    const bool fp64 = ctx->precision == DDNM_FP64;
+    if ((rc = copy_in(ctx, P.mu, mu, (size_t)B * 2, mem_kind, st))) return rc;
+    if (x0 && (rc = copy_in(ctx, P.x, x0, (size_t)B * P.n_D, mem_kind, st))) return rc;
+    if (lam0 && (rc = copy_in(ctx, P.lam, lam0, (size_t)B * P.n_C, mem_kind, st))) return rc;
+    k_init<<<B, 128, 0, st>>>(P, B, x0 != nullptr, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0);
+    CK(cudaGetLastError());
+    ctx->tm.other_launches++;
+    const int max_passes = 3 + ctx->opt.max_iter * (ctx->opt.max_backtracks + 1);
+    P.tol = ctx->opt.tol;
+    P.c1 = ctx->opt.armijo_c1;
+    P.beta = ctx->opt.beta;
+    P.max_iter = ctx->opt.max_iter;
+    P.max_bt = ctx->opt.max_backtracks;
+    const int check_every = 4;
+    for (int pass = 0; pass < max_passes; ++pass) {
+        rc = fp64 ? launch_eval<double>(ctx, P, B, st) : launch_eval<float>(ctx, P, B, st);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
+        const int k = tstart(ctx, 2, st);
+        k_step<<<B, STEP_THREADS, ctx->step_smem, st>>>(P, B);
+        CK(cudaGetLastError());
+        tstop(ctx, k, st);
+        ctx->tm.step_launches++;
+        if (pass % check_every == check_every - 1 || pass == max_passes - 1) {
+            CK(cudaMemcpyAsync(ctx->h_active, P.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (*ctx->h_active == 0) break;
+        }
+    }
+    if (x_out && (rc = copy_out(ctx, x_out, P.x, (size_t)B * P.n_D * 8, mem_kind, st))) return rc;
+    if (lam_out && (rc = copy_out(ctx, lam_out, P.lam, (size_t)B * P.n_C * 8, mem_kind, st))) return rc;
+    if (stats) {
+        Tmp t;
+        ddnm_stats* dstats = stats;
+        if (mem_kind == DDNM_MEM_HOST) {
+            CK(cudaMalloc(&t.p, (size_t)B * sizeof(ddnm_stats)));
+            dstats = (ddnm_stats*)t.p;
+        }
+        k_stats<<<(B + 127) / 128, 128, 0, st>>>(P, B, dstats);
+        CK(cudaGetLastError());
+        ctx->tm.other_launches++;
+        if (mem_kind == DDNM_MEM_HOST) {
+            CK(cudaMemcpyAsync(stats, dstats, (size_t)B * sizeof(ddnm_stats), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+    }
+    if (state_out) {
+        Tmp t;
+        double* dstate = state_out;
+        if (mem_kind == DDNM_MEM_HOST) {
+            CK(cudaMalloc(&t.p, (size_t)B * P.N_x * 8));
+            dstate = (double*)t.p;
+        }
+        rc = fp64 ? reconstruct<double>(ctx, P, B, P.x, dstate, st) : reconstruct<float>(ctx, P, B, P.x, dstate, st);
+        if (rc) return rc;
+        if (mem_kind == DDNM_MEM_HOST) {
+            CK(cudaMemcpyAsync(state_out, dstate, (size_t)B * P.N_x * 8, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+    }
+    if (mem_kind == DDNM_MEM_HOST) CK(cudaStreamSynchronize(st));
+    return tflush(ctx, st);
+}
+
+namespace {
+// One evaluation at (x, lam) for B instances (no iteration).
+template <typename T>
+int eval_once(ddnm_ctx* ctx, ProbDev& P, int B, const double* mu, const double* x, const double* lam, int mem_kind,
+              cudaStream_t st, double* r_hr_dev) {
+    int rc;
+    if ((rc = copy_in(ctx, P.mu, mu, (size_t)B * 2, mem_kind, st))) return rc;
+    if ((rc = copy_in(ctx, P.x, x, (size_t)B * P.n_D, mem_kind, st))) return rc;
+    if (lam && (rc = copy_in(ctx, P.lam, lam, (size_t)B * P.n_C, mem_kind, st))) return rc;
+    k_init<<<B, 128, 0, st>>>(P, B, 1, lam != nullptr, MODE_INIT1);
+    CK(cudaGetLastError());
+    ctx->tm.other_launches++;
+    P.r_hr = r_hr_dev;
+    return launch_eval<T>(ctx, P, B, st);
+}
+}  // namespace
+
+extern "C" int ddnm_residual(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam, double* F_out,
+                             double* r_hr_out, double* r_full_out, int mem_kind, void* stream) {
+    int rc = prepare(ctx, B, mem_kind);
+    if (rc) return rc;
+    if (!mu || !x) return ddnm_fail(ctx, DDNM_E_INVALID, "mu and x are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProbDev P = ctx->pd;
+    const bool fp64 = ctx->precision == DDNM_FP64;
+    const bool host = mem_kind == DDNM_MEM_HOST;
+    Tmp tF, tR, tS, tRF;
+    double* dF = F_out;
+    double* dR = r_hr_out;
+    if (host && F_out) { CK(cudaMalloc(&tF.p, (size_t)B * (P.n_D + P.n_C) * 8)); dF = (double*)tF.p; }
+    if (host && r_hr_out) { CK(cudaMalloc(&tR.p, (size_t)B * P.sum_NB * 8)); dR = (double*)tR.p; }
+    rc = fp64 ? eval_once<double>(ctx, P, B, mu, x, lam, mem_kind, st, dR) : eval_once<float>(ctx, P, B, mu, x, lam, mem_kind, st, dR);
+    if (rc) return rc;
+    if (dF) {
+        k_gather<<<B, 128, 0, st>>>(P, B, dF, nullptr, nullptr, nullptr);
+        CK(cudaGetLastError());
+        ctx->tm.other_launches++;
+    }
+    if (r_full_out) {
+        CK(cudaMalloc(&tS.p, (size_t)B * P.N_x * 8));
+        double* dstate = (double*)tS.p;
+        rc = fp64 ? reconstruct<double>(ctx, P, B, P.x, dstate, st) : reconstruct<float>(ctx, P, B, P.x, dstate, st);
+        if (rc) return rc;
+        double* dRF = r_full_out;
+        if (host) { CK(cudaMalloc(&tRF.p, (size_t)B * P.N_x * 8)); dRF = (double*)tRF.p; }
+        const long long tot = (long long)B * P.nx * P.ny;
+        k_fom_residual<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, B, dstate, dRF);
+        CK(cudaGetLastError());
+        ctx->tm.other_launches++;
+        if (host) CK(cudaMemcpyAsync(r_full_out, dRF, (size_t)B * P.N_x * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (host && F_out) CK(cudaMemcpyAsync(F_out, dF, (size_t)B * (P.n_D + P.n_C) * 8, cudaMemcpyDeviceToHost, st));
+    if (host && r_hr_out) CK(cudaMemcpyAsync(r_hr_out, dR, (size_t)B * P.sum_NB * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));   // temporaries are freed on return
+    return tflush(ctx, st);
+}
+
+extern "C" int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam, double* H_out,
+                              double* D_out, double* Atil_out, int mem_kind, void* stream) {
+    int rc = prepare(ctx, B, mem_kind);
+    if (rc) return rc;
+    if (!mu || !x) return ddnm_fail(ctx, DDNM_E_INVALID, "mu and x are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    ProbDev P = ctx->pd;
+    const bool fp64 = ctx->precision == DDNM_FP64;
+    const bool host = mem_kind == DDNM_MEM_HOST;
+    size_t hsum = 0, dsum = 0;
+    for (const SubDev& S : ctx->hsub) {
+        hsum += (size_t)S.ni * S.ni;
+        dsum += (size_t)P.n_C * S.nG;
+    }
+    Tmp tH, tD, tA;
+    double *dH = H_out, *dD = D_out, *dA = Atil_out;
+    if (host && H_out) { CK(cudaMalloc(&tH.p, B * hsum * 8)); dH = (double*)tH.p; }
+    if (host && D_out) { CK(cudaMalloc(&tD.p, B * dsum * 8)); dD = (double*)tD.p; }
+    if (host && Atil_out) { CK(cudaMalloc(&tA.p, (size_t)B * P.n_C * 8)); dA = (double*)tA.p; }
+    rc = fp64 ? eval_once<double>(ctx, P, B, mu, x, lam, mem_kind, st, nullptr)
+              : eval_once<float>(ctx, P, B, mu, x, lam, mem_kind, st, nullptr);
+    if (rc) return rc;
+    k_gather<<<B, 128, 0, st>>>(P, B, nullptr, dH, dD, dA);
+    CK(cudaGetLastError());
+    ctx->tm.other_launches++;
+    if (host && H_out) CK(cudaMemcpyAsync(H_out, dH, B * hsum * 8, cudaMemcpyDeviceToHost, st));
+    if (host && D_out) CK(cudaMemcpyAsync(D_out, dD, B * dsum * 8, cudaMemcpyDeviceToHost, st));
+    if (host && Atil_out) CK(cudaMemcpyAsync(Atil_out, dA, (size_t)B * P.n_C * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return tflush(ctx, st);
+}
+
+extern "C" int ddnm_timing_enable(ddnm_ctx* ctx, int on) {
+    if (!ctx) return DDNM_E_INVALID;
+    ctx->timing = on != 0;
+    ctx->n_events = 0;
+    if (on) ctx->tm = ddnm_timing{};
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_get_timing(const ddnm_ctx* ctx, ddnm_timing* out) {
+    if (!ctx || !out) return DDNM_E_INVALID;
+    *out = ctx->tm;
+    return DDNM_OK;
+}
+
+void ddnm_release_events(ddnm_ctx* ctx) {
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    ctx->events.clear();
+}
