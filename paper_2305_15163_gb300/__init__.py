@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libddnm.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2305_15163_gb300.build` "
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2305_15163_gb300/build.py` "
                       "(or __graft_entry__.build()); there is no fallback implementation")
 _lib = C.CDLL(LIB_PATH)
 

@@ -1,6 +1,7 @@
 """Build libddnm.so (the C-ABI library) in-tree for sm_103a with nvcc.
 
-Usage: python -m paper_2305_15163_gb300.build [--verbose-ptxas]
+Usage: python paper_2305_15163_gb300/build.py [--verbose-ptxas]
+(run as a script: importing the package itself requires the built library)
 """
 from __future__ import annotations
 
