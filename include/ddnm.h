@@ -241,6 +241,32 @@ int ddnm_residual(ddnm_ctx* ctx, int B, const double* mu, const double* x, const
 int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam,
                    double* H_out, double* D_out, double* Atil_out, int mem_kind, void* stream);
 
+/* ddnm_residual without any device allocation.  The paper has no counterpart of
+ * this call: it exists for callers that cannot call cudaMalloc -- code running
+ * under a device-memory cap or a pool that forbids growth, latency-critical
+ * loops where an allocation's implicit device synchronisation is not
+ * acceptable, or code that must not allocate after start-up.
+ *
+ * Computes F = [rho_0; ...; rho_{n-1}; Atil] (B x (n_D + n_C)) at (x, lam) like
+ * ddnm_residual's F_out.  mu (B x 2), x (B x n_D), lam (B x n_C, or NULL for
+ * lambda = 0) and F_out are DEVICE pointers; the work is queued on `stream`
+ * and the call returns without waiting.  Nothing is allocated: the scratch
+ * the evaluation needs lives in one static device array of 16 MiB that every
+ * GPU loading the library holds until the process exits.
+ *  - The decoder and constraint tables must already be on the device: make one
+ *    allocating call (ddnm_residual, ddnm_linearize or ddnm_solve_batch) on ctx
+ *    first, else DDNM_E_STATE.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - B beyond what fits in 16 MiB (about 110 instances of the 128x128 4x4
+ *    workload) returns DDNM_E_UNSUPPORTED with the limit in the message.
+ *  - All calls share the array and it keeps the last call's contents; calls
+ *    that overlap on the GPU (two streams, or two threads) race on it and give
+ *    wrong results.  Serialise them. */
+int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam,
+                          double* F_out, void* stream);
+
 /* Turn per-kernel timing on (resets the counters) or off.  While on, every
  * compute call synchronises its stream before returning. */
 int ddnm_timing_enable(ddnm_ctx* ctx, int on);

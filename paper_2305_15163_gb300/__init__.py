@@ -89,6 +89,7 @@ _sig = {
     "ddnm_solve_batch": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_linearize": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
+    "ddnm_residual_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
     "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
@@ -225,6 +226,15 @@ def ddnm_linearize(ctx, B, mu, x, lam, H_out, D_out, Atil_out):
     kind = _mem_kind(mu, x, lam, H_out, D_out, Atil_out)
     _check(ctx, _lib.ddnm_linearize(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(H_out), _ptr(D_out),
                                     _ptr(Atil_out), kind, _stream(kind)))
+
+
+def ddnm_residual_noalloc(ctx, B, mu, x, lam, F_out):
+    """F at (x, lam) with no device allocation; all arrays are torch CUDA tensors (device memory),
+    queued on the current torch stream.  For callers that cannot allocate device memory; the
+    tables must already be on the device (one allocating call on ctx first).  Calls that overlap
+    on the GPU race on the library's shared static scratch."""
+    _check(ctx, _lib.ddnm_residual_noalloc(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(F_out),
+                                           _stream(DDNM_MEM_DEVICE)))
 
 
 def ddnm_timing_enable(ctx, on=True):

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "ddnm_ctx.h"
@@ -1071,4 +1072,127 @@ extern "C" int ddnm_get_timing(const ddnm_ctx* ctx, ddnm_timing* out) {
 void ddnm_release_events(ddnm_ctx* ctx) {
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     ctx->events.clear();
+}
+
+// ------------------------------------------------------------------ evaluation without allocation
+//
+// ddnm_residual_noalloc: the evaluation of ddnm_residual (F only) for callers that cannot allocate
+// device memory (see include/ddnm.h).  Its scratch -- per-instance solver state, Dirichlet data,
+// interface outputs, per-subdomain Gauss-Newton / Schur blocks, Atil -- lives in the file-scope array
+// below instead of the context's workspace.  Each GPU that loads this library holds the array until
+// the process exits.  All calls share it: calls that overlap on the GPU race on it.
+
+#define DDNM_NOALLOC_SCRATCH_BYTES (16u << 20)   /* 16 MiB */
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DDNM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_noalloc_scratch on each device, looked up once per device (with that device
+// current) on the first no-allocation call there.  The host-side name of the array is only a stand-in.
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {};
+
+int noalloc_scratch(ddnm_ctx* ctx, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 128) return ddnm_fail(ctx, DDNM_E_INVALID, "device ordinal out of range");
+    if (!g_noalloc_addr[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return ddnm_fail(ctx, DDNM_E_CUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
+                                                   cudaGetErrorString(e));
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *out = g_noalloc_addr[ctx->device];
+    return DDNM_OK;
+}
+
+// per-instance state and Dirichlet data for one evaluation (no copies of the caller's inputs)
+__global__ void k_noalloc_init(ProbDev P, int B) {
+    const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    if (b >= B) return;
+    const double a = P.mu[2 * b], lm = P.mu[2 * b + 1];
+    for (int p = tid; p < P.n_bnd; p += nth) {
+        const double x = P.bx0 + P.bnd_ij[2 * p] * P.hx, y = P.by0 + P.bnd_ij[2 * p + 1] * P.hy;
+        double u, v;
+        exact_uv(x, y, a, lm, P.nu, u, v);
+        P.bnd[((size_t)b * P.n_bnd + p) * 2] = u;
+        P.bnd[((size_t)b * P.n_bnd + p) * 2 + 1] = v;
+    }
+    if (tid == 0) {
+        int* ist = P.ist + (size_t)b * INST_INTS;
+        for (int k = 0; k < INST_INTS; ++k) ist[k] = 0;
+        ist[I_STATUS] = ST_RUNNING;
+        ist[I_MODE] = MODE_INIT1;
+    }
+}
+
+template <typename T>
+int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->eval_smem);
+    if (e != cudaSuccess) return cfail(ctx, e, "cudaFuncSetAttribute(k_eval)");
+    k_noalloc_init<<<B, 128, 0, st>>>(P, B);
+    k_eval<T><<<B * P.n_sub, EVAL_THREADS, ctx->eval_smem, st>>>(P, B);
+    k_constraint<T><<<dim3(P.n_C, B), CON_THREADS, 0, st>>>(P, B);
+    k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cfail(ctx, e, "no-allocation evaluation launch");
+    return DDNM_OK;
+}
+
+}  // namespace
+
+extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam,
+                                     double* F_out, void* stream) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (B < 1 || !mu || !x || !F_out) return ddnm_fail(ctx, DDNM_E_INVALID, "B >= 1 and device mu, x, F_out are required");
+    if (!ctx->finalized)
+        return ddnm_fail(ctx, DDNM_E_STATE,
+                         "the decoder and constraint tables are not on the device yet: make one allocating call "
+                         "(ddnm_residual, ddnm_linearize or ddnm_solve_batch) first");
+    ProbDev P = ctx->pd;
+    const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t o = 0;
+    const size_t o_ist = o; o = al(o + (size_t)B * INST_INTS * 4);
+    const size_t o_dst = o; o = al(o + (size_t)B * INST_DBLS * 8);
+    const size_t o_bnd = o; o = al(o + (size_t)B * std::max(P.n_bnd, 1) * 2 * 8);
+    const size_t o_gG = o; o = al(o + (size_t)B * P.sum_NG * tsize);
+    const size_t o_blk = o; o = al(o + (size_t)B * P.blk_stride * 8);
+    const size_t o_At = o; o = al(o + (size_t)B * P.n_C * 8);
+    const size_t o_lz = o; o = al(o + (size_t)B * P.n_C * 8);
+    if (o > DDNM_NOALLOC_SCRATCH_BYTES) {
+        const size_t per = o / B + 1;
+        return ddnm_fail(ctx, DDNM_E_UNSUPPORTED,
+                         "ddnm_residual_noalloc: " + std::to_string(B) + " instances need " + std::to_string(o) +
+                             " bytes of scratch, the static array holds " + std::to_string(DDNM_NOALLOC_SCRATCH_BYTES) +
+                             " (about " + std::to_string(DDNM_NOALLOC_SCRATCH_BYTES / per) + " instances of this problem)");
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cfail(ctx, e, "cudaSetDevice");
+    void* base = nullptr;
+    int rc = noalloc_scratch(ctx, &base);
+    if (rc) return rc;
+    char* s = (char*)base;
+    cudaStream_t st = (cudaStream_t)stream;
+    P.mu = const_cast<double*>(mu);        // read only by the kernels below
+    P.xt = const_cast<double*>(x);         // read only by k_eval
+    P.ist = (int*)(s + o_ist);
+    P.dst = (double*)(s + o_dst);
+    P.bnd = (double*)(s + o_bnd);
+    P.gG = (void*)(s + o_gG);
+    P.blk = (double*)(s + o_blk);
+    P.Atil = (double*)(s + o_At);
+    P.r_hr = nullptr;
+    if (lam) {
+        P.lamt = const_cast<double*>(lam);  // read only by k_eval
+    } else {
+        // the array keeps the previous call's contents: the zero multiplier must be cleared each call
+        P.lamt = (double*)(s + o_lz);
+        e = cudaMemsetAsync(P.lamt, 0, (size_t)B * P.n_C * 8, st);
+        if (e != cudaSuccess) return cfail(ctx, e, "cudaMemsetAsync(zero multipliers)");
+    }
+    return ctx->precision == DDNM_FP64 ? noalloc_eval<double>(ctx, P, B, F_out, st)
+                                       : noalloc_eval<float>(ctx, P, B, F_out, st);
 }
