@@ -22,6 +22,7 @@ struct SubHost {
     std::vector<int> hr_rows;    // local residual-row ids
     std::vector<int> hr_ops;     // HR_INTS per row
     std::vector<int> need;       // interior outputs the stencils use (I_o), ascending local indices
+    std::vector<std::vector<int>> chunk_need;   // the same per chunk of HR_CHUNK collocation rows
     int nO = 0, nG = 0;
 };
 
@@ -53,6 +54,8 @@ struct ddnm_ctx {
     double* d_C = nullptr;
     int* d_bnd_ij = nullptr;
     ddnm::SubDev* d_sub = nullptr;
+    ddnm::ChunkDev* d_chunk = nullptr;
+    std::vector<ddnm::ChunkDev> hchunk;
 
     // workspace for up to cap_B instances
     int cap_B = 0;

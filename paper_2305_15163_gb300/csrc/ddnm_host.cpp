@@ -205,16 +205,26 @@ extern "C" int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out) {
                 }
             }
         }
+        // interior outputs the stencils need: per chunk of HR_CHUNK rows (chunk-local slots) and in total (I_o)
+        const int nch = (nb + HR_CHUNK - 1) / HR_CHUNK;
+        sd.chunk_need.assign(nch, {});
         for (int k = 0; k < nb; ++k)
             for (int o = 0; o < 6; ++o) {
                 int v = raw[k * HR_INTS + 1 + o];
                 if (v >= 0) {
                     int li = find_sorted(sd.interior, v);
-                    if (li >= 0) sd.need.push_back(li);
+                    if (li >= 0) {
+                        sd.need.push_back(li);
+                        sd.chunk_need[k / HR_CHUNK].push_back(li);
+                    }
                 }
             }
         std::sort(sd.need.begin(), sd.need.end());
         sd.need.erase(std::unique(sd.need.begin(), sd.need.end()), sd.need.end());
+        for (auto& cn : sd.chunk_need) {
+            std::sort(cn.begin(), cn.end());
+            cn.erase(std::unique(cn.begin(), cn.end()), cn.end());
+        }
         // second pass: operand codes
         for (int k = 0; k < nb; ++k) {
             sd.hr_ops.push_back(raw[k * HR_INTS]);
@@ -224,7 +234,7 @@ extern "C" int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out) {
                 if (v >= 0) {
                     int li = find_sorted(sd.interior, v);
                     if (li >= 0) {
-                        code = (OP_INTERIOR << OP_SHIFT) | find_sorted(sd.need, li);
+                        code = (OP_INTERIOR << OP_SHIFT) | find_sorted(sd.chunk_need[k / HR_CHUNK], li);
                     } else {
                         int gi = find_sorted(sd.interface, v);
                         if (gi < 0) return bail(DDNM_E_INVALID, "internal: stencil operand outside the subdomain");
@@ -255,6 +265,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_C);
     cudaFree(ctx->d_bnd_ij);
     cudaFree(ctx->d_sub);
+    cudaFree(ctx->d_chunk);
     cudaFree(ctx->d_ws);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
     ddnm_release_events(ctx);
@@ -364,21 +375,21 @@ struct Pools {
     long long addv(const double* p, size_t n) {
         long long o = (long long)v.size();
         v.insert(v.end(), p, p + n);
-        while (v.size() % 4) v.push_back(0.0);   // keep 16-byte alignment for float and double views
+        while (v.size() % 4) v.push_back(0.0);   // 16-byte alignment of every array, float and double views
         return o;
     }
     long long addi(const int* p, size_t n) {
         long long o = (long long)i.size();
         i.insert(i.end(), p, p + n);
-        while (i.size() % 4) i.push_back(-1);
+        while (i.size() % 4) i.push_back(0);
         return o;
     }
 };
 
-// HR subnet of Sec. 5.4: hidden set I_h = union of the mask columns of the rows I_o (ascending);
-// W1~ = W1[I_h], b1~ = b1[I_h], W2~ = W2[I_o, I_h] with columns renumbered into I_h.
-void build_subnet(const DecoderHost& d, const std::vector<int>& Io, Pools& P, long long& w1, long long& b1,
-                  long long& w2, long long& out, long long& col, int& h) {
+// Hidden layer of the HR subnet (Sec. 5.4): I_h = union of the mask columns of the rows Io, ascending;
+// W1~ = W1[I_h] (rows padded to round4(n)), b1~ = b1[I_h].  pos maps a hidden unit to its place in I_h.
+void subnet_hidden(const DecoderHost& d, const std::vector<int>& Io, Pools& P, long long& w1, long long& b1, int& h,
+                   std::vector<int>& pos) {
     std::vector<int> Ih;
     for (int r : Io)
         for (int t = 0; t < d.K; ++t) {
@@ -387,29 +398,39 @@ void build_subnet(const DecoderHost& d, const std::vector<int>& Io, Pools& P, lo
         }
     std::sort(Ih.begin(), Ih.end());
     Ih.erase(std::unique(Ih.begin(), Ih.end()), Ih.end());
-    std::vector<int> pos(d.w, -1);
+    pos.assign(d.w, -1);
     for (size_t k = 0; k < Ih.size(); ++k) pos[Ih[k]] = (int)k;
-    std::vector<double> W1s, b1s, w2s, sc;
-    std::vector<int> cs;
-    for (int c : Ih) {
-        for (int k = 0; k < d.n; ++k) W1s.push_back(d.W1[(size_t)c * d.n + k]);
-        b1s.push_back(d.b1[c]);
+    const int n4 = round4(d.n);
+    std::vector<double> W1s((size_t)Ih.size() * n4, 0.0), b1s;
+    for (size_t k = 0; k < Ih.size(); ++k) {
+        for (int j = 0; j < d.n; ++j) W1s[k * n4 + j] = d.W1[(size_t)Ih[k] * d.n + j];
+        b1s.push_back(d.b1[Ih[k]]);
     }
-    for (int r : Io) {
-        for (int t = 0; t < d.K; ++t) {
-            int c = d.cols[(size_t)r * d.K + t];
-            cs.push_back(c >= 0 ? pos[c] : -1);
-            w2s.push_back(c >= 0 ? d.vals[(size_t)r * d.K + t] : 0.0);
-        }
-    }
-    for (int r : Io) sc.push_back(d.scale[r]);
-    for (int r : Io) sc.push_back(d.offset[r]);
     h = (int)Ih.size();
     w1 = P.addv(W1s.data(), W1s.size());
     b1 = P.addv(b1s.data(), b1s.size());
-    w2 = P.addv(w2s.data(), w2s.size());
-    out = P.addv(sc.data(), sc.size());
+}
+
+// Output rows `rows` of the subnet W2~ (Eq. subnet) in slot-major ELL (Kp slots; padding column 0 value 0),
+// columns renumbered into I_h, followed by their scale and offset.
+void subnet_rows(const DecoderHost& d, const std::vector<int>& rows, const std::vector<int>& pos, int Kp, Pools& P,
+                 long long& col, long long& val, long long& so) {
+    const size_t m = rows.size();
+    std::vector<int> cs(Kp * m, 0);
+    std::vector<double> vs(Kp * m, 0.0), sc;
+    for (size_t r = 0; r < m; ++r)
+        for (int t = 0; t < d.K; ++t) {
+            int c = d.cols[(size_t)rows[r] * d.K + t];
+            if (c >= 0) {
+                cs[t * m + r] = pos[c];
+                vs[t * m + r] = d.vals[(size_t)rows[r] * d.K + t];
+            }
+        }
+    for (int r : rows) sc.push_back(d.scale[r]);
+    for (int r : rows) sc.push_back(d.offset[r]);
     col = P.addi(cs.data(), cs.size());
+    val = P.addv(vs.data(), vs.size());
+    so = P.addv(sc.data(), sc.size());
 }
 }  // namespace
 
@@ -424,6 +445,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     Pools P;
     std::vector<int> hr_all;
     ctx->hsub.assign(ns, SubDev{});
+    ctx->hchunk.clear();
     int xoff = 0, hr_off = 0, blk = 0;
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
     ctx->eval_smem = 0;
@@ -437,17 +459,32 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         SubDev& S = ctx->hsub[s];
         S.nO = sd.nO; S.nG = sd.nG; S.ni = sd.nO + sd.nG; S.xoff = xoff; xoff += S.ni;
         S.NB = (int)sd.hr_rows.size(); S.hr_off = hr_off; hr_off += S.NB;
-        S.K = dO.K; S.actO = dO.act; S.actG = dG.act;
+        S.K = dO.K; S.Kp = round4(dO.K); S.actO = dO.act; S.actG = dG.act;
         S.goff = ctx->goff[s];
-        S.mO = (int)sd.need.size();
         S.NG = (int)sd.interface.size();
-        build_subnet(dO, sd.need, P, S.w1O, S.b1O, S.w2O, S.outO, S.colO, S.hO);
+        // interior subnet over I_o = all outputs the stencils need; one slot-major table per HR chunk
+        std::vector<int> posO, posG;
+        subnet_hidden(dO, sd.need, P, S.w1O, S.b1O, S.hO, posO);
+        S.n_chunks = (int)sd.chunk_need.size();
+        S.chunk0 = (int)ctx->hchunk.size();
+        S.mmax = 0;
+        for (int q = 0; q < S.n_chunks; ++q) {
+            ChunkDev c{};
+            c.q0 = q * HR_CHUNK;
+            c.nq = std::min(HR_CHUNK, S.NB - c.q0);
+            c.m = (int)sd.chunk_need[q].size();
+            subnet_rows(dO, sd.chunk_need[q], posO, S.Kp, P, c.col, c.val, c.so);
+            S.mmax = std::max(S.mmax, c.m);
+            ctx->hchunk.push_back(c);
+        }
         for (int r : sd.need)
             for (int t = 0; t < dO.K; ++t) ctx->nnzO[s] += dO.cols[(size_t)r * dO.K + t] >= 0;
-        for (int c : dG.cols) ctx->nnzG[s] += c >= 0;
+        // interface subnet over all interface outputs (the WFPC constraint is not hyper-reduced)
         std::vector<int> allG(S.NG);
         for (int r = 0; r < S.NG; ++r) allG[r] = r;
-        build_subnet(dG, allG, P, S.w1G, S.b1G, S.w2G, S.outG, S.colG, S.hG);
+        subnet_hidden(dG, allG, P, S.w1G, S.b1G, S.hG, posG);
+        subnet_rows(dG, allG, posG, S.Kp, P, S.colG, S.valG, S.soG);
+        for (int c : dG.cols) ctx->nnzG[s] += c >= 0;
         // M_i = C A_i, stored N^G x n_C
         std::vector<double> M((size_t)S.NG * nC, 0.0);
         for (int r = 0; r < ctx->N_A; ++r) {
@@ -495,12 +532,12 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain needs " + std::to_string(ctx->eval_smem) +
                                                       " bytes of shared memory (device limit " + std::to_string(dev_max) + ")");
     if (ctx->rec_smem > dev_max) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "decoder too wide for reconstruction");
-    ctx->step_smem = (int)((size_t)nC * nC + 4 * nC + 2 * MAX_NI * 4) * 8;
+    ctx->step_smem = (int)((size_t)nC * nC + 4 * nC + (size_t)nC * (MAX_MF + 1) + MAX_MF * MAX_MF + 2 * MAX_MF) * 8;
     // upload
     cudaFree(ctx->d_vpool); cudaFree(ctx->d_ipool); cudaFree(ctx->d_hr); cudaFree(ctx->d_con);
-    cudaFree(ctx->d_C); cudaFree(ctx->d_bnd_ij); cudaFree(ctx->d_sub);
+    cudaFree(ctx->d_C); cudaFree(ctx->d_bnd_ij); cudaFree(ctx->d_sub); cudaFree(ctx->d_chunk);
     ctx->d_vpool = nullptr; ctx->d_ipool = nullptr; ctx->d_hr = nullptr; ctx->d_con = nullptr;
-    ctx->d_C = nullptr; ctx->d_bnd_ij = nullptr; ctx->d_sub = nullptr;
+    ctx->d_C = nullptr; ctx->d_bnd_ij = nullptr; ctx->d_sub = nullptr; ctx->d_chunk = nullptr;
     if (tsize == 8) {
         CK(cudaMalloc(&ctx->d_vpool, P.v.size() * 8));
         CK(cudaMemcpy(ctx->d_vpool, P.v.data(), P.v.size() * 8, cudaMemcpyHostToDevice));
@@ -523,15 +560,19 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_bnd_ij, ctx->bnd_ij.data(), ctx->bnd_ij.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_sub, ns * sizeof(SubDev)));
     CK(cudaMemcpy(ctx->d_sub, ctx->hsub.data(), ns * sizeof(SubDev), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_chunk, std::max<size_t>(ctx->hchunk.size(), 1) * sizeof(ChunkDev)));
+    CK(cudaMemcpy(ctx->d_chunk, ctx->hchunk.data(), ctx->hchunk.size() * sizeof(ChunkDev), cudaMemcpyHostToDevice));
 
     ProbDev& pd = ctx->pd;
     pd = ProbDev{};
     pd.n_sub = ns; pd.n_D = ctx->n_D; pd.n_C = nC; pd.N_A = ctx->N_A;
     pd.sum_NG = ctx->sum_NG; pd.sum_NB = ctx->sum_NB; pd.n_bnd = (int)ctx->bnd_ij.size() / 2;
     pd.N_x = 2 * ctx->N; pd.nx = ctx->nx; pd.ny = ctx->ny;
+    pd.n_split = (ctx->N_A + CON_SPLIT - 1) / CON_SPLIT;
     pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
     pd.blk_stride = blk;
-    pd.sub = ctx->d_sub; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool; pd.hr = ctx->d_hr;
+    pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
+    pd.hr = ctx->d_hr;
     pd.con_lo = ctx->d_con; pd.con_hi = ctx->d_con + ctx->N_A; pd.C = ctx->d_C; pd.bnd_ij = ctx->d_bnd_ij;
     ctx->cap_B = 0;   // workspace pointers are re-carved on the next reserve
     ctx->finalized = true;
@@ -553,7 +594,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     size_t o_lamt = o; o = al(o + (size_t)cap * pd.n_C * 8);
     size_t o_s = o; o = al(o + (size_t)cap * pd.n_D * 8);
     size_t o_slam = o; o = al(o + (size_t)cap * pd.n_C * 8);
-    size_t o_At = o; o = al(o + (size_t)cap * pd.n_C * 8);
+    size_t o_At = o; o = al(o + (size_t)cap * pd.n_split * pd.n_C * 8);
     size_t o_dst = o; o = al(o + (size_t)cap * INST_DBLS * 8);
     size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
     size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * 8);
@@ -599,10 +640,11 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
     for (int s = 0; s < ctx->n_sub; ++s) {
         const SubDev& S = ctx->hsub[s];
         const double ni = S.ni, nO = S.nO, nG = S.nG;
+        const double mO = (double)ctx->subs[s].need.size();   // |I_o|: distinct interior outputs the stencils use
         // hidden layers: z = W1 x + b1 (2 h n), P = sigma'(z) W1 (h n)
         f += 3.0 * (S.hO * nO + S.hG * nG);
         // outputs and Jacobian rows over the mask nonzeros, then de-normalisation
-        f += 2.0 * ctx->nnzO[s] * (nO + 1) + 2.0 * ctx->nnzG[s] * (nG + 1) + S.mO * (nO + 2) + S.NG * (nG + 2);
+        f += 2.0 * ctx->nnzO[s] * (nO + 1) + 2.0 * ctx->nnzG[s] * (nG + 1) + mO * (nO + 2) + S.NG * (nG + 2);
         // residual row, 6 partials, chain rule R = sum_o d_o J_o
         f += S.NB * (30.0 + 12.0 * ni);
         // H = R^T R (upper triangle) and R^T r
@@ -612,9 +654,9 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         // FP64: rho += D^T lambda, Cholesky, t, W = L_GG^{-1} D^T, u, S_i = W^T W
         f64 += 2 * nC * nG + ni * ni * ni / 3.0 + ni * ni + nC * nG * nG + 2 * nC * nG + 2.0 * nC * nC * nG;
         // bytes: subnet weights, tables and M_i once; per instance latents, multipliers, block outputs
-        bytes += tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] + 2.0 * (S.mO + S.NG) +
+        bytes += tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] + 2.0 * (mO + S.NG) +
                         S.NG * nC) +
-                 4.0 * ((double)S.mO * S.K + (double)S.NG * S.K + 7.0 * S.NB) +
+                 4.0 * (mO * S.K + (double)S.NG * S.K + 7.0 * S.NB) +
                  8.0 * (blk_layout(S.ni, S.nG, ctx->n_C).size) + tsz * S.NG;
         // step: sum of S_i and u_i, back-substitution per subdomain
         step += nC * nC + nC + 2.0 * nG * nC + ni * ni;

@@ -12,8 +12,10 @@ constexpr int MAX_NG = 8;      // n_i^G
 constexpr int MAX_K = 64;      // ELL slots of a decoder output row
 constexpr int MAX_NC = 128;    // weak constraints
 constexpr int EVAL_THREADS = 256;
-constexpr int STEP_THREADS = 128;
+constexpr int STEP_THREADS = 256;
 constexpr int CON_THREADS = 256;
+constexpr int CON_SPLIT = 512; // constraint rows per constraint CTA (the N_A axis is split)
+constexpr int HR_CHUNK = 128;  // collocation rows per evaluation chunk (bounds shared memory)
 
 // HR stencil operand codes: (kind << 28) | index
 constexpr int OP_SHIFT = 28;
@@ -27,35 +29,52 @@ constexpr int ST_RUNNING = -1;
 enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_KKTFAIL, I_PAD, INST_INTS };
 enum { D_PHI0 = 0, D_ALPHA, D_PHI, D_ALPHA_LAST, INST_DBLS };
 
+__host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+
+// One chunk of a subdomain's collocation rows with the interior decoder outputs it needs.
+struct ChunkDev {
+    int q0, nq;                    // first collocation row (subdomain-local) and row count
+    int m;                         // interior outputs needed by these rows (chunk-local slots 0..m-1)
+    int pad;
+    long long col;                 // int pool: Kp x m ELL columns (slot-major), renumbered into I_h
+    long long val;                 // value pool: Kp x m ELL values (slot-major)
+    long long so;                  // value pool: scale[m], offset[m]
+};
+
 // One subdomain: latent sizes, HR rows, subnet layout, offsets into the pools.
 struct SubDev {
     int nO, nG, ni, xoff;          // latent dims and offset of xh_i in xh
     int NB, hr_off;                // collocation rows, offset into the HR table
-    int hO, mO;                    // interior subnet: hidden units |I_h|, needed outputs |I_o|
-    int hG, NG;                    // interface subnet: hidden units, outputs (all N^G)
-    int K;                         // ELL slots per output row
+    int hO, hG, NG;                // hidden units of the interior / interface subnets, interface outputs
+    int Kp;                        // ELL slots per row, padded to a multiple of 4 (padding: column 0, value 0)
     int actO, actG;
     int goff;                      // offset of this subdomain's interface outputs in the concatenation
+    int n_chunks, chunk0, mmax;    // HR chunks: count, first index in the chunk table, max outputs per chunk
     int smem_bytes;                // dynamic shared memory the evaluation of this subdomain needs
-    long long w1O, b1O, w2O, outO; // interior subnet in the value pool (outO: scale[mO], offset[mO])
-    long long colO;                // interior subnet ELL columns (compacted to I_h) in the int pool
-    long long w1G, b1G, w2G, outG; // interface subnet
-    long long colG;
+    int blk;                       // offset of this subdomain's block in an instance's block area
+    long long w1O, b1O;            // interior subnet hidden layer: W1~ (hO x round4(nO)), b1~ (hO)
+    long long w1G, b1G;            // interface subnet hidden layer: W1~ (hG x round4(nG)), b1~ (hG)
+    long long colG, valG, soG;     // interface outputs, all rows: ELL slot-major (Kp x NG), scale/offset
     long long M;                   // M_i = C A_i stored N^G x n_C (row = interface output), value pool
-    // per-instance block (doubles) of this subdomain
-    int blk;                       // offset of the block
     // full (not subnet) decoders for reconstruction
-    int NO_full, wO_full, wG_full;
+    int NO_full, wO_full, wG_full, K;
     long long fw1O, fb1O, fw2O, foutO, fcolO;
     long long fw1G, fb1G, fw2G, foutG, fcolG;
-    long long own;                 // offset into the owned-variable table (int pool): NO_full + NG entries, 1 = owned
-    long long ids;                 // global variable ids of interior then interface outputs (int pool)
+    long long own;                 // int pool: NO_full + NG flags, 1 = variable owned by this subdomain
+    long long ids;                 // int pool: global ids of interior then interface outputs
 };
 
 // per-subdomain block layout (doubles) inside an instance's block area
 struct BlkLayout {
-    int H, rho, D, L, t, W, S, u, phi, flag, size;
+    int H, rho, D, L, rinv, t, W, S, u, G, phi, flag, size;
 };
+
+// per-subdomain flag values written by the evaluation
+constexpr double FLAG_PD = 0.0;          // H_i positive definite: Schur pieces L, t, W, u, S valid
+constexpr double FLAG_OMEGA_FAIL = 1.0;  // H_i^{OO} not positive definite: not solvable by this route
+constexpr double FLAG_GAMMA_SING = 2.0;  // H_i^{OO} PD but H_i not: L (first n^O columns), t (t_O, then
+                                         // rho_G - L_GO t_O) and G = H_GG - L_GO L_GO^T are valid
+constexpr int MAX_MF = 32;               // interface unknowns of such subdomains handled per instance
 
 __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
     BlkLayout b;
@@ -64,10 +83,12 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
     b.rho = o; o += ni;
     b.D = o; o += nC * nG;
     b.L = o; o += ni * ni;
+    b.rinv = o; o += ni;           // 1 / L_jj
     b.t = o; o += ni;
     b.W = o; o += nG * nC;
     b.S = o; o += nC * nC;
     b.u = o; o += nC;
+    b.G = o; o += nG * nG;         // Schur complement of H^{OO} in H_i (used when H_i is singular)
     b.phi = o; o += 1;
     b.flag = o; o += 1;
     b.size = o;
@@ -77,11 +98,13 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
 struct ProbDev {
     int n_sub, n_D, n_C, N_A, sum_NG, sum_NB, n_bnd, N_x;
     int nx, ny;
+    int n_split;                   // constraint CTAs per instance (ceil(N_A / CON_SPLIT))
     double hx, hy, nu, bx0, by0;
     double tol, c1, beta;
     int max_iter, max_bt;
     int blk_stride;                // doubles per instance of the block area
     const SubDev* sub;
+    const ChunkDev* chunk;
     const void* vpool;             // decoder values and M_i, float (MIXED) or double (FP64)
     const int* ipool;
     const int* hr;                 // HR_INTS per collocation row, all subdomains
@@ -97,7 +120,7 @@ struct ProbDev {
     double* lamt;
     double* s;
     double* slam;
-    double* Atil;
+    double* Atil;                  // B x n_split x n_C partial sums of C * jump
     double* dst;                   // INST_DBLS per instance
     int* ist;                      // INST_INTS per instance
     double* bnd;                   // B x n_bnd x 2 (u, v)
@@ -109,8 +132,8 @@ struct ProbDev {
 
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {
-    int sx, sO, PO, sG, PG, yO, JO, yG, JG, Rr, red;      // value-type arrays
-    int dH, drho, dD, dL, dt, dW, dlam;                    // double arrays
+    int sx, hidO, hidG, outG, outO, Rr, red;   // value-type arrays
+    int dlam, dH, drho, dD, dL, drinv, dt, dW, dG; // double arrays
     int bytes;
 };
 
@@ -118,25 +141,24 @@ __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 
 __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize) {
     EvalSmem e;
+    const int rO = round4(s.nO + 1), rG = round4(s.nG + 1);
     int o = 0;
     e.sx = o; o = align16(o + MAX_NI * tsize);
-    e.sO = o; o = align16(o + s.hO * tsize);
-    e.PO = o; o = align16(o + s.hO * s.nO * tsize);
-    e.sG = o; o = align16(o + s.hG * tsize);
-    e.PG = o; o = align16(o + s.hG * s.nG * tsize);
-    e.yO = o; o = align16(o + s.mO * tsize);
-    e.JO = o; o = align16(o + s.mO * s.nO * tsize);
-    e.yG = o; o = align16(o + s.NG * tsize);
-    e.JG = o; o = align16(o + s.NG * s.nG * tsize);
-    e.Rr = o; o = align16(o + s.NB * (s.ni + 1) * tsize);
+    e.hidO = o; o = align16(o + s.hO * rO * tsize);          // [sigma, sigma' W1 row] per hidden unit
+    e.hidG = o; o = align16(o + s.hG * rG * tsize);
+    e.outG = o; o = align16(o + s.NG * rG * tsize);          // [y, Jacobian row] per interface output
+    e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
+    e.Rr = o; o = align16(o + HR_CHUNK * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
     e.red = o; o = align16(o + EVAL_THREADS * tsize);
+    e.dlam = o; o = align16(o + nC * 8);
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
     e.dD = o; o = align16(o + nC * s.nG * 8);
     e.dL = o; o = align16(o + s.ni * s.ni * 8);
+    e.drinv = o; o = align16(o + s.ni * 8);
     e.dt = o; o = align16(o + s.ni * 8);
     e.dW = o; o = align16(o + s.nG * nC * 8);
-    e.dlam = o; o = align16(o + nC * 8);
+    e.dG = o; o = align16(o + s.nG * s.nG * 8);
     e.bytes = o;
     return e;
 }

@@ -71,81 +71,135 @@ __device__ double block_sum(double v, double* scratch /* >= 32 */) {
     return t;
 }
 
-// In-place lower Cholesky of the n x n row-major matrix A in shared memory, whole CTA.
-// Returns false (uniformly) when a pivot is not positive and finite (H not PD, Lemma 1).
-__device__ bool block_cholesky(double* A, int n, int* s_ok) {
+// In-place lower Cholesky A = L L^T of the n x n row-major matrix A in shared memory (whole CTA).
+// Pivots go through rsqrt: L_jj = d * rsqrt(d) and rinv[j] = rsqrt(d), so no FP64 division or square
+// root sits on the critical path (each FP64 warp instruction costs 64 cycles on this part).
+// Returns false (uniformly) when a pivot is not positive and finite (Lemma 1 fails).
+__device__ bool block_cholesky(double* A, double* rinv, int n) {
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int j = 0; j < n; ++j) {
         __syncthreads();
-        if (tid == 0) {
-            const double d = A[j * n + j];
-            const int ok = (d > 0.0) && isfinite(d);
-            *s_ok = ok;
-            if (ok) A[j * n + j] = sqrt(d);
-        }
-        __syncthreads();
-        if (!*s_ok) return false;
-        const double djj = A[j * n + j];
-        for (int i = j + 1 + tid; i < n; i += nth) A[i * n + j] /= djj;
+        const double d = A[j * n + j];
+        if (!(d > 0.0) || !isfinite(d)) return false;
+        const double r = rsqrt(d);
+        for (int i = j + 1 + tid; i < n; i += nth) A[i * n + j] *= r;
         __syncthreads();
         const int m = n - j - 1;
         for (int e = tid; e < m * m; e += nth) {
             const int i = j + 1 + e / m, k = j + 1 + e % m;
             if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
         }
+        if (tid == 0) {
+            A[j * n + j] = d * r;
+            rinv[j] = r;
+        }
     }
     __syncthreads();
     return true;
 }
 
-// Solve L L^T x = x in place (L from block_cholesky), whole CTA.
-__device__ void block_chol_solve(const double* L, int n, double* x) {
+// x <- L^{-1} x and x <- L^{-T} x in place, with L, rinv from block_cholesky (whole CTA).
+__device__ void block_fwd(const double* L, const double* rinv, int n, double* x) {
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int j = 0; j < n; ++j) {
         __syncthreads();
-        if (tid == 0) x[j] /= L[j * n + j];
-        __syncthreads();
-        const double xj = x[j];
+        const double xj = x[j] * rinv[j];
         for (int i = j + 1 + tid; i < n; i += nth) x[i] -= L[i * n + j] * xj;
-    }
-    for (int j = n - 1; j >= 0; --j) {
-        __syncthreads();
-        if (tid == 0) x[j] /= L[j * n + j];
-        __syncthreads();
-        const double xj = x[j];
-        for (int i = tid; i < j; i += nth) x[i] -= L[j * n + i] * xj;
+        if (tid == 0) x[j] = xj;
     }
     __syncthreads();
 }
 
+__device__ void block_bwd(const double* L, const double* rinv, int n, double* x) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int j = n - 1; j >= 0; --j) {
+        __syncthreads();
+        const double xj = x[j] * rinv[j];
+        for (int i = tid; i < j; i += nth) x[i] -= L[j * n + i] * xj;
+        if (tid == 0) x[j] = xj;
+    }
+    __syncthreads();
+}
+
+// Solve L L^T x = x in place (whole CTA).
+__device__ void block_chol_solve(const double* L, const double* rinv, int n, double* x) {
+    block_fwd(L, rinv, n, x);
+    block_bwd(L, rinv, n, x);
+}
+
+// 4 consecutive values, 16-byte aligned (float4) or 32-byte aligned (two double2)
+__device__ __forceinline__ void ld4(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* o) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* o) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* o) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+}
+
+// One decoder output row of an ELL table in slot-major layout (Kp slots, padding slots hold column 0,
+// value 0): acc[k] = sum_t val_t * hid[col_t][k] for k < R (R = round4(n+1) <= RMAX), i.e. the raw output
+// (k = 0) and its Jacobian row (k >= 1) through the hidden rows [sigma, sigma' W1].
+template <typename T, int RMAX>
+__device__ __forceinline__ void ell_row(const int* col, const T* val, int stride, int Kp, const T* hid, int R,
+                                        T* acc) {
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) acc[k] = T(0);
+#pragma unroll 4
+    for (int t = 0; t < Kp; ++t) {
+        const int c = col[(size_t)t * stride];
+        const T v = val[(size_t)t * stride];
+        const T* h = hid + (size_t)c * R;
+#pragma unroll
+        for (int k = 0; k < RMAX; k += 4) {
+            if (k < R) {
+                T hv[4];
+                ld4(h + k, hv);
+                acc[k] += v * hv[0];
+                acc[k + 1] += v * hv[1];
+                acc[k + 2] += v * hv[2];
+                acc[k + 3] += v * hv[3];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------ evaluation
 
+// One (instance, subdomain) evaluation.  Chunked over the collocation rows so that shared memory stays
+// bounded for any subdomain size; every decoder table is read slot-major (consecutive threads ->
+// consecutive addresses).
 template <typename T>
 __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned char* smem) {
     const EvalSmem L = eval_smem(S, P.n_C, (int)sizeof(T));
     T* sx = (T*)(smem + L.sx);
-    T* sO = (T*)(smem + L.sO);
-    T* PO = (T*)(smem + L.PO);
-    T* sG = (T*)(smem + L.sG);
-    T* PG = (T*)(smem + L.PG);
-    T* yO = (T*)(smem + L.yO);
-    T* JO = (T*)(smem + L.JO);
-    T* yG = (T*)(smem + L.yG);
-    T* JG = (T*)(smem + L.JG);
+    T* hidO = (T*)(smem + L.hidO);
+    T* hidG = (T*)(smem + L.hidG);
+    T* outG = (T*)(smem + L.outG);
+    T* outO = (T*)(smem + L.outO);
     T* Rr = (T*)(smem + L.Rr);
     T* red = (T*)(smem + L.red);
+    double* dlam = (double*)(smem + L.dlam);
     double* dH = (double*)(smem + L.dH);
     double* drho = (double*)(smem + L.drho);
     double* dD = (double*)(smem + L.dD);
     double* dL = (double*)(smem + L.dL);
+    double* drinv = (double*)(smem + L.drinv);
     double* dt = (double*)(smem + L.dt);
     double* dW = (double*)(smem + L.dW);
-    double* dlam = (double*)(smem + L.dlam);
 
     const T* V = (const T*)P.vpool;
     const int* IP = P.ipool;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C;
+    const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C, NG = S.NG;
+    const int rO = round4(nO + 1), rG = round4(nG + 1);
     const int ld = ni + 1;
 
     // latent coordinates and multipliers of the trial point
@@ -153,160 +207,76 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     for (int c = tid; c < nC; c += nth) dlam[c] = P.lamt[(size_t)b * nC + c];
     __syncthreads();
 
-    // hidden layers of both subnets: sigma(z) and P = sigma'(z) W1 (rows of I_h)
+    // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :]] (zero padded to a multiple of 4)
     for (int c = tid; c < S.hO + S.hG; c += nth) {
         const bool g = c >= S.hO;
         const int cc = g ? c - S.hO : c;
-        const int n = g ? nG : nO;
-        const T* W1 = V + (g ? S.w1G : S.w1O) + (size_t)cc * n;
+        const int n = g ? nG : nO, w4 = round4(n), R = g ? rG : rO;
+        const T* W1 = V + (g ? S.w1G : S.w1O) + (size_t)cc * w4;
         const T* xs = sx + (g ? nO : 0);
+        T w[MAX_NI];
+#pragma unroll
+        for (int k = 0; k < MAX_NI; k += 4)
+            if (k < w4) ld4(W1 + k, w + k);
         T z = V[(g ? S.b1G : S.b1O) + cc];
-        for (int k = 0; k < n; ++k) z += W1[k] * xs[k];
-        T s, ds;
-        activation<T>(g ? S.actG : S.actO, z, s, ds);
-        (g ? sG : sO)[cc] = s;
-        T* Pr = (g ? PG : PO) + (size_t)cc * n;
-        for (int k = 0; k < n; ++k) Pr[k] = ds * W1[k];
-    }
-    __syncthreads();
-
-    // decoder outputs and Jacobian rows: needed interior rows (I_o) and all interface rows
-    T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
-    for (int r = tid; r < S.mO + S.NG; r += nth) {
-        const bool g = r >= S.mO;
-        const int rr = g ? r - S.mO : r;
-        const int n = g ? nG : nO;
-        const int* cols = IP + (g ? S.colG : S.colO) + (size_t)rr * S.K;
-        const T* vals = V + (g ? S.w2G : S.w2O) + (size_t)rr * S.K;
-        const T* sv = g ? sG : sO;
-        const T* Pm = g ? PG : PO;
-        T y = T(0);
-        T J[MAX_NI];
-#pragma unroll
-        for (int k = 0; k < MAX_NI; ++k) J[k] = T(0);
-        for (int t = 0; t < S.K; ++t) {
-            const int c = cols[t];
-            if (c < 0) break;
-            const T v = vals[t];
-            y += v * sv[c];
-            const T* pc = Pm + (size_t)c * n;
-#pragma unroll
-            for (int k = 0; k < MAX_NI; ++k)
-                if (k < n) J[k] += v * pc[k];
-        }
-        const long long ob = g ? S.outG : S.outO;
-        const int cnt = g ? S.NG : S.mO;
-        const T sc = V[ob + rr], off = V[ob + cnt + rr];
-        y = off + sc * y;
-        T* yv = g ? yG : yO;
-        T* Jv = (g ? JG : JO) + (size_t)rr * n;
-        yv[rr] = y;
 #pragma unroll
         for (int k = 0; k < MAX_NI; ++k)
-            if (k < n) Jv[k] = sc * J[k];
-        if (g) gout[rr] = y;
+            if (k < n) z += w[k] * xs[k];
+        T s, ds;
+        activation<T>(g ? S.actG : S.actO, z, s, ds);
+        T row[MAX_NI + 4];
+        row[0] = s;
+#pragma unroll
+        for (int k = 0; k < MAX_NI; ++k) row[k + 1] = (k < n) ? ds * w[k] : T(0);
+#pragma unroll
+        for (int k = MAX_NI + 1; k < MAX_NI + 4; ++k) row[k] = T(0);
+        T* dst = (g ? hidG : hidO) + (size_t)cc * R;
+#pragma unroll
+        for (int k = 0; k < MAX_NI + 4; k += 4)
+            if (k < R) st4(dst + k, row + k);
     }
     __syncthreads();
 
-    // collocated residual rows, stencil partials, chain rule
+    // interface outputs (all rows): [g^G_r, dg^G_r/dxh] into shared memory; g^G to global for the jump
     {
-        const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
-        const double* bnd = P.bnd + (size_t)b * P.n_bnd * 2;
-        const T ax = T(0.5 / P.hx), ay = T(0.5 / P.hy);
-        const T cx = T(P.nu / (P.hx * P.hx)), cy = T(P.nu / (P.hy * P.hy));
-        for (int q = tid; q < S.NB; q += nth) {
-            const int* op = hr + (size_t)q * HR_INTS;
-            const int comp = op[0];
-            T f[6];
+        T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
+        const int* col = IP + S.colG;
+        const T* val = V + S.valG;
+        const T* so = V + S.soG;
+        for (int r = tid; r < NG; r += nth) {
+            T acc[MAX_NG + 4];
+            ell_row<T, MAX_NG + 4>(col + r, val + r, NG, S.Kp, hidG, rG, acc);
+            const T sc = so[r], off = so[NG + r];
+            T row[MAX_NG + 4];
+            row[0] = off + sc * acc[0];
 #pragma unroll
-            for (int o = 0; o < 6; ++o) {
-                const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
-                f[o] = kind == OP_INTERIOR ? yO[idx] : (kind == OP_INTERFACE ? yG[idx] : (T)bnd[idx]);
-            }
-            const T up = comp == 0 ? f[0] : f[5];
-            const T vp = comp == 0 ? f[5] : f[0];
-            const T dxf = f[1] - f[2], dyf = f[3] - f[4];
-            const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
-                        cy * (f[3] - T(2) * f[0] + f[4]);
-            T d[6];
-            d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
-            d[1] = -up * ax + cx;
-            d[2] = up * ax + cx;
-            d[3] = -vp * ay + cy;
-            d[4] = vp * ay + cy;
-            d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
-            T R[MAX_NI];
+            for (int k = 1; k < MAX_NG + 4; ++k) row[k] = sc * acc[k];
+            T* dst = outG + (size_t)r * rG;
 #pragma unroll
-            for (int k = 0; k < MAX_NI; ++k) R[k] = T(0);
-#pragma unroll
-            for (int o = 0; o < 6; ++o) {
-                const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
-                if (kind == OP_INTERIOR) {
-                    const T* j = JO + (size_t)idx * nO;
-#pragma unroll
-                    for (int k = 0; k < MAX_NI; ++k)
-                        if (k < nO) R[k] += d[o] * j[k];
-                } else if (kind == OP_INTERFACE) {
-                    const T* j = JG + (size_t)idx * nG - nO;
-#pragma unroll
-                    for (int k = 0; k < MAX_NI; ++k)
-                        if (k >= nO && k < ni) R[k] += d[o] * j[k];
-                }
-            }
-            T* row = Rr + (size_t)q * ld;
-#pragma unroll
-            for (int k = 0; k < MAX_NI; ++k)
-                if (k < ni) row[k] = R[k];
-            row[ni] = r;
-            if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + q] = (double)r;
+            for (int k = 0; k < MAX_NG + 4; k += 4)
+                if (k < rG) st4(dst + k, row + k);
+            gout[r] = row[0];
         }
     }
     __syncthreads();
 
-    // H_i = R^T R (symmetric) and R^T r
-    {
-        const int npair = ni * (ni + 1) / 2;
-        for (int p = tid; p < npair + ni; p += nth) {
-            int a, c;
-            if (p < npair) {
-                int rem = p;
-                a = 0;
-                while (rem >= ni - a) {
-                    rem -= ni - a;
-                    ++a;
-                }
-                c = a + rem;
-            } else {
-                a = p - npair;
-                c = ni;
-            }
-            T acc = T(0);
-            for (int q = 0; q < S.NB; ++q) acc += Rr[(size_t)q * ld + a] * Rr[(size_t)q * ld + c];
-            if (p < npair) {
-                dH[a * ni + c] = (double)acc;
-                dH[c * ni + a] = (double)acc;
-            } else {
-                drho[a] = (double)acc;
-            }
-        }
-    }
-    // D_i = M_i^T-contraction: D[c][k] = sum_rows M[row][c] JG[row][k], M = C A_i
+    // D_i[c][k] = sum_rows M[row][c] dg^G[row][k], M = C A_i (stored N^G x n_C)
     {
         const int nout = nC * nG;
         const T* M = V + S.M;
         if (nout <= nth) {
             const int groups = nth / nout;
             if (tid < groups * nout) {
-                const int o = tid % nout, g = tid / nout;
+                const int o = tid % nout, gq = tid / nout;
                 const int c = o % nC, k = o / nC;
                 T acc = T(0);
-                for (int row = g; row < S.NG; row += groups) acc += M[(size_t)row * nC + c] * JG[(size_t)row * nG + k];
+                for (int row = gq; row < NG; row += groups) acc += M[(size_t)row * nC + c] * outG[(size_t)row * rG + 1 + k];
                 red[tid] = acc;
             }
             __syncthreads();
             if (tid < nout) {
                 T acc = T(0);
-                for (int g = 0; g < groups; ++g) acc += red[g * nout + tid];
+                for (int gq = 0; gq < groups; ++gq) acc += red[gq * nout + tid];
                 const int c = tid % nC, k = tid / nC;
                 dD[c * nG + k] = (double)acc;
             }
@@ -314,94 +284,214 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int o = tid; o < nout; o += nth) {
                 const int c = o % nC, k = o / nC;
                 T acc = T(0);
-                for (int row = 0; row < S.NG; ++row) acc += M[(size_t)row * nC + c] * JG[(size_t)row * nG + k];
+                for (int row = 0; row < NG; ++row) acc += M[(size_t)row * nC + c] * outG[(size_t)row * rG + 1 + k];
                 dD[c * nG + k] = (double)acc;
             }
         }
     }
-    __syncthreads();
 
-    // rho_i = R^T r + E_i^T lambda (E_i = [0, D_i])
-    if (tid < ni) {
-        double v = drho[tid];
-        if (tid >= nO) {
-            const int k = tid - nO;
-            for (int c = 0; c < nC; ++c) v += dD[c * nG + k] * dlam[c];
+    // collocation rows, chunk by chunk: needed interior outputs, residual rows and partials, chain rule,
+    // then the running sums of H_i = R^T R and R^T r (thread p owns one entry)
+    const int npair = ni * (ni + 1) / 2;
+    int pa = 0, pc = 0;
+    if (tid < npair) {
+        int rem = tid;
+        while (rem >= ni - pa) {
+            rem -= ni - pa;
+            ++pa;
         }
-        drho[tid] = v;
+        pc = pa + rem;
+    } else if (tid < npair + ni) {
+        pa = tid - npair;
+        pc = ni;
+    }
+    T hacc = T(0);
+    {
+        const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
+        const double* bnd = P.bnd + (size_t)b * P.n_bnd * 2;
+        const T ax = T(0.5 / P.hx), ay = T(0.5 / P.hy);
+        const T cx = T(P.nu / (P.hx * P.hx)), cy = T(P.nu / (P.hy * P.hy));
+        for (int q = 0; q < S.n_chunks; ++q) {
+            const ChunkDev Cq = P.chunk[S.chunk0 + q];
+            __syncthreads();   // previous chunk's outO / Rr fully consumed
+            {
+                const int* col = IP + Cq.col;
+                const T* val = V + Cq.val;
+                const T* so = V + Cq.so;
+                for (int r = tid; r < Cq.m; r += nth) {
+                    T acc[MAX_NI + 4];
+                    ell_row<T, MAX_NI + 4>(col + r, val + r, Cq.m, S.Kp, hidO, rO, acc);
+                    const T sc = so[r], off = so[Cq.m + r];
+                    T row[MAX_NI + 4];
+                    row[0] = off + sc * acc[0];
+#pragma unroll
+                    for (int k = 1; k < MAX_NI + 4; ++k) row[k] = sc * acc[k];
+                    T* dst = outO + (size_t)r * rO;
+#pragma unroll
+                    for (int k = 0; k < MAX_NI + 4; k += 4)
+                        if (k < rO) st4(dst + k, row + k);
+                }
+            }
+            __syncthreads();
+            for (int ql = tid; ql < Cq.nq; ql += nth) {
+                const int* op = hr + (size_t)(Cq.q0 + ql) * HR_INTS;
+                const int comp = op[0];
+                T f[6];
+#pragma unroll
+                for (int o = 0; o < 6; ++o) {
+                    const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
+                    f[o] = kind == OP_INTERIOR ? outO[(size_t)idx * rO]
+                                               : (kind == OP_INTERFACE ? outG[(size_t)idx * rG] : (T)bnd[idx]);
+                }
+                const T up = comp == 0 ? f[0] : f[5];
+                const T vp = comp == 0 ? f[5] : f[0];
+                const T dxf = f[1] - f[2], dyf = f[3] - f[4];
+                const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
+                            cy * (f[3] - T(2) * f[0] + f[4]);
+                T d[6];
+                d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
+                d[1] = -up * ax + cx;
+                d[2] = up * ax + cx;
+                d[3] = -vp * ay + cy;
+                d[4] = vp * ay + cy;
+                d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
+                T R[MAX_NI];
+#pragma unroll
+                for (int k = 0; k < MAX_NI; ++k) R[k] = T(0);
+#pragma unroll
+                for (int o = 0; o < 6; ++o) {
+                    const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
+                    if (kind == OP_INTERIOR) {
+                        const T* j = outO + (size_t)idx * rO + 1;
+#pragma unroll
+                        for (int k = 0; k < MAX_NI; ++k)
+                            if (k < nO) R[k] += d[o] * j[k];
+                    } else if (kind == OP_INTERFACE) {
+                        const T* j = outG + (size_t)idx * rG + 1 - nO;
+#pragma unroll
+                        for (int k = 0; k < MAX_NI; ++k)
+                            if (k >= nO && k < ni) R[k] += d[o] * j[k];
+                    }
+                }
+                T* row = Rr + (size_t)ql * ld;
+#pragma unroll
+                for (int k = 0; k < MAX_NI; ++k)
+                    if (k < ni) row[k] = R[k];
+                row[ni] = r;
+                if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + Cq.q0 + ql] = (double)r;
+            }
+            __syncthreads();
+            if (tid < npair + ni)
+                for (int ql = 0; ql < Cq.nq; ++ql) hacc += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
+        }
+    }
+    if (tid < npair) {
+        dH[pa * ni + pc] = (double)hacc;
+        dH[pc * ni + pa] = (double)hacc;
+    } else if (tid < npair + ni) {
+        drho[pa] = (double)hacc;
     }
     __syncthreads();
 
+    // FP64 tail (warp 0, every lane busy where the structure allows):
+    // rho_i = R^T r + E_i^T lambda; H = L L^T; t = L^{-1} rho; W = L_GG^{-1} D^T (the Omega rows of
+    // L^{-1} E^T vanish); u = W^T t_G; ||rho_i||^2.  Lemma 1 only needs H_i PD on null(E_i): when the
+    // collocation rows do not see every interface direction, H_i is singular in its G block while
+    // H_i^{OO} is PD.  The Cholesky then stops after the O columns and the step kernel handles the
+    // subdomain through G = H_GG - L_GO L_GO^T (snapshot taken after the O columns).
     double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
     const BlkLayout BL = blk_layout(ni, nG, nC);
-    for (int e = tid; e < ni * ni; e += nth) blk[BL.H + e] = dH[e];
-    if (tid < ni) blk[BL.rho + tid] = drho[tid];
-    for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
-
-    // FP64 per-subdomain Schur pieces (warp 0): H = L L^T, t = L^{-1} rho,
-    // W = L_GG^{-1} D^T (the Omega rows of L^{-1} E^T vanish), u = W^T t_G
-    __shared__ int s_ok;
+    double* dGs = (double*)(smem + L.dG);
+    __shared__ int s_flag;
     if (tid < 32) {
         const int lane = tid;
+        if (lane < ni) {
+            double v = drho[lane];
+            if (lane >= nO)
+                for (int c = 0; c < nC; ++c) v += dD[c * nG + lane - nO] * dlam[c];
+            drho[lane] = v;
+            dt[lane] = v;
+        }
         for (int e = lane; e < ni * ni; e += 32) dL[e] = dH[e];
         __syncwarp();
-        bool ok = true;
+        int flag = 0;
         for (int j = 0; j < ni; ++j) {
-            const double d = dL[j * ni + j];
-            ok = (d > 0.0) && isfinite(d);
-            if (!ok) break;
-            const double sd = sqrt(d);
+            if (j == nO)      // Schur complement of H^{OO}: the untouched trailing block
+                for (int e = lane; e < nG * nG; e += 32) dGs[e] = dL[(nO + e / nG) * ni + nO + e % nG];
             __syncwarp();
-            if (lane == 0) dL[j * ni + j] = sd;
-            for (int i = j + 1 + lane; i < ni; i += 32) dL[i * ni + j] /= sd;
+            const double d = dL[j * ni + j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                flag = j < nO ? 1 : 2;
+                break;
+            }
+            const double r = rsqrt(d);
+            for (int i = j + 1 + lane; i < ni; i += 32) dL[i * ni + j] *= r;
             __syncwarp();
             const int m = ni - j - 1;
             for (int e = lane; e < m * m; e += 32) {
                 const int i = j + 1 + e / m, k = j + 1 + e % m;
                 if (k <= i) dL[i * ni + k] -= dL[i * ni + j] * dL[k * ni + j];
             }
-            __syncwarp();
-        }
-        if (ok) {
             if (lane == 0) {
-                for (int i = 0; i < ni; ++i) {
-                    double v = drho[i];
-                    for (int k = 0; k < i; ++k) v -= dL[i * ni + k] * dt[k];
-                    dt[i] = v / dL[i * ni + i];
-                }
+                dL[j * ni + j] = d * r;
+                drinv[j] = r;
             }
             __syncwarp();
+        }
+        if (flag != 1) {
+            const int nf = flag == 0 ? ni : nO;       // forward substitution over the factored columns
+            for (int j = 0; j < nf; ++j) {
+                const double tj = dt[j] * drinv[j];
+                for (int i = j + 1 + lane; i < ni; i += 32) dt[i] -= dL[i * ni + j] * tj;
+                __syncwarp();
+                if (lane == 0) dt[j] = tj;
+                __syncwarp();
+            }
+        }
+        if (flag == 0) {
             for (int c = lane; c < nC; c += 32) {
                 double uc = 0.0;
                 for (int k = 0; k < nG; ++k) {
                     double v = dD[c * nG + k];
                     for (int m = 0; m < k; ++m) v -= dL[(nO + k) * ni + nO + m] * dW[m * nC + c];
-                    v /= dL[(nO + k) * ni + nO + k];
+                    v *= drinv[nO + k];
                     dW[k * nC + c] = v;
                     uc += v * dt[nO + k];
                 }
                 blk[BL.u + c] = uc;
             }
         }
+        double ph = lane < ni ? drho[lane] * drho[lane] : 0.0;
+        ph = warp_sum(ph);
         if (lane == 0) {
-            double ph = 0.0;
-            for (int i = 0; i < ni; ++i) ph += drho[i] * drho[i];
             blk[BL.phi] = ph;
-            blk[BL.flag] = ok ? 0.0 : 1.0;
-            s_ok = ok;
+            blk[BL.flag] = (double)flag;
+            s_flag = flag;
         }
     }
     __syncthreads();
-    if (s_ok) {
+    for (int e = tid; e < ni * ni; e += nth) blk[BL.H + e] = dH[e];
+    if (tid < ni) blk[BL.rho + tid] = drho[tid];
+    for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
+    if (s_flag != 1) {
         for (int e = tid; e < ni * ni; e += nth) blk[BL.L + e] = dL[e];
-        if (tid < ni) blk[BL.t + tid] = dt[tid];
+        if (tid < ni) {
+            blk[BL.t + tid] = dt[tid];
+            blk[BL.rinv + tid] = drinv[tid];
+        }
+    }
+    if (s_flag == 2)
+        for (int e = tid; e < nG * nG; e += nth) blk[BL.G + e] = dGs[e];
+    if (s_flag == 0) {
         for (int e = tid; e < nG * nC; e += nth) blk[BL.W + e] = dW[e];
-        // S_i = W^T W  (n_C x n_C)
+        // S_i = W^T W (n_C x n_C, symmetric: each entry of the lower triangle once, mirrored)
         for (int e = tid; e < nC * nC; e += nth) {
             const int c1 = e / nC, c2 = e % nC;
+            if (c2 > c1) continue;
             double v = 0.0;
             for (int k = 0; k < nG; ++k) v += dW[k * nC + c1] * dW[k * nC + c2];
-            blk[BL.S + e] = v;
+            blk[BL.S + c1 * nC + c2] = v;
+            blk[BL.S + c2 * nC + c1] = v;
         }
     }
 }
@@ -415,20 +505,28 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B) {
     eval_item<T>(P, P.sub[si], b, smem);
 }
 
-// Atil = C * jump with jump = sum_i A_i g_i^G (each row: g_lo - g_hi), FP64
+// Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
+// Atil_c += sum_r C[c][r] jump_r, one warp per row c of C; partials per (instance, slice).
 template <typename T>
 __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
-    __shared__ double scratch[32];
-    const int c = blockIdx.x, b = blockIdx.y;
+    __shared__ double jump[CON_SPLIT];
+    const int sp = blockIdx.x, b = blockIdx.y;
     if (b >= B) return;
     if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
+    const int r0 = sp * CON_SPLIT, nr = min(CON_SPLIT, P.N_A - r0);
     const T* g = (const T*)P.gG + (size_t)b * P.sum_NG;
-    const double* Cr = P.C + (size_t)c * P.N_A;
-    double acc = 0.0;
-    for (int r = threadIdx.x; r < P.N_A; r += blockDim.x)
-        acc += Cr[r] * ((double)g[P.con_lo[r]] - (double)g[P.con_hi[r]]);
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) P.Atil[(size_t)b * P.n_C + c] = acc;
+    for (int r = threadIdx.x; r < nr; r += blockDim.x)
+        jump[r] = (double)g[P.con_lo[r0 + r]] - (double)g[P.con_hi[r0 + r]];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double* out = P.Atil + ((size_t)b * P.n_split + sp) * P.n_C;
+    for (int c = w; c < P.n_C; c += nw) {
+        const double* Cr = P.C + (size_t)c * P.N_A + r0;
+        double acc = 0.0;
+        for (int r = lane; r < nr; r += 32) acc += Cr[r] * jump[r];
+        acc = warp_sum(acc);
+        if (lane == 0) out[c] = acc;
+    }
 }
 
 // ------------------------------------------------------------------------ SQP step
@@ -436,7 +534,7 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
 __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     extern __shared__ __align__(16) double sm[];
     __shared__ double scratch[32];
-    __shared__ int s_ok;
+    __shared__ double zb[STEP_THREADS / 32][MAX_NI];
     const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     if (b >= B) return;
     int* ist = P.ist + (size_t)b * INST_INTS;
@@ -446,21 +544,28 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     double* blk = P.blk + (size_t)b * P.blk_stride;
     double* Sm = sm;                  // nC x nC
     double* rhs = Sm + nC * nC;       // nC
+    double* At = rhs + nC;            // nC: Atil (sum of the slice partials)
+    double* rv = At + nC;             // nC: reciprocal pivots
     double* x_ = P.x + (size_t)b * nD;
     double* xt = P.xt + (size_t)b * nD;
     double* s_ = P.s + (size_t)b * nD;
     double* lam = P.lam + (size_t)b * nC;
     double* lamt = P.lamt + (size_t)b * nC;
     double* slam = P.slam + (size_t)b * nC;
-    const double* At = P.Atil + (size_t)b * nC;
 
-    // merit phi^2 = sum_i ||rho_i||^2 + ||Atil||^2, and whether any H_i was not PD
+    for (int c = tid; c < nC; c += nth) {
+        double a = 0.0;
+        for (int sp = 0; sp < P.n_split; ++sp) a += P.Atil[((size_t)b * P.n_split + sp) * nC + c];
+        At[c] = a;
+    }
+    __syncthreads();
+    // merit phi^2 = sum_i ||rho_i||^2 + ||Atil||^2; subdomains whose H_i^{OO} was not PD
     double acc = 0.0, fl = 0.0;
     for (int i = tid; i < ns; i += nth) {
         const SubDev& S = P.sub[i];
         const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
         acc += blk[S.blk + BL.phi];
-        fl += blk[S.blk + BL.flag];
+        fl += blk[S.blk + BL.flag] == FLAG_OMEGA_FAIL ? 1.0 : 0.0;
     }
     for (int c = tid; c < nC; c += nth) acc += At[c] * At[c];
     const double phi2 = block_sum(acc, scratch);
@@ -496,12 +601,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
             }
             rhs[c] = v;
         }
-        __syncthreads();
-        if (!block_cholesky(Sm, nC, &s_ok)) {
+        if (!block_cholesky(Sm, rv, nC)) {
             if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
             return;
         }
-        block_chol_solve(Sm, nC, rhs);
+        block_chol_solve(Sm, rv, nC, rhs);
         for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
         if (tid == 0) {
             ist[I_MODE] = MODE_INIT1;
@@ -552,13 +656,46 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         return;
     }
 
-    // Schur complement of Eq. (sqp_system): S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T W_i,
-    // S s_lambda = Atil - sum_i E_i H_i^{-1} rho_i = Atil - sum_i u_i
+    // Schur complement of Eq. (sqp_system) over the subdomains with H_i PD:
+    //   S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T W_i,  r = Atil - sum_i E_i H_i^{-1} rho_i = Atil - sum_i u_i.
+    // Subdomains F with H_i singular in the G block (H_i^{OO} PD) keep their interface steps s_F as
+    // unknowns: with Z = L_S^{-1} D_F, q = L_S^{-1} r and G_F = H_GG - L_GO L_GO^T,
+    //   (G_F + Z^T Z) s_F = -(rho_G - L_GO t_O)_F - Z^T q,   s_lambda = L_S^{-T} (q + Z s_F).
+    __shared__ int s_nF, s_mF, s_over;
+    __shared__ int fsub[MAX_MF], fcol_sub[MAX_MF], fcol_k[MAX_MF];
+    if (tid == 0) {
+        int nF = 0, mF = 0, over = 0;
+        for (int i = 0; i < ns; ++i) {
+            const SubDev& S = P.sub[i];
+            if (blk[S.blk + blk_layout(S.ni, S.nG, nC).flag] == FLAG_GAMMA_SING) {
+                if (mF + S.nG > MAX_MF) {
+                    over = 1;
+                    break;
+                }
+                fsub[nF++] = i;
+                for (int k = 0; k < S.nG; ++k) {
+                    fcol_sub[mF] = i;
+                    fcol_k[mF] = k;
+                    ++mF;
+                }
+            }
+        }
+        s_nF = nF;
+        s_mF = mF;
+        s_over = over;
+    }
+    __syncthreads();
+    const int nF = s_nF, mF = s_mF;
+    if (s_over) {
+        if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
+        return;
+    }
     for (int e = tid; e < nC * nC; e += nth) {
         double v = 0.0;
         for (int i = 0; i < ns; ++i) {
             const SubDev& S = P.sub[i];
-            v += blk[S.blk + blk_layout(S.ni, S.nG, nC).S + e];
+            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+            if (blk[S.blk + BL.flag] == FLAG_PD) v += blk[S.blk + BL.S + e];
         }
         Sm[e] = v;
     }
@@ -566,40 +703,124 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         double v = At[c];
         for (int i = 0; i < ns; ++i) {
             const SubDev& S = P.sub[i];
-            v -= blk[S.blk + blk_layout(S.ni, S.nG, nC).u + c];
+            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+            if (blk[S.blk + BL.flag] == FLAG_PD) v -= blk[S.blk + BL.u + c];
         }
         rhs[c] = v;
     }
-    __syncthreads();
-    if (!block_cholesky(Sm, nC, &s_ok)) {
+    if (!block_cholesky(Sm, rv, nC)) {
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
         return;
     }
-    block_chol_solve(Sm, nC, rhs);
-    // s_i = -L_i^{-T} (t_i + W_i s_lambda), one warp per subdomain
+    double* Z = rv + nC;                  // nC x MAX_MF, row-major with row stride mF + 1 (last column: q)
+    double* T = Z + nC * (MAX_MF + 1);    // MAX_MF x MAX_MF
+    double* rT = T + MAX_MF * MAX_MF;     // MAX_MF reciprocal pivots of T
+    double* sF = rT + MAX_MF;             // MAX_MF
+    if (mF == 0) {
+        block_chol_solve(Sm, rv, nC, rhs);
+    } else {
+        const int ldz = mF + 1;
+        for (int e = tid; e < nC * ldz; e += nth) {
+            const int c = e / ldz, a = e % ldz;
+            double v;
+            if (a == mF) {
+                v = rhs[c];
+            } else {
+                const SubDev& S = P.sub[fcol_sub[a]];
+                v = blk[S.blk + blk_layout(S.ni, S.nG, nC).D + c * S.nG + fcol_k[a]];
+            }
+            Z[e] = v;
+        }
+        // [Z q] <- L_S^{-1} [D_F r]
+        for (int j = 0; j < nC; ++j) {
+            __syncthreads();
+            const double r = rv[j];
+            for (int a = tid; a < ldz; a += nth) Z[j * ldz + a] *= r;
+            __syncthreads();
+            const int m = nC - j - 1;
+            for (int e = tid; e < m * ldz; e += nth) {
+                const int i = j + 1 + e / ldz, a = e % ldz;
+                Z[i * ldz + a] -= Sm[i * nC + j] * Z[j * ldz + a];
+            }
+        }
+        __syncthreads();
+        // T = G_F + Z^T Z, right-hand side -(t~_G)_F - Z^T q
+        for (int e = tid; e < mF * mF; e += nth) {
+            const int a = e / mF, c2 = e % mF;
+            double v = 0.0;
+            for (int c = 0; c < nC; ++c) v += Z[c * ldz + a] * Z[c * ldz + c2];
+            if (fcol_sub[a] == fcol_sub[c2]) {
+                const SubDev& S = P.sub[fcol_sub[a]];
+                v += blk[S.blk + blk_layout(S.ni, S.nG, nC).G + fcol_k[a] * S.nG + fcol_k[c2]];
+            }
+            T[e] = v;
+        }
+        for (int a = tid; a < mF; a += nth) {
+            const SubDev& S = P.sub[fcol_sub[a]];
+            double v = -blk[S.blk + blk_layout(S.ni, S.nG, nC).t + S.nO + fcol_k[a]];
+            for (int c = 0; c < nC; ++c) v -= Z[c * ldz + a] * Z[c * ldz + mF];
+            sF[a] = v;
+        }
+        if (!block_cholesky(T, rT, mF)) {
+            if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
+            return;
+        }
+        block_chol_solve(T, rT, mF, sF);
+        for (int c = tid; c < nC; c += nth) {
+            double v = Z[c * ldz + mF];
+            for (int a = 0; a < mF; ++a) v += Z[c * ldz + a] * sF[a];
+            rhs[c] = v;
+        }
+        block_bwd(Sm, rv, nC, rhs);
+    }
+    // per-subdomain steps, one warp per subdomain:
+    //   H_i PD:           s_i = -L_i^{-T} (t_i + W_i s_lambda)
+    //   G-singular (F):   s_G from s_F,  s_O = -L_OO^{-T} (t_O + L_GO^T s_G)
     {
         const int w = tid >> 5, lane = tid & 31, nw = nth >> 5;
+        double* z = zb[w];
         for (int i = w; i < ns; i += nw) {
             const SubDev& S = P.sub[i];
             const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
             const double* Li = blk + S.blk + BL.L;
+            const double* ri = blk + S.blk + BL.rinv;
             const double* ti = blk + S.blk + BL.t;
             const double* Wi = blk + S.blk + BL.W;
-            if (lane == 0) {
-                double z[MAX_NI];
-                for (int k = 0; k < S.ni; ++k) z[k] = ti[k];
+            const bool sing = blk[S.blk + BL.flag] == FLAG_GAMMA_SING;
+            int nb = S.ni;                    // rows solved by back-substitution
+            if (!sing) {
+                if (lane < S.ni) z[lane] = ti[lane];
+                __syncwarp();
                 for (int k = 0; k < S.nG; ++k) {
                     double v = 0.0;
-                    for (int c = 0; c < nC; ++c) v += Wi[k * nC + c] * rhs[c];
-                    z[S.nO + k] += v;
+                    for (int c = lane; c < nC; c += 32) v += Wi[k * nC + c] * rhs[c];
+                    v = warp_sum(v);
+                    if (lane == 0) z[S.nO + k] += v;
                 }
-                for (int k = S.ni - 1; k >= 0; --k) {
-                    double v = z[k];
-                    for (int m = k + 1; m < S.ni; ++m) v -= Li[m * S.ni + k] * z[m];
-                    z[k] = v / Li[k * S.ni + k];
+            } else {
+                int a0 = 0;
+                for (int f = 0; f < nF; ++f) {
+                    if (fsub[f] == i) break;
+                    a0 += P.sub[fsub[f]].nG;
                 }
-                for (int k = 0; k < S.ni; ++k) s_[S.xoff + k] = -z[k];
+                if (lane < S.nG) s_[S.xoff + S.nO + lane] = sF[a0 + lane];
+                if (lane < S.nO) {
+                    double v = ti[lane];
+                    for (int k = 0; k < S.nG; ++k) v += Li[(S.nO + k) * S.ni + lane] * sF[a0 + k];
+                    z[lane] = v;
+                }
+                nb = S.nO;
             }
+            __syncwarp();
+            for (int k = nb - 1; k >= 0; --k) {
+                const double zk = z[k] * ri[k];
+                if (lane < k) z[lane] -= Li[k * S.ni + lane] * zk;
+                __syncwarp();
+                if (lane == 0) z[k] = zk;
+                __syncwarp();
+            }
+            if (lane < nb) s_[S.xoff + lane] = -z[lane];
+            __syncwarp();
         }
     }
     __syncthreads();
@@ -697,7 +918,8 @@ __global__ void k_gather(ProbDev P, int B, double* F, double* H, double* D, doub
         doff += nC * S.nG;
     }
     for (int c = tid; c < nC; c += nth) {
-        const double a = P.Atil[(size_t)b * nC + c];
+        double a = 0.0;
+        for (int sp = 0; sp < P.n_split; ++sp) a += P.Atil[((size_t)b * P.n_split + sp) * nC + c];
         if (F) F[(size_t)b * (P.n_D + nC) + P.n_D + c] = a;
         if (At) At[(size_t)b * nC + c] = a;
     }
@@ -843,7 +1065,7 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st) {
     tstop(ctx, k, st);
     ctx->tm.eval_launches++;
     k = tstart(ctx, 1, st);
-    k_constraint<T><<<dim3(P.n_C, B), CON_THREADS, 0, st>>>(P, B);
+    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, 0, st>>>(P, B);
     CK(cudaGetLastError());
     tstop(ctx, k, st);
     ctx->tm.constraint_launches++;
@@ -1134,7 +1356,7 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
     if (e != cudaSuccess) return cfail(ctx, e, "cudaFuncSetAttribute(k_eval)");
     k_noalloc_init<<<B, 128, 0, st>>>(P, B);
     k_eval<T><<<B * P.n_sub, EVAL_THREADS, ctx->eval_smem, st>>>(P, B);
-    k_constraint<T><<<dim3(P.n_C, B), CON_THREADS, 0, st>>>(P, B);
+    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, 0, st>>>(P, B);
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cfail(ctx, e, "no-allocation evaluation launch");
@@ -1160,7 +1382,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     const size_t o_bnd = o; o = al(o + (size_t)B * std::max(P.n_bnd, 1) * 2 * 8);
     const size_t o_gG = o; o = al(o + (size_t)B * P.sum_NG * tsize);
     const size_t o_blk = o; o = al(o + (size_t)B * P.blk_stride * 8);
-    const size_t o_At = o; o = al(o + (size_t)B * P.n_C * 8);
+    const size_t o_At = o; o = al(o + (size_t)B * P.n_split * P.n_C * 8);
     const size_t o_lz = o; o = al(o + (size_t)B * P.n_C * 8);
     if (o > DDNM_NOALLOC_SCRATCH_BYTES) {
         const size_t per = o / B + 1;

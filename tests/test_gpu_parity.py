@@ -44,7 +44,7 @@ TOL = {FP64: 1e-6, MIXED: 1e-4}
 TOL_EVAL = {FP64: 1e-9, MIXED: 2e-5}
 
 EVAL_CASES = [("c1", FP64), ("c1", MIXED), ("tiny12x10_2x2", FP64), ("tiny12x10_2x2", MIXED),
-              ("tiny13x9_3x2", FP64), ("tiny13x9_3x2", MIXED), ("c2", MIXED), ("c2", FP64)]
+              ("tiny13x9_3x2", FP64), ("tiny13x9_3x2", MIXED), ("c2", MIXED), ("c2", FP64), ("c3", MIXED)]
 
 
 @pytest.mark.parametrize("name,prec", EVAL_CASES)
@@ -69,7 +69,8 @@ def test_one_evaluation(name, prec):
 
 @pytest.mark.parametrize("name,prec,K", [("c1", FP64, 1), ("c1", FP64, 2), ("c1", FP64, 3), ("c1", FP64, 15),
                                          ("tiny12x10_2x2", FP64, 6), ("tiny13x9_3x2", FP64, 4),
-                                         ("c1", MIXED, 1), ("c1", MIXED, 3), ("tiny12x10_2x2", MIXED, 3)])
+                                         ("c1", MIXED, 1), ("c1", MIXED, 3), ("tiny12x10_2x2", MIXED, 3),
+                                         ("c3", MIXED, 2)])
 def test_fixed_iterations(name, prec, K):
     """K SQP iterations (tol = 0): same iterates, same line-search decisions, same counts."""
     wl, fom, dd, rom, raw, s = case(name, prec)
