@@ -26,6 +26,13 @@ struct SubHost {
     int nO = 0, nG = 0;
 };
 
+// subdomains sharing the padded record widths of the evaluation kernel
+struct EvalClass {
+    int ro, rg;      // round4(n^O + 1), round4(n^G + 1)
+    int off, n;      // range in the class index table
+    int smem;        // largest dynamic shared memory of its subdomains
+};
+
 struct ddnm_ctx {
     // problem
     int nx = 0, ny = 0, kx = 0, ky = 0, n_sub = 0, N = 0, n_C = 0, N_A = 0;
@@ -55,6 +62,8 @@ struct ddnm_ctx {
     int* d_bnd_ij = nullptr;
     ddnm::SubDev* d_sub = nullptr;
     ddnm::ChunkDev* d_chunk = nullptr;
+    std::vector<EvalClass> eval_classes;
+    int* d_classes = nullptr;          // subdomain indices, grouped by class
     std::vector<ddnm::ChunkDev> hchunk;
 
     // workspace for up to cap_B instances

@@ -266,6 +266,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_bnd_ij);
     cudaFree(ctx->d_sub);
     cudaFree(ctx->d_chunk);
+    cudaFree(ctx->d_classes);
     cudaFree(ctx->d_ws);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
     ddnm_release_events(ctx);
@@ -459,7 +460,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         SubDev& S = ctx->hsub[s];
         S.nO = sd.nO; S.nG = sd.nG; S.ni = sd.nO + sd.nG; S.xoff = xoff; xoff += S.ni;
         S.NB = (int)sd.hr_rows.size(); S.hr_off = hr_off; hr_off += S.NB;
-        S.K = dO.K; S.Kp = round4(dO.K); S.actO = dO.act; S.actG = dG.act;
+        S.K = dO.K; S.Kp = (dO.K + 7) & ~7; S.actO = dO.act; S.actG = dG.act;
         S.goff = ctx->goff[s];
         S.NG = (int)sd.interface.size();
         // interior subnet over I_o = all outputs the stencils need; one slot-major table per HR chunk
@@ -521,11 +522,29 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         S.ids = P.addi(ids.data(), ids.size());
         S.blk = blk;
         blk += blk_layout(S.ni, S.nG, nC).size;
-        hr_all.insert(hr_all.end(), sd.hr_ops.begin(), sd.hr_ops.end());
+        for (int o = 0; o < HR_INTS; ++o)            // operand-major: consecutive rows are consecutive ints
+            for (int q = 0; q < S.NB; ++q) hr_all.push_back(sd.hr_ops[(size_t)q * HR_INTS + o]);
         S.smem_bytes = eval_smem(S, nC, (int)tsize).bytes;
         ctx->eval_smem = std::max(ctx->eval_smem, S.smem_bytes);
         ctx->rec_smem = std::max(ctx->rec_smem, (int)(std::max(dO.w, dG.w) * tsize));
     }
+    // width classes of the evaluation kernel
+    ctx->eval_classes.clear();
+    std::vector<int> cls;
+    for (int ro = 4; ro <= 16; ro += 4)
+        for (int rg = 4; rg <= 12; rg += 4) {
+            EvalClass c{ro, rg, (int)cls.size(), 0, 0};
+            for (int s = 0; s < ns; ++s) {
+                const SubDev& S = ctx->hsub[s];
+                if (round4(S.nO + 1) == ro && round4(S.nG + 1) == rg) {
+                    cls.push_back(s);
+                    c.smem = std::max(c.smem, S.smem_bytes);
+                }
+            }
+            c.n = (int)cls.size() - c.off;
+            if (c.n) ctx->eval_classes.push_back(c);
+        }
+    if ((int)cls.size() != ns) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "latent dims outside the kernel classes");
     int dev_max = 0;
     CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (ctx->eval_smem > dev_max)
@@ -560,6 +579,10 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_bnd_ij, ctx->bnd_ij.data(), ctx->bnd_ij.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_sub, ns * sizeof(SubDev)));
     CK(cudaMemcpy(ctx->d_sub, ctx->hsub.data(), ns * sizeof(SubDev), cudaMemcpyHostToDevice));
+    cudaFree(ctx->d_classes);
+    ctx->d_classes = nullptr;
+    CK(cudaMalloc(&ctx->d_classes, cls.size() * sizeof(int)));
+    CK(cudaMemcpy(ctx->d_classes, cls.data(), cls.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_chunk, std::max<size_t>(ctx->hchunk.size(), 1) * sizeof(ChunkDev)));
     CK(cudaMemcpy(ctx->d_chunk, ctx->hchunk.data(), ctx->hchunk.size() * sizeof(ChunkDev), cudaMemcpyHostToDevice));
 
@@ -570,6 +593,11 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.N_x = 2 * ctx->N; pd.nx = ctx->nx; pd.ny = ctx->ny;
     pd.n_split = (ctx->N_A + CON_SPLIT - 1) / CON_SPLIT;
     pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
+    pd.cst[0] = 0.5 / ctx->hx;
+    pd.cst[1] = 0.5 / ctx->hy;
+    pd.cst[2] = ctx->nu / (ctx->hx * ctx->hx);
+    pd.cst[3] = ctx->nu / (ctx->hy * ctx->hy);
+    for (int k = 0; k < 4; ++k) pd.cstf[k] = (float)pd.cst[k];
     pd.blk_stride = blk;
     pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
     pd.hr = ctx->d_hr;
@@ -597,7 +625,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     size_t o_At = o; o = al(o + (size_t)cap * pd.n_split * pd.n_C * 8);
     size_t o_dst = o; o = al(o + (size_t)cap * INST_DBLS * 8);
     size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
-    size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * 8);
+    size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * tsize);
     size_t o_gG = o; o = al(o + (size_t)cap * pd.sum_NG * tsize);
     size_t o_blk = o; o = al(o + (size_t)cap * pd.blk_stride * 8);
     size_t o_act = o; o = al(o + 64);
@@ -619,7 +647,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     pd.Atil = (double*)(base + o_At);
     pd.dst = (double*)(base + o_dst);
     pd.ist = (int*)(base + o_ist);
-    pd.bnd = (double*)(base + o_bnd);
+    pd.bnd = (void*)(base + o_bnd);
     pd.gG = (void*)(base + o_gG);
     pd.blk = (double*)(base + o_blk);
     pd.active = (int*)(base + o_act);

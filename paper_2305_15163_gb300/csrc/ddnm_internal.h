@@ -44,9 +44,9 @@ struct ChunkDev {
 // One subdomain: latent sizes, HR rows, subnet layout, offsets into the pools.
 struct SubDev {
     int nO, nG, ni, xoff;          // latent dims and offset of xh_i in xh
-    int NB, hr_off;                // collocation rows, offset into the HR table
+    int NB, hr_off;                // collocation rows, offset into the HR table (rows; the table is HR_INTS x N_B)
     int hO, hG, NG;                // hidden units of the interior / interface subnets, interface outputs
-    int Kp;                        // ELL slots per row, padded to a multiple of 4 (padding: column 0, value 0)
+    int Kp;                        // ELL slots per row, padded to a multiple of 8 (padding: column 0, value 0)
     int actO, actG;
     int goff;                      // offset of this subdomain's interface outputs in the concatenation
     int n_chunks, chunk0, mmax;    // HR chunks: count, first index in the chunk table, max outputs per chunk
@@ -70,10 +70,10 @@ struct BlkLayout {
 };
 
 // per-subdomain flag values written by the evaluation
-constexpr double FLAG_PD = 0.0;          // H_i positive definite: Schur pieces L, t, W, u, S valid
+constexpr double FLAG_PD = 0.0;          // H_i positive definite: L, rinv, t, W, u, S valid
 constexpr double FLAG_OMEGA_FAIL = 1.0;  // H_i^{OO} not positive definite: not solvable by this route
-constexpr double FLAG_GAMMA_SING = 2.0;  // H_i^{OO} PD but H_i not: L (first n^O columns), t (t_O, then
-                                         // rho_G - L_GO t_O) and G = H_GG - L_GO L_GO^T are valid
+constexpr double FLAG_GAMMA_SING = 2.0;  // H_i^{OO} PD but H_i not: L, rinv (first n^O columns), t (t_O,
+                                         // then rho_G - L_GO t_O) and G = H_GG - L_GO D_O L_GO^T valid
 constexpr int MAX_MF = 32;               // interface unknowns of such subdomains handled per instance
 
 __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
@@ -83,7 +83,7 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
     b.rho = o; o += ni;
     b.D = o; o += nC * nG;
     b.L = o; o += ni * ni;
-    b.rinv = o; o += ni;           // 1 / L_jj
+    b.rinv = o; o += ni;           // 1 / D_jj of H_i = L D L^T (L unit lower, stored below the diagonal)
     b.t = o; o += ni;
     b.W = o; o += nG * nC;
     b.S = o; o += nC * nC;
@@ -100,6 +100,8 @@ struct ProbDev {
     int nx, ny;
     int n_split;                   // constraint CTAs per instance (ceil(N_A / CON_SPLIT))
     double hx, hy, nu, bx0, by0;
+    double cst[4];                 // stencil constants 1/(2h_x), 1/(2h_y), nu/h_x^2, nu/h_y^2 (from the host)
+    float cstf[4];                 // the same in FP32
     double tol, c1, beta;
     int max_iter, max_bt;
     int blk_stride;                // doubles per instance of the block area
@@ -107,7 +109,7 @@ struct ProbDev {
     const ChunkDev* chunk;
     const void* vpool;             // decoder values and M_i, float (MIXED) or double (FP64)
     const int* ipool;
-    const int* hr;                 // HR_INTS per collocation row, all subdomains
+    const int* hr;                 // per subdomain HR_INTS x N_B (operand-major), all subdomains
     const int* con_lo;             // flat interface index (goff + local) of the +1 side of each constraint row
     const int* con_hi;             // ... of the -1 side
     const double* C;               // n_C x N_A
@@ -123,7 +125,7 @@ struct ProbDev {
     double* Atil;                  // B x n_split x n_C partial sums of C * jump
     double* dst;                   // INST_DBLS per instance
     int* ist;                      // INST_INTS per instance
-    double* bnd;                   // B x n_bnd x 2 (u, v)
+    void* bnd;                     // B x n_bnd x 2 (u, v) Dirichlet data, value type
     void* gG;                      // B x sum_NG interface outputs (value type)
     double* blk;                   // B x blk_stride
     double* r_hr;                  // optional output B x sum_NB
@@ -149,7 +151,7 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.outG = o; o = align16(o + s.NG * rG * tsize);          // [y, Jacobian row] per interface output
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
     e.Rr = o; o = align16(o + HR_CHUNK * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
-    e.red = o; o = align16(o + EVAL_THREADS * tsize);
+    e.red = o; o = align16(o + (EVAL_THREADS / 32) * nC * s.nG * tsize);   // D_i partials per warp
     e.dlam = o; o = align16(o + nC * 8);
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);

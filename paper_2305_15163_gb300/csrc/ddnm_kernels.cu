@@ -71,60 +71,91 @@ __device__ double block_sum(double v, double* scratch /* >= 32 */) {
     return t;
 }
 
-// In-place lower Cholesky A = L L^T of the n x n row-major matrix A in shared memory (whole CTA).
-// Pivots go through rsqrt: L_jj = d * rsqrt(d) and rinv[j] = rsqrt(d), so no FP64 division or square
-// root sits on the critical path (each FP64 warp instruction costs 64 cycles on this part).
-// Returns false (uniformly) when a pivot is not positive and finite (Lemma 1 fails).
-__device__ bool block_cholesky(double* A, double* rinv, int n) {
+// In-place A = L D L^T of the n x n symmetric row-major matrix A in shared memory (whole CTA): the
+// strictly lower part becomes the unit lower factor L, the diagonal keeps D, rd[j] = 1 / D_jj.
+// One reciprocal per pivot (no square root), and the next pivot is updated and inverted by thread 0
+// while the other threads update the rest of the trailing matrix, so each column costs one barrier.
+// Returns false (uniformly) when a pivot is not positive and finite.
+__device__ bool block_ldl(double* A, double* rd, int n) {
     const int tid = threadIdx.x, nth = blockDim.x;
-    for (int j = 0; j < n; ++j) {
-        __syncthreads();
-        const double d = A[j * n + j];
-        if (!(d > 0.0) || !isfinite(d)) return false;
-        const double r = rsqrt(d);
-        for (int i = j + 1 + tid; i < n; i += nth) A[i * n + j] *= r;
-        __syncthreads();
-        const int m = n - j - 1;
-        for (int e = tid; e < m * m; e += nth) {
-            const int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
-        }
-        if (tid == 0) {
-            A[j * n + j] = d * r;
-            rinv[j] = r;
-        }
+    __shared__ int s_ok;
+    __syncthreads();
+    if (tid == 0) {
+        const double d = A[0];
+        const int ok = (d > 0.0) && isfinite(d);
+        s_ok = ok;
+        rd[0] = ok ? 1.0 / d : 0.0;
     }
     __syncthreads();
+    if (!s_ok) return false;
+    for (int j = 0; j < n; ++j) {
+        const double r = rd[j];
+        const int m = n - j - 1;
+        if (m > 0) {
+            if (tid == 0) {
+                const double l = A[(j + 1) * n + j];
+                const double a = A[(j + 1) * n + j + 1] - l * r * l;
+                A[(j + 1) * n + j + 1] = a;
+                const int ok = (a > 0.0) && isfinite(a);
+                s_ok = ok;
+                rd[j + 1] = ok ? 1.0 / a : 0.0;
+            } else {
+                const int ntri = m * (m + 1) / 2;
+                for (int e = tid; e < ntri; e += nth - 1) {
+                    int i = 0, rem = e;
+                    while (rem > i) {
+                        rem -= i + 1;
+                        ++i;
+                    }
+                    const int ii = j + 1 + i, kk = j + 1 + rem;
+                    A[ii * n + kk] -= A[ii * n + j] * r * A[kk * n + j];
+                }
+            }
+        }
+        if (j > 0)
+            for (int i = j + tid; i < n; i += nth) A[i * n + j - 1] *= rd[j - 1];
+        __syncthreads();
+        if (!s_ok) return false;
+    }
     return true;
 }
 
-// x <- L^{-1} x and x <- L^{-T} x in place, with L, rinv from block_cholesky (whole CTA).
-__device__ void block_fwd(const double* L, const double* rinv, int n, double* x) {
+// x <- (L D L^T)^{-1} x with the factors of block_ldl (whole CTA; warp-synchronous when n <= 32).
+__device__ void block_ldl_solve(const double* A, const double* rd, int n, double* x) {
     const int tid = threadIdx.x, nth = blockDim.x;
+    if (n <= 32) {
+        if (tid < 32) {
+            const int lane = tid;
+            for (int j = 0; j < n; ++j) {
+                __syncwarp();
+                const double xj = x[j];
+                if (lane > j && lane < n) x[lane] -= A[lane * n + j] * xj;
+            }
+            __syncwarp();
+            if (lane < n) x[lane] *= rd[lane];
+            for (int k = n - 1; k >= 0; --k) {
+                __syncwarp();
+                const double xk = x[k];
+                if (lane < k) x[lane] -= A[k * n + lane] * xk;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        return;
+    }
     for (int j = 0; j < n; ++j) {
         __syncthreads();
-        const double xj = x[j] * rinv[j];
-        for (int i = j + 1 + tid; i < n; i += nth) x[i] -= L[i * n + j] * xj;
-        if (tid == 0) x[j] = xj;
+        const double xj = x[j];
+        for (int i = j + 1 + tid; i < n; i += nth) x[i] -= A[i * n + j] * xj;
     }
     __syncthreads();
-}
-
-__device__ void block_bwd(const double* L, const double* rinv, int n, double* x) {
-    const int tid = threadIdx.x, nth = blockDim.x;
-    for (int j = n - 1; j >= 0; --j) {
+    for (int i = tid; i < n; i += nth) x[i] *= rd[i];
+    for (int k = n - 1; k >= 0; --k) {
         __syncthreads();
-        const double xj = x[j] * rinv[j];
-        for (int i = tid; i < j; i += nth) x[i] -= L[j * n + i] * xj;
-        if (tid == 0) x[j] = xj;
+        const double xk = x[k];
+        for (int i = tid; i < k; i += nth) x[i] -= A[k * n + i] * xk;
     }
     __syncthreads();
-}
-
-// Solve L L^T x = x in place (whole CTA).
-__device__ void block_chol_solve(const double* L, const double* rinv, int n, double* x) {
-    block_fwd(L, rinv, n, x);
-    block_bwd(L, rinv, n, x);
 }
 
 // 4 consecutive values, 16-byte aligned (float4) or 32-byte aligned (two double2)
@@ -144,28 +175,32 @@ __device__ __forceinline__ void st4(double* p, const double* o) {
     reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
 }
 
-// One decoder output row of an ELL table in slot-major layout (Kp slots, padding slots hold column 0,
-// value 0): acc[k] = sum_t val_t * hid[col_t][k] for k < R (R = round4(n+1) <= RMAX), i.e. the raw output
-// (k = 0) and its Jacobian row (k >= 1) through the hidden rows [sigma, sigma' W1].
-template <typename T, int RMAX>
-__device__ __forceinline__ void ell_row(const int* col, const T* val, int stride, int Kp, const T* hid, int R,
-                                        T* acc) {
+// One decoder output row of an ELL table in slot-major layout (Kp slots, a multiple of 8; padding slots
+// hold column 0, value 0): acc[k] += sum_t val_t * hid[col_t][k] for k < R, i.e. the raw output (k = 0)
+// and its Jacobian row (k >= 1) through the hidden records [sigma, sigma' W1].  The column and value loads
+// of 8 slots are issued before their gathers so that 16 global loads per thread are in flight.
+template <typename T, int R>
+__device__ __forceinline__ void ell_accumulate(const int* col, const T* val, int stride, int Kp, const T* hid,
+                                               T* acc) {
+    for (int t0 = 0; t0 < Kp; t0 += 8) {
+        int c[8];
+        T v[8];
 #pragma unroll
-    for (int k = 0; k < RMAX; ++k) acc[k] = T(0);
-#pragma unroll 4
-    for (int t = 0; t < Kp; ++t) {
-        const int c = col[(size_t)t * stride];
-        const T v = val[(size_t)t * stride];
-        const T* h = hid + (size_t)c * R;
+        for (int u = 0; u < 8; ++u) {
+            c[u] = col[(size_t)(t0 + u) * stride];
+            v[u] = val[(size_t)(t0 + u) * stride];
+        }
 #pragma unroll
-        for (int k = 0; k < RMAX; k += 4) {
-            if (k < R) {
+        for (int u = 0; u < 8; ++u) {
+            const T* h = hid + (size_t)c[u] * R;
+#pragma unroll
+            for (int k = 0; k < R; k += 4) {
                 T hv[4];
                 ld4(h + k, hv);
-                acc[k] += v * hv[0];
-                acc[k + 1] += v * hv[1];
-                acc[k + 2] += v * hv[2];
-                acc[k + 3] += v * hv[3];
+                acc[k] += v[u] * hv[0];
+                acc[k + 1] += v[u] * hv[1];
+                acc[k + 2] += v[u] * hv[2];
+                acc[k + 3] += v[u] * hv[3];
             }
         }
     }
@@ -173,10 +208,20 @@ __device__ __forceinline__ void ell_row(const int* col, const T* val, int stride
 
 // ------------------------------------------------------------------------ evaluation
 
-// One (instance, subdomain) evaluation.  Chunked over the collocation rows so that shared memory stays
+// stencil constants 1/(2h_x), 1/(2h_y), nu/h_x^2, nu/h_y^2 in the value type (precomputed on the host)
+template <typename T>
+__device__ __forceinline__ T cst(const ProbDev& P, int k);
+template <>
+__device__ __forceinline__ float cst<float>(const ProbDev& P, int k) { return P.cstf[k]; }
+template <>
+__device__ __forceinline__ double cst<double>(const ProbDev& P, int k) { return P.cst[k]; }
+
+// One (instance, subdomain) evaluation.  RO = round4(n^O + 1) and RG = round4(n^G + 1) are the padded
+// widths of the [value, Jacobian row] records; they are compile-time so that every inner loop has a fixed
+// trip count (no predicated-off lanes).  Chunked over the collocation rows so that shared memory stays
 // bounded for any subdomain size; every decoder table is read slot-major (consecutive threads ->
 // consecutive addresses).
-template <typename T>
+template <typename T, int RO, int RG>
 __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned char* smem) {
     const EvalSmem L = eval_smem(S, P.n_C, (int)sizeof(T));
     T* sx = (T*)(smem + L.sx);
@@ -199,99 +244,62 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     const int* IP = P.ipool;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C, NG = S.NG;
-    const int rO = round4(nO + 1), rG = round4(nG + 1);
     const int ld = ni + 1;
+    constexpr int WO = RO - 1 > 0 ? ((RO - 1 + 3) & ~3) : 4;   // padded W1 row width of the interior subnet
+    constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
     // latent coordinates and multipliers of the trial point
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
     for (int c = tid; c < nC; c += nth) dlam[c] = P.lamt[(size_t)b * nC + c];
     __syncthreads();
 
-    // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :]] (zero padded to a multiple of 4)
+    // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]
     for (int c = tid; c < S.hO + S.hG; c += nth) {
         const bool g = c >= S.hO;
-        const int cc = g ? c - S.hO : c;
-        const int n = g ? nG : nO, w4 = round4(n), R = g ? rG : rO;
-        const T* W1 = V + (g ? S.w1G : S.w1O) + (size_t)cc * w4;
-        const T* xs = sx + (g ? nO : 0);
-        T w[MAX_NI];
+        if (!g) {
+            const T* W1 = V + S.w1O + (size_t)c * round4(nO);
+            T w[WO];
 #pragma unroll
-        for (int k = 0; k < MAX_NI; k += 4)
-            if (k < w4) ld4(W1 + k, w + k);
-        T z = V[(g ? S.b1G : S.b1O) + cc];
-#pragma unroll
-        for (int k = 0; k < MAX_NI; ++k)
-            if (k < n) z += w[k] * xs[k];
-        T s, ds;
-        activation<T>(g ? S.actG : S.actO, z, s, ds);
-        T row[MAX_NI + 4];
-        row[0] = s;
-#pragma unroll
-        for (int k = 0; k < MAX_NI; ++k) row[k + 1] = (k < n) ? ds * w[k] : T(0);
-#pragma unroll
-        for (int k = MAX_NI + 1; k < MAX_NI + 4; ++k) row[k] = T(0);
-        T* dst = (g ? hidG : hidO) + (size_t)cc * R;
-#pragma unroll
-        for (int k = 0; k < MAX_NI + 4; k += 4)
-            if (k < R) st4(dst + k, row + k);
-    }
-    __syncthreads();
-
-    // interface outputs (all rows): [g^G_r, dg^G_r/dxh] into shared memory; g^G to global for the jump
-    {
-        T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
-        const int* col = IP + S.colG;
-        const T* val = V + S.valG;
-        const T* so = V + S.soG;
-        for (int r = tid; r < NG; r += nth) {
-            T acc[MAX_NG + 4];
-            ell_row<T, MAX_NG + 4>(col + r, val + r, NG, S.Kp, hidG, rG, acc);
-            const T sc = so[r], off = so[NG + r];
-            T row[MAX_NG + 4];
-            row[0] = off + sc * acc[0];
-#pragma unroll
-            for (int k = 1; k < MAX_NG + 4; ++k) row[k] = sc * acc[k];
-            T* dst = outG + (size_t)r * rG;
-#pragma unroll
-            for (int k = 0; k < MAX_NG + 4; k += 4)
-                if (k < rG) st4(dst + k, row + k);
-            gout[r] = row[0];
-        }
-    }
-    __syncthreads();
-
-    // D_i[c][k] = sum_rows M[row][c] dg^G[row][k], M = C A_i (stored N^G x n_C)
-    {
-        const int nout = nC * nG;
-        const T* M = V + S.M;
-        if (nout <= nth) {
-            const int groups = nth / nout;
-            if (tid < groups * nout) {
-                const int o = tid % nout, gq = tid / nout;
-                const int c = o % nC, k = o / nC;
-                T acc = T(0);
-                for (int row = gq; row < NG; row += groups) acc += M[(size_t)row * nC + c] * outG[(size_t)row * rG + 1 + k];
-                red[tid] = acc;
+            for (int k = 0; k < WO; k += 4) {
+                if (k < round4(nO)) ld4(W1 + k, w + k);
+                else w[k] = w[k + 1] = w[k + 2] = w[k + 3] = T(0);
             }
-            __syncthreads();
-            if (tid < nout) {
-                T acc = T(0);
-                for (int gq = 0; gq < groups; ++gq) acc += red[gq * nout + tid];
-                const int c = tid % nC, k = tid / nC;
-                dD[c * nG + k] = (double)acc;
-            }
+            T z = V[S.b1O + c];
+#pragma unroll
+            for (int k = 0; k < WO; ++k) z += w[k] * (k < nO ? sx[k] : T(0));
+            T s, ds;
+            activation<T>(S.actO, z, s, ds);
+            T row[RO];
+            row[0] = s;
+#pragma unroll
+            for (int k = 1; k < RO; ++k) row[k] = (k - 1 < WO) ? ds * w[k - 1] : T(0);
+#pragma unroll
+            for (int k = 0; k < RO; k += 4) st4(hidO + (size_t)c * RO + k, row + k);
         } else {
-            for (int o = tid; o < nout; o += nth) {
-                const int c = o % nC, k = o / nC;
-                T acc = T(0);
-                for (int row = 0; row < NG; ++row) acc += M[(size_t)row * nC + c] * outG[(size_t)row * rG + 1 + k];
-                dD[c * nG + k] = (double)acc;
+            const int cc = c - S.hO;
+            const T* W1 = V + S.w1G + (size_t)cc * round4(nG);
+            T w[WG];
+#pragma unroll
+            for (int k = 0; k < WG; k += 4) {
+                if (k < round4(nG)) ld4(W1 + k, w + k);
+                else w[k] = w[k + 1] = w[k + 2] = w[k + 3] = T(0);
             }
+            T z = V[S.b1G + cc];
+#pragma unroll
+            for (int k = 0; k < WG; ++k) z += w[k] * (k < nG ? sx[nO + k] : T(0));
+            T s, ds;
+            activation<T>(S.actG, z, s, ds);
+            T row[RG];
+            row[0] = s;
+#pragma unroll
+            for (int k = 1; k < RG; ++k) row[k] = (k - 1 < WG) ? ds * w[k - 1] : T(0);
+#pragma unroll
+            for (int k = 0; k < RG; k += 4) st4(hidG + (size_t)cc * RG + k, row + k);
         }
     }
+    __syncthreads();
 
-    // collocation rows, chunk by chunk: needed interior outputs, residual rows and partials, chain rule,
-    // then the running sums of H_i = R^T R and R^T r (thread p owns one entry)
+    // H_i = R^T R and R^T r: thread p owns one entry (a <= c), running sum over the chunks
     const int npair = ni * (ni + 1) / 2;
     int pa = 0, pc = 0;
     if (tid < npair) {
@@ -306,84 +314,164 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         pc = ni;
     }
     T hacc = T(0);
-    {
-        const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
-        const double* bnd = P.bnd + (size_t)b * P.n_bnd * 2;
-        const T ax = T(0.5 / P.hx), ay = T(0.5 / P.hy);
-        const T cx = T(P.nu / (P.hx * P.hx)), cy = T(P.nu / (P.hy * P.hy));
-        for (int q = 0; q < S.n_chunks; ++q) {
-            const ChunkDev Cq = P.chunk[S.chunk0 + q];
-            __syncthreads();   // previous chunk's outO / Rr fully consumed
-            {
-                const int* col = IP + Cq.col;
-                const T* val = V + Cq.val;
-                const T* so = V + Cq.so;
-                for (int r = tid; r < Cq.m; r += nth) {
-                    T acc[MAX_NI + 4];
-                    ell_row<T, MAX_NI + 4>(col + r, val + r, Cq.m, S.Kp, hidO, rO, acc);
-                    const T sc = so[r], off = so[Cq.m + r];
-                    T row[MAX_NI + 4];
-                    row[0] = off + sc * acc[0];
+    const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
+    const T* bnd = (const T*)P.bnd + (size_t)b * P.n_bnd * 2;
+    const T ax = cst<T>(P, 0), ay = cst<T>(P, 1), cx = cst<T>(P, 2), cy = cst<T>(P, 3);
+    T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
+    const int nout = nC * nG;
+    const int nwarp = nth >> 5;
+    for (int q = 0; q < S.n_chunks; ++q) {
+        const ChunkDev Cq = P.chunk[S.chunk0 + q];
+        // decoder outputs of this chunk's interior rows (and, with the first chunk, all interface rows)
+        {
+            const int nG_items = q == 0 ? NG : 0;
+            for (int it = tid; it < Cq.m + nG_items; it += nth) {
+                if (it < Cq.m) {
+                    const int r = it;
+                    T acc[RO];
 #pragma unroll
-                    for (int k = 1; k < MAX_NI + 4; ++k) row[k] = sc * acc[k];
-                    T* dst = outO + (size_t)r * rO;
+                    for (int k = 0; k < RO; ++k) acc[k] = T(0);
+                    const int* col = IP + Cq.col + r;
+                    const T* val = V + Cq.val + r;
+                    ell_accumulate<T, RO>(col, val, Cq.m, S.Kp, hidO, acc);
+                    const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
+                    acc[0] = off + sc * acc[0];
 #pragma unroll
-                    for (int k = 0; k < MAX_NI + 4; k += 4)
-                        if (k < rO) st4(dst + k, row + k);
+                    for (int k = 1; k < RO; ++k) acc[k] *= sc;
+#pragma unroll
+                    for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
+                } else {
+                    const int r = it - Cq.m;
+                    T acc[RG];
+#pragma unroll
+                    for (int k = 0; k < RG; ++k) acc[k] = T(0);
+                    const int* col = IP + S.colG + r;
+                    const T* val = V + S.valG + r;
+                    ell_accumulate<T, RG>(col, val, NG, S.Kp, hidG, acc);
+                    const T sc = V[S.soG + r], off = V[S.soG + NG + r];
+                    acc[0] = off + sc * acc[0];
+#pragma unroll
+                    for (int k = 1; k < RG; ++k) acc[k] *= sc;
+#pragma unroll
+                    for (int k = 0; k < RG; k += 4) st4(outG + (size_t)r * RG + k, acc + k);
+                    gout[r] = acc[0];
                 }
             }
-            __syncthreads();
-            for (int ql = tid; ql < Cq.nq; ql += nth) {
-                const int* op = hr + (size_t)(Cq.q0 + ql) * HR_INTS;
-                const int comp = op[0];
-                T f[6];
-#pragma unroll
-                for (int o = 0; o < 6; ++o) {
-                    const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
-                    f[o] = kind == OP_INTERIOR ? outO[(size_t)idx * rO]
-                                               : (kind == OP_INTERFACE ? outG[(size_t)idx * rG] : (T)bnd[idx]);
-                }
-                const T up = comp == 0 ? f[0] : f[5];
-                const T vp = comp == 0 ? f[5] : f[0];
-                const T dxf = f[1] - f[2], dyf = f[3] - f[4];
-                const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
-                            cy * (f[3] - T(2) * f[0] + f[4]);
-                T d[6];
-                d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
-                d[1] = -up * ax + cx;
-                d[2] = up * ax + cx;
-                d[3] = -vp * ay + cy;
-                d[4] = vp * ay + cy;
-                d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
-                T R[MAX_NI];
-#pragma unroll
-                for (int k = 0; k < MAX_NI; ++k) R[k] = T(0);
-#pragma unroll
-                for (int o = 0; o < 6; ++o) {
-                    const int code = op[1 + o], kind = code >> OP_SHIFT, idx = code & OP_MASK;
-                    if (kind == OP_INTERIOR) {
-                        const T* j = outO + (size_t)idx * rO + 1;
-#pragma unroll
-                        for (int k = 0; k < MAX_NI; ++k)
-                            if (k < nO) R[k] += d[o] * j[k];
-                    } else if (kind == OP_INTERFACE) {
-                        const T* j = outG + (size_t)idx * rG + 1 - nO;
-#pragma unroll
-                        for (int k = 0; k < MAX_NI; ++k)
-                            if (k >= nO && k < ni) R[k] += d[o] * j[k];
-                    }
-                }
-                T* row = Rr + (size_t)ql * ld;
-#pragma unroll
-                for (int k = 0; k < MAX_NI; ++k)
-                    if (k < ni) row[k] = R[k];
-                row[ni] = r;
-                if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + Cq.q0 + ql] = (double)r;
-            }
-            __syncthreads();
-            if (tid < npair + ni)
-                for (int ql = 0; ql < Cq.nq; ++ql) hacc += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
         }
+        __syncthreads();
+        // D_i[c][k] = sum_rows M[row][c] dg^G[row][k] (M = C A_i, N^G x n_C): warp w takes rows w, w+8, ...,
+        // lane l the rows c = l, l+32, ... of C; partials per warp in `red`, summed after the barrier
+        if (q == 0) {
+            const int w = tid >> 5, lane = tid & 31;
+            const T* M = V + S.M;
+            for (int c0 = 0; c0 < nC; c0 += 32) {
+                const int c = c0 + lane;
+                T acc[RG - 1];
+#pragma unroll
+                for (int k = 0; k < RG - 1; ++k) acc[k] = T(0);
+                if (c < nC) {
+                    int row = w;
+                    for (; row + 3 * nwarp < NG; row += 4 * nwarp) {
+                        T m[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) m[u] = M[(size_t)(row + u * nwarp) * nC + c];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const T* j = outG + (size_t)(row + u * nwarp) * RG + 1;
+#pragma unroll
+                            for (int k = 0; k < RG - 1; ++k) acc[k] += m[u] * j[k];
+                        }
+                    }
+                    for (; row < NG; row += nwarp) {
+                        const T m = M[(size_t)row * nC + c];
+                        const T* j = outG + (size_t)row * RG + 1;
+#pragma unroll
+                        for (int k = 0; k < RG - 1; ++k) acc[k] += m * j[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < RG - 1; ++k)
+                        if (k < nG) red[((size_t)w * nC + c) * nG + k] = acc[k];
+                }
+            }
+        }
+        // collocation rows of the chunk
+        {
+            for (int it = tid; it < Cq.nq; it += nth) {
+                {
+                    const int qq = Cq.q0 + it;
+                    const int comp = hr[qq];
+                    int code[6];
+#pragma unroll
+                    for (int o = 0; o < 6; ++o) code[o] = hr[(size_t)(o + 1) * S.NB + qq];
+                    T f[6];
+#pragma unroll
+                    for (int o = 0; o < 6; ++o) {
+                        const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
+                        f[o] = kind == OP_INTERIOR ? outO[(size_t)idx * RO]
+                                                   : (kind == OP_INTERFACE ? outG[(size_t)idx * RG] : bnd[idx]);
+                    }
+                    const T up = comp == 0 ? f[0] : f[5];
+                    const T vp = comp == 0 ? f[5] : f[0];
+                    const T dxf = f[1] - f[2], dyf = f[3] - f[4];
+                    const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
+                                cy * (f[3] - T(2) * f[0] + f[4]);
+                    T d[6];
+                    d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
+                    d[1] = -up * ax + cx;
+                    d[2] = up * ax + cx;
+                    d[3] = -vp * ay + cy;
+                    d[4] = vp * ay + cy;
+                    d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
+                    T RO_[RO - 1 > 0 ? RO - 1 : 1], RG_[RG - 1 > 0 ? RG - 1 : 1];
+#pragma unroll
+                    for (int k = 0; k < RO - 1; ++k) RO_[k] = T(0);
+#pragma unroll
+                    for (int k = 0; k < RG - 1; ++k) RG_[k] = T(0);
+#pragma unroll
+                    for (int o = 0; o < 6; ++o) {
+                        const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
+                        if (kind == OP_INTERIOR) {
+                            const T* j = outO + (size_t)idx * RO + 1;
+#pragma unroll
+                            for (int k = 0; k < RO - 1; ++k) RO_[k] += d[o] * j[k];
+                        } else if (kind == OP_INTERFACE) {
+                            const T* j = outG + (size_t)idx * RG + 1;
+#pragma unroll
+                            for (int k = 0; k < RG - 1; ++k) RG_[k] += d[o] * j[k];
+                        }
+                    }
+                    T* row = Rr + (size_t)it * ld;
+#pragma unroll
+                    for (int k = 0; k < RO - 1; ++k)
+                        if (k < nO) row[k] = RO_[k];
+#pragma unroll
+                    for (int k = 0; k < RG - 1; ++k)
+                        if (k < nG) row[nO + k] = RG_[k];
+                    row[ni] = r;
+                    if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < npair + ni) {
+            T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
+            int ql = 0;
+            for (; ql + 3 < Cq.nq; ql += 4) {
+                h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
+                h1 += Rr[(size_t)(ql + 1) * ld + pa] * Rr[(size_t)(ql + 1) * ld + pc];
+                h2 += Rr[(size_t)(ql + 2) * ld + pa] * Rr[(size_t)(ql + 2) * ld + pc];
+                h3 += Rr[(size_t)(ql + 3) * ld + pa] * Rr[(size_t)(ql + 3) * ld + pc];
+            }
+            for (; ql < Cq.nq; ++ql) h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
+            hacc += (h0 + h1) + (h2 + h3);
+        }
+        if (q == 0)
+            for (int o = tid; o < nout; o += nth) {
+                T acc = T(0);
+                for (int w = 0; w < nwarp; ++w) acc += red[(size_t)w * nout + o];
+                dD[o] = (double)acc;
+            }
+        if (q + 1 < S.n_chunks) __syncthreads();   // outO / Rr reused by the next chunk
     }
     if (tid < npair) {
         dH[pa * ni + pc] = (double)hacc;
@@ -393,12 +481,13 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
     __syncthreads();
 
-    // FP64 tail (warp 0, every lane busy where the structure allows):
-    // rho_i = R^T r + E_i^T lambda; H = L L^T; t = L^{-1} rho; W = L_GG^{-1} D^T (the Omega rows of
-    // L^{-1} E^T vanish); u = W^T t_G; ||rho_i||^2.  Lemma 1 only needs H_i PD on null(E_i): when the
-    // collocation rows do not see every interface direction, H_i is singular in its G block while
-    // H_i^{OO} is PD.  The Cholesky then stops after the O columns and the step kernel handles the
-    // subdomain through G = H_GG - L_GO L_GO^T (snapshot taken after the O columns).
+    // FP64 tail (warp 0): rho_i = R^T r + E_i^T lambda and ||rho_i||^2; H_i = L D L^T (unit lower L,
+    // one reciprocal per pivot: FP64 division and square root sit on this part's slowest path);
+    // t = L^{-1} rho; W = L_GG^{-1} D_i^T (the Omega rows of L^{-1} E_i^T vanish); with the interface
+    // pivots D_G: u = W^T D_G^{-1} t_G and S_i = W^T D_G^{-1} W.  Lemma 1 only needs H_i PD on
+    // null(E_i): when the collocation rows miss an interface direction, H_i is singular in its G block
+    // while H_i^{OO} is PD; the factorisation then stops after the O columns and the step kernel solves
+    // the subdomain through G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).
     double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
     const BlkLayout BL = blk_layout(ni, nG, nC);
     double* dGs = (double*)(smem + L.dG);
@@ -416,7 +505,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         __syncwarp();
         int flag = 0;
         for (int j = 0; j < ni; ++j) {
-            if (j == nO)      // Schur complement of H^{OO}: the untouched trailing block
+            if (j == nO)      // Schur complement of H^{OO}: the trailing block after the O columns
                 for (int e = lane; e < nG * nG; e += 32) dGs[e] = dL[(nO + e / nG) * ni + nO + e % nG];
             __syncwarp();
             const double d = dL[j * ni + j];
@@ -424,27 +513,27 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
                 flag = j < nO ? 1 : 2;
                 break;
             }
-            const double r = rsqrt(d);
-            for (int i = j + 1 + lane; i < ni; i += 32) dL[i * ni + j] *= r;
-            __syncwarp();
+            const double r = 1.0 / d;
             const int m = ni - j - 1;
-            for (int e = lane; e < m * m; e += 32) {
-                const int i = j + 1 + e / m, k = j + 1 + e % m;
-                if (k <= i) dL[i * ni + k] -= dL[i * ni + j] * dL[k * ni + j];
+            for (int e = lane; e < m * (m + 1) / 2; e += 32) {     // trailing lower triangle, unscaled column j
+                int i = 0, rem = e;
+                while (rem > i) {
+                    rem -= i + 1;
+                    ++i;
+                }
+                const int ii = j + 1 + i, kk = j + 1 + rem;
+                dL[ii * ni + kk] -= dL[ii * ni + j] * r * dL[kk * ni + j];
             }
-            if (lane == 0) {
-                dL[j * ni + j] = d * r;
-                drinv[j] = r;
-            }
+            __syncwarp();
+            for (int i = j + 1 + lane; i < ni; i += 32) dL[i * ni + j] *= r;   // column j of L
+            if (lane == 0) drinv[j] = r;
             __syncwarp();
         }
         if (flag != 1) {
-            const int nf = flag == 0 ? ni : nO;       // forward substitution over the factored columns
+            const int nf = flag == 0 ? ni : nO;       // unit forward substitution over the factored columns
             for (int j = 0; j < nf; ++j) {
-                const double tj = dt[j] * drinv[j];
+                const double tj = dt[j];
                 for (int i = j + 1 + lane; i < ni; i += 32) dt[i] -= dL[i * ni + j] * tj;
-                __syncwarp();
-                if (lane == 0) dt[j] = tj;
                 __syncwarp();
             }
         }
@@ -454,9 +543,8 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
                 for (int k = 0; k < nG; ++k) {
                     double v = dD[c * nG + k];
                     for (int m = 0; m < k; ++m) v -= dL[(nO + k) * ni + nO + m] * dW[m * nC + c];
-                    v *= drinv[nO + k];
                     dW[k * nC + c] = v;
-                    uc += v * dt[nO + k];
+                    uc += v * drinv[nO + k] * dt[nO + k];
                 }
                 blk[BL.u + c] = uc;
             }
@@ -484,25 +572,47 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         for (int e = tid; e < nG * nG; e += nth) blk[BL.G + e] = dGs[e];
     if (s_flag == 0) {
         for (int e = tid; e < nG * nC; e += nth) blk[BL.W + e] = dW[e];
-        // S_i = W^T W (n_C x n_C, symmetric: each entry of the lower triangle once, mirrored)
-        for (int e = tid; e < nC * nC; e += nth) {
-            const int c1 = e / nC, c2 = e % nC;
-            if (c2 > c1) continue;
+        // S_i = W^T D_G^{-1} W (n_C x n_C, symmetric: lower triangle computed once, mirrored)
+        for (int e = tid; e < nC * (nC + 1) / 2; e += nth) {
+            int c1 = 0, rem = e;
+            while (rem > c1) {
+                rem -= c1 + 1;
+                ++c1;
+            }
+            const int c2 = rem;
             double v = 0.0;
-            for (int k = 0; k < nG; ++k) v += dW[k * nC + c1] * dW[k * nC + c2];
+            for (int k = 0; k < nG; ++k) v += dW[k * nC + c1] * drinv[nO + k] * dW[k * nC + c2];
             blk[BL.S + c1 * nC + c2] = v;
             blk[BL.S + c2 * nC + c1] = v;
         }
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B) {
+// One launch per class of subdomains sharing the padded record widths (RO, RG): CTA = (instance,
+// subdomain of the class), subs = the class's subdomain indices.
+template <typename T, int RO, int RG>
+__global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B, const int* subs, int nsub) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int b = blockIdx.x / P.n_sub, si = blockIdx.x - (blockIdx.x / P.n_sub) * P.n_sub;
+    const int b = blockIdx.x / nsub, si = subs[blockIdx.x - (blockIdx.x / nsub) * nsub];
     if (b >= B) return;
     if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
-    eval_item<T>(P, P.sub[si], b, smem);
+    eval_item<T, RO, RG>(P, P.sub[si], b, smem);
+}
+
+// host side: the kernel of a width class
+template <typename T>
+using EvalKernel = void (*)(ProbDev, int, const int*, int);
+
+template <typename T>
+EvalKernel<T> eval_kernel(int ro, int rg) {
+#define DDNM_EVAL_CASE(A, G) \
+    if (ro == A && rg == G) return k_eval<T, A, G>;
+    DDNM_EVAL_CASE(4, 4) DDNM_EVAL_CASE(4, 8) DDNM_EVAL_CASE(4, 12)
+    DDNM_EVAL_CASE(8, 4) DDNM_EVAL_CASE(8, 8) DDNM_EVAL_CASE(8, 12)
+    DDNM_EVAL_CASE(12, 4) DDNM_EVAL_CASE(12, 8) DDNM_EVAL_CASE(12, 12)
+    DDNM_EVAL_CASE(16, 4) DDNM_EVAL_CASE(16, 8) DDNM_EVAL_CASE(16, 12)
+#undef DDNM_EVAL_CASE
+    return nullptr;
 }
 
 // Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
@@ -554,9 +664,15 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     double* slam = P.slam + (size_t)b * nC;
 
     for (int c = tid; c < nC; c += nth) {
-        double a = 0.0;
-        for (int sp = 0; sp < P.n_split; ++sp) a += P.Atil[((size_t)b * P.n_split + sp) * nC + c];
-        At[c] = a;
+        const double* ap = P.Atil + (size_t)b * P.n_split * nC + c;
+        double a0 = 0.0, a1 = 0.0;
+        int sp = 0;
+        for (; sp + 1 < P.n_split; sp += 2) {
+            a0 += ap[(size_t)sp * nC];
+            a1 += ap[(size_t)(sp + 1) * nC];
+        }
+        if (sp < P.n_split) a0 += ap[(size_t)sp * nC];
+        At[c] = a0 + a1;
     }
     __syncthreads();
     // merit phi^2 = sum_i ||rho_i||^2 + ||Atil||^2; subdomains whose H_i^{OO} was not PD
@@ -601,11 +717,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
             }
             rhs[c] = v;
         }
-        if (!block_cholesky(Sm, rv, nC)) {
+        if (!block_ldl(Sm, rv, nC)) {
             if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
             return;
         }
-        block_chol_solve(Sm, rv, nC, rhs);
+        block_ldl_solve(Sm, rv, nC, rhs);
         for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
         if (tid == 0) {
             ist[I_MODE] = MODE_INIT1;
@@ -656,18 +772,22 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         return;
     }
 
-    // Schur complement of Eq. (sqp_system) over the subdomains with H_i PD:
-    //   S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T W_i,  r = Atil - sum_i E_i H_i^{-1} rho_i = Atil - sum_i u_i.
+    // Schur complement of Eq. (sqp_system) over the subdomains with H_i PD (H_i = L_i D_i L_i^T):
+    //   S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G^{-1} W_i,  r = Atil - sum_i u_i.
     // Subdomains F with H_i singular in the G block (H_i^{OO} PD) keep their interface steps s_F as
-    // unknowns: with Z = L_S^{-1} D_F, q = L_S^{-1} r and G_F = H_GG - L_GO L_GO^T,
-    //   (G_F + Z^T Z) s_F = -(rho_G - L_GO t_O)_F - Z^T q,   s_lambda = L_S^{-T} (q + Z s_F).
+    // unknowns: with S = L_S D_S L_S^T, Z = L_S^{-1} D_F, q = L_S^{-1} r and G_F the Schur complements,
+    //   (G_F + Z^T D_S^{-1} Z) s_F = -(rho_G - L_GO t_O)_F - Z^T D_S^{-1} q,
+    //   s_lambda = L_S^{-T} D_S^{-1} (q + Z s_F).
     __shared__ int s_nF, s_mF, s_over;
     __shared__ int fsub[MAX_MF], fcol_sub[MAX_MF], fcol_k[MAX_MF];
+    __shared__ int sflag[64];
     if (tid == 0) {
         int nF = 0, mF = 0, over = 0;
         for (int i = 0; i < ns; ++i) {
             const SubDev& S = P.sub[i];
-            if (blk[S.blk + blk_layout(S.ni, S.nG, nC).flag] == FLAG_GAMMA_SING) {
+            const int fl = (int)blk[S.blk + blk_layout(S.ni, S.nG, nC).flag];
+            if (i < 64) sflag[i] = fl;
+            if (fl == 2) {
                 if (mF + S.nG > MAX_MF) {
                     over = 1;
                     break;
@@ -682,7 +802,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         }
         s_nF = nF;
         s_mF = mF;
-        s_over = over;
+        s_over = over || ns > 64;
     }
     __syncthreads();
     const int nF = s_nF, mF = s_mF;
@@ -690,34 +810,59 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
         return;
     }
-    for (int e = tid; e < nC * nC; e += nth) {
-        double v = 0.0;
-        for (int i = 0; i < ns; ++i) {
+    // S (lower triangle, mirrored) and r: the subdomain loads of each entry are independent
+    for (int e = tid; e < nC * (nC + 1) / 2 + nC; e += nth) {
+        int c1 = -1, c2 = 0;
+        if (e < nC * (nC + 1) / 2) {
+            int rem = e;
+            c1 = 0;
+            while (rem > c1) {
+                rem -= c1 + 1;
+                ++c1;
+            }
+            c2 = rem;
+        }
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int i = 0;
+        for (; i + 3 < ns; i += 4) {
+            double w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const SubDev& S = P.sub[i + u];
+                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+                w[u] = sflag[i + u] != 0 ? 0.0
+                       : (c1 >= 0 ? blk[S.blk + BL.S + c1 * nC + c2] : blk[S.blk + BL.u + (e - nC * (nC + 1) / 2)]);
+            }
+            v0 += w[0];
+            v1 += w[1];
+            v2 += w[2];
+            v3 += w[3];
+        }
+        for (; i < ns; ++i) {
             const SubDev& S = P.sub[i];
             const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-            if (blk[S.blk + BL.flag] == FLAG_PD) v += blk[S.blk + BL.S + e];
+            if (sflag[i] == 0)
+                v0 += c1 >= 0 ? blk[S.blk + BL.S + c1 * nC + c2] : blk[S.blk + BL.u + (e - nC * (nC + 1) / 2)];
         }
-        Sm[e] = v;
-    }
-    for (int c = tid; c < nC; c += nth) {
-        double v = At[c];
-        for (int i = 0; i < ns; ++i) {
-            const SubDev& S = P.sub[i];
-            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-            if (blk[S.blk + BL.flag] == FLAG_PD) v -= blk[S.blk + BL.u + c];
+        const double v = (v0 + v1) + (v2 + v3);
+        if (c1 >= 0) {
+            Sm[c1 * nC + c2] = v;
+            Sm[c2 * nC + c1] = v;
+        } else {
+            const int c = e - nC * (nC + 1) / 2;
+            rhs[c] = At[c] - v;
         }
-        rhs[c] = v;
     }
-    if (!block_cholesky(Sm, rv, nC)) {
+    if (!block_ldl(Sm, rv, nC)) {
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
         return;
     }
-    double* Z = rv + nC;                  // nC x MAX_MF, row-major with row stride mF + 1 (last column: q)
+    double* Z = rv + nC;                  // nC x (mF + 1), row-major (last column: q)
     double* T = Z + nC * (MAX_MF + 1);    // MAX_MF x MAX_MF
     double* rT = T + MAX_MF * MAX_MF;     // MAX_MF reciprocal pivots of T
     double* sF = rT + MAX_MF;             // MAX_MF
     if (mF == 0) {
-        block_chol_solve(Sm, rv, nC, rhs);
+        block_ldl_solve(Sm, rv, nC, rhs);
     } else {
         const int ldz = mF + 1;
         for (int e = tid; e < nC * ldz; e += nth) {
@@ -731,11 +876,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
             }
             Z[e] = v;
         }
-        // [Z q] <- L_S^{-1} [D_F r]
+        // [Z q] <- L_S^{-1} [D_F r]   (unit lower)
         for (int j = 0; j < nC; ++j) {
-            __syncthreads();
-            const double r = rv[j];
-            for (int a = tid; a < ldz; a += nth) Z[j * ldz + a] *= r;
             __syncthreads();
             const int m = nC - j - 1;
             for (int e = tid; e < m * ldz; e += nth) {
@@ -744,11 +886,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
             }
         }
         __syncthreads();
-        // T = G_F + Z^T Z, right-hand side -(t~_G)_F - Z^T q
+        // T = G_F + Z^T D_S^{-1} Z, right-hand side -(t~_G)_F - Z^T D_S^{-1} q
         for (int e = tid; e < mF * mF; e += nth) {
             const int a = e / mF, c2 = e % mF;
             double v = 0.0;
-            for (int c = 0; c < nC; ++c) v += Z[c * ldz + a] * Z[c * ldz + c2];
+            for (int c = 0; c < nC; ++c) v += Z[c * ldz + a] * rv[c] * Z[c * ldz + c2];
             if (fcol_sub[a] == fcol_sub[c2]) {
                 const SubDev& S = P.sub[fcol_sub[a]];
                 v += blk[S.blk + blk_layout(S.ni, S.nG, nC).G + fcol_k[a] * S.nG + fcol_k[c2]];
@@ -758,24 +900,30 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         for (int a = tid; a < mF; a += nth) {
             const SubDev& S = P.sub[fcol_sub[a]];
             double v = -blk[S.blk + blk_layout(S.ni, S.nG, nC).t + S.nO + fcol_k[a]];
-            for (int c = 0; c < nC; ++c) v -= Z[c * ldz + a] * Z[c * ldz + mF];
+            for (int c = 0; c < nC; ++c) v -= Z[c * ldz + a] * rv[c] * Z[c * ldz + mF];
             sF[a] = v;
         }
-        if (!block_cholesky(T, rT, mF)) {
+        if (!block_ldl(T, rT, mF)) {
             if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
             return;
         }
-        block_chol_solve(T, rT, mF, sF);
+        block_ldl_solve(T, rT, mF, sF);
         for (int c = tid; c < nC; c += nth) {
             double v = Z[c * ldz + mF];
             for (int a = 0; a < mF; ++a) v += Z[c * ldz + a] * sF[a];
-            rhs[c] = v;
+            rhs[c] = v * rv[c];
         }
-        block_bwd(Sm, rv, nC, rhs);
+        // rhs <- L_S^{-T} rhs  (unit upper)
+        for (int k = nC - 1; k >= 0; --k) {
+            __syncthreads();
+            const double xk = rhs[k];
+            for (int i = tid; i < k; i += nth) rhs[i] -= Sm[k * nC + i] * xk;
+        }
+        __syncthreads();
     }
-    // per-subdomain steps, one warp per subdomain:
-    //   H_i PD:           s_i = -L_i^{-T} (t_i + W_i s_lambda)
-    //   G-singular (F):   s_G from s_F,  s_O = -L_OO^{-T} (t_O + L_GO^T s_G)
+    // per-subdomain steps, one warp per subdomain (H_i = L D L^T):
+    //   H_i PD:           s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda])
+    //   G-singular (F):   s_G from s_F,  s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G)
     {
         const int w = tid >> 5, lane = tid & 31, nw = nth >> 5;
         double* z = zb[w];
@@ -786,16 +934,27 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
             const double* ri = blk + S.blk + BL.rinv;
             const double* ti = blk + S.blk + BL.t;
             const double* Wi = blk + S.blk + BL.W;
-            const bool sing = blk[S.blk + BL.flag] == FLAG_GAMMA_SING;
+            const bool sing = sflag[i] == 2;
             int nb = S.ni;                    // rows solved by back-substitution
             if (!sing) {
-                if (lane < S.ni) z[lane] = ti[lane];
-                __syncwarp();
-                for (int k = 0; k < S.nG; ++k) {
-                    double v = 0.0;
-                    for (int c = lane; c < nC; c += 32) v += Wi[k * nC + c] * rhs[c];
-                    v = warp_sum(v);
-                    if (lane == 0) z[S.nO + k] += v;
+                double part[MAX_NG];
+#pragma unroll
+                for (int k = 0; k < MAX_NG; ++k) part[k] = 0.0;
+                for (int c = lane; c < nC; c += 32) {
+                    const double yc = rhs[c];
+#pragma unroll
+                    for (int k = 0; k < MAX_NG; ++k)
+                        if (k < S.nG) part[k] += Wi[k * nC + c] * yc;
+                }
+#pragma unroll
+                for (int k = 0; k < MAX_NG; ++k)
+                    if (k < S.nG) part[k] = warp_sum(part[k]);
+                if (lane < S.ni) {
+                    double v = ti[lane];
+#pragma unroll
+                    for (int k = 0; k < MAX_NG; ++k)
+                        if (k < S.nG && lane == S.nO + k) v += part[k];
+                    z[lane] = v * ri[lane];
                 }
             } else {
                 int a0 = 0;
@@ -805,20 +964,18 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
                 }
                 if (lane < S.nG) s_[S.xoff + S.nO + lane] = sF[a0 + lane];
                 if (lane < S.nO) {
-                    double v = ti[lane];
+                    double v = ti[lane] * ri[lane];
                     for (int k = 0; k < S.nG; ++k) v += Li[(S.nO + k) * S.ni + lane] * sF[a0 + k];
                     z[lane] = v;
                 }
                 nb = S.nO;
             }
-            __syncwarp();
             for (int k = nb - 1; k >= 0; --k) {
-                const double zk = z[k] * ri[k];
+                __syncwarp();
+                const double zk = z[k];
                 if (lane < k) z[lane] -= Li[k * S.ni + lane] * zk;
-                __syncwarp();
-                if (lane == 0) z[k] = zk;
-                __syncwarp();
             }
+            __syncwarp();
             if (lane < nb) s_[S.xoff + lane] = -z[lane];
             __syncwarp();
         }
@@ -840,7 +997,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
 // ------------------------------------------------------------------------ set-up / outputs
 
 // start state of every instance and its Dirichlet data
-__global__ void k_init(ProbDev P, int B, int has_x0, int has_lam0, int mode) {
+__global__ void k_init(ProbDev P, int B, int has_x0, int has_lam0, int mode, int fp64) {
     const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     if (b >= B) return;
     for (int k = tid; k < P.n_D; k += nth) {
@@ -860,8 +1017,14 @@ __global__ void k_init(ProbDev P, int B, int has_x0, int has_lam0, int mode) {
         const double x = P.bx0 + P.bnd_ij[2 * p] * P.hx, y = P.by0 + P.bnd_ij[2 * p + 1] * P.hy;
         double u, v;
         exact_uv(x, y, a, lm, P.nu, u, v);
-        P.bnd[((size_t)b * P.n_bnd + p) * 2] = u;
-        P.bnd[((size_t)b * P.n_bnd + p) * 2 + 1] = v;
+        const size_t o = ((size_t)b * P.n_bnd + p) * 2;
+        if (fp64) {
+            ((double*)P.bnd)[o] = u;
+            ((double*)P.bnd)[o + 1] = v;
+        } else {
+            ((float*)P.bnd)[o] = (float)u;
+            ((float*)P.bnd)[o + 1] = (float)v;
+        }
     }
     if (tid == 0) {
         int* ist = P.ist + (size_t)b * INST_INTS;
@@ -1051,7 +1214,8 @@ int tflush(ddnm_ctx* ctx, cudaStream_t st) {
 
 template <typename T>
 int set_smem_attrs(ddnm_ctx* ctx) {
-    CK(cudaFuncSetAttribute(k_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->eval_smem));
+    for (const auto& g : ctx->eval_classes)
+        CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem));
     CK(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->step_smem));
     CK(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(ctx->rec_smem, 16)));
     return DDNM_OK;
@@ -1060,10 +1224,12 @@ int set_smem_attrs(ddnm_ctx* ctx) {
 template <typename T>
 int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st) {
     int k = tstart(ctx, 0, st);
-    k_eval<T><<<B * P.n_sub, EVAL_THREADS, ctx->eval_smem, st>>>(P, B);
-    CK(cudaGetLastError());
+    for (const auto& g : ctx->eval_classes) {
+        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n);
+        CK(cudaGetLastError());
+        ctx->tm.eval_launches++;
+    }
     tstop(ctx, k, st);
-    ctx->tm.eval_launches++;
     k = tstart(ctx, 1, st);
     k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, 0, st>>>(P, B);
     CK(cudaGetLastError());
@@ -1128,7 +1294,7 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
     if ((rc = copy_in(ctx, P.mu, mu, (size_t)B * 2, mem_kind, st))) return rc;
     if (x0 && (rc = copy_in(ctx, P.x, x0, (size_t)B * P.n_D, mem_kind, st))) return rc;
     if (lam0 && (rc = copy_in(ctx, P.lam, lam0, (size_t)B * P.n_C, mem_kind, st))) return rc;
-    k_init<<<B, 128, 0, st>>>(P, B, x0 != nullptr, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0);
+    k_init<<<B, 128, 0, st>>>(P, B, x0 != nullptr, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0, fp64);
     CK(cudaGetLastError());
     ctx->tm.other_launches++;
     const int max_passes = 3 + ctx->opt.max_iter * (ctx->opt.max_backtracks + 1);
@@ -1197,7 +1363,7 @@ int eval_once(ddnm_ctx* ctx, ProbDev& P, int B, const double* mu, const double* 
     if ((rc = copy_in(ctx, P.mu, mu, (size_t)B * 2, mem_kind, st))) return rc;
     if ((rc = copy_in(ctx, P.x, x, (size_t)B * P.n_D, mem_kind, st))) return rc;
     if (lam && (rc = copy_in(ctx, P.lam, lam, (size_t)B * P.n_C, mem_kind, st))) return rc;
-    k_init<<<B, 128, 0, st>>>(P, B, 1, lam != nullptr, MODE_INIT1);
+    k_init<<<B, 128, 0, st>>>(P, B, 1, lam != nullptr, MODE_INIT1, (int)(sizeof(T) == 8));
     CK(cudaGetLastError());
     ctx->tm.other_launches++;
     P.r_hr = r_hr_dev;
@@ -1331,7 +1497,7 @@ int noalloc_scratch(ddnm_ctx* ctx, void** out) {
 }
 
 // per-instance state and Dirichlet data for one evaluation (no copies of the caller's inputs)
-__global__ void k_noalloc_init(ProbDev P, int B) {
+__global__ void k_noalloc_init(ProbDev P, int B, int fp64) {
     const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     if (b >= B) return;
     const double a = P.mu[2 * b], lm = P.mu[2 * b + 1];
@@ -1339,8 +1505,14 @@ __global__ void k_noalloc_init(ProbDev P, int B) {
         const double x = P.bx0 + P.bnd_ij[2 * p] * P.hx, y = P.by0 + P.bnd_ij[2 * p + 1] * P.hy;
         double u, v;
         exact_uv(x, y, a, lm, P.nu, u, v);
-        P.bnd[((size_t)b * P.n_bnd + p) * 2] = u;
-        P.bnd[((size_t)b * P.n_bnd + p) * 2 + 1] = v;
+        const size_t o = ((size_t)b * P.n_bnd + p) * 2;
+        if (fp64) {
+            ((double*)P.bnd)[o] = u;
+            ((double*)P.bnd)[o + 1] = v;
+        } else {
+            ((float*)P.bnd)[o] = (float)u;
+            ((float*)P.bnd)[o + 1] = (float)v;
+        }
     }
     if (tid == 0) {
         int* ist = P.ist + (size_t)b * INST_INTS;
@@ -1352,10 +1524,14 @@ __global__ void k_noalloc_init(ProbDev P, int B) {
 
 template <typename T>
 int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_eval<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->eval_smem);
-    if (e != cudaSuccess) return cfail(ctx, e, "cudaFuncSetAttribute(k_eval)");
-    k_noalloc_init<<<B, 128, 0, st>>>(P, B);
-    k_eval<T><<<B * P.n_sub, EVAL_THREADS, ctx->eval_smem, st>>>(P, B);
+    cudaError_t e = cudaSuccess;
+    for (const auto& g : ctx->eval_classes) {
+        e = cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
+        if (e != cudaSuccess) return cfail(ctx, e, "cudaFuncSetAttribute(k_eval)");
+    }
+    k_noalloc_init<<<B, 128, 0, st>>>(P, B, (int)(sizeof(T) == 8));
+    for (const auto& g : ctx->eval_classes)
+        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n);
     k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, 0, st>>>(P, B);
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
@@ -1402,7 +1578,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     P.xt = const_cast<double*>(x);         // read only by k_eval
     P.ist = (int*)(s + o_ist);
     P.dst = (double*)(s + o_dst);
-    P.bnd = (double*)(s + o_bnd);
+    P.bnd = (void*)(s + o_bnd);
     P.gG = (void*)(s + o_gG);
     P.blk = (double*)(s + o_blk);
     P.Atil = (double*)(s + o_At);
