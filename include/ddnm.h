@@ -81,6 +81,7 @@ enum {
 };
 /* per-instance flags (ddnm_stats.flags, bit mask) */
 #define DDNM_FLAG_LS_FAIL 1   /* some line search took its last trial without passing Armijo */
+#define DDNM_FLAG_WS_FALLBACK 2 /* learned warm start enabled, but the default start had the smaller merit */
 
 /* Problem statement (Sec. 2, 3.1, 7.1). */
 typedef struct ddnm_problem {
@@ -266,6 +267,47 @@ int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, cons
  *    wrong results.  Serialise them. */
 int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam,
                           double* F_out, void* stream);
+
+/* ---- Learned warm start (replaces the paper's RBF starting point, Sec. 7.2) ----
+ * An MLP z = (mu - mu_c)/mu_s -> a1 = tanh(W1 z + b1) -> a2 = tanh(W2 a1 + b2) -> y = W3 a2 + b3,
+ * xh0 = out_mean + out_std * y, trained on the device with hand-written forward, backward and Adam
+ * kernels (bfloat16 weights in the products, FP32 accumulation and FP32 master weights).
+ * Flat FP32 parameter layout: W1 (H x 2), b1 (H), W2 (H x H), b2 (H), W3 (n_D x H), b3 (n_D). */
+
+/* Set the architecture (hidden width H, 1..4096) and the initial parameters (host, copied);
+ * resets the Adam state and the normalisation (identity). */
+int ddnm_ws_init(ddnm_ctx* ctx, int hidden, const float* params);
+
+/* Input/output standardisation: mu_c[2], mu_s[2], out_mean[n_D], out_std[n_D] (host). */
+int ddnm_ws_set_norm(ddnm_ctx* ctx, const double* mu_c, const double* mu_s, const double* out_mean,
+                     const double* out_std);
+
+/* Mean squared error and its gradient (P floats, host) on one batch of standardised inputs z
+ * (nb x 2) and targets t (nb x n_D), at the current parameters (no update). */
+int ddnm_ws_loss_grad(ddnm_ctx* ctx, int nb, const float* z, const float* t, float* grad, double* loss);
+
+/* Mini-batch Adam (lr; beta1 0.9, beta2 0.999, eps 1e-8) on n samples mu (n x 2) -> x_star (n x n_D),
+ * host FP64 arrays; order (epochs x n) gives each epoch's sample order (NULL: 0..n-1).  The
+ * standardisation is taken from the training set.  losses (epochs, may be NULL) receives each
+ * epoch's mean batch loss. */
+int ddnm_ws_train(ddnm_ctx* ctx, int n, const double* mu, const double* x_star, int epochs, int batch, double lr,
+                  const int* order, double* losses);
+
+/* xh0 = MLP(mu) for B instances (mem_kind as in ddnm_solve_batch); a row with a non-finite
+ * prediction is replaced by the default start 0. */
+int ddnm_ws_predict(ddnm_ctx* ctx, int B, const double* mu, double* x0, int mem_kind, void* stream);
+
+/* Current parameters (P floats) and normalisation (4 + 2 n_D doubles); either may be NULL. */
+int ddnm_ws_get_params(const ddnm_ctx* ctx, float* params, double* norm);
+
+/* With on != 0, ddnm_solve_batch calls with x0 == lam0 == NULL start each instance from the MLP
+ * prediction; the default start xh0 = 0 is linearised alongside and kept when its merit is not larger
+ * (flag DDNM_FLAG_WS_FALLBACK).  The screening evaluations are counted in n_evals. */
+int ddnm_ws_enable(ddnm_ctx* ctx, int on);
+
+/* Checkpoint of the warm start ("DDNMWS01", H, n_D, Adam step count, parameters, normalisation). */
+int ddnm_ws_save(const ddnm_ctx* ctx, const char* path);
+int ddnm_ws_load(ddnm_ctx* ctx, const char* path);
 
 /* Turn per-kernel timing on (resets the counters) or off.  While on, every
  * compute call synchronises its stream before returning. */

@@ -263,3 +263,31 @@ def decoders_for(wl: Workload, interior_ids: list, interface_ids: list, act: str
 def hr_sets(wl: Workload) -> list[np.ndarray]:
     return [hr_rows(nr, nb, i, SEED_HR + wl.seed_offset)
             for i, (nr, nb) in enumerate(zip(wl.residual_rows(), wl.hr_counts()))]
+
+
+# ------------------------------------------------------------ learned warm start (MLP)
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round FP32/FP64 values to the nearest bfloat16 (round to nearest even), returned as float32."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(f.shape)
+
+
+def mlp_init(n_in: int, hidden: int, n_out: int, seed: int = SEED_MLP) -> np.ndarray:
+    """Initial parameters of the warm-start MLP n_in -> hidden -> hidden -> n_out, flat float32 in the order
+    W1 (hidden x n_in), b1, W2 (hidden x hidden), b2, W3 (n_out x hidden), b3.  Weights ~ N(0, 1/fan_in),
+    biases 0, all bf16-representable."""
+    r = rng("mlp", seed, n_in, hidden, n_out)
+    parts = []
+    for fo, fi in ((hidden, n_in), (hidden, hidden), (n_out, hidden)):
+        parts.append(bf16_round(r.standard_normal((fo, fi)) / math.sqrt(fi)).ravel())
+        parts.append(np.zeros(fo, dtype=np.float32))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_order(n: int, epochs: int, seed: int = SEED_MLP) -> np.ndarray:
+    """Sample order of each training epoch (epochs x n, int32): one permutation per epoch."""
+    r = rng("mlp", seed, 999, n, epochs)
+    return np.stack([r.permutation(n) for _ in range(epochs)]).astype(np.int32)

@@ -28,7 +28,7 @@ DDNM_ACT = {"swish": 0, "sigmoid": 1, "identity": 2}
 DDNM_MEM_HOST, DDNM_MEM_DEVICE = 0, 1
 DDNM_DECODER_INTERIOR, DDNM_DECODER_INTERFACE = 0, 1
 DDNM_CONVERGED, DDNM_MAX_ITER, DDNM_NONFINITE, DDNM_KKT_FAIL = 0, 1, 2, 3
-DDNM_FLAG_LS_FAIL = 1
+DDNM_FLAG_LS_FAIL, DDNM_FLAG_WS_FALLBACK = 1, 2
 
 _ip = C.POINTER(C.c_int)
 _dp = C.POINTER(C.c_double)
@@ -90,6 +90,15 @@ _sig = {
     "ddnm_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_linearize": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_residual_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "ddnm_ws_init": (C.c_int, [_vp, C.c_int, _vp]),
+    "ddnm_ws_set_norm": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "ddnm_ws_loss_grad": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "ddnm_ws_train": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_double, _vp, _vp]),
+    "ddnm_ws_predict": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
+    "ddnm_ws_get_params": (C.c_int, [_vp, _vp, _vp]),
+    "ddnm_ws_enable": (C.c_int, [_vp, C.c_int]),
+    "ddnm_ws_save": (C.c_int, [_vp, C.c_char_p]),
+    "ddnm_ws_load": (C.c_int, [_vp, C.c_char_p]),
     "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
     "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
@@ -235,6 +244,64 @@ def ddnm_residual_noalloc(ctx, B, mu, x, lam, F_out):
     on the GPU race on the library's shared static scratch."""
     _check(ctx, _lib.ddnm_residual_noalloc(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(F_out),
                                            _stream(DDNM_MEM_DEVICE)))
+
+
+def mlp_param_count(n_in, H, n_out):
+    return H * n_in + H + H * H + H + n_out * H + n_out
+
+
+def ddnm_ws_init(ctx, hidden, params):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    _check(ctx, _lib.ddnm_ws_init(ctx, hidden, p.ctypes.data))
+
+
+def ddnm_ws_set_norm(ctx, mu_c, mu_s, out_mean, out_std):
+    a = [_f64(v) for v in (mu_c, mu_s, out_mean, out_std)]
+    _check(ctx, _lib.ddnm_ws_set_norm(ctx, *[v.ctypes.data for v in a]))
+
+
+def ddnm_ws_loss_grad(ctx, z, t, n_params):
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.float32))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float32))
+    g = np.zeros(n_params, dtype=np.float32)
+    loss = C.c_double()
+    _check(ctx, _lib.ddnm_ws_loss_grad(ctx, z.shape[0], z.ctypes.data, t.ctypes.data, g.ctypes.data, C.byref(loss)))
+    return loss.value, g
+
+
+def ddnm_ws_train(ctx, mu, x_star, epochs, batch, lr, order=None):
+    mu, x_star = _f64(mu), _f64(x_star)
+    o = None if order is None else _i32(order)
+    losses = np.zeros(max(epochs, 1))
+    _check(ctx, _lib.ddnm_ws_train(ctx, mu.shape[0], mu.ctypes.data, x_star.ctypes.data, epochs, batch, lr,
+                                   None if o is None else o.ctypes.data, losses.ctypes.data))
+    return losses[:epochs]
+
+
+def ddnm_ws_predict(ctx, mu, n_out):
+    mu = _f64(mu).reshape(-1, 2)
+    x0 = np.zeros((mu.shape[0], n_out))
+    _check(ctx, _lib.ddnm_ws_predict(ctx, mu.shape[0], mu.ctypes.data, x0.ctypes.data, DDNM_MEM_HOST, None))
+    return x0
+
+
+def ddnm_ws_get_params(ctx, n_params, n_out):
+    p = np.zeros(n_params, dtype=np.float32)
+    nrm = np.zeros(4 + 2 * n_out)
+    _check(ctx, _lib.ddnm_ws_get_params(ctx, p.ctypes.data, nrm.ctypes.data))
+    return p, nrm
+
+
+def ddnm_ws_enable(ctx, on=True):
+    _check(ctx, _lib.ddnm_ws_enable(ctx, int(bool(on))))
+
+
+def ddnm_ws_save(ctx, path):
+    _check(ctx, _lib.ddnm_ws_save(ctx, os.fsencode(path)))
+
+
+def ddnm_ws_load(ctx, path):
+    _check(ctx, _lib.ddnm_ws_load(ctx, os.fsencode(path)))
 
 
 def ddnm_timing_enable(ctx, on=True):

@@ -1,5 +1,6 @@
 // Library context: host copy of the problem and device handles.  Internal.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -24,6 +25,24 @@ struct SubHost {
     std::vector<int> need;       // interior outputs the stencils use (I_o), ascending local indices
     std::vector<std::vector<int>> chunk_need;   // the same per chunk of HR_CHUNK collocation rows
     int nO = 0, nG = 0;
+};
+
+// learned warm start (ddnm_mlp.cu): MLP mu -> xh0 with FP32 master weights and a bfloat16 copy
+struct WarmStart {
+    bool ready = false, enabled = false;
+    int H = 0, n = 0;                  // hidden width, outputs (= n_D)
+    long long steps = 0;               // Adam steps taken
+    float* p = nullptr;                // parameters (FP32 master)
+    __nv_bfloat16* pb = nullptr;       // bfloat16 copy read by the GEMMs
+    float* m = nullptr;                // Adam moments
+    float* v = nullptr;
+    float* norm = nullptr;             // mu_c[2], mu_s[2], out_mean[n], out_std[n]
+    void* act = nullptr;               // batch buffers
+    int cap = 0;
+    float *z = nullptr, *a1 = nullptr, *a2 = nullptr, *y = nullptr, *t = nullptr;
+    float *dy = nullptr, *d2 = nullptr, *d1 = nullptr, *g = nullptr;
+    double* lpart = nullptr;
+    void* data = nullptr;              // training set on the device
 };
 
 // subdomains sharing the padded record widths of the evaluation kernel
@@ -73,6 +92,8 @@ struct ddnm_ctx {
 
     std::vector<long long> nnzO, nnzG;   // mask nonzeros of the interior subnet rows / all interface rows
 
+    WarmStart ws;
+
     // per-kernel timing (ddnm_timing_enable)
     bool timing = false;
     ddnm_timing tm{};
@@ -88,3 +109,5 @@ int ddnm_fail(ddnm_ctx* ctx, int code, const std::string& msg);
 int ddnm_finalize(ddnm_ctx* ctx);
 int ddnm_reserve(ddnm_ctx* ctx, int B);
 void ddnm_release_events(ddnm_ctx* ctx);
+void ddnm_ws_release(ddnm_ctx* ctx);
+int ddnm_ws_predict_dev(ddnm_ctx* ctx, int B, const double* mu_dev, double* x0_dev, int* fell_back, cudaStream_t st);

@@ -270,6 +270,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_ws);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
     ddnm_release_events(ctx);
+    ddnm_ws_release(ctx);
     delete ctx;
 }
 

@@ -1161,6 +1161,45 @@ __global__ void k_fom_residual(ProbDev P, int B, const double* state, double* re
     res[(size_t)b * P.N_x + N + p] = rv;
 }
 
+// Warm-start screening: instance b started from the learned prediction, instance B + b from the default
+// start xh0 = 0.  After both start-up passes the one with the smaller merit (a finite one; the default
+// start wins ties and failures of the prediction) continues in slot b.  Both screenings count as evaluations.
+__global__ void k_ws_select(ProbDev P, int B) {
+    const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    if (b >= B) return;
+    int* iw = P.ist + (size_t)b * INST_INTS;
+    int* iz = P.ist + (size_t)(B + b) * INST_INTS;
+    double* dw = P.dst + (size_t)b * INST_DBLS;
+    double* dz = P.dst + (size_t)(B + b) * INST_DBLS;
+    auto valid = [](const int* is, const double* ds) {
+        return (is[I_STATUS] == ST_RUNNING || is[I_STATUS] == DDNM_CONVERGED) && isfinite(ds[D_PHI0]);
+    };
+    const bool vw = valid(iw, dw), vz = valid(iz, dz);
+    const bool use_zero = !vw || (vz && !(dw[D_PHI0] < dz[D_PHI0]));
+    const int evals = iw[I_NEVALS] + iz[I_NEVALS];
+    __syncthreads();
+    if (use_zero) {
+        const size_t nD = P.n_D, nC = P.n_C;
+        for (size_t k = tid; k < nD; k += nth) {
+            P.x[b * nD + k] = P.x[(B + b) * nD + k];
+            P.xt[b * nD + k] = P.xt[(B + b) * nD + k];
+            P.s[b * nD + k] = P.s[(B + b) * nD + k];
+        }
+        for (size_t c = tid; c < nC; c += nth) {
+            P.lam[b * nC + c] = P.lam[(B + b) * nC + c];
+            P.lamt[b * nC + c] = P.lamt[(B + b) * nC + c];
+            P.slam[b * nC + c] = P.slam[(B + b) * nC + c];
+        }
+        if (tid < INST_DBLS) dw[tid] = dz[tid];
+        if (tid < INST_INTS) iw[tid] = iz[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        iw[I_NEVALS] = evals;
+        if (use_zero) iw[I_FLAGS] |= DDNM_FLAG_WS_FALLBACK;
+    }
+}
+
 // ------------------------------------------------------------------------ host drivers
 
 struct Launch {
@@ -1284,7 +1323,11 @@ struct Tmp {
 extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const double* x0, const double* lam0,
                                 double* x_out, double* lam_out, double* state_out, ddnm_stats* stats, int mem_kind,
                                 void* stream) {
-    int rc = prepare(ctx, B, mem_kind);
+    // learned warm start: instances [0, B) start from the MLP prediction, a shadow copy [B, 2B) from the
+    // default start; after the two start-up passes each instance keeps the start with the smaller merit
+    const bool ws = ctx && ctx->ws.enabled && !x0 && !lam0;
+    const int Bw = ws ? 2 * B : B;
+    int rc = prepare(ctx, Bw, mem_kind);
     if (rc) return rc;
     if (!mu) return ddnm_fail(ctx, DDNM_E_INVALID, "mu is NULL");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1294,7 +1337,12 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
     if ((rc = copy_in(ctx, P.mu, mu, (size_t)B * 2, mem_kind, st))) return rc;
     if (x0 && (rc = copy_in(ctx, P.x, x0, (size_t)B * P.n_D, mem_kind, st))) return rc;
     if (lam0 && (rc = copy_in(ctx, P.lam, lam0, (size_t)B * P.n_C, mem_kind, st))) return rc;
-    k_init<<<B, 128, 0, st>>>(P, B, x0 != nullptr, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0, fp64);
+    if (ws) {
+        CK(cudaMemcpyAsync(P.mu + (size_t)B * 2, P.mu, (size_t)B * 2 * 8, cudaMemcpyDeviceToDevice, st));
+        if ((rc = ddnm_ws_predict_dev(ctx, B, P.mu, P.x, nullptr, st))) return rc;
+        CK(cudaMemsetAsync(P.x + (size_t)B * P.n_D, 0, (size_t)B * P.n_D * 8, st));
+    }
+    k_init<<<Bw, 128, 0, st>>>(P, Bw, x0 != nullptr || ws, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0, fp64);
     CK(cudaGetLastError());
     ctx->tm.other_launches++;
     const int max_passes = 3 + ctx->opt.max_iter * (ctx->opt.max_backtracks + 1);
@@ -1304,15 +1352,23 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
     P.max_iter = ctx->opt.max_iter;
     P.max_bt = ctx->opt.max_backtracks;
     const int check_every = 4;
+    int Bp = Bw;                      // instances in the passes (2B during the warm-start screening)
     for (int pass = 0; pass < max_passes; ++pass) {
-        rc = fp64 ? launch_eval<double>(ctx, P, B, st) : launch_eval<float>(ctx, P, B, st);
+        rc = fp64 ? launch_eval<double>(ctx, P, Bp, st) : launch_eval<float>(ctx, P, Bp, st);
         if (rc) return rc;
         CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
         const int k = tstart(ctx, 2, st);
-        k_step<<<B, STEP_THREADS, ctx->step_smem, st>>>(P, B);
+        k_step<<<Bp, STEP_THREADS, ctx->step_smem, st>>>(P, Bp);
         CK(cudaGetLastError());
         tstop(ctx, k, st);
         ctx->tm.step_launches++;
+        if (ws && pass == 1) {        // both starts linearised: keep the better one per instance
+            k_ws_select<<<B, 128, 0, st>>>(P, B);
+            CK(cudaGetLastError());
+            ctx->tm.other_launches++;
+            Bp = B;
+            continue;
+        }
         if (pass % check_every == check_every - 1 || pass == max_passes - 1) {
             CK(cudaMemcpyAsync(ctx->h_active, P.active, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
