@@ -185,6 +185,96 @@ def workload_config(cfg):
             "stopping": "||F||_2 < 1e-4 or 15 SQP iterations (Sec. 7.1)"}
 
 
+# ------------------------------------------------------------------------ learned warm start (c4)
+
+def run_warmstart(args, lib, torch):
+    """MLP 2 -> 256 -> 256 -> n_D trained on 4096 SQP solutions of the 128x128 4x4 setup (paper's stopping
+    rule, default start), judged on 1024 held-out mu: iterations the SQP needs from the learned start to
+    reach the merit the default start ends with after 15 iterations, final merits, and solves/s of the
+    warm-started solve (mixed precision) next to the plain FP64 solve."""
+    wl = inputs.workload("c2")
+    B = wl.batch
+    s = lib.Solver(wl)
+    dec_o, dec_g = inputs.decoders_for(wl, [d["interior"] for d in s.subs], [d["interface"] for d in s.subs])
+    Cm = inputs.test_matrix(wl.n_c(), s.sizes.N_A)
+    s.load(dec_o, dec_g, Cm)
+    s.options()
+    nD = s.sizes.n_D
+
+    def solve_all(solver, mu):
+        xs, sts = [], []
+        for b0 in range(0, len(mu), B):
+            x, lam, st = solver.solve(mu[b0:b0 + B])
+            xs.append(x)
+            sts.append(st)
+        return np.concatenate(xs), np.concatenate(sts)
+
+    t0 = time.perf_counter()
+    mu_tr = inputs.mu_batch(4096, seed=1001)
+    x_tr, _ = solve_all(s, mu_tr)
+    t_data = time.perf_counter() - t0
+    H, epochs = 256, 60
+    lib.ddnm_ws_init(s.ctx, H, inputs.mlp_init(2, H, nD))
+    t0 = time.perf_counter()
+    losses = lib.ddnm_ws_train(s.ctx, mu_tr, x_tr, epochs, 64, 2e-3, inputs.mlp_order(4096, epochs))
+    t_train = time.perf_counter() - t0
+    mu_te = inputs.mu_batch(1024, seed=2002)
+
+    def timed(solver, mu):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st = solve_all(solver, mu)
+        torch.cuda.synchronize()
+        return len(mu) / (time.perf_counter() - t), st
+
+    lib.ddnm_ws_enable(s.ctx, False)
+    solve_all(s, mu_te[:B])
+    v_plain, st_plain = timed(s, mu_te)
+    lib.ddnm_ws_enable(s.ctx, True)
+    v_ws, st_ws = timed(s, mu_te)
+    reach = np.full(len(mu_te), -1)
+    for K in range(1, 16):
+        s.options(tol=0.0, max_iter=K)
+        _, st = solve_all(s, mu_te)
+        newly = (st["merit"] <= st_plain["merit"]) & (reach < 0)
+        reach[newly] = K
+    # throughput at equal final merit: the learned start with the iteration budget that reaches the
+    # default start's 15-iteration merit for every held-out instance
+    k_eq = int(reach.max()) if (reach > 0).all() else 15
+    s.options(tol=0.0, max_iter=k_eq)
+    v_ws_eq, st_ws_eq = timed(s, mu_te)
+    s.options()
+    lib.ddnm_ws_enable(s.ctx, False)
+    # plain FP64 solve of the same workload on the same GPU
+    s64 = lib.Solver(wl, precision=lib.DDNM_FP64)
+    s64.load(dec_o, dec_g, Cm)
+    s64.options()
+    solve_all(s64, mu_te[:B])
+    v_fp64, st_fp64 = timed(s64, mu_te[:256])
+    reached = reach > 0
+    line = {"metric": METRIC, "value": v_ws, "unit": UNIT, "n_gpus": 1, "steps": len(mu_te) // B, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 KKT",
+            "data": "synthetic",
+            "config": {"workload": "c4: learned warm start on the 128x128 4x4 setup, MLP 2-256-256-144 (bf16 "
+                                   "weights, fp32 accumulation), 4096 training solutions, 1024 held-out mu"},
+            "warm_start": {"train_seconds": t_train, "data_seconds": t_data, "epochs": epochs,
+                           "loss_first_last": [float(losses[0]), float(losses[-1])],
+                           "fraction_reaching_plain_final_merit": float(reached.mean()),
+                           "mean_iters_to_plain_final_merit": float(reach[reached].mean()) if reached.any() else None,
+                           "plain_iters": float(st_plain["iters"].mean()),
+                           "median_final_merit_plain": float(np.median(st_plain["merit"])),
+                           "median_final_merit_warm": float(np.median(st_ws["merit"])),
+                           "fallback_fraction": float(np.mean(st_ws["flags"] & lib.DDNM_FLAG_WS_FALLBACK > 0)),
+                           "solves_per_s_plain_mixed": v_plain, "solves_per_s_warm_mixed": v_ws,
+                           "equal_merit_iters": k_eq, "solves_per_s_warm_mixed_equal_merit": v_ws_eq,
+                           "equal_merit_holds": bool(np.all(st_ws_eq["merit"] <= st_plain["merit"])),
+                           "solves_per_s_plain_fp64": v_fp64,
+                           "median_final_merit_plain_fp64": float(np.median(st_fp64["merit"]))}}
+    print(json.dumps(line))
+    s.close()
+    s64.close()
+
+
 # ------------------------------------------------------------------------ our arm
 
 def main():
@@ -202,6 +292,9 @@ def main():
     import torch
     import paper_2305_15163_gb300 as lib
 
+    if args.config == "c4":
+        torch.cuda.set_device(0)
+        return run_warmstart(args, lib, torch)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

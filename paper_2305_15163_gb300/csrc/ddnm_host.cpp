@@ -55,6 +55,7 @@ extern "C" int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out) {
         !p->hr_count || !p->hr_rows)
         return bail(DDNM_E_INVALID, "missing or non-positive problem fields");
     if (p->kx * p->ky < 2) return bail(DDNM_E_UNSUPPORTED, "at least two subdomains are needed (WFPC constraints)");
+    if (p->kx * p->ky > MAX_SUB) return bail(DDNM_E_UNSUPPORTED, "at most 256 subdomains");
     if (p->device < 0) return bail(DDNM_E_INVALID, "negative device ordinal");
     if (!(p->nu > 0) || !(p->box[1] > p->box[0]) || !(p->box[3] > p->box[2]))
         return bail(DDNM_E_INVALID, "nu and the box must be positive");
@@ -624,6 +625,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     size_t o_s = o; o = al(o + (size_t)cap * pd.n_D * 8);
     size_t o_slam = o; o = al(o + (size_t)cap * pd.n_C * 8);
     size_t o_At = o; o = al(o + (size_t)cap * pd.n_split * pd.n_C * 8);
+    size_t o_Ss = o; o = al(o + (size_t)cap * ((size_t)pd.n_C * pd.n_C + pd.n_C) * 8);
     size_t o_dst = o; o = al(o + (size_t)cap * INST_DBLS * 8);
     size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
     size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * tsize);
@@ -646,6 +648,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     pd.s = (double*)(base + o_s);
     pd.slam = (double*)(base + o_slam);
     pd.Atil = (double*)(base + o_At);
+    pd.Ssum = (double*)(base + o_Ss);
     pd.dst = (double*)(base + o_dst);
     pd.ist = (int*)(base + o_ist);
     pd.bnd = (void*)(base + o_bnd);

@@ -11,6 +11,7 @@ constexpr int MAX_NI = 16;     // n_i^O + n_i^G per subdomain
 constexpr int MAX_NG = 8;      // n_i^G
 constexpr int MAX_K = 64;      // ELL slots of a decoder output row
 constexpr int MAX_NC = 128;    // weak constraints
+constexpr int MAX_SUB = 256;   // subdomains
 constexpr int EVAL_THREADS = 256;
 constexpr int STEP_THREADS = 256;
 constexpr int CON_THREADS = 256;
@@ -26,7 +27,10 @@ constexpr int HR_INTS = 7;     // comp, then operands: centre, E, W, N, S (same 
 // per-instance solver state
 enum { MODE_INIT0 = 0, MODE_INIT1 = 1, MODE_LS = 2 };
 constexpr int ST_RUNNING = -1;
-enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_KKTFAIL, I_PAD, INST_INTS };
+enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_XTMODE, I_PAD, INST_INTS };
+// how the next evaluation forms its trial point xt (ist[I_XTMODE]): unchanged (xt = x), a new SQP step
+// (each subdomain back-substitutes s_i from s_lambda, then xt = x + s), or a backtrack (xt = x + alpha s)
+enum { XT_KEEP = 0, XT_NEWSTEP = 1, XT_BACKTRACK = 2 };
 enum { D_PHI0 = 0, D_ALPHA, D_PHI, D_ALPHA_LAST, INST_DBLS };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
@@ -123,6 +127,7 @@ struct ProbDev {
     double* s;
     double* slam;
     double* Atil;                  // B x n_split x n_C partial sums of C * jump
+    double* Ssum;                  // B x (n_C^2 + n_C): sum over the PD subdomains of S_i (full) and u_i
     double* dst;                   // INST_DBLS per instance
     int* ist;                      // INST_INTS per instance
     void* bnd;                     // B x n_bnd x 2 (u, v) Dirichlet data, value type

@@ -216,6 +216,75 @@ __device__ __forceinline__ float cst<float>(const ProbDev& P, int k) { return P.
 template <>
 __device__ __forceinline__ double cst<double>(const ProbDev& P, int k) { return P.cst[k]; }
 
+// Trial point of this subdomain for the coming evaluation (ist[I_XTMODE]).  On a new SQP step the
+// subdomain back-substitutes its own piece of the KKT solution of Eq. (sqp_system) from s_lambda, with the
+// L D L^T factors of the accepted evaluation: s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda]) when H_i is PD,
+// s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G) with s_G from the step kernel when H_i is singular in its G
+// block.  Then xt_i = x_i + alpha s_i (Eq. sqp_update); alpha = 1 on a new step.
+__device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z) {
+    const int xm = P.ist[(size_t)b * INST_INTS + I_XTMODE];
+    if (xm == XT_KEEP) return;
+    const int tid = threadIdx.x, nC = P.n_C, ni = S.ni, nO = S.nO, nG = S.nG;
+    const double* x = P.x + (size_t)b * P.n_D + S.xoff;
+    double* xt = P.xt + (size_t)b * P.n_D + S.xoff;
+    double* s = P.s + (size_t)b * P.n_D + S.xoff;
+    if (xm == XT_NEWSTEP) {
+        if (tid < 32) {
+            const int lane = tid;
+            const double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
+            const BlkLayout BL = blk_layout(ni, nG, nC);
+            const double* Li = blk + BL.L;
+            const double* ri = blk + BL.rinv;
+            const double* ti = blk + BL.t;
+            const double* Wi = blk + BL.W;
+            const double* y = P.slam + (size_t)b * nC;
+            int nb;
+            if (blk[BL.flag] == FLAG_PD) {
+                double part[MAX_NG];
+#pragma unroll
+                for (int k = 0; k < MAX_NG; ++k) part[k] = 0.0;
+                for (int c = lane; c < nC; c += 32) {
+                    const double yc = y[c];
+#pragma unroll
+                    for (int k = 0; k < MAX_NG; ++k)
+                        if (k < nG) part[k] += Wi[k * nC + c] * yc;
+                }
+#pragma unroll
+                for (int k = 0; k < MAX_NG; ++k)
+                    if (k < nG) part[k] = warp_sum(part[k]);
+                if (lane < ni) {
+                    double v = ti[lane];
+#pragma unroll
+                    for (int k = 0; k < MAX_NG; ++k)
+                        if (k < nG && lane == nO + k) v += part[k];
+                    z[lane] = v * ri[lane];
+                }
+                nb = ni;
+            } else {
+                if (lane < nO) {
+                    double v = ti[lane] * ri[lane];
+                    for (int k = 0; k < nG; ++k) v += Li[(nO + k) * ni + lane] * s[nO + k];
+                    z[lane] = v;
+                }
+                nb = nO;
+            }
+            for (int k = nb - 1; k >= 0; --k) {
+                __syncwarp();
+                const double zk = z[k];
+                if (lane < k) z[lane] -= Li[k * ni + lane] * zk;
+            }
+            __syncwarp();
+            if (lane < nb) s[lane] = -z[lane];
+        }
+        __syncthreads();
+        if (tid < ni) xt[tid] = x[tid] + s[tid];
+    } else {
+        const double alpha = P.dst[(size_t)b * INST_DBLS + D_ALPHA];
+        if (tid < ni) xt[tid] = x[tid] + alpha * s[tid];
+    }
+    __syncthreads();
+}
+
 // One (instance, subdomain) evaluation.  RO = round4(n^O + 1) and RG = round4(n^G + 1) are the padded
 // widths of the [value, Jacobian row] records; they are compile-time so that every inner loop has a fixed
 // trip count (no predicated-off lanes).  Chunked over the collocation rows so that shared memory stays
@@ -249,6 +318,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
     // latent coordinates and multipliers of the trial point
+    form_trial(P, S, b, dt);
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
     for (int c = tid; c < nC; c += nth) dlam[c] = P.lamt[(size_t)b * nC + c];
     __syncthreads();
@@ -637,6 +707,47 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
         acc = warp_sum(acc);
         if (lane == 0) out[c] = acc;
     }
+    // this slice's share of the Schur sums over the subdomains with H_i PD: S = sum_i S_i (lower
+    // triangle, mirrored) and sum_i u_i, for the step kernel
+    __shared__ unsigned char pd[MAX_SUB];
+    const int nC = P.n_C, ns = P.n_sub;
+    const double* blk = P.blk + (size_t)b * P.blk_stride;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        const SubDev& S = P.sub[i];
+        pd[i] = blk[S.blk + blk_layout(S.ni, S.nG, nC).flag] == FLAG_PD;
+    }
+    __syncthreads();
+    const int ntri = nC * (nC + 1) / 2, NE = ntri + nC;
+    const int per = (NE + P.n_split - 1) / P.n_split;
+    double* Ss = P.Ssum + (size_t)b * ((size_t)nC * nC + nC);
+    for (int e = sp * per + threadIdx.x; e < min(NE, (sp + 1) * per); e += blockDim.x) {
+        int off_in_blk, c1 = -1, c2 = 0;
+        if (e < ntri) {
+            int rem = e;
+            c1 = 0;
+            while (rem > c1) {
+                rem -= c1 + 1;
+                ++c1;
+            }
+            c2 = rem;
+        }
+        double v0 = 0.0, v1 = 0.0;
+        for (int i = 0; i < ns; ++i) {
+            if (!pd[i]) continue;
+            const SubDev& S = P.sub[i];
+            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+            off_in_blk = c1 >= 0 ? BL.S + c1 * nC + c2 : BL.u + (e - ntri);
+            if (i & 1) v1 += blk[S.blk + off_in_blk];
+            else v0 += blk[S.blk + off_in_blk];
+        }
+        const double v = v0 + v1;
+        if (c1 >= 0) {
+            Ss[c1 * nC + c2] = v;
+            Ss[c2 * nC + c1] = v;
+        } else {
+            Ss[(size_t)nC * nC + (e - ntri)] = v;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------ SQP step
@@ -644,7 +755,6 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
 __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     extern __shared__ __align__(16) double sm[];
     __shared__ double scratch[32];
-    __shared__ double zb[STEP_THREADS / 32][MAX_NI];
     const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     if (b >= B) return;
     int* ist = P.ist + (size_t)b * INST_INTS;
@@ -725,6 +835,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
         if (tid == 0) {
             ist[I_MODE] = MODE_INIT1;
+            ist[I_XTMODE] = XT_KEEP;
             atomicAdd(P.active, 1);
         }
         return;
@@ -741,11 +852,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     }
     if (!accept) {
         const double a = alpha * P.beta;
-        for (int k = tid; k < nD; k += nth) xt[k] = x_[k] + a * s_[k];
         for (int c = tid; c < nC; c += nth) lamt[c] = lam[c] + a * slam[c];
         if (tid == 0) {
             dst[D_ALPHA] = a;
             ist[I_NBT] = nbt + 1;
+            ist[I_XTMODE] = XT_BACKTRACK;       // the evaluation forms xt = x + alpha s
             atomicAdd(P.active, 1);
         }
         return;
@@ -780,13 +891,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     //   s_lambda = L_S^{-T} D_S^{-1} (q + Z s_F).
     __shared__ int s_nF, s_mF, s_over;
     __shared__ int fsub[MAX_MF], fcol_sub[MAX_MF], fcol_k[MAX_MF];
-    __shared__ int sflag[64];
     if (tid == 0) {
         int nF = 0, mF = 0, over = 0;
         for (int i = 0; i < ns; ++i) {
             const SubDev& S = P.sub[i];
             const int fl = (int)blk[S.blk + blk_layout(S.ni, S.nG, nC).flag];
-            if (i < 64) sflag[i] = fl;
             if (fl == 2) {
                 if (mF + S.nG > MAX_MF) {
                     over = 1;
@@ -802,7 +911,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         }
         s_nF = nF;
         s_mF = mF;
-        s_over = over || ns > 64;
+        s_over = over;
     }
     __syncthreads();
     const int nF = s_nF, mF = s_mF;
@@ -810,48 +919,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
         return;
     }
-    // S (lower triangle, mirrored) and r: the subdomain loads of each entry are independent
-    for (int e = tid; e < nC * (nC + 1) / 2 + nC; e += nth) {
-        int c1 = -1, c2 = 0;
-        if (e < nC * (nC + 1) / 2) {
-            int rem = e;
-            c1 = 0;
-            while (rem > c1) {
-                rem -= c1 + 1;
-                ++c1;
-            }
-            c2 = rem;
-        }
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-        int i = 0;
-        for (; i + 3 < ns; i += 4) {
-            double w[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const SubDev& S = P.sub[i + u];
-                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-                w[u] = sflag[i + u] != 0 ? 0.0
-                       : (c1 >= 0 ? blk[S.blk + BL.S + c1 * nC + c2] : blk[S.blk + BL.u + (e - nC * (nC + 1) / 2)]);
-            }
-            v0 += w[0];
-            v1 += w[1];
-            v2 += w[2];
-            v3 += w[3];
-        }
-        for (; i < ns; ++i) {
-            const SubDev& S = P.sub[i];
-            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-            if (sflag[i] == 0)
-                v0 += c1 >= 0 ? blk[S.blk + BL.S + c1 * nC + c2] : blk[S.blk + BL.u + (e - nC * (nC + 1) / 2)];
-        }
-        const double v = (v0 + v1) + (v2 + v3);
-        if (c1 >= 0) {
-            Sm[c1 * nC + c2] = v;
-            Sm[c2 * nC + c1] = v;
-        } else {
-            const int c = e - nC * (nC + 1) / 2;
-            rhs[c] = At[c] - v;
-        }
+    // S and r = Atil - sum_i u_i from the sums the constraint kernel formed over the PD subdomains
+    {
+        const double* Ss = P.Ssum + (size_t)b * ((size_t)nC * nC + nC);
+        for (int e = tid; e < nC * nC; e += nth) Sm[e] = Ss[e];
+        for (int c = tid; c < nC; c += nth) rhs[c] = At[c] - Ss[(size_t)nC * nC + c];
     }
     if (!block_ldl(Sm, rv, nC)) {
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
@@ -921,67 +993,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         }
         __syncthreads();
     }
-    // per-subdomain steps, one warp per subdomain (H_i = L D L^T):
-    //   H_i PD:           s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda])
-    //   G-singular (F):   s_G from s_F,  s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G)
-    {
-        const int w = tid >> 5, lane = tid & 31, nw = nth >> 5;
-        double* z = zb[w];
-        for (int i = w; i < ns; i += nw) {
-            const SubDev& S = P.sub[i];
-            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-            const double* Li = blk + S.blk + BL.L;
-            const double* ri = blk + S.blk + BL.rinv;
-            const double* ti = blk + S.blk + BL.t;
-            const double* Wi = blk + S.blk + BL.W;
-            const bool sing = sflag[i] == 2;
-            int nb = S.ni;                    // rows solved by back-substitution
-            if (!sing) {
-                double part[MAX_NG];
-#pragma unroll
-                for (int k = 0; k < MAX_NG; ++k) part[k] = 0.0;
-                for (int c = lane; c < nC; c += 32) {
-                    const double yc = rhs[c];
-#pragma unroll
-                    for (int k = 0; k < MAX_NG; ++k)
-                        if (k < S.nG) part[k] += Wi[k * nC + c] * yc;
-                }
-#pragma unroll
-                for (int k = 0; k < MAX_NG; ++k)
-                    if (k < S.nG) part[k] = warp_sum(part[k]);
-                if (lane < S.ni) {
-                    double v = ti[lane];
-#pragma unroll
-                    for (int k = 0; k < MAX_NG; ++k)
-                        if (k < S.nG && lane == S.nO + k) v += part[k];
-                    z[lane] = v * ri[lane];
-                }
-            } else {
-                int a0 = 0;
-                for (int f = 0; f < nF; ++f) {
-                    if (fsub[f] == i) break;
-                    a0 += P.sub[fsub[f]].nG;
-                }
-                if (lane < S.nG) s_[S.xoff + S.nO + lane] = sF[a0 + lane];
-                if (lane < S.nO) {
-                    double v = ti[lane] * ri[lane];
-                    for (int k = 0; k < S.nG; ++k) v += Li[(S.nO + k) * S.ni + lane] * sF[a0 + k];
-                    z[lane] = v;
-                }
-                nb = S.nO;
-            }
-            for (int k = nb - 1; k >= 0; --k) {
-                __syncwarp();
-                const double zk = z[k];
-                if (lane < k) z[lane] -= Li[k * S.ni + lane] * zk;
-            }
-            __syncwarp();
-            if (lane < nb) s_[S.xoff + lane] = -z[lane];
-            __syncwarp();
-        }
+    // interface steps of the G-singular subdomains; every other piece of s is back-substituted by the
+    // evaluation of the subdomain itself (form_trial)
+    for (int a = tid; a < mF; a += nth) {
+        const SubDev& S = P.sub[fcol_sub[a]];
+        s_[S.xoff + S.nO + fcol_k[a]] = sF[a];
     }
     __syncthreads();
-    for (int k = tid; k < nD; k += nth) xt[k] = x_[k] + s_[k];
     for (int c = tid; c < nC; c += nth) {
         slam[c] = rhs[c];
         lamt[c] = lam[c] + rhs[c];
@@ -990,6 +1008,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
         dst[D_ALPHA] = 1.0;
         ist[I_NBT] = 0;
         ist[I_MODE] = MODE_LS;
+        ist[I_XTMODE] = XT_NEWSTEP;
         atomicAdd(P.active, 1);
     }
 }
@@ -1034,6 +1053,7 @@ __global__ void k_init(ProbDev P, int B, int has_x0, int has_lam0, int mode, int
         ist[I_NBT] = 0;
         ist[I_FLAGS] = 0;
         ist[I_NEVALS] = 0;
+        ist[I_XTMODE] = XT_KEEP;
         double* dst = P.dst + (size_t)b * INST_DBLS;
         dst[D_PHI0] = 0.0;
         dst[D_ALPHA] = 1.0;
@@ -1190,6 +1210,9 @@ __global__ void k_ws_select(ProbDev P, int B) {
             P.lamt[b * nC + c] = P.lamt[(B + b) * nC + c];
             P.slam[b * nC + c] = P.slam[(B + b) * nC + c];
         }
+        const double* bz = P.blk + (size_t)(B + b) * P.blk_stride;
+        double* bw = P.blk + (size_t)b * P.blk_stride;
+        for (int k = tid; k < P.blk_stride; k += nth) bw[k] = bz[k];
         if (tid < INST_DBLS) dw[tid] = dz[tid];
         if (tid < INST_INTS) iw[tid] = iz[tid];
     }
@@ -1615,6 +1638,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     const size_t o_gG = o; o = al(o + (size_t)B * P.sum_NG * tsize);
     const size_t o_blk = o; o = al(o + (size_t)B * P.blk_stride * 8);
     const size_t o_At = o; o = al(o + (size_t)B * P.n_split * P.n_C * 8);
+    const size_t o_Ss = o; o = al(o + (size_t)B * ((size_t)P.n_C * P.n_C + P.n_C) * 8);
     const size_t o_lz = o; o = al(o + (size_t)B * P.n_C * 8);
     if (o > DDNM_NOALLOC_SCRATCH_BYTES) {
         const size_t per = o / B + 1;
@@ -1638,6 +1662,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     P.gG = (void*)(s + o_gG);
     P.blk = (double*)(s + o_blk);
     P.Atil = (double*)(s + o_At);
+    P.Ssum = (double*)(s + o_Ss);
     P.r_hr = nullptr;
     if (lam) {
         P.lamt = const_cast<double*>(lam);  // read only by k_eval
