@@ -309,6 +309,52 @@ int ddnm_ws_enable(ddnm_ctx* ctx, int on);
 int ddnm_ws_save(const ddnm_ctx* ctx, const char* path);
 int ddnm_ws_load(ddnm_ctx* ctx, const char* path);
 
+/* ---- Launch plan (batching of many mu and uneven subdomains) ----
+ * By default ddnm_solve_batch queues the whole SQP loop of a batch as ONE CUDA
+ * graph launch.  The graph runs the start-up passes of Sec. 4.1 / 7.2 (and the
+ * warm-start screening), then splits the batch into `chains` groups of
+ * consecutive instances.  Each group iterates in its own device-side while
+ * loop, a conditional graph node.  The loop stops when every instance of the
+ * group has finished, and at the latest after 3 + max_iter * (max_backtracks
+ * + 1) passes.  One group's small FP64 KKT kernels then overlap another
+ * group's evaluation.
+ * Inside a pass, each width class of subdomains (equal padded latent widths) is
+ * one evaluation launch.  With eval_persist > 0 that launch is persistent:
+ * eval_persist CTAs per SM claim (instance, subdomain) items from a device
+ * counter, largest subdomains first.
+ * Results do not depend on the plan, bit for bit: instances are independent, and every kernel sums in
+ * a fixed order.  Atil in particular is one pairwise tree over 512-row blocks of the constraint rows,
+ * whatever con_split is.  The graph is captured on first use and
+ * re-captured when B, the options, the plan or the device tables change.
+ * Per-kernel timing (ddnm_timing_enable) runs the host-driven loop instead. */
+typedef struct ddnm_tune {
+    int graph;          /* 1: graph-resident loop (default); 0: host-driven passes */
+    int chains;         /* instance groups iterating concurrently, 1..16 (capped at B) */
+    int con_split;      /* constraint rows per constraint CTA: 512, 1024 or 2048 */
+    int eval_persist;   /* persistent evaluation: CTAs per SM per width class (1..8), or 0 for one CTA per item */
+} ddnm_tune;
+
+/* Set / read the plan.  DDNM_E_INVALID outside the ranges above. */
+int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t);
+int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t);
+
+/* Autotuner: times ddnm_solve_batch on this batch (B, mu; mem_kind as in
+ * ddnm_solve_batch) under candidate plans and keeps the fastest in ctx.
+ *  - Each candidate gets one untimed solve, then `reps` solves timed with CUDA
+ *    events on `stream`; the median decides.
+ *  - The search is coordinate-wise:
+ *      chains       in {1, 2, 4, 8, 16}, capped at B;
+ *      eval_persist in {0, 1, 2, 4};
+ *      con_split    in {512, 1024, 2048}.
+ *    Each knob is swept with the best values found so far for the others.
+ *  - max_iter > 0 caps the SQP iterations of the timed solves, to keep tuning
+ *    short (the options are restored on return).
+ *  - best (may be NULL) receives the chosen plan, best_ms (may be NULL) its
+ *    median time per solve call.
+ * No result of a tuning solve is returned. */
+int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kind, void* stream, int max_iter, int reps,
+                  ddnm_tune* best, float* best_ms);
+
 /* Turn per-kernel timing on (resets the counters) or off.  While on, every
  * compute call synchronises its stream before returning. */
 int ddnm_timing_enable(ddnm_ctx* ctx, int on);

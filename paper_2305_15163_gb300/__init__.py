@@ -72,6 +72,10 @@ class ddnm_work(C.Structure):
                 ("constraint_fp64_flops", C.c_double), ("step_fp64_flops", C.c_double)]
 
 
+class ddnm_tune(C.Structure):
+    _fields_ = [("graph", C.c_int), ("chains", C.c_int), ("con_split", C.c_int), ("eval_persist", C.c_int)]
+
+
 STATS_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("flags", np.int32),
                         ("n_evals", np.int32), ("merit", np.float64), ("alpha_last", np.float64)])
 
@@ -102,6 +106,10 @@ _sig = {
     "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
     "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
+    "ddnm_set_tune": (C.c_int, [_vp, C.POINTER(ddnm_tune)]),
+    "ddnm_get_tune": (C.c_int, [_vp, C.POINTER(ddnm_tune)]),
+    "ddnm_autotune": (C.c_int, [_vp, C.c_int, _vp, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(ddnm_tune),
+                                C.POINTER(C.c_float)]),
 }
 for _n, (_res, _args) in _sig.items():
     _f = getattr(_lib, _n)
@@ -318,6 +326,27 @@ def ddnm_get_work(ctx) -> dict:
     w = ddnm_work()
     _check(ctx, _lib.ddnm_get_work(ctx, C.byref(w)))
     return {k: getattr(w, k) for k, _ in ddnm_work._fields_}
+
+
+def ddnm_set_tune(ctx, graph=1, chains=1, con_split=512, eval_persist=0):
+    t = ddnm_tune(int(graph), int(chains), int(con_split), int(eval_persist))
+    _check(ctx, _lib.ddnm_set_tune(ctx, C.byref(t)))
+
+
+def ddnm_get_tune(ctx) -> dict:
+    t = ddnm_tune()
+    _check(ctx, _lib.ddnm_get_tune(ctx, C.byref(t)))
+    return {k: getattr(t, k) for k, _ in ddnm_tune._fields_}
+
+
+def ddnm_autotune(ctx, mu, max_iter=0, reps=3, stream=None):
+    """Autotune the launch plan on host mu (B x 2); returns (plan dict, median ms per solve)."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    t = ddnm_tune()
+    ms = C.c_float()
+    _check(ctx, _lib.ddnm_autotune(ctx, int(mu.shape[0]), mu.ctypes.data, DDNM_MEM_HOST, stream, int(max_iter),
+                                   int(reps), C.byref(t), C.byref(ms)))
+    return {k: getattr(t, k) for k, _ in ddnm_tune._fields_}, float(ms.value)
 
 
 # ------------------------------------------------------------------ convenience wrapper

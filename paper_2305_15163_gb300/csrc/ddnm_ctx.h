@@ -101,6 +101,19 @@ struct ddnm_ctx {
     std::vector<int> event_kind;       // 0 eval, 1 constraint, 2 step for each recorded pair
     size_t n_events = 0;               // pairs in use for the current call
 
+    // launch plan and the captured solve graph (ddnm_kernels.cu)
+    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0};
+    long long gen = 0;                 // bumped whenever device tables or workspace pointers change
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<long long> gkey;       // what the captured graph was built for
+    cudaStream_t cap_main = nullptr, cap_body = nullptr;   // capture streams
+    int n_sm = 0;
+    int* h_pass = nullptr;             // pinned: loop passes per instance group of the last graph solve
+    cudaEvent_t pass_ev = nullptr;
+    bool pass_pending = false;
+    int pending_chains = 0, pending_classes = 0;
+
     std::string err;
 };
 
@@ -109,5 +122,6 @@ int ddnm_fail(ddnm_ctx* ctx, int code, const std::string& msg);
 int ddnm_finalize(ddnm_ctx* ctx);
 int ddnm_reserve(ddnm_ctx* ctx, int B);
 void ddnm_release_events(ddnm_ctx* ctx);
+void ddnm_release_graph(ddnm_ctx* ctx);
 void ddnm_ws_release(ddnm_ctx* ctx);
 int ddnm_ws_predict_dev(ddnm_ctx* ctx, int B, const double* mu_dev, double* x0_dev, int* fell_back, cudaStream_t st);

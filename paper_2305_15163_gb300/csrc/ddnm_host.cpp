@@ -270,6 +270,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_classes);
     cudaFree(ctx->d_ws);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
+    ddnm_release_graph(ctx);
     ddnm_release_events(ctx);
     ddnm_ws_release(ctx);
     delete ctx;
@@ -544,6 +545,13 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 }
             }
             c.n = (int)cls.size() - c.off;
+            // largest subdomains first: the persistent evaluation hands out items in this order
+            auto cost = [&](int s) {
+                const SubDev& S = ctx->hsub[s];
+                return (double)ctx->nnzO[s] * (S.nO + 1) + (double)ctx->nnzG[s] * (S.nG + 1) +
+                       (double)S.NB * S.ni * (S.ni + 6);
+            };
+            std::stable_sort(cls.begin() + c.off, cls.end(), [&](int a, int b) { return cost(a) > cost(b); });
             if (c.n) ctx->eval_classes.push_back(c);
         }
     if ((int)cls.size() != ns) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "latent dims outside the kernel classes");
@@ -593,6 +601,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.n_sub = ns; pd.n_D = ctx->n_D; pd.n_C = nC; pd.N_A = ctx->N_A;
     pd.sum_NG = ctx->sum_NG; pd.sum_NB = ctx->sum_NB; pd.n_bnd = (int)ctx->bnd_ij.size() / 2;
     pd.N_x = 2 * ctx->N; pd.nx = ctx->nx; pd.ny = ctx->ny;
+    pd.con_split = CON_SPLIT;
     pd.n_split = (ctx->N_A + CON_SPLIT - 1) / CON_SPLIT;
     pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
     pd.cst[0] = 0.5 / ctx->hx;
@@ -605,6 +614,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.hr = ctx->d_hr;
     pd.con_lo = ctx->d_con; pd.con_hi = ctx->d_con + ctx->N_A; pd.C = ctx->d_C; pd.bnd_ij = ctx->d_bnd_ij;
     ctx->cap_B = 0;   // workspace pointers are re-carved on the next reserve
+    ++ctx->gen;
     ctx->finalized = true;
     return DDNM_OK;
 }
@@ -624,14 +634,15 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     size_t o_lamt = o; o = al(o + (size_t)cap * pd.n_C * 8);
     size_t o_s = o; o = al(o + (size_t)cap * pd.n_D * 8);
     size_t o_slam = o; o = al(o + (size_t)cap * pd.n_C * 8);
-    size_t o_At = o; o = al(o + (size_t)cap * pd.n_split * pd.n_C * 8);
+    const size_t max_split = ((size_t)pd.N_A + MIN_CON_SPLIT - 1) / MIN_CON_SPLIT;   // any con_split of the plan
+    size_t o_At = o; o = al(o + (size_t)cap * max_split * pd.n_C * 8);
     size_t o_Ss = o; o = al(o + (size_t)cap * ((size_t)pd.n_C * pd.n_C + pd.n_C) * 8);
     size_t o_dst = o; o = al(o + (size_t)cap * INST_DBLS * 8);
     size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
     size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * tsize);
     size_t o_gG = o; o = al(o + (size_t)cap * pd.sum_NG * tsize);
     size_t o_blk = o; o = al(o + (size_t)cap * pd.blk_stride * 8);
-    size_t o_act = o; o = al(o + 64);
+    size_t o_act = o; o = al(o + (size_t)CTL_INTS * 4);
     cudaFree(ctx->d_ws);
     ctx->d_ws = nullptr;
     ctx->cap_B = 0;
@@ -655,7 +666,10 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     pd.gG = (void*)(base + o_gG);
     pd.blk = (double*)(base + o_blk);
     pd.active = (int*)(base + o_act);
+    pd.pass = pd.active + MAX_CHAINS;
+    pd.ctr = pd.pass + MAX_CHAINS;
     ctx->cap_B = cap;
+    ++ctx->gen;   // captured solve graphs hold workspace pointers
     return DDNM_OK;
 }
 

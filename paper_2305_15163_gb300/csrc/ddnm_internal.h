@@ -15,7 +15,11 @@ constexpr int MAX_SUB = 256;   // subdomains
 constexpr int EVAL_THREADS = 256;
 constexpr int STEP_THREADS = 256;
 constexpr int CON_THREADS = 256;
-constexpr int CON_SPLIT = 512; // constraint rows per constraint CTA (the N_A axis is split)
+constexpr int CON_SPLIT = 512; // default constraint rows per constraint CTA (the N_A axis is split)
+constexpr int CON_BLOCK = 512;  // constraint rows of one canonical partial of Atil (fixes the summation order)
+constexpr int MIN_CON_SPLIT = CON_BLOCK, MAX_CON_SPLIT = 4 * CON_BLOCK;
+constexpr int MAX_CHAINS = 16; // instance groups iterating concurrently inside the solve graph
+constexpr int MAX_CLASSES = 12; // width classes (RO, RG) of the evaluation kernel
 constexpr int HR_CHUNK = 128;  // collocation rows per evaluation chunk (bounds shared memory)
 
 // HR stencil operand codes: (kind << 28) | index
@@ -102,7 +106,8 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
 struct ProbDev {
     int n_sub, n_D, n_C, N_A, sum_NG, sum_NB, n_bnd, N_x;
     int nx, ny;
-    int n_split;                   // constraint CTAs per instance (ceil(N_A / CON_SPLIT))
+    int n_split;                   // constraint CTAs per instance (ceil(N_A / con_split))
+    int con_split;                 // constraint rows per constraint CTA
     double hx, hy, nu, bx0, by0;
     double cst[4];                 // stencil constants 1/(2h_x), 1/(2h_y), nu/h_x^2, nu/h_y^2 (from the host)
     float cstf[4];                 // the same in FP32
@@ -135,7 +140,13 @@ struct ProbDev {
     double* blk;                   // B x blk_stride
     double* r_hr;                  // optional output B x sum_NB
     int* active;                   // count of running instances after a step pass
+    int* pass;                     // loop passes of the solve graph's instance group
+    int* ctr;                      // MAX_CLASSES work counters of the persistent evaluation
 };
+
+// Control area at the end of the workspace: per instance group, the running count, the loop passes and the
+// persistent evaluation's work counters.
+constexpr int CTL_INTS = MAX_CHAINS * (2 + MAX_CLASSES);
 
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {

@@ -60,6 +60,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // sum over the CTA; every thread gets the result
+// v[0], v[s], ..., v[(n-1)s] summed as a pairwise tree over the values padded with zeros to a power of
+// two (adding the zero subtrees is exact, so a slice of the tree computed elsewhere can be passed in as
+// one value).  Streaming form: a stack of complete subtrees, merged like a binary counter.
+__device__ double tree_sum(const double* v, int n, size_t s) {
+    double stk[33];
+    int top = 0;
+    for (int i = 0; i < n; ++i) {
+        double x = v[(size_t)i * s];
+        for (int k = i; k & 1; k >>= 1) x = stk[--top] + x;
+        stk[top++] = x;
+    }
+    double acc = top ? stk[--top] : 0.0;
+    while (top) acc = stk[--top] + acc;
+    return acc;
+}
+
 __device__ double block_sum(double v, double* scratch /* >= 32 */) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
@@ -658,20 +674,39 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
 }
 
-// One launch per class of subdomains sharing the padded record widths (RO, RG): CTA = (instance,
-// subdomain of the class), subs = the class's subdomain indices.
+// One launch per class of subdomains sharing the padded record widths (RO, RG).  Items are (instance,
+// subdomain of the class); item k is instance k % B of subdomain subs[k / B] (subs: the class's subdomains,
+// largest first).  With ctr == NULL CTA k takes item k; otherwise the grid is persistent and its CTAs claim
+// items from the counter *ctr (zero before the launch) until none are left.
 template <typename T, int RO, int RG>
-__global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B, const int* subs, int nsub) {
+__global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int b = blockIdx.x / nsub, si = subs[blockIdx.x - (blockIdx.x / nsub) * nsub];
-    if (b >= B) return;
-    if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
-    eval_item<T, RO, RG>(P, P.sub[si], b, smem);
+    const int items = B * nsub;
+    if (!ctr) {
+        const int k = blockIdx.x;
+        if (k >= items) return;
+        const int b = k % B;
+        if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
+        eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, smem);
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+        __syncthreads();
+        const int k = s_item;
+        __syncthreads();                  // every thread has its item before s_item is claimed again
+        if (k >= items) return;
+        const int b = k % B;
+        if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) continue;
+        eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, smem);
+        __syncthreads();                  // shared memory is reused by the next item
+    }
 }
 
 // host side: the kernel of a width class
 template <typename T>
-using EvalKernel = void (*)(ProbDev, int, const int*, int);
+using EvalKernel = void (*)(ProbDev, int, const int*, int, int*);
 
 template <typename T>
 EvalKernel<T> eval_kernel(int ro, int rg) {
@@ -689,23 +724,35 @@ EvalKernel<T> eval_kernel(int ro, int rg) {
 // Atil_c += sum_r C[c][r] jump_r, one warp per row c of C; partials per (instance, slice).
 template <typename T>
 __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
-    __shared__ double jump[CON_SPLIT];
+    extern __shared__ double jump[];      // con_split doubles
     const int sp = blockIdx.x, b = blockIdx.y;
     if (b >= B) return;
     if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
-    const int r0 = sp * CON_SPLIT, nr = min(CON_SPLIT, P.N_A - r0);
+    const int r0 = sp * P.con_split, nr = min(P.con_split, P.N_A - r0);
     const T* g = (const T*)P.gG + (size_t)b * P.sum_NG;
     for (int r = threadIdx.x; r < nr; r += blockDim.x)
         jump[r] = (double)g[P.con_lo[r0 + r]] - (double)g[P.con_hi[r0 + r]];
     __syncthreads();
+    // one warp per row c of C; the slice is cut into CON_BLOCK-row blocks (lane l sums rows l, l+32, ...
+    // of a block, then a warp sum), and the blocks are combined as a pairwise tree.  With the step kernel
+    // combining the slices the same way, Atil is one fixed pairwise tree over the blocks whatever the
+    // slice size (a power of two times CON_BLOCK): the result does not depend on the launch plan.
+    __shared__ double part[CON_THREADS / 32][MAX_CON_SPLIT / CON_BLOCK];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nb = P.con_split / CON_BLOCK;
     double* out = P.Atil + ((size_t)b * P.n_split + sp) * P.n_C;
     for (int c = w; c < P.n_C; c += nw) {
         const double* Cr = P.C + (size_t)c * P.N_A + r0;
-        double acc = 0.0;
-        for (int r = lane; r < nr; r += 32) acc += Cr[r] * jump[r];
-        acc = warp_sum(acc);
-        if (lane == 0) out[c] = acc;
+        for (int k = 0; k < nb; ++k) {
+            const int hi = min(nr, (k + 1) * CON_BLOCK);
+            double acc = 0.0;
+            for (int r = k * CON_BLOCK + lane; r < hi; r += 32) acc += Cr[r] * jump[r];
+            acc = warp_sum(acc);
+            if (lane == 0) part[w][k] = acc;
+        }
+        __syncwarp();
+        if (lane == 0) out[c] = tree_sum(part[w], nb, 1);
+        __syncwarp();
     }
     // this slice's share of the Schur sums over the subdomains with H_i PD: S = sum_i S_i (lower
     // triangle, mirrored) and sum_i u_i, for the step kernel
@@ -773,17 +820,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
     double* lamt = P.lamt + (size_t)b * nC;
     double* slam = P.slam + (size_t)b * nC;
 
-    for (int c = tid; c < nC; c += nth) {
-        const double* ap = P.Atil + (size_t)b * P.n_split * nC + c;
-        double a0 = 0.0, a1 = 0.0;
-        int sp = 0;
-        for (; sp + 1 < P.n_split; sp += 2) {
-            a0 += ap[(size_t)sp * nC];
-            a1 += ap[(size_t)(sp + 1) * nC];
-        }
-        if (sp < P.n_split) a0 += ap[(size_t)sp * nC];
-        At[c] = a0 + a1;
-    }
+    for (int c = tid; c < nC; c += nth) At[c] = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
     __syncthreads();
     // merit phi^2 = sum_i ||rho_i||^2 + ||Atil||^2; subdomains whose H_i^{OO} was not PD
     double acc = 0.0, fl = 0.0;
@@ -1101,8 +1138,7 @@ __global__ void k_gather(ProbDev P, int B, double* F, double* H, double* D, doub
         doff += nC * S.nG;
     }
     for (int c = tid; c < nC; c += nth) {
-        double a = 0.0;
-        for (int sp = 0; sp < P.n_split; ++sp) a += P.Atil[((size_t)b * P.n_split + sp) * nC + c];
+        const double a = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
         if (F) F[(size_t)b * (P.n_D + nC) + P.n_D + c] = a;
         if (At) At[(size_t)b * nC + c] = a;
     }
@@ -1223,6 +1259,18 @@ __global__ void k_ws_select(ProbDev P, int B) {
     }
 }
 
+// End of one pass of an instance group's loop in the solve graph: count the pass, clear the running
+// count and the evaluation counters for the next pass, and stop the loop (the conditional node's
+// handle) once no instance of the group is running or the pass limit is reached.  One thread.
+__global__ void k_loop(int* active, int* pass, int* ctr, int p0, int max_passes, cudaGraphConditionalHandle h) {
+    const int a = *active;
+    const int p = *pass + 1;
+    *pass = p;
+    *active = 0;
+    for (int k = 0; k < MAX_CLASSES; ++k) ctr[k] = 0;
+    if (a == 0 || p0 + p >= max_passes) cudaGraphSetConditional(h, 0);
+}
+
 // ------------------------------------------------------------------------ host drivers
 
 struct Launch {
@@ -1283,21 +1331,73 @@ int set_smem_attrs(ddnm_ctx* ctx) {
     return DDNM_OK;
 }
 
+// One pass's evaluation (one launch per width class) and constraint launches for the B instances of P.
+// persist: the evaluation launches are persistent; zero_ctr: clear their work counters first (the loop
+// kernel of the solve graph clears them otherwise).
 template <typename T>
-int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st) {
+int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist = false, bool zero_ctr = true) {
     int k = tstart(ctx, 0, st);
-    for (const auto& g : ctx->eval_classes) {
-        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n);
+    if (persist && zero_ctr) CK(cudaMemsetAsync(P.ctr, 0, MAX_CLASSES * sizeof(int), st));
+    for (size_t ci = 0; ci < ctx->eval_classes.size(); ++ci) {
+        const EvalClass& g = ctx->eval_classes[ci];
+        const int items = B * g.n;
+        int grid = items;
+        int* ctr = nullptr;
+        if (persist) {
+            grid = std::min(items, ctx->n_sm * ctx->tune.eval_persist);
+            ctr = P.ctr + ci;
+        }
+        eval_kernel<T>(g.ro, g.rg)<<<grid, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, ctr);
         CK(cudaGetLastError());
         ctx->tm.eval_launches++;
     }
     tstop(ctx, k, st);
     k = tstart(ctx, 1, st);
-    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, 0, st>>>(P, B);
+    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B);
     CK(cudaGetLastError());
     tstop(ctx, k, st);
     ctx->tm.constraint_launches++;
     return DDNM_OK;
+}
+
+// One SQP pass (evaluation, constraint residual, KKT step) of the B instances of P.  host_style: clear the
+// running count before the step (the loop kernel of the solve graph does it otherwise).
+template <typename T>
+int run_pass(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist, bool host_style) {
+    int rc = launch_eval<T>(ctx, P, B, st, persist, host_style);
+    if (rc) return rc;
+    if (host_style) CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
+    const int k = tstart(ctx, 2, st);
+    k_step<<<B, STEP_THREADS, ctx->step_smem, st>>>(P, B);
+    CK(cudaGetLastError());
+    tstop(ctx, k, st);
+    ctx->tm.step_launches++;
+    return DDNM_OK;
+}
+
+// The instances [b0, b0 + n) of P as a batch of their own, with instance group c's control counters.
+ProbDev group_view(const ProbDev& P, int b0, int c, size_t tsize) {
+    ProbDev Q = P;
+    const size_t b = (size_t)b0, nD = P.n_D, nC = P.n_C;
+    Q.mu += 2 * b;
+    Q.x += b * nD;
+    Q.lam += b * nC;
+    Q.xt += b * nD;
+    Q.lamt += b * nC;
+    Q.s += b * nD;
+    Q.slam += b * nC;
+    Q.Atil += b * P.n_split * nC;
+    Q.Ssum += b * (nC * nC + nC);
+    Q.dst += b * INST_DBLS;
+    Q.ist += b * INST_INTS;
+    Q.bnd = (char*)P.bnd + b * P.n_bnd * 2 * tsize;
+    Q.gG = (char*)P.gG + b * P.sum_NG * tsize;
+    Q.blk += b * P.blk_stride;
+    if (Q.r_hr) Q.r_hr += b * P.sum_NB;
+    Q.active = P.active + c;
+    Q.pass = P.pass + c;
+    Q.ctr = P.ctr + (size_t)c * MAX_CLASSES;
+    return Q;
 }
 
 // copy n doubles from the caller (host or device memory) into device memory
@@ -1322,6 +1422,7 @@ int prepare(ddnm_ctx* ctx, int B, int mem_kind) {
     CK(cudaSetDevice(ctx->device));
     rc = ddnm_reserve(ctx, B);
     if (rc) return rc;
+    if (!ctx->n_sm) CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
     rc = ctx->precision == DDNM_FP64 ? set_smem_attrs<double>(ctx) : set_smem_attrs<float>(ctx);
     return rc;
 }
@@ -1340,6 +1441,165 @@ struct Tmp {
     void* p = nullptr;
     ~Tmp() { cudaFree(p); }
 };
+
+// ------------------------------------------------------------------ solve graph (launch plan)
+
+// Launch counts of the last graph solve: the loop passes per instance group are read back with the
+// results and folded into the counters when next needed.
+void fold_pending(ddnm_ctx* ctx) {
+    if (!ctx->pass_pending) return;
+    ctx->pass_pending = false;
+    if (cudaEventSynchronize(ctx->pass_ev) != cudaSuccess) return;
+    long long passes = 0;
+    for (int c = 0; c < ctx->pending_chains; ++c) passes += ctx->h_pass[c];
+    ctx->tm.eval_launches += passes * ctx->pending_classes;
+    ctx->tm.constraint_launches += passes;
+    ctx->tm.step_launches += passes;
+    ctx->tm.other_launches += passes;          // the loop kernel
+}
+
+void drop_graph(ddnm_ctx* ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+    ctx->gkey.clear();
+}
+
+int n_groups(const ddnm_ctx* ctx, int B) { return std::max(1, std::min(ctx->tune.chains, B)); }
+
+// Capture the solve of B instances (Bw with the warm-start shadow copies) as one graph:
+//   clear the control area -> k_init -> [warm start: two screening passes over Bw, k_ws_select]
+//   -> per instance group, a conditional while node whose body is one pass + k_loop.
+template <typename T>
+int build_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool has_x0, bool has_lam0,
+                int max_passes) {
+    drop_graph(ctx);
+    if (!ctx->cap_main) CK(cudaStreamCreateWithFlags(&ctx->cap_main, cudaStreamNonBlocking));
+    if (!ctx->cap_body) CK(cudaStreamCreateWithFlags(&ctx->cap_body, cudaStreamNonBlocking));
+    const ddnm_timing tm_saved = ctx->tm;      // capturing is not launching
+    const bool persist = ctx->tune.eval_persist > 0;
+    const size_t tsize = sizeof(T);
+    cudaGraph_t G = nullptr;
+    CK(cudaGraphCreate(&G, 0));
+    cudaStream_t cs = ctx->cap_main, cb = ctx->cap_body;
+    auto abort_capture = [&](int rc) {
+        cudaStreamCaptureStatus status;
+        cudaGraph_t t = nullptr;
+        if (cudaStreamIsCapturing(cb, &status) == cudaSuccess && status != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(cb, &t);
+        t = nullptr;
+        if (cudaStreamIsCapturing(cs, &status) == cudaSuccess && status != cudaStreamCaptureStatusNone)
+            cudaStreamEndCapture(cs, &t);
+        cudaGraphDestroy(G);
+        cudaGetLastError();
+        ctx->tm = tm_saved;
+        return rc;
+    };
+    cudaError_t e = cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamBeginCaptureToGraph"));
+    e = cudaMemsetAsync(P.active, 0, CTL_INTS * sizeof(int), cs);
+    if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "capture: clear control area"));
+    k_init<<<Bw, 128, 0, cs>>>(P, Bw, has_x0 || ws, has_lam0, has_lam0 ? MODE_INIT1 : MODE_INIT0, (int)(tsize == 8));
+    int p0 = 0;
+    if (ws) {
+        for (int pass = 0; pass < 2; ++pass) {
+            const int rc = run_pass<T>(ctx, P, Bw, cs, persist, true);
+            if (rc) return abort_capture(rc);
+        }
+        k_ws_select<<<B, 128, 0, cs>>>(P, B);
+        e = cudaMemsetAsync(P.active, 0, CTL_INTS * sizeof(int), cs);
+        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "capture: clear control area"));
+        p0 = 2;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "capture: start-up launches"));
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamGetCaptureInfo"));
+    const std::vector<cudaGraphNode_t> start(deps, deps + ndeps);
+    const int K = n_groups(ctx, B);
+    std::vector<cudaGraphNode_t> loops;
+    for (int c = 0; c < K; ++c) {
+        const int b0 = (int)((long long)B * c / K), b1 = (int)((long long)B * (c + 1) / K);
+        const ProbDev Q = group_view(P, b0, c, tsize);
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaGraphConditionalHandleCreate"));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, G, start.data(), nullptr, start.size(), &np);
+        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaGraphAddNode(while)"));
+        loops.push_back(node);
+        e = cudaStreamBeginCaptureToGraph(cb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamBeginCaptureToGraph(body)"));
+        const int rc = run_pass<T>(ctx, Q, b1 - b0, cb, persist, false);
+        if (rc) return abort_capture(rc);
+        k_loop<<<1, 1, 0, cb>>>(Q.active, Q.pass, Q.ctr, p0, max_passes, h);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "capture: loop kernel"));
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(cb, &body);
+        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamEndCapture(body)"));
+    }
+    e = cudaStreamUpdateCaptureDependencies(cs, loops.data(), nullptr, loops.size(), cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamUpdateCaptureDependencies"));
+    cudaGraph_t done = nullptr;
+    e = cudaStreamEndCapture(cs, &done);
+    if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamEndCapture"));
+    ctx->tm = tm_saved;
+    e = cudaGraphInstantiate(&ctx->gexec, G, 0);
+    if (e != cudaSuccess) {
+        ctx->gexec = nullptr;
+        cudaGraphDestroy(G);
+        return cfail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->graph = G;
+    return DDNM_OK;
+}
+
+template <typename T>
+int solve_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool has_x0, bool has_lam0, int max_passes,
+                cudaStream_t st) {
+    fold_pending(ctx);
+    auto bits = [](double v) {
+        long long b;
+        std::memcpy(&b, &v, 8);
+        return b;
+    };
+    const ddnm_options& o = ctx->opt;
+    const std::vector<long long> key{ctx->gen, B, Bw, ws, has_x0, has_lam0, (long long)sizeof(T), max_passes,
+                                     bits(o.tol), bits(o.armijo_c1), bits(o.beta), o.max_iter, o.max_backtracks,
+                                     ctx->tune.chains, ctx->tune.con_split, ctx->tune.eval_persist, ctx->n_sm};
+    if (!ctx->gexec || key != ctx->gkey) {
+        const int rc = build_graph<T>(ctx, P, B, Bw, ws, has_x0, has_lam0, max_passes);
+        if (rc) return rc;
+        ctx->gkey = key;
+    }
+    if (!ctx->h_pass) CK(cudaMallocHost(&ctx->h_pass, MAX_CHAINS * sizeof(int)));
+    if (!ctx->pass_ev) CK(cudaEventCreateWithFlags(&ctx->pass_ev, cudaEventDisableTiming));
+    CK(cudaGraphLaunch(ctx->gexec, st));
+    const int cls = (int)ctx->eval_classes.size();
+    ctx->tm.other_launches += 1 + (ws ? 1 : 0);                // k_init, k_ws_select
+    if (ws) {
+        ctx->tm.eval_launches += 2 * cls;
+        ctx->tm.constraint_launches += 2;
+        ctx->tm.step_launches += 2;
+    }
+    CK(cudaMemcpyAsync(ctx->h_pass, P.pass, MAX_CHAINS * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ctx->pass_ev, st));
+    ctx->pass_pending = true;
+    ctx->pending_chains = n_groups(ctx, B);
+    ctx->pending_classes = cls;
+    return DDNM_OK;
+}
 
 }  // namespace
 
@@ -1365,37 +1625,41 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
         if ((rc = ddnm_ws_predict_dev(ctx, B, P.mu, P.x, nullptr, st))) return rc;
         CK(cudaMemsetAsync(P.x + (size_t)B * P.n_D, 0, (size_t)B * P.n_D * 8, st));
     }
-    k_init<<<Bw, 128, 0, st>>>(P, Bw, x0 != nullptr || ws, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0, fp64);
-    CK(cudaGetLastError());
-    ctx->tm.other_launches++;
     const int max_passes = 3 + ctx->opt.max_iter * (ctx->opt.max_backtracks + 1);
     P.tol = ctx->opt.tol;
     P.c1 = ctx->opt.armijo_c1;
     P.beta = ctx->opt.beta;
     P.max_iter = ctx->opt.max_iter;
     P.max_bt = ctx->opt.max_backtracks;
-    const int check_every = 4;
-    int Bp = Bw;                      // instances in the passes (2B during the warm-start screening)
-    for (int pass = 0; pass < max_passes; ++pass) {
-        rc = fp64 ? launch_eval<double>(ctx, P, Bp, st) : launch_eval<float>(ctx, P, Bp, st);
+    P.con_split = ctx->tune.con_split;
+    P.n_split = (P.N_A + P.con_split - 1) / P.con_split;
+    if (ctx->tune.graph && !ctx->timing) {
+        rc = fp64 ? solve_graph<double>(ctx, P, B, Bw, ws, x0 != nullptr, lam0 != nullptr, max_passes, st)
+                  : solve_graph<float>(ctx, P, B, Bw, ws, x0 != nullptr, lam0 != nullptr, max_passes, st);
         if (rc) return rc;
-        CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
-        const int k = tstart(ctx, 2, st);
-        k_step<<<Bp, STEP_THREADS, ctx->step_smem, st>>>(P, Bp);
+    } else {
+        // host-driven passes: the running count is read back every few passes
+        k_init<<<Bw, 128, 0, st>>>(P, Bw, x0 != nullptr || ws, lam0 != nullptr, lam0 ? MODE_INIT1 : MODE_INIT0, fp64);
         CK(cudaGetLastError());
-        tstop(ctx, k, st);
-        ctx->tm.step_launches++;
-        if (ws && pass == 1) {        // both starts linearised: keep the better one per instance
-            k_ws_select<<<B, 128, 0, st>>>(P, B);
-            CK(cudaGetLastError());
-            ctx->tm.other_launches++;
-            Bp = B;
-            continue;
-        }
-        if (pass % check_every == check_every - 1 || pass == max_passes - 1) {
-            CK(cudaMemcpyAsync(ctx->h_active, P.active, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (*ctx->h_active == 0) break;
+        ctx->tm.other_launches++;
+        const bool persist = ctx->tune.eval_persist > 0;
+        const int check_every = 4;
+        int Bp = Bw;                      // instances in the passes (2B during the warm-start screening)
+        for (int pass = 0; pass < max_passes; ++pass) {
+            rc = fp64 ? run_pass<double>(ctx, P, Bp, st, persist, true) : run_pass<float>(ctx, P, Bp, st, persist, true);
+            if (rc) return rc;
+            if (ws && pass == 1) {        // both starts linearised: keep the better one per instance
+                k_ws_select<<<B, 128, 0, st>>>(P, B);
+                CK(cudaGetLastError());
+                ctx->tm.other_launches++;
+                Bp = B;
+                continue;
+            }
+            if (pass % check_every == check_every - 1 || pass == max_passes - 1) {
+                CK(cudaMemcpyAsync(ctx->h_active, P.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (*ctx->h_active == 0) break;
+            }
         }
     }
     if (x_out && (rc = copy_out(ctx, x_out, P.x, (size_t)B * P.n_D * 8, mem_kind, st))) return rc;
@@ -1524,6 +1788,7 @@ extern "C" int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const doub
 
 extern "C" int ddnm_timing_enable(ddnm_ctx* ctx, int on) {
     if (!ctx) return DDNM_E_INVALID;
+    fold_pending(ctx);
     ctx->timing = on != 0;
     ctx->n_events = 0;
     if (on) ctx->tm = ddnm_timing{};
@@ -1532,8 +1797,107 @@ extern "C" int ddnm_timing_enable(ddnm_ctx* ctx, int on) {
 
 extern "C" int ddnm_get_timing(const ddnm_ctx* ctx, ddnm_timing* out) {
     if (!ctx || !out) return DDNM_E_INVALID;
+    fold_pending(const_cast<ddnm_ctx*>(ctx));
     *out = ctx->tm;
     return DDNM_OK;
+}
+
+void ddnm_release_graph(ddnm_ctx* ctx) {
+    fold_pending(ctx);
+    drop_graph(ctx);
+    if (ctx->cap_main) cudaStreamDestroy(ctx->cap_main);
+    if (ctx->cap_body) cudaStreamDestroy(ctx->cap_body);
+    if (ctx->pass_ev) cudaEventDestroy(ctx->pass_ev);
+    if (ctx->h_pass) cudaFreeHost(ctx->h_pass);
+    ctx->cap_main = ctx->cap_body = nullptr;
+    ctx->pass_ev = nullptr;
+    ctx->h_pass = nullptr;
+}
+
+extern "C" int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t) {
+    if (!ctx || !t) return DDNM_E_INVALID;
+    const bool pow2 = t->con_split > 0 && (t->con_split & (t->con_split - 1)) == 0;
+    if (t->graph < 0 || t->graph > 1 || t->chains < 1 || t->chains > MAX_CHAINS || !pow2 ||
+        t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8)
+        return ddnm_fail(ctx, DDNM_E_INVALID,
+                         "tune: graph 0/1, chains 1..16, con_split 512, 1024 or 2048, eval_persist 0..8");
+    ctx->tune = *t;
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t) {
+    if (!ctx || !t) return DDNM_E_INVALID;
+    *t = ctx->tune;
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kind, void* stream, int max_iter,
+                             int reps, ddnm_tune* best, float* best_ms) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (B < 1 || !mu || max_iter < 0) return ddnm_fail(ctx, DDNM_E_INVALID, "autotune: B >= 1, mu and max_iter >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ddnm_options opt_saved = ctx->opt;
+    const bool timing_saved = ctx->timing;
+    if (max_iter > 0) ctx->opt.max_iter = max_iter;
+    ctx->timing = false;
+    reps = std::max(1, std::min(reps, 64));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = DDNM_OK;
+    auto finish = [&](int r) {
+        ctx->opt = opt_saved;
+        ctx->timing = timing_saved;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return r;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return finish(ddnm_fail(ctx, DDNM_E_CUDA, "autotune: event creation failed"));
+    auto time_plan = [&](const ddnm_tune& t, float* ms) -> int {
+        ctx->tune = t;
+        int r = ddnm_solve_batch(ctx, B, mu, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, mem_kind, stream);
+        if (r) return r;
+        std::vector<float> v;
+        for (int k = 0; k < reps; ++k) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return ddnm_fail(ctx, DDNM_E_CUDA, "autotune: event record");
+            r = ddnm_solve_batch(ctx, B, mu, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, mem_kind, stream);
+            if (r) return r;
+            float m = 0.f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&m, e0, e1) != cudaSuccess)
+                return ddnm_fail(ctx, DDNM_E_CUDA, "autotune: event timing");
+            v.push_back(m);
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v[v.size() / 2];
+        return DDNM_OK;
+    };
+    ddnm_tune cur = ctx->tune;
+    cur.graph = 1;
+    float cur_ms = 0.f;
+    if ((rc = time_plan(cur, &cur_ms))) return finish(rc);
+    auto sweep = [&](int ddnm_tune::*knob, std::initializer_list<int> values) -> int {
+        for (int v : values) {
+            if (v == cur.*knob) continue;
+            if (knob == &ddnm_tune::chains && v > B) continue;
+            ddnm_tune t = cur;
+            t.*knob = v;
+            float ms = 0.f;
+            const int r = time_plan(t, &ms);
+            if (r) return r;
+            if (ms < cur_ms) {
+                cur = t;
+                cur_ms = ms;
+            }
+        }
+        return DDNM_OK;
+    };
+    if ((rc = sweep(&ddnm_tune::chains, {1, 2, 4, 8, 16}))) return finish(rc);
+    if ((rc = sweep(&ddnm_tune::eval_persist, {0, 1, 2, 4}))) return finish(rc);
+    if ((rc = sweep(&ddnm_tune::con_split, {512, 1024, 2048}))) return finish(rc);
+    ctx->tune = cur;
+    if (best) *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    return finish(DDNM_OK);
 }
 
 void ddnm_release_events(ddnm_ctx* ctx) {
@@ -1610,8 +1974,8 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
     }
     k_noalloc_init<<<B, 128, 0, st>>>(P, B, (int)(sizeof(T) == 8));
     for (const auto& g : ctx->eval_classes)
-        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n);
-    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, 0, st>>>(P, B);
+        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, nullptr);
+    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B);
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cfail(ctx, e, "no-allocation evaluation launch");

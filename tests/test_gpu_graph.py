@@ -1,0 +1,126 @@
+"""Launch plan of the batched solve: the graph-resident SQP loop (one CUDA graph launch with a device-side
+while loop per instance group), the persistent evaluation and the constraint-slice size change how the work
+is scheduled, never what is computed.  Every plan gives bit-identical iterates, multipliers and
+per-instance statistics to the host-driven loop; the autotuner returns a valid plan and the solve under it
+still matches the oracle."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import setup
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+lib = pytest.importorskip("paper_2305_15163_gb300")
+
+FP64, MIXED = 0, 1
+HOST = dict(graph=0, chains=1, con_split=512, eval_persist=0)
+PLANS = [dict(graph=1, chains=1, con_split=512, eval_persist=0),
+         dict(graph=1, chains=3, con_split=1024, eval_persist=2),
+         dict(graph=1, chains=16, con_split=2048, eval_persist=1),
+         dict(graph=1, chains=4, con_split=512, eval_persist=4),
+         dict(graph=0, chains=1, con_split=2048, eval_persist=3)]
+
+
+def solver(name, prec):
+    wl = inputs.workload(name)
+    s = lib.Solver(wl, precision=prec)
+    dec_o, dec_g = inputs.decoders_for(wl, [d["interior"] for d in s.subs], [d["interface"] for d in s.subs])
+    s.load(dec_o, dec_g, inputs.test_matrix(wl.n_c(), s.sizes.N_A))
+    return wl, s
+
+
+def same(a, b):
+    xa, la, sa = a
+    xb, lb, sb = b
+    assert np.array_equal(xa, xb) and np.array_equal(la, lb)
+    for f in ("iters", "status", "flags", "n_evals", "merit", "alpha_last"):
+        assert np.array_equal(sa[f], sb[f]), f
+
+
+@pytest.mark.parametrize("name,prec,B", [("c2", MIXED, 13), ("c2", FP64, 5), ("c3", MIXED, 7), ("c1", FP64, 1),
+                                         ("tiny13x9_3x2", MIXED, 4)])
+def test_plans_are_bit_identical(name, prec, B):
+    wl, s = solver(name, prec)
+    mu = inputs.mu_batch(B, seed=31)
+    s.options(tol=0.0, max_iter=4)
+    lib.ddnm_set_tune(s.ctx, **HOST)
+    ref = s.solve(mu)
+    for plan in PLANS:
+        lib.ddnm_set_tune(s.ctx, **plan)
+        same(s.solve(mu), ref)
+        same(s.solve(mu), ref)                 # replay of the captured graph
+    s.options()
+    lib.ddnm_set_tune(s.ctx, **HOST)
+    ref = s.solve(mu)                          # stopping rule active: groups finish at different passes
+    lib.ddnm_set_tune(s.ctx, graph=1, chains=min(B, 5), con_split=1024, eval_persist=2)
+    same(s.solve(mu), ref)
+    s.close()
+
+
+def test_graph_with_warm_start_and_starts():
+    """The warm-start screening runs inside the graph (2B instances, then the selection); explicit starts
+    x0 / lam0 skip it.  Both match the host-driven loop bit for bit."""
+    wl, s = solver("c2", MIXED)
+    nD, nC = s.sizes.n_D, s.sizes.n_C
+    lib.ddnm_ws_init(s.ctx, 64, inputs.mlp_init(2, 64, nD))
+    mu = inputs.mu_batch(64, seed=9)
+    x_tr, _, _ = s.solve(mu)
+    lib.ddnm_ws_train(s.ctx, mu, x_tr, 20, 32, 2e-3, inputs.mlp_order(64, 20))
+    lib.ddnm_ws_enable(s.ctx, True)
+    mu_te = inputs.mu_batch(11, seed=10)
+    s.options(tol=0.0, max_iter=3)
+    lib.ddnm_set_tune(s.ctx, **HOST)
+    ref = s.solve(mu_te)
+    lib.ddnm_set_tune(s.ctx, graph=1, chains=4, con_split=1024, eval_persist=2)
+    same(s.solve(mu_te), ref)
+    lib.ddnm_ws_enable(s.ctx, False)
+    r = np.random.default_rng(2)
+    x0, lam0 = 0.1 * r.standard_normal((11, nD)), r.standard_normal((11, nC))
+    lib.ddnm_set_tune(s.ctx, **HOST)
+    ref = s.solve(mu_te, x0=x0, lam0=lam0)
+    lib.ddnm_set_tune(s.ctx, graph=1, chains=2, con_split=512, eval_persist=0)
+    same(s.solve(mu_te, x0=x0, lam0=lam0), ref)
+    s.close()
+
+
+def test_launch_counts_of_graph_solve():
+    """The graph's loop passes are read back: per pass and instance group one launch per width class,
+    one constraint, one step and one loop-control kernel."""
+    wl, s = solver("c3", MIXED)
+    mu = inputs.mu_batch(6, seed=3)
+    s.options(tol=0.0, max_iter=2)
+    lib.ddnm_timing_enable(s.ctx, True)
+    lib.ddnm_timing_enable(s.ctx, False)           # counters reset, timing (host loop) off
+    t0 = lib.ddnm_get_timing(s.ctx)
+    lib.ddnm_set_tune(s.ctx, graph=1, chains=2, con_split=512, eval_persist=0)
+    x, lam, st = s.solve(mu)
+    t1 = lib.ddnm_get_timing(s.ctx)
+    steps = t1["step_launches"] - t0["step_launches"]
+    evals = t1["eval_launches"] - t0["eval_launches"]
+    assert steps == t1["constraint_launches"] - t0["constraint_launches"]
+    assert evals % steps == 0 and evals // steps >= 1
+    assert int(st["n_evals"].max()) <= steps <= 2 * (3 + 2 * 21)
+    s.close()
+
+
+def test_autotune_then_parity_with_oracle():
+    wl = inputs.workload("c1")
+    fom, dd, rom, raw = setup.build(wl)
+    s = lib.Solver(wl, precision=FP64)
+    s.load(raw["dec_o"], raw["dec_g"], raw["C"])
+    mu = inputs.mu_batch(3)
+    plan, ms = lib.ddnm_autotune(s.ctx, mu, max_iter=2, reps=2)
+    assert plan["graph"] == 1 and 1 <= plan["chains"] <= 3 and plan["con_split"] in (512, 1024, 2048)
+    assert plan["eval_persist"] in (0, 1, 2, 4) and ms > 0
+    assert lib.ddnm_get_tune(s.ctx) == plan
+    s.options(tol=0.0, max_iter=3)
+    x, lam, st = s.solve(mu)
+    for b in range(3):
+        res = rom.solve(mu[b], tol=0.0, max_iter=3)
+        assert np.linalg.norm(x[b] - res.x) <= 1e-6 * max(np.linalg.norm(res.x), 1e-300)
+        assert np.linalg.norm(lam[b] - res.lam) <= 1e-6 * max(np.linalg.norm(res.lam), 1e-300)
+    s.close()
