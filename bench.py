@@ -395,7 +395,7 @@ def main():
     work = lib.ddnm_get_work(s.ctx)
     pk = peaks()
     evals_per_step = float(st["n_evals"].sum())
-    kern = {"k_eval": tm["eval_ms"], "k_constraint": tm["constraint_ms"], "k_step": tm["step_ms"]}
+    kern = {"k_eval": tm["eval_ms"], "k_constraint": tm["constraint_ms"], "k_kkt": tm["step_ms"]}
     dom = max(kern, key=kern.get)
     if dom == "k_eval":
         fl = work["eval_flops"] * evals_per_step * kb

@@ -152,11 +152,12 @@ typedef struct ddnm_stats {
 typedef struct ddnm_timing {
     double eval_ms;             /* k_eval: fused decoder / residual / Gauss-Newton blocks */
     double constraint_ms;       /* k_constraint: FP64 weak-constraint residual */
-    double step_ms;             /* k_step: FP64 Schur KKT solve, Armijo, update */
+    double step_ms;             /* k_kkt: merit, Armijo, update; FP64 per-subdomain L D L^T, Schur sums and
+                                   border solve of the KKT system */
     long long eval_launches;
     long long constraint_launches;
     long long step_launches;
-    long long other_launches;   /* set-up, statistics, reconstruction kernels */
+    long long other_launches;   /* set-up, statistics, reconstruction, loop-control kernels */
 } ddnm_timing;
 
 /* Algorithmic work of ONE evaluation of ONE instance (all subdomains), counted
@@ -165,11 +166,13 @@ typedef struct ddnm_timing {
 typedef struct ddnm_work {
     double eval_flops;          /* value-type flops of k_eval: hidden layers, decoder outputs and
                                    Jacobian rows, residual rows and chain rule, H_i and R_i^T r_i, D_i */
-    double eval_fp64_flops;     /* FP64 flops of k_eval: per-subdomain Cholesky and Schur pieces */
+    double eval_fp64_flops;     /* FP64 flops of k_eval: rho_i += D_i^T lambda, ||rho_i||^2 */
     double eval_bytes;          /* unique global bytes one instance-evaluation must touch
                                    (weights and tables counted once, latents, outputs) */
     double constraint_fp64_flops;  /* 2 n_C N_A */
-    double step_fp64_flops;     /* Schur assembly + n_C Cholesky + back-substitution, per accepted step */
+    double step_fp64_flops;     /* per accepted point: per-subdomain L D L^T, t, W, u; the Schur sums
+                                   S = sum_i W_i^T D_G^{-1} W_i and sum_i u_i; the n_C L D L^T and solves;
+                                   the back-substitution */
 } ddnm_work;
 
 typedef struct ddnm_ctx ddnm_ctx;

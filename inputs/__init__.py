@@ -174,10 +174,10 @@ def band_mask(n_out: int, width: int, nnz_band: int) -> np.ndarray:
     offs = np.concatenate([np.arange(nnz_band) - sep, np.arange(nnz_band), np.arange(nnz_band) + sep])
     cols = c0 + offs[None, :]
     ok = (cols >= 0) & (cols < width)
-    out = np.full(cols.shape, -1, dtype=np.int32)
-    for i in range(n_out):                   # compact valid columns to the front, ascending
-        v = cols[i][ok[i]]
-        out[i, : v.size] = v
+    # compact the valid columns of every row to the front, keeping their ascending order
+    order = np.argsort(~ok, axis=1, kind="stable")
+    out = np.take_along_axis(cols, order, axis=1).astype(np.int32)
+    out[~np.take_along_axis(ok, order, axis=1)] = -1
     return out
 
 

@@ -72,7 +72,7 @@ struct ddnm_ctx {
     bool finalized = false;
     std::vector<ddnm::SubDev> hsub;
     ddnm::ProbDev pd{};
-    int eval_smem = 0, step_smem = 0, rec_smem = 0;
+    int eval_smem = 0, kkt_smem = 0, rec_smem = 0, ss_rows = 0;
     void* d_vpool = nullptr;
     int* d_ipool = nullptr;
     int* d_hr = nullptr;
@@ -81,6 +81,8 @@ struct ddnm_ctx {
     int* d_bnd_ij = nullptr;
     ddnm::SubDev* d_sub = nullptr;
     ddnm::ChunkDev* d_chunk = nullptr;
+    ddnm::TileDev* d_tiles = nullptr;
+    std::vector<ddnm::TileDev> htiles;
     std::vector<EvalClass> eval_classes;
     int* d_classes = nullptr;          // subdomain indices, grouped by class
     std::vector<ddnm::ChunkDev> hchunk;

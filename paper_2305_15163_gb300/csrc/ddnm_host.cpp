@@ -267,6 +267,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_bnd_ij);
     cudaFree(ctx->d_sub);
     cudaFree(ctx->d_chunk);
+    cudaFree(ctx->d_tiles);
     cudaFree(ctx->d_classes);
     cudaFree(ctx->d_ws);
     if (ctx->h_active) cudaFreeHost(ctx->h_active);
@@ -436,6 +437,53 @@ void subnet_rows(const DecoderHost& d, const std::vector<int>& rows, const std::
     val = P.addv(vs.data(), vs.size());
     so = P.addv(sc.data(), sc.size());
 }
+// The same rows as dense-window tiles (TileDev) for the banded masks of Sec. 5.1, where consecutive rows
+// share most of their columns: a warp then reads each hidden record of a tile's window once (a broadcast)
+// instead of once per row and mask entry.  Returns false, adding nothing, when the windows would hold
+// more than 2.5 values per mask entry (a scattered mask keeps the ELL table).
+bool subnet_tiles(const DecoderHost& d, const std::vector<int>& rows, const std::vector<int>& pos, int h, Pools& P,
+                  std::vector<TileDev>& tiles, int& tile0, int& ntiles) {
+    const size_t m = rows.size();
+    const int hpad = round4(h);
+    size_t nnz = 0, stored = 0;
+    std::vector<TileDev> loc;
+    std::vector<std::vector<double>> vals;
+    for (size_t t0 = 0; t0 < m; t0 += 32) {
+        const size_t t1 = std::min(m, t0 + 32);
+        int lo = 1 << 30, hi = -1;
+        for (size_t r = t0; r < t1; ++r)
+            for (int k = 0; k < d.K; ++k) {
+                const int c = d.cols[(size_t)rows[r] * d.K + k];
+                if (c < 0) continue;
+                lo = std::min(lo, pos[c]);
+                hi = std::max(hi, pos[c]);
+                ++nnz;
+            }
+        if (hi < 0) lo = hi = 0;
+        const int tw = round4(hi - lo + 1);
+        if (tw > hpad) return false;
+        const int c0 = std::min(lo, hpad - tw);
+        std::vector<double> v((size_t)tw * 32, 0.0);
+        for (size_t r = t0; r < t1; ++r)
+            for (int k = 0; k < d.K; ++k) {
+                const int c = d.cols[(size_t)rows[r] * d.K + k];
+                if (c < 0) continue;
+                const int j = pos[c] - c0, lane = (int)(r - t0);
+                v[(size_t)(j / 4) * 128 + lane * 4 + j % 4] = d.vals[(size_t)rows[r] * d.K + k];
+            }
+        stored += v.size();
+        loc.push_back(TileDev{c0, tw, 0});
+        vals.push_back(std::move(v));
+    }
+    if (m == 0 || (double)stored > 2.5 * (double)nnz) return false;
+    tile0 = (int)tiles.size();
+    ntiles = (int)loc.size();
+    for (size_t t = 0; t < loc.size(); ++t) {
+        loc[t].voff = P.addv(vals[t].data(), vals[t].size());
+        tiles.push_back(loc[t]);
+    }
+    return true;
+}
 }  // namespace
 
 int ddnm_finalize(ddnm_ctx* ctx) {
@@ -450,6 +498,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     std::vector<int> hr_all;
     ctx->hsub.assign(ns, SubDev{});
     ctx->hchunk.clear();
+    ctx->htiles.clear();
     int xoff = 0, hr_off = 0, blk = 0;
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
     ctx->eval_smem = 0;
@@ -478,6 +527,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
             c.nq = std::min(HR_CHUNK, S.NB - c.q0);
             c.m = (int)sd.chunk_need[q].size();
             subnet_rows(dO, sd.chunk_need[q], posO, S.Kp, P, c.col, c.val, c.so);
+            if (!subnet_tiles(dO, sd.chunk_need[q], posO, S.hO, P, ctx->htiles, c.tile0, c.ntiles)) c.ntiles = 0;
             S.mmax = std::max(S.mmax, c.m);
             ctx->hchunk.push_back(c);
         }
@@ -488,6 +538,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         for (int r = 0; r < S.NG; ++r) allG[r] = r;
         subnet_hidden(dG, allG, P, S.w1G, S.b1G, S.hG, posG);
         subnet_rows(dG, allG, posG, S.Kp, P, S.colG, S.valG, S.soG);
+        if (!subnet_tiles(dG, allG, posG, S.hG, P, ctx->htiles, S.tileG0, S.ntilesG)) S.ntilesG = 0;
         for (int c : dG.cols) ctx->nnzG[s] += c >= 0;
         // M_i = C A_i, stored N^G x n_C
         std::vector<double> M((size_t)S.NG * nC, 0.0);
@@ -561,7 +612,35 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain needs " + std::to_string(ctx->eval_smem) +
                                                       " bytes of shared memory (device limit " + std::to_string(dev_max) + ")");
     if (ctx->rec_smem > dev_max) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "decoder too wide for reconstruction");
-    ctx->step_smem = (int)((size_t)nC * nC + 4 * nC + (size_t)nC * (MAX_MF + 1) + MAX_MF * MAX_MF + 2 * MAX_MF) * 8;
+    int fac_stride = 0, sum_nG = 0;
+    for (const SubDev& S : ctx->hsub) {
+        fac_stride = std::max(fac_stride, S.ni * S.ni + 2 * S.ni + S.nG * S.nG);
+        sum_nG += S.nG;
+    }
+    fac_stride = (fac_stride + 1) & ~1;
+    ctx->ss_rows = std::min(sum_nG, std::max(MAX_NG, SS_ROWS_DBL / nC));   // staged rows of W per chunk
+    // k_kkt: S, rhs, Atil, pivots, sum u, then one area used in turn by the factorisation scratch of every
+    // warp, the W staging of the Schur sums, and Z, T of the border solve
+    const size_t work = std::max({(size_t)(KKT_THREADS / 32) * fac_stride, (size_t)2 * ctx->ss_rows * nC,
+                                  (size_t)nC * (MAX_MF + 1) + MAX_MF * MAX_MF + 2 * MAX_MF});
+    ctx->kkt_smem = (int)(((size_t)nC * nC + 4 * nC + work) * 8);
+    if (ctx->kkt_smem > dev_max)
+        return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "KKT step needs " + std::to_string(ctx->kkt_smem) +
+                                                      " bytes of shared memory (device limit " + std::to_string(dev_max) + ")");
+    // Schur-sum chunks: consecutive subdomains whose interface rows fit the staging area
+    std::vector<int> ss_chunk{0};
+    {
+        int rows = 0;
+        for (int i = 0; i < ns; ++i) {
+            if (rows + ctx->hsub[i].nG > ctx->ss_rows) {
+                ss_chunk.push_back(i);
+                rows = 0;
+            }
+            rows += ctx->hsub[i].nG;
+        }
+        ss_chunk.push_back(ns);
+    }
+    const long long ss_chunk_off = P.addi(ss_chunk.data(), ss_chunk.size());
     // upload
     cudaFree(ctx->d_vpool); cudaFree(ctx->d_ipool); cudaFree(ctx->d_hr); cudaFree(ctx->d_con);
     cudaFree(ctx->d_C); cudaFree(ctx->d_bnd_ij); cudaFree(ctx->d_sub); cudaFree(ctx->d_chunk);
@@ -595,12 +674,21 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_classes, cls.data(), cls.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_chunk, std::max<size_t>(ctx->hchunk.size(), 1) * sizeof(ChunkDev)));
     CK(cudaMemcpy(ctx->d_chunk, ctx->hchunk.data(), ctx->hchunk.size() * sizeof(ChunkDev), cudaMemcpyHostToDevice));
+    cudaFree(ctx->d_tiles);
+    ctx->d_tiles = nullptr;
+    CK(cudaMalloc(&ctx->d_tiles, std::max<size_t>(ctx->htiles.size(), 1) * sizeof(TileDev)));
+    if (!ctx->htiles.empty())
+        CK(cudaMemcpy(ctx->d_tiles, ctx->htiles.data(), ctx->htiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice));
 
     ProbDev& pd = ctx->pd;
     pd = ProbDev{};
     pd.n_sub = ns; pd.n_D = ctx->n_D; pd.n_C = nC; pd.N_A = ctx->N_A;
     pd.sum_NG = ctx->sum_NG; pd.sum_NB = ctx->sum_NB; pd.n_bnd = (int)ctx->bnd_ij.size() / 2;
     pd.N_x = 2 * ctx->N; pd.nx = ctx->nx; pd.ny = ctx->ny;
+    pd.fac_stride = fac_stride;
+    pd.ss_rows = ctx->ss_rows;
+    pd.n_ss_chunks = (int)ss_chunk.size() - 1;
+    pd.ss_chunk = ctx->d_ipool + ss_chunk_off;
     pd.con_split = CON_SPLIT;
     pd.n_split = (ctx->N_A + CON_SPLIT - 1) / CON_SPLIT;
     pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
@@ -610,7 +698,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.cst[3] = ctx->nu / (ctx->hy * ctx->hy);
     for (int k = 0; k < 4; ++k) pd.cstf[k] = (float)pd.cst[k];
     pd.blk_stride = blk;
-    pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
+    pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.tiles = ctx->d_tiles; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
     pd.hr = ctx->d_hr;
     pd.con_lo = ctx->d_con; pd.con_hi = ctx->d_con + ctx->N_A; pd.C = ctx->d_C; pd.bnd_ij = ctx->d_bnd_ij;
     ctx->cap_B = 0;   // workspace pointers are re-carved on the next reserve
@@ -682,7 +770,7 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         if (rc) return rc;
     }
     const double nC = ctx->n_C, tsz = ctx->precision == DDNM_FP64 ? 8.0 : 4.0;
-    double f = 0, f64 = 0, bytes = 0, step = 0;
+    double f = 0, f64 = 0, bytes = 0, step = 0, fac = 0;
     for (int s = 0; s < ctx->n_sub; ++s) {
         const SubDev& S = ctx->hsub[s];
         const double ni = S.ni, nO = S.nO, nG = S.nG;
@@ -697,15 +785,18 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         f += 2.0 * S.NB * (ni * (ni + 1) / 2 + ni);
         // D_i = (C A_i) dg^G/dxh
         f += 2.0 * nC * S.NG * nG;
-        // FP64: rho += D^T lambda, Cholesky, t, W = L_GG^{-1} D^T, u, S_i = W^T W
-        f64 += 2 * nC * nG + ni * ni * ni / 3.0 + ni * ni + nC * nG * nG + 2 * nC * nG + 2.0 * nC * nC * nG;
+        // FP64 in the evaluation: rho += D^T lambda, ||rho_i||^2
+        f64 += 2 * nC * nG + 2 * ni;
+        // FP64 at an accepted point: L D L^T, t, W = L_GG^{-1} D^T, u (k_factor); lower triangle of
+        // W^T D_G^{-1} W summed into S (k_ssum)
+        fac += ni * ni * ni / 3.0 + ni * ni + nC * nG * nG + 3 * nC * nG + nC * (nC + 1) * nG + nC;
         // bytes: subnet weights, tables and M_i once; per instance latents, multipliers, block outputs
         bytes += tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] + 2.0 * (mO + S.NG) +
                         S.NG * nC) +
                  4.0 * (mO * S.K + (double)S.NG * S.K + 7.0 * S.NB) +
                  8.0 * (blk_layout(S.ni, S.nG, ctx->n_C).size) + tsz * S.NG;
-        // step: sum of S_i and u_i, back-substitution per subdomain
-        step += nC * nC + nC + 2.0 * nG * nC + ni * ni;
+        // back-substitution per subdomain (in the next evaluation)
+        step += 2.0 * nG * nC + ni * ni;
     }
     bytes += 8.0 * (ctx->n_D + nC + 2);
     step += nC * nC * nC / 3.0 + 2.0 * nC * nC;
@@ -713,6 +804,6 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
     out->eval_fp64_flops = f64;
     out->eval_bytes = bytes;
     out->constraint_fp64_flops = 2.0 * nC * ctx->N_A + ctx->N_A;
-    out->step_fp64_flops = step;
+    out->step_fp64_flops = step + fac;
     return DDNM_OK;
 }

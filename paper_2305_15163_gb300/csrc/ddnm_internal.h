@@ -32,6 +32,8 @@ constexpr int HR_INTS = 7;     // comp, then operands: centre, E, W, N, S (same 
 enum { MODE_INIT0 = 0, MODE_INIT1 = 1, MODE_LS = 2 };
 constexpr int ST_RUNNING = -1;
 enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_XTMODE, I_PAD, INST_INTS };
+constexpr int KKT_THREADS = 512;   // k_kkt: one CTA per instance, a warp per subdomain factorisation
+constexpr int SS_ROWS_DBL = 4096;  // staged W rows (doubles) per Schur-sum chunk, each for W and D_G^{-1} W
 // how the next evaluation forms its trial point xt (ist[I_XTMODE]): unchanged (xt = x), a new SQP step
 // (each subdomain back-substitutes s_i from s_lambda, then xt = x + s), or a backtrack (xt = x + alpha s)
 enum { XT_KEEP = 0, XT_NEWSTEP = 1, XT_BACKTRACK = 2 };
@@ -39,14 +41,23 @@ enum { D_PHI0 = 0, D_ALPHA, D_PHI, D_ALPHA_LAST, INST_DBLS };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
+// 32 consecutive output rows of a decoder subnet whose mask columns (in I_h numbering) all lie in the
+// window [c0, c0 + tw) (tw a multiple of 4, c0 + tw <= round4(|I_h|)): values dense over the window, zero
+// off the mask, stored [tw / 4][32 rows][4 columns] in the value pool at voff.
+struct TileDev {
+    int c0, tw;
+    long long voff;
+};
+
 // One chunk of a subdomain's collocation rows with the interior decoder outputs it needs.
 struct ChunkDev {
     int q0, nq;                    // first collocation row (subdomain-local) and row count
     int m;                         // interior outputs needed by these rows (chunk-local slots 0..m-1)
-    int pad;
+    int ntiles;                    // dense-window tiles of these outputs (0: the ELL table is used)
     long long col;                 // int pool: Kp x m ELL columns (slot-major), renumbered into I_h
     long long val;                 // value pool: Kp x m ELL values (slot-major)
     long long so;                  // value pool: scale[m], offset[m]
+    int tile0, pad;                // first tile in the tile table
 };
 
 // One subdomain: latent sizes, HR rows, subnet layout, offsets into the pools.
@@ -63,6 +74,7 @@ struct SubDev {
     long long w1O, b1O;            // interior subnet hidden layer: W1~ (hO x round4(nO)), b1~ (hO)
     long long w1G, b1G;            // interface subnet hidden layer: W1~ (hG x round4(nG)), b1~ (hG)
     long long colG, valG, soG;     // interface outputs, all rows: ELL slot-major (Kp x NG), scale/offset
+    int tileG0, ntilesG;           // dense-window tiles of the interface outputs (0 tiles: ELL)
     long long M;                   // M_i = C A_i stored N^G x n_C (row = interface output), value pool
     // full (not subnet) decoders for reconstruction
     int NO_full, wO_full, wG_full, K;
@@ -74,11 +86,11 @@ struct SubDev {
 
 // per-subdomain block layout (doubles) inside an instance's block area
 struct BlkLayout {
-    int H, rho, D, L, rinv, t, W, S, u, G, phi, flag, size;
+    int H, rho, D, L, rinv, t, W, u, G, phi, flag, size;
 };
 
-// per-subdomain flag values written by the evaluation
-constexpr double FLAG_PD = 0.0;          // H_i positive definite: L, rinv, t, W, u, S valid
+// per-subdomain flag values written by the factorisation
+constexpr double FLAG_PD = 0.0;          // H_i positive definite: L, rinv, t, W, u valid
 constexpr double FLAG_OMEGA_FAIL = 1.0;  // H_i^{OO} not positive definite: not solvable by this route
 constexpr double FLAG_GAMMA_SING = 2.0;  // H_i^{OO} PD but H_i not: L, rinv (first n^O columns), t (t_O,
                                          // then rho_G - L_GO t_O) and G = H_GG - L_GO D_O L_GO^T valid
@@ -94,7 +106,6 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
     b.rinv = o; o += ni;           // 1 / D_jj of H_i = L D L^T (L unit lower, stored below the diagonal)
     b.t = o; o += ni;
     b.W = o; o += nG * nC;
-    b.S = o; o += nC * nC;
     b.u = o; o += nC;
     b.G = o; o += nG * nG;         // Schur complement of H^{OO} in H_i (used when H_i is singular)
     b.phi = o; o += 1;
@@ -106,6 +117,10 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
 struct ProbDev {
     int n_sub, n_D, n_C, N_A, sum_NG, sum_NB, n_bnd, N_x;
     int nx, ny;
+    int fac_stride;                // factorisation scratch doubles per warp: max_i n_i^2 + 2 n_i + (n_i^G)^2
+    int ss_rows;                   // rows of W staged per Schur-sum chunk
+    int n_ss_chunks;               // Schur-sum chunks: subdomains [ss_chunk[k], ss_chunk[k + 1])
+    const int* ss_chunk;
     int n_split;                   // constraint CTAs per instance (ceil(N_A / con_split))
     int con_split;                 // constraint rows per constraint CTA
     double hx, hy, nu, bx0, by0;
@@ -116,6 +131,7 @@ struct ProbDev {
     int blk_stride;                // doubles per instance of the block area
     const SubDev* sub;
     const ChunkDev* chunk;
+    const TileDev* tiles;
     const void* vpool;             // decoder values and M_i, float (MIXED) or double (FP64)
     const int* ipool;
     const int* hr;                 // per subdomain HR_INTS x N_B (operand-major), all subdomains
@@ -151,7 +167,7 @@ constexpr int CTL_INTS = MAX_CHAINS * (2 + MAX_CLASSES);
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {
     int sx, hidO, hidG, outG, outO, Rr, red;   // value-type arrays
-    int dlam, dH, drho, dD, dL, drinv, dt, dW, dG; // double arrays
+    int dlam, dH, drho, dD, dt;                // double arrays
     int bytes;
 };
 
@@ -162,8 +178,8 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     const int rO = round4(s.nO + 1), rG = round4(s.nG + 1);
     int o = 0;
     e.sx = o; o = align16(o + MAX_NI * tsize);
-    e.hidO = o; o = align16(o + s.hO * rO * tsize);          // [sigma, sigma' W1 row] per hidden unit
-    e.hidG = o; o = align16(o + s.hG * rG * tsize);
+    e.hidO = o; o = align16(o + round4(s.hO) * rO * tsize);  // [sigma, sigma' W1 row] per hidden unit (+ zero rows)
+    e.hidG = o; o = align16(o + round4(s.hG) * rG * tsize);
     e.outG = o; o = align16(o + s.NG * rG * tsize);          // [y, Jacobian row] per interface output
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
     e.Rr = o; o = align16(o + HR_CHUNK * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
@@ -172,11 +188,7 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
     e.dD = o; o = align16(o + nC * s.nG * 8);
-    e.dL = o; o = align16(o + s.ni * s.ni * 8);
-    e.drinv = o; o = align16(o + s.ni * 8);
     e.dt = o; o = align16(o + s.ni * 8);
-    e.dW = o; o = align16(o + s.nG * nC * 8);
-    e.dG = o; o = align16(o + s.nG * s.nG * 8);
     e.bytes = o;
     return e;
 }

@@ -222,6 +222,53 @@ __device__ __forceinline__ void ell_accumulate(const int* col, const T* val, int
     }
 }
 
+// 32 consecutive decoder output rows of a dense-window tile, lane = row: acc[k] = sum_j val[lane][j] *
+// hid[c0 + j][k] over the tile's window.  Every lane reads the same hidden record (one broadcast shared-
+// memory wavefront per 16 bytes) and its own 4 window values per vector load (coalesced over the warp);
+// three such loads are kept in flight ahead of their use.
+template <typename T, int R>
+__device__ __forceinline__ void tile_quad(const T* h, const T* v, T* acc) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const T* hr = h + u * R;
+#pragma unroll
+        for (int k = 0; k < R; k += 4) {
+            T hv[4];
+            ld4(hr + k, hv);
+            acc[k] += v[u] * hv[0];
+            acc[k + 1] += v[u] * hv[1];
+            acc[k + 2] += v[u] * hv[2];
+            acc[k + 3] += v[u] * hv[3];
+        }
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void tile_accumulate(const TileDev& TD, const T* V, const T* hid, int lane, T* acc) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = T(0);
+    const T* vp = V + TD.voff + lane * 4;
+    const T* h = hid + (size_t)TD.c0 * R;
+    const int tw = TD.tw;
+    // three quads of window values in flight: b0, b1, b2 hold columns j, j + 4, j + 8
+    T b0[4], b1[4] = {T(0), T(0), T(0), T(0)}, b2[4] = {T(0), T(0), T(0), T(0)};
+    ld4(vp, b0);
+    if (4 < tw) ld4(vp + 4 * 32, b1);
+    if (8 < tw) ld4(vp + 8 * 32, b2);
+    for (int j = 0; j < tw; j += 12) {
+        tile_quad<T, R>(h + (size_t)j * R, b0, acc);
+        if (j + 12 < tw) ld4(vp + (size_t)(j + 12) * 32, b0);
+        if (j + 4 < tw) {
+            tile_quad<T, R>(h + (size_t)(j + 4) * R, b1, acc);
+            if (j + 16 < tw) ld4(vp + (size_t)(j + 16) * 32, b1);
+        }
+        if (j + 8 < tw) {
+            tile_quad<T, R>(h + (size_t)(j + 8) * R, b2, acc);
+            if (j + 20 < tw) ld4(vp + (size_t)(j + 20) * 32, b2);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------ evaluation
 
 // stencil constants 1/(2h_x), 1/(2h_y), nu/h_x^2, nu/h_y^2 in the value type (precomputed on the host)
@@ -320,10 +367,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     double* dH = (double*)(smem + L.dH);
     double* drho = (double*)(smem + L.drho);
     double* dD = (double*)(smem + L.dD);
-    double* dL = (double*)(smem + L.dL);
-    double* drinv = (double*)(smem + L.drinv);
     double* dt = (double*)(smem + L.dt);
-    double* dW = (double*)(smem + L.dW);
 
     const T* V = (const T*)P.vpool;
     const int* IP = P.ipool;
@@ -339,7 +383,10 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     for (int c = tid; c < nC; c += nth) dlam[c] = P.lamt[(size_t)b * nC + c];
     __syncthreads();
 
-    // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]
+    // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]; the rows that pad each
+    // record array to a multiple of 4 are zero (dense-window tiles may span them with zero values)
+    for (int e = tid; e < (round4(S.hO) - S.hO) * RO; e += nth) hidO[(size_t)S.hO * RO + e] = T(0);
+    for (int e = tid; e < (round4(S.hG) - S.hG) * RG; e += nth) hidG[(size_t)S.hG * RG + e] = T(0);
     for (int c = tid; c < S.hO + S.hG; c += nth) {
         const bool g = c >= S.hO;
         if (!g) {
@@ -408,11 +455,43 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     const int nwarp = nth >> 5;
     for (int q = 0; q < S.n_chunks; ++q) {
         const ChunkDev Cq = P.chunk[S.chunk0 + q];
-        // decoder outputs of this chunk's interior rows (and, with the first chunk, all interface rows)
+        // decoder outputs of this chunk's interior rows (and, with the first chunk, all interface rows):
+        // dense-window tiles, warp per tile, where the host built them; the ELL tables otherwise
         {
-            const int nG_items = q == 0 ? NG : 0;
-            for (int it = tid; it < Cq.m + nG_items; it += nth) {
-                if (it < Cq.m) {
+            const int tO = Cq.ntiles, tG = q == 0 ? S.ntilesG : 0;
+            const int w = tid >> 5, lane = tid & 31;
+            for (int t = w; t < tO + tG; t += nwarp) {
+                if (t < tO) {
+                    T acc[RO];
+                    tile_accumulate<T, RO>(P.tiles[Cq.tile0 + t], V, hidO, lane, acc);
+                    const int r = t * 32 + lane;
+                    if (r < Cq.m) {
+                        const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
+                        acc[0] = off + sc * acc[0];
+#pragma unroll
+                        for (int k = 1; k < RO; ++k) acc[k] *= sc;
+#pragma unroll
+                        for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
+                    }
+                } else {
+                    T acc[RG];
+                    tile_accumulate<T, RG>(P.tiles[S.tileG0 + t - tO], V, hidG, lane, acc);
+                    const int r = (t - tO) * 32 + lane;
+                    if (r < NG) {
+                        const T sc = V[S.soG + r], off = V[S.soG + NG + r];
+                        acc[0] = off + sc * acc[0];
+#pragma unroll
+                        for (int k = 1; k < RG; ++k) acc[k] *= sc;
+#pragma unroll
+                        for (int k = 0; k < RG; k += 4) st4(outG + (size_t)r * RG + k, acc + k);
+                        gout[r] = acc[0];
+                    }
+                }
+            }
+            const int mO = tO ? 0 : Cq.m;                 // rows left to the ELL tables
+            const int mG = (q == 0 && !S.ntilesG) ? NG : 0;
+            for (int it = tid; it < mO + mG; it += nth) {
+                if (it < mO) {
                     const int r = it;
                     T acc[RO];
 #pragma unroll
@@ -427,7 +506,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
 #pragma unroll
                     for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
                 } else {
-                    const int r = it - Cq.m;
+                    const int r = it - mO;
                     T acc[RG];
 #pragma unroll
                     for (int k = 0; k < RG; ++k) acc[k] = T(0);
@@ -567,119 +646,40 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
     __syncthreads();
 
-    // FP64 tail (warp 0): rho_i = R^T r + E_i^T lambda and ||rho_i||^2; H_i = L D L^T (unit lower L,
-    // one reciprocal per pivot: FP64 division and square root sit on this part's slowest path);
-    // t = L^{-1} rho; W = L_GG^{-1} D_i^T (the Omega rows of L^{-1} E_i^T vanish); with the interface
-    // pivots D_G: u = W^T D_G^{-1} t_G and S_i = W^T D_G^{-1} W.  Lemma 1 only needs H_i PD on
-    // null(E_i): when the collocation rows miss an interface direction, H_i is singular in its G block
-    // while H_i^{OO} is PD; the factorisation then stops after the O columns and the step kernel solves
-    // the subdomain through G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).
+    // rho_i = R^T r + E_i^T lambda in FP64 (E_i = [0, D_i]: only the interface entries get D_i^T lambda),
+    // warp k forming entry n^O + k with its lanes over the multipliers; then phi_i = ||rho_i||^2.  The
+    // factorisation of H_i is left to k_factor, which runs only at accepted points.
     double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
     const BlkLayout BL = blk_layout(ni, nG, nC);
-    double* dGs = (double*)(smem + L.dG);
-    __shared__ int s_flag;
-    if (tid < 32) {
-        const int lane = tid;
-        if (lane < ni) {
-            double v = drho[lane];
-            if (lane >= nO)
-                for (int c = 0; c < nC; ++c) v += dD[c * nG + lane - nO] * dlam[c];
-            drho[lane] = v;
-            dt[lane] = v;
-        }
-        for (int e = lane; e < ni * ni; e += 32) dL[e] = dH[e];
-        __syncwarp();
-        int flag = 0;
-        for (int j = 0; j < ni; ++j) {
-            if (j == nO)      // Schur complement of H^{OO}: the trailing block after the O columns
-                for (int e = lane; e < nG * nG; e += 32) dGs[e] = dL[(nO + e / nG) * ni + nO + e % nG];
-            __syncwarp();
-            const double d = dL[j * ni + j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                flag = j < nO ? 1 : 2;
-                break;
-            }
-            const double r = 1.0 / d;
-            const int m = ni - j - 1;
-            for (int e = lane; e < m * (m + 1) / 2; e += 32) {     // trailing lower triangle, unscaled column j
-                int i = 0, rem = e;
-                while (rem > i) {
-                    rem -= i + 1;
-                    ++i;
-                }
-                const int ii = j + 1 + i, kk = j + 1 + rem;
-                dL[ii * ni + kk] -= dL[ii * ni + j] * r * dL[kk * ni + j];
-            }
-            __syncwarp();
-            for (int i = j + 1 + lane; i < ni; i += 32) dL[i * ni + j] *= r;   // column j of L
-            if (lane == 0) drinv[j] = r;
-            __syncwarp();
-        }
-        if (flag != 1) {
-            const int nf = flag == 0 ? ni : nO;       // unit forward substitution over the factored columns
-            for (int j = 0; j < nf; ++j) {
-                const double tj = dt[j];
-                for (int i = j + 1 + lane; i < ni; i += 32) dt[i] -= dL[i * ni + j] * tj;
-                __syncwarp();
-            }
-        }
-        if (flag == 0) {
-            for (int c = lane; c < nC; c += 32) {
-                double uc = 0.0;
-                for (int k = 0; k < nG; ++k) {
-                    double v = dD[c * nG + k];
-                    for (int m = 0; m < k; ++m) v -= dL[(nO + k) * ni + nO + m] * dW[m * nC + c];
-                    dW[k * nC + c] = v;
-                    uc += v * drinv[nO + k] * dt[nO + k];
-                }
-                blk[BL.u + c] = uc;
-            }
-        }
-        double ph = lane < ni ? drho[lane] * drho[lane] : 0.0;
-        ph = warp_sum(ph);
-        if (lane == 0) {
-            blk[BL.phi] = ph;
-            blk[BL.flag] = (double)flag;
-            s_flag = flag;
+    {
+        const int w = tid >> 5, lane = tid & 31;
+        for (int k = w; k < nG; k += nwarp) {
+            double v = 0.0;
+            for (int c = lane; c < nC; c += 32) v += dD[c * nG + k] * dlam[c];
+            v = warp_sum(v);
+            if (lane == 0) drho[nO + k] += v;
         }
     }
     __syncthreads();
+    if (tid < 32) {
+        const double r = tid < ni ? drho[tid] : 0.0;
+        const double ph = warp_sum(r * r);
+        if (tid == 0) blk[BL.phi] = ph;
+    }
     for (int e = tid; e < ni * ni; e += nth) blk[BL.H + e] = dH[e];
     if (tid < ni) blk[BL.rho + tid] = drho[tid];
     for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
-    if (s_flag != 1) {
-        for (int e = tid; e < ni * ni; e += nth) blk[BL.L + e] = dL[e];
-        if (tid < ni) {
-            blk[BL.t + tid] = dt[tid];
-            blk[BL.rinv + tid] = drinv[tid];
-        }
-    }
-    if (s_flag == 2)
-        for (int e = tid; e < nG * nG; e += nth) blk[BL.G + e] = dGs[e];
-    if (s_flag == 0) {
-        for (int e = tid; e < nG * nC; e += nth) blk[BL.W + e] = dW[e];
-        // S_i = W^T D_G^{-1} W (n_C x n_C, symmetric: lower triangle computed once, mirrored)
-        for (int e = tid; e < nC * (nC + 1) / 2; e += nth) {
-            int c1 = 0, rem = e;
-            while (rem > c1) {
-                rem -= c1 + 1;
-                ++c1;
-            }
-            const int c2 = rem;
-            double v = 0.0;
-            for (int k = 0; k < nG; ++k) v += dW[k * nC + c1] * drinv[nO + k] * dW[k * nC + c2];
-            blk[BL.S + c1 * nC + c2] = v;
-            blk[BL.S + c2 * nC + c1] = v;
-        }
-    }
 }
 
 // One launch per class of subdomains sharing the padded record widths (RO, RG).  Items are (instance,
 // subdomain of the class); item k is instance k % B of subdomain subs[k / B] (subs: the class's subdomains,
 // largest first).  With ctr == NULL CTA k takes item k; otherwise the grid is persistent and its CTAs claim
 // items from the counter *ctr (zero before the launch) until none are left.
+// register budget: 4 CTAs per SM for the narrow records, 3 or 2 for the wider ones (no spills)
+__host__ __device__ constexpr int eval_min_ctas(int ro, int rg) { return ro + rg <= 12 ? 4 : (ro + rg <= 20 ? 3 : 2); }
+
 template <typename T, int RO, int RG>
-__global__ void __launch_bounds__(EVAL_THREADS) k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr) {
+__global__ void __launch_bounds__(EVAL_THREADS, eval_min_ctas(RO, RG)) k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int items = B * nsub;
     if (!ctr) {
@@ -754,219 +754,319 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
         if (lane == 0) out[c] = tree_sum(part[w], nb, 1);
         __syncwarp();
     }
-    // this slice's share of the Schur sums over the subdomains with H_i PD: S = sum_i S_i (lower
-    // triangle, mirrored) and sum_i u_i, for the step kernel
-    __shared__ unsigned char pd[MAX_SUB];
-    const int nC = P.n_C, ns = P.n_sub;
-    const double* blk = P.blk + (size_t)b * P.blk_stride;
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-        const SubDev& S = P.sub[i];
-        pd[i] = blk[S.blk + blk_layout(S.ni, S.nG, nC).flag] == FLAG_PD;
-    }
-    __syncthreads();
-    const int ntri = nC * (nC + 1) / 2, NE = ntri + nC;
-    const int per = (NE + P.n_split - 1) / P.n_split;
-    double* Ss = P.Ssum + (size_t)b * ((size_t)nC * nC + nC);
-    for (int e = sp * per + threadIdx.x; e < min(NE, (sp + 1) * per); e += blockDim.x) {
-        int off_in_blk, c1 = -1, c2 = 0;
-        if (e < ntri) {
-            int rem = e;
-            c1 = 0;
-            while (rem > c1) {
-                rem -= c1 + 1;
-                ++c1;
-            }
-            c2 = rem;
-        }
-        double v0 = 0.0, v1 = 0.0;
-        for (int i = 0; i < ns; ++i) {
-            if (!pd[i]) continue;
-            const SubDev& S = P.sub[i];
-            const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-            off_in_blk = c1 >= 0 ? BL.S + c1 * nC + c2 : BL.u + (e - ntri);
-            if (i & 1) v1 += blk[S.blk + off_in_blk];
-            else v0 += blk[S.blk + off_in_blk];
-        }
-        const double v = v0 + v1;
-        if (c1 >= 0) {
-            Ss[c1 * nC + c2] = v;
-            Ss[c2 * nC + c1] = v;
-        } else {
-            Ss[(size_t)nC * nC + (e - ntri)] = v;
-        }
-    }
 }
 
 // ------------------------------------------------------------------------ SQP step
 
-__global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
-    extern __shared__ __align__(16) double sm[];
+// FP64 factorisation of the Gauss-Newton block of subdomain i of instance b at an accepted point, one
+// warp (scratch: fac_stride doubles): H_i = L D L^T (unit lower L, one reciprocal per pivot),
+// t = L^{-1} rho_i, W = L_GG^{-1} D_i^T (the Omega rows of L^{-1} E_i^T vanish), u_i = W^T D_G^{-1} t_G.
+// Lemma 1 only needs H_i PD on null(E_i): when the collocation rows miss an interface direction, H_i is
+// singular in its G block while H_i^{OO} is PD; the factorisation then stops after the O columns and the
+// subdomain is handled through G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).  Returns the
+// flag (FLAG_PD, FLAG_OMEGA_FAIL, FLAG_GAMMA_SING as 0, 1, 2), also stored in the block.
+__device__ int factor_sub(const ProbDev& P, const SubDev& S, double* blk, double* L, int lane) {
+    const int ni = S.ni, nO = S.nO, nG = S.nG, nC = P.n_C;
+    const BlkLayout BL = blk_layout(ni, nG, nC);
+    double* t = L + ni * ni;
+    double* rinv = t + ni;
+    double* G = rinv + ni;
+    for (int e = lane; e < ni * ni; e += 32) L[e] = blk[BL.H + e];
+    if (lane < ni) t[lane] = blk[BL.rho + lane];
+    __syncwarp();
+    int flag = 0;
+    for (int j = 0; j < ni; ++j) {
+        if (j == nO) {
+            for (int e = lane; e < nG * nG; e += 32) G[e] = L[(nO + e / nG) * ni + nO + e % nG];
+            __syncwarp();
+        }
+        const double d = L[j * ni + j];
+        if (!(d > 0.0) || !isfinite(d)) {   // d is the same for every lane: a uniform branch
+            flag = j < nO ? 1 : 2;
+            break;
+        }
+        const double r = 1.0 / d;
+        const int m = ni - j - 1;
+        for (int e = lane; e < m * (m + 1) / 2; e += 32) {     // trailing lower triangle, unscaled column j
+            int i = 0, rem = e;
+            while (rem > i) {
+                rem -= i + 1;
+                ++i;
+            }
+            const int ii = j + 1 + i, kk = j + 1 + rem;
+            L[ii * ni + kk] -= L[ii * ni + j] * r * L[kk * ni + j];
+        }
+        __syncwarp();
+        for (int i = j + 1 + lane; i < ni; i += 32) L[i * ni + j] *= r;   // column j of L
+        if (lane == 0) rinv[j] = r;
+        __syncwarp();
+    }
+    if (flag != 1) {
+        const int nf = flag == 0 ? ni : nO;       // unit forward substitution over the factored columns
+        for (int j = 0; j < nf; ++j) {
+            const double tj = t[j];
+            for (int i = j + 1 + lane; i < ni; i += 32) t[i] -= L[i * ni + j] * tj;
+            __syncwarp();
+        }
+        for (int e = lane; e < ni * ni; e += 32) blk[BL.L + e] = L[e];
+        if (lane < ni) {
+            blk[BL.t + lane] = t[lane];
+            blk[BL.rinv + lane] = rinv[lane];
+        }
+    }
+    if (flag == 0) {
+        for (int c = lane; c < nC; c += 32) {
+            double wv[MAX_NG];
+            double uc = 0.0;
+#pragma unroll
+            for (int k = 0; k < MAX_NG; ++k) {
+                if (k < nG) {
+                    double v = blk[BL.D + c * nG + k];
+#pragma unroll
+                    for (int m = 0; m < k; ++m) v -= L[(nO + k) * ni + nO + m] * wv[m];
+                    wv[k] = v;
+                    blk[BL.W + k * nC + c] = v;
+                    uc += v * rinv[nO + k] * t[nO + k];
+                }
+            }
+            blk[BL.u + c] = uc;
+        }
+    }
+    if (flag == 2)
+        for (int e = lane; e < nG * nG; e += 32) blk[BL.G + e] = G[e];
+    if (lane == 0) blk[BL.flag] = (double)flag;
+    __syncwarp();
+    return flag;
+}
+
+// One SQP pass's work after the evaluation and the constraint residual, one CTA per instance:
+//  1. judge the evaluation: merit phi = ||F||_2 with F = [rho_1 .. rho_n; Atil] (Sec. 4.1), Armijo
+//     backtracking test, update and stopping rule (Eq. sqp_update, Sec. 7.1).  A rejected trial becomes
+//     the next backtrack (the evaluation forms xt = x + alpha beta s); the start-up pass solves for the
+//     least-squares multiplier (Sec. 7.2);
+//  2. at an accepted point that does not stop: factor every subdomain's block (a warp per subdomain);
+//  3. the border of the Schur complement of Eq. (sqp_system) over the subdomains with H_i PD,
+//       S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G,i^{-1} W_i,   r = Atil - sum_i u_i,
+//     each entry summed over the subdomains in index order (rows k ascending inside one), W_i and
+//     D_G^{-1} W_i staged in shared memory a chunk of subdomains at a time;
+//  4. S = L_S D_S L_S^T and s_lambda; the subdomains F whose H_i is singular in the G block keep their
+//     interface steps s_F as unknowns: with Z = L_S^{-1} D_F, q = L_S^{-1} r and G_F their Schur
+//     complements, (G_F + Z^T D_S^{-1} Z) s_F = -(rho_G - L_GO t_O)_F - Z^T D_S^{-1} q and
+//     s_lambda = L_S^{-T} D_S^{-1} (q + Z s_F).  Every other piece of s is back-substituted by the
+//     evaluation of its subdomain (form_trial).
+__global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
+    extern __shared__ __align__(16) double ksm[];
     __shared__ double scratch[32];
+    __shared__ int s_mF, s_over, s_fail;
+    __shared__ int fcol_sub[MAX_MF], fcol_k[MAX_MF];
+    __shared__ unsigned char s_fl[MAX_SUB];
     const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    const int w = tid >> 5, lane = tid & 31, nw = nth >> 5;
     if (b >= B) return;
     int* ist = P.ist + (size_t)b * INST_INTS;
     double* dst = P.dst + (size_t)b * INST_DBLS;
     if (ist[I_STATUS] != ST_RUNNING) return;
     const int nC = P.n_C, ns = P.n_sub, nD = P.n_D;
     double* blk = P.blk + (size_t)b * P.blk_stride;
-    double* Sm = sm;                  // nC x nC
+    double* Sm = ksm;                 // nC x nC (lower triangle used)
     double* rhs = Sm + nC * nC;       // nC
-    double* At = rhs + nC;            // nC: Atil (sum of the slice partials)
+    double* At = rhs + nC;            // nC: Atil
     double* rv = At + nC;             // nC: reciprocal pivots
-    double* x_ = P.x + (size_t)b * nD;
-    double* xt = P.xt + (size_t)b * nD;
-    double* s_ = P.s + (size_t)b * nD;
+    double* us = rv + nC;             // nC: sum_i u_i
+    double* work = us + nC;           // union: factor scratch | W staging | Z, T
     double* lam = P.lam + (size_t)b * nC;
     double* lamt = P.lamt + (size_t)b * nC;
     double* slam = P.slam + (size_t)b * nC;
 
-    for (int c = tid; c < nC; c += nth) At[c] = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
-    __syncthreads();
-    // merit phi^2 = sum_i ||rho_i||^2 + ||Atil||^2; subdomains whose H_i^{OO} was not PD
-    double acc = 0.0, fl = 0.0;
-    for (int i = tid; i < ns; i += nth) {
-        const SubDev& S = P.sub[i];
-        const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-        acc += blk[S.blk + BL.phi];
-        fl += blk[S.blk + BL.flag] == FLAG_OMEGA_FAIL ? 1.0 : 0.0;
-    }
-    for (int c = tid; c < nC; c += nth) acc += At[c] * At[c];
-    const double phi2 = block_sum(acc, scratch);
-    const bool fail = block_sum(fl, scratch) != 0.0;
-    const double phi = sqrt(phi2);
-    const int mode = ist[I_MODE];
-    const int iters0 = ist[I_ITERS], nbt = ist[I_NBT];
-    const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
-    __syncthreads();
-    if (tid == 0) ist[I_NEVALS] += 1;
-
-    if (mode == MODE_INIT0) {
-        // least-squares multiplier (Sec. 7.2): min_l sum_i ||rho_i^G + D_i^T l||^2 at lambda = 0,
-        // normal equations (sum_i D_i D_i^T) l = -sum_i D_i rho_i^G
-        for (int e = tid; e < nC * nC; e += nth) {
-            const int c1 = e / nC, c2 = e % nC;
-            double v = 0.0;
-            for (int i = 0; i < ns; ++i) {
-                const SubDev& S = P.sub[i];
-                const double* D = blk + S.blk + blk_layout(S.ni, S.nG, nC).D;
-                for (int k = 0; k < S.nG; ++k) v += D[c1 * S.nG + k] * D[c2 * S.nG + k];
-            }
-            Sm[e] = v;
+    // ---- 1. merit, Armijo, update
+    {
+        double acc = 0.0;
+        for (int i = tid; i < ns; i += nth) {
+            const SubDev& S = P.sub[i];
+            acc += blk[S.blk + blk_layout(S.ni, S.nG, nC).phi];
         }
         for (int c = tid; c < nC; c += nth) {
-            double v = 0.0;
-            for (int i = 0; i < ns; ++i) {
-                const SubDev& S = P.sub[i];
-                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-                const double* D = blk + S.blk + BL.D;
-                const double* rho = blk + S.blk + BL.rho;
-                for (int k = 0; k < S.nG; ++k) v -= D[c * S.nG + k] * rho[S.nO + k];
-            }
-            rhs[c] = v;
+            const double a = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
+            At[c] = a;
+            acc += a * a;
         }
-        if (!block_ldl(Sm, rv, nC)) {
-            if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
+        const double phi2 = block_sum(acc, scratch);   // barriers inside: every thread has read ist
+        const double phi = sqrt(phi2);
+        const int mode = ist[I_MODE];
+        const int iters0 = ist[I_ITERS], nbt = ist[I_NBT];
+        const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
+        __syncthreads();
+        if (mode == MODE_INIT0) {
+            if (tid == 0) ist[I_NEVALS] += 1;
+        } else {
+            bool accept = true, lsfail = false;
+            if (mode == MODE_LS && !(phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0)) {
+                if (nbt < P.max_bt) accept = false;
+                else lsfail = true;
+            }
+            if (!accept) {
+                const double a = alpha * P.beta;
+                for (int c = tid; c < nC; c += nth) lamt[c] = lam[c] + a * slam[c];
+                if (tid == 0) {
+                    ist[I_NEVALS] += 1;
+                    dst[D_ALPHA] = a;
+                    ist[I_NBT] = nbt + 1;
+                    ist[I_XTMODE] = XT_BACKTRACK;
+                    atomicAdd(P.active, 1);
+                }
+                return;
+            }
+            double* x_ = P.x + (size_t)b * nD;
+            const double* xt = P.xt + (size_t)b * nD;
+            for (int k = tid; k < nD; k += nth) x_[k] = xt[k];
+            for (int c = tid; c < nC; c += nth) lam[c] = lamt[c];
+            const int iters = iters0 + (mode == MODE_LS ? 1 : 0);
+            int status = ST_RUNNING;
+            if (!isfinite(phi)) status = DDNM_NONFINITE;
+            else if (phi < P.tol) status = DDNM_CONVERGED;
+            else if (iters >= P.max_iter) status = DDNM_MAX_ITER;
+            if (tid == 0) {
+                ist[I_NEVALS] += 1;
+                ist[I_ITERS] = iters;
+                dst[D_PHI0] = phi;
+                dst[D_PHI] = phi;
+                if (mode == MODE_LS) dst[D_ALPHA_LAST] = alpha;
+                if (lsfail) ist[I_FLAGS] |= DDNM_FLAG_LS_FAIL;
+                if (status != ST_RUNNING) ist[I_STATUS] = status;
+            }
+            if (status != ST_RUNNING) return;
+        }
+        if (mode == MODE_INIT0) {
+            // least-squares multiplier (Sec. 7.2): min_l sum_i ||rho_i^G + D_i^T l||^2 at lambda = 0,
+            // normal equations (sum_i D_i D_i^T) l = -sum_i D_i rho_i^G
+            for (int e = tid; e < nC * nC; e += nth) {
+                const int c1 = e / nC, c2 = e % nC;
+                double v = 0.0;
+                for (int i = 0; i < ns; ++i) {
+                    const SubDev& S = P.sub[i];
+                    const double* D = blk + S.blk + blk_layout(S.ni, S.nG, nC).D;
+                    for (int k = 0; k < S.nG; ++k) v += D[c1 * S.nG + k] * D[c2 * S.nG + k];
+                }
+                Sm[e] = v;
+            }
+            for (int c = tid; c < nC; c += nth) {
+                double v = 0.0;
+                for (int i = 0; i < ns; ++i) {
+                    const SubDev& S = P.sub[i];
+                    const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+                    const double* D = blk + S.blk + BL.D;
+                    const double* rho = blk + S.blk + BL.rho;
+                    for (int k = 0; k < S.nG; ++k) v -= D[c * S.nG + k] * rho[S.nO + k];
+                }
+                rhs[c] = v;
+            }
+            if (!block_ldl(Sm, rv, nC)) {
+                if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
+                return;
+            }
+            block_ldl_solve(Sm, rv, nC, rhs);
+            for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
+            if (tid == 0) {
+                ist[I_MODE] = MODE_INIT1;
+                ist[I_XTMODE] = XT_KEEP;
+                atomicAdd(P.active, 1);
+            }
             return;
         }
-        block_ldl_solve(Sm, rv, nC, rhs);
-        for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
-        if (tid == 0) {
-            ist[I_MODE] = MODE_INIT1;
-            ist[I_XTMODE] = XT_KEEP;
-            atomicAdd(P.active, 1);
-        }
-        return;
     }
 
-    bool accept = true;
-    bool lsfail = false;
-    if (mode == MODE_LS) {
-        const bool armijo = phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0;
-        if (!armijo) {
-            if (nbt < P.max_bt) accept = false;
-            else lsfail = true;
-        }
+    // ---- 2. factor the subdomain blocks, a warp per subdomain
+    for (int i = w; i < ns; i += nw) {
+        const SubDev& S = P.sub[i];
+        const int fl = factor_sub(P, S, blk + S.blk, work + (size_t)w * P.fac_stride, lane);
+        if (lane == 0) s_fl[i] = (unsigned char)fl;
     }
-    if (!accept) {
-        const double a = alpha * P.beta;
-        for (int c = tid; c < nC; c += nth) lamt[c] = lam[c] + a * slam[c];
-        if (tid == 0) {
-            dst[D_ALPHA] = a;
-            ist[I_NBT] = nbt + 1;
-            ist[I_XTMODE] = XT_BACKTRACK;       // the evaluation forms xt = x + alpha s
-            atomicAdd(P.active, 1);
-        }
-        return;
-    }
-    // accept the trial point
-    for (int k = tid; k < nD; k += nth) x_[k] = xt[k];
-    for (int c = tid; c < nC; c += nth) lam[c] = lamt[c];
-    const int iters = iters0 + (mode == MODE_LS ? 1 : 0);
-    int status = ST_RUNNING;
-    if (!isfinite(phi)) status = DDNM_NONFINITE;
-    else if (phi < P.tol) status = DDNM_CONVERGED;
-    else if (iters >= P.max_iter) status = DDNM_MAX_ITER;
-    else if (fail) status = DDNM_KKT_FAIL;
+    for (int e = tid; e < nC * nC; e += nth) Sm[e] = 0.0;
+    for (int c = tid; c < nC; c += nth) us[c] = 0.0;
+    __syncthreads();
     if (tid == 0) {
-        ist[I_ITERS] = iters;
-        dst[D_PHI0] = phi;
-        dst[D_PHI] = phi;
-        if (mode == MODE_LS) dst[D_ALPHA_LAST] = alpha;
-        if (lsfail) ist[I_FLAGS] |= DDNM_FLAG_LS_FAIL;
-    }
-    if (status != ST_RUNNING) {
-        __syncthreads();
-        if (tid == 0) ist[I_STATUS] = status;
-        return;
-    }
-
-    // Schur complement of Eq. (sqp_system) over the subdomains with H_i PD (H_i = L_i D_i L_i^T):
-    //   S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G^{-1} W_i,  r = Atil - sum_i u_i.
-    // Subdomains F with H_i singular in the G block (H_i^{OO} PD) keep their interface steps s_F as
-    // unknowns: with S = L_S D_S L_S^T, Z = L_S^{-1} D_F, q = L_S^{-1} r and G_F the Schur complements,
-    //   (G_F + Z^T D_S^{-1} Z) s_F = -(rho_G - L_GO t_O)_F - Z^T D_S^{-1} q,
-    //   s_lambda = L_S^{-T} D_S^{-1} (q + Z s_F).
-    __shared__ int s_nF, s_mF, s_over;
-    __shared__ int fsub[MAX_MF], fcol_sub[MAX_MF], fcol_k[MAX_MF];
-    if (tid == 0) {
-        int nF = 0, mF = 0, over = 0;
+        int mF = 0, over = 0, fail = 0;
         for (int i = 0; i < ns; ++i) {
-            const SubDev& S = P.sub[i];
-            const int fl = (int)blk[S.blk + blk_layout(S.ni, S.nG, nC).flag];
+            const int fl = s_fl[i];
+            if (fl == 1) fail = 1;
             if (fl == 2) {
-                if (mF + S.nG > MAX_MF) {
+                const int nG = P.sub[i].nG;
+                if (mF + nG > MAX_MF) {
                     over = 1;
-                    break;
+                    continue;
                 }
-                fsub[nF++] = i;
-                for (int k = 0; k < S.nG; ++k) {
+                for (int k = 0; k < nG; ++k) {
                     fcol_sub[mF] = i;
                     fcol_k[mF] = k;
                     ++mF;
                 }
             }
         }
-        s_nF = nF;
         s_mF = mF;
         s_over = over;
+        s_fail = fail;
     }
     __syncthreads();
-    const int nF = s_nF, mF = s_mF;
-    if (s_over) {
+    const int mF = s_mF;
+    if (s_fail || s_over) {      // H_i^{OO} not PD somewhere, or too many singular interface blocks
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
         return;
     }
-    // S and r = Atil - sum_i u_i from the sums the constraint kernel formed over the PD subdomains
+
+    // ---- 3. Schur sums S (lower triangle) and sum_i u_i
     {
-        const double* Ss = P.Ssum + (size_t)b * ((size_t)nC * nC + nC);
-        for (int e = tid; e < nC * nC; e += nth) Sm[e] = Ss[e];
-        for (int c = tid; c < nC; c += nth) rhs[c] = At[c] - Ss[(size_t)nC * nC + c];
+        double* Wsh = work;                                  // ss_rows x nC
+        double* Wr = work + (size_t)P.ss_rows * nC;          // ss_rows x nC, row k scaled by 1 / D_kk
+        const int ntri = nC * (nC + 1) / 2, NE = ntri + nC;
+        for (int ch = 0; ch < P.n_ss_chunks; ++ch) {
+            const int i0 = P.ss_chunk[ch], i1 = P.ss_chunk[ch + 1];
+            int rows = 0;
+            for (int i = i0; i < i1; ++i) {
+                const SubDev& S = P.sub[i];
+                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+                const double* bi = blk + S.blk;
+                const bool pd = s_fl[i] == 0;
+                for (int e = tid; e < S.nG * nC; e += nth) {
+                    const int k = e / nC;
+                    const double wv = pd ? bi[BL.W + e] : 0.0;
+                    const double r = pd ? bi[BL.rinv + S.nO + k] : 0.0;
+                    Wsh[(size_t)rows * nC + e] = wv;
+                    Wr[(size_t)rows * nC + e] = wv * r;
+                }
+                rows += S.nG;
+            }
+            __syncthreads();
+            for (int e = tid; e < NE; e += nth) {
+                if (e < ntri) {
+                    int c1 = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                    while (c1 * (c1 + 1) / 2 > e) --c1;
+                    while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
+                    const int c2 = e - c1 * (c1 + 1) / 2;
+                    double v = Sm[c1 * nC + c2];
+                    for (int r = 0; r < rows; ++r) v += Wr[r * nC + c1] * Wsh[r * nC + c2];
+                    Sm[c1 * nC + c2] = v;
+                } else {
+                    const int c = e - ntri;
+                    double v = us[c];
+                    for (int i = i0; i < i1; ++i) {
+                        if (s_fl[i] != 0) continue;
+                        const SubDev& S = P.sub[i];
+                        v += blk[S.blk + blk_layout(S.ni, S.nG, nC).u + c];
+                    }
+                    us[c] = v;
+                }
+            }
+            __syncthreads();
+        }
+        for (int c = tid; c < nC; c += nth) rhs[c] = At[c] - us[c];
     }
+
+    // ---- 4. the border system
     if (!block_ldl(Sm, rv, nC)) {
         if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
         return;
     }
-    double* Z = rv + nC;                  // nC x (mF + 1), row-major (last column: q)
+    double* Z = work;                     // nC x (mF + 1), row-major (last column: q)
     double* T = Z + nC * (MAX_MF + 1);    // MAX_MF x MAX_MF
     double* rT = T + MAX_MF * MAX_MF;     // MAX_MF reciprocal pivots of T
     double* sF = rT + MAX_MF;             // MAX_MF
@@ -1029,14 +1129,13 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(ProbDev P, int B) {
             for (int i = tid; i < k; i += nth) rhs[i] -= Sm[k * nC + i] * xk;
         }
         __syncthreads();
+        double* s_ = P.s + (size_t)b * nD;
+        for (int a = tid; a < mF; a += nth) {
+            const SubDev& S = P.sub[fcol_sub[a]];
+            s_[S.xoff + S.nO + fcol_k[a]] = sF[a];
+        }
+        __syncthreads();
     }
-    // interface steps of the G-singular subdomains; every other piece of s is back-substituted by the
-    // evaluation of the subdomain itself (form_trial)
-    for (int a = tid; a < mF; a += nth) {
-        const SubDev& S = P.sub[fcol_sub[a]];
-        s_[S.xoff + S.nO + fcol_k[a]] = sF[a];
-    }
-    __syncthreads();
     for (int c = tid; c < nC; c += nth) {
         slam[c] = rhs[c];
         lamt[c] = lam[c] + rhs[c];
@@ -1326,7 +1425,7 @@ template <typename T>
 int set_smem_attrs(ddnm_ctx* ctx) {
     for (const auto& g : ctx->eval_classes)
         CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem));
-    CK(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->step_smem));
+    CK(cudaFuncSetAttribute(k_kkt, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->kkt_smem));
     CK(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(ctx->rec_smem, 16)));
     return DDNM_OK;
 }
@@ -1368,7 +1467,7 @@ int run_pass(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persi
     if (rc) return rc;
     if (host_style) CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
     const int k = tstart(ctx, 2, st);
-    k_step<<<B, STEP_THREADS, ctx->step_smem, st>>>(P, B);
+    k_kkt<<<B, KKT_THREADS, ctx->kkt_smem, st>>>(P, B);
     CK(cudaGetLastError());
     tstop(ctx, k, st);
     ctx->tm.step_launches++;
@@ -1454,7 +1553,7 @@ void fold_pending(ddnm_ctx* ctx) {
     for (int c = 0; c < ctx->pending_chains; ++c) passes += ctx->h_pass[c];
     ctx->tm.eval_launches += passes * ctx->pending_classes;
     ctx->tm.constraint_launches += passes;
-    ctx->tm.step_launches += passes;
+    ctx->tm.step_launches += passes;           // k_kkt
     ctx->tm.other_launches += passes;          // the loop kernel
 }
 

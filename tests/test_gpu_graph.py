@@ -89,7 +89,7 @@ def test_graph_with_warm_start_and_starts():
 
 def test_launch_counts_of_graph_solve():
     """The graph's loop passes are read back: per pass and instance group one launch per width class,
-    one constraint, one step and one loop-control kernel."""
+    then the constraint, KKT-step and loop-control kernels."""
     wl, s = solver("c3", MIXED)
     mu = inputs.mu_batch(6, seed=3)
     s.options(tol=0.0, max_iter=2)
@@ -99,11 +99,11 @@ def test_launch_counts_of_graph_solve():
     lib.ddnm_set_tune(s.ctx, graph=1, chains=2, con_split=512, eval_persist=0)
     x, lam, st = s.solve(mu)
     t1 = lib.ddnm_get_timing(s.ctx)
-    steps = t1["step_launches"] - t0["step_launches"]
+    passes = t1["constraint_launches"] - t0["constraint_launches"]
     evals = t1["eval_launches"] - t0["eval_launches"]
-    assert steps == t1["constraint_launches"] - t0["constraint_launches"]
-    assert evals % steps == 0 and evals // steps >= 1
-    assert int(st["n_evals"].max()) <= steps <= 2 * (3 + 2 * 21)
+    assert t1["step_launches"] - t0["step_launches"] == passes            # k_kkt
+    assert evals % passes == 0 and evals // passes >= 1
+    assert int(st["n_evals"].max()) <= passes <= 2 * (3 + 2 * 21)
     s.close()
 
 
