@@ -109,6 +109,43 @@ class Burgers:
         Jvv = D(u) @ self.Bx + D(self.By @ v - bvy) + D(v) @ self.By + self.L
         return sp.bmat([[Juu, Juv], [Jvu, Jvv]], format="csr")
 
+    # -- the same, restricted to some residual rows ----------------------------------------
+    # Eq. (burgers_discretized) row by row: the rows `rows` (ascending global ids; u rows are < N) of r and
+    # of dr/dx, built from those rows of B_x, B_y and L only, so that the cost follows the rows (the
+    # collocation rows of Sec. 5.3) rather than the grid.
+    def _split_rows(self, rows):
+        rows = np.asarray(rows, dtype=np.int64)
+        if rows.size > 1 and np.any(np.diff(rows) <= 0):
+            raise ValueError("rows must be ascending")
+        N = self.N
+        return rows[rows < N], rows[rows >= N] - N
+
+    def residual_rows(self, x, mu, rows, bvec=None):
+        N = self.N
+        u, v = x[:N], x[N:]
+        bux, buy, cu, bvx, bvy, cv = self.boundary_vectors(mu) if bvec is None else bvec
+        pu, pv = self._split_rows(rows)
+        ru = u[pu] * (self.Bx[pu] @ u - bux[pu]) + v[pu] * (self.By[pu] @ u - buy[pu]) + self.L[pu] @ u + cu[pu]
+        rv = u[pv] * (self.Bx[pv] @ v - bvx[pv]) + v[pv] * (self.By[pv] @ v - bvy[pv]) + self.L[pv] @ v + cv[pv]
+        return np.concatenate([ru, rv])
+
+    def jacobian_rows(self, x, mu, rows, bvec=None):
+        """Rows `rows` of dr/dx (sparse |rows| x 2N)."""
+        N = self.N
+        u, v = x[:N], x[N:]
+        bux, buy, cu, bvx, bvy, cv = self.boundary_vectors(mu) if bvec is None else bvec
+        pu, pv = self._split_rows(rows)
+        D = sp.diags
+
+        def sel(p):          # rows e_p^T of the identity
+            return sp.csr_matrix((np.ones(p.size), (np.arange(p.size), p)), shape=(p.size, N))
+
+        Juu = D(self.Bx[pu] @ u - bux[pu]) @ sel(pu) + D(u[pu]) @ self.Bx[pu] + D(v[pu]) @ self.By[pu] + self.L[pu]
+        Juv = D(self.By[pu] @ u - buy[pu]) @ sel(pu)
+        Jvu = D(self.Bx[pv] @ v - bvx[pv]) @ sel(pv)
+        Jvv = D(u[pv]) @ self.Bx[pv] + D(self.By[pv] @ v - bvy[pv]) @ sel(pv) + D(v[pv]) @ self.By[pv] + self.L[pv]
+        return sp.bmat([[Juu, Juv], [Jvu, Jvv]], format="csr")
+
     # -- monolithic FOM solve ------------------------------------------------------------
     def newton(self, mu, x0=None, rtol=1e-12, max_iter=50):
         """Newton on r(x; mu) = 0 from x0 (default 0), sparse LU; stops at

@@ -70,29 +70,27 @@ def _neighbours(p, nx, ny):
 def decompose(nx: int, ny: int, xb, yb) -> Decomposition:
     N = nx * ny
     kx, ky = len(xb) - 1, len(yb) - 1
-    owner = np.empty(N, dtype=np.int64)
+    n = kx * ky
     owned = []
     for sy in range(ky):
         for sx in range(kx):
-            s = sy * kx + sx
             ii, jj = np.meshgrid(np.arange(xb[sx], xb[sx + 1]), np.arange(yb[sy], yb[sy + 1]))
-            nodes = np.sort((jj * nx + ii).ravel())
-            owner[nodes] = s
-            owned.append(nodes)
-    n = kx * ky
-    # dependency node sets and, for every node, the subdomains whose residuals it enters
+            owned.append(np.sort((jj * nx + ii).ravel()))
+    # dependency node sets (owned nodes and their in-grid 5-point neighbours) and, for every node, the
+    # subdomains whose residuals it enters, in ascending order (a node enters at most 3 of them)
     dep = []
-    enters = [set() for _ in range(N)]
+    cnt = np.zeros(N, dtype=np.int64)
+    enters = np.full((N, 5), -1, dtype=np.int64)
     for s in range(n):
-        d = set()
-        for p in owned[s]:
-            d.update(_neighbours(int(p), nx, ny))
-        dep.append(np.array(sorted(d), dtype=np.int64))
-        for q in d:
-            enters[q].add(s)
+        p = owned[s]
+        i, j = p % nx, p // nx
+        d = np.unique(np.concatenate([p, p[i > 0] - 1, p[i < nx - 1] + 1, p[j > 0] - nx, p[j < ny - 1] + nx]))
+        dep.append(d)
+        enters[d, cnt[d]] = s
+        cnt[d] += 1
     subs = []
     for s in range(n):
-        shared = np.array([len(enters[q]) > 1 for q in dep[s]])
+        shared = cnt[dep[s]] > 1
         inter_nodes = dep[s][~shared]
         face_nodes = dep[s][shared]
         subs.append(Subdomain(
@@ -100,35 +98,32 @@ def decompose(nx: int, ny: int, xb, yb) -> Decomposition:
             res_rows=np.concatenate([owned[s], N + owned[s]]),
             interior=np.concatenate([inter_nodes, N + inter_nodes]),
             interface=np.concatenate([face_nodes, N + face_nodes])))
-    # compatibility rows, by global variable then chain position
-    loc = [dict(zip(sd.interface.tolist(), range(sd.interface.size))) for sd in subs]
-    rows, cols_sub, cols_loc, vals, row_var, row_pair = [], [], [], [], [], []
-    ports: dict = {}
-    r = 0
-    for var in range(2 * N):
-        S = sorted(enters[var % N])
-        if len(S) < 2:
-            continue
-        ports[tuple(S)] = ports.get(tuple(S), 0) + 1
-        for k in range(len(S) - 1):
-            lo, hi = S[k], S[k + 1]
-            rows += [r, r]
-            cols_sub += [lo, hi]
-            cols_loc += [loc[lo][var], loc[hi][var]]
-            vals += [1.0, -1.0]
-            row_var.append(var)
-            row_pair.append((lo, hi))
-            r += 1
-    rows = np.array(rows, dtype=np.int64)
-    cols_sub = np.array(cols_sub, dtype=np.int64)
-    cols_loc = np.array(cols_loc, dtype=np.int64)
-    vals = np.array(vals)
+    # compatibility rows, by global variable then chain position: for each shared variable with sorted
+    # sharing set S, the rows x_{S0} - x_{S1}, x_{S1} - x_{S2}, ...
+    q = np.flatnonzero(cnt > 1)
+    var = np.concatenate([q, N + q])
+    node = var % N
+    npair = cnt[node] - 1
+    row_var = np.repeat(var, npair)
+    k = np.arange(row_var.size) - np.repeat(np.cumsum(npair) - npair, npair)
+    lo = enters[node.repeat(npair), k]
+    hi = enters[node.repeat(npair), k + 1]
+    r = row_var.size
+    rows = np.arange(r)
     A = []
     for s in range(n):
-        m = cols_sub == s
-        A.append(sp.csr_matrix((vals[m], (rows[m], cols_loc[m])), shape=(r, subs[s].interface.size)))
-    return Decomposition(nx, ny, subs, A, ports, np.array(row_var, dtype=np.int64),
-                         np.array(row_pair, dtype=np.int64).reshape(-1, 2))
+        iface = subs[s].interface
+        ml, mh = lo == s, hi == s
+        rr = np.concatenate([rows[ml], rows[mh]])
+        cc = np.concatenate([np.searchsorted(iface, row_var[ml]), np.searchsorted(iface, row_var[mh])])
+        vv = np.concatenate([np.ones(ml.sum()), -np.ones(mh.sum())])
+        A.append(sp.csr_matrix((vv, (rr, cc)), shape=(r, iface.size)))
+    ports: dict = {}
+    keys, counts = np.unique(enters[q, :], axis=0, return_counts=True)
+    for key, c in zip(keys, counts):
+        ports[tuple(int(v) for v in key if v >= 0)] = 2 * int(c)     # u and v of each shared node
+    return Decomposition(nx, ny, subs, A, ports, row_var.astype(np.int64),
+                         np.stack([lo, hi], 1).astype(np.int64).reshape(-1, 2))
 
 
 def restrict(dd: Decomposition, x: np.ndarray):

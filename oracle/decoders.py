@@ -65,6 +65,49 @@ class MaskedDecoder:
     def value_jacobian(self, x):
         return self.value(x), self.jacobian(x)
 
+    def value_jacobian_rows(self, x, rows):
+        """Values and Jacobian rows at the outputs `rows` only."""
+        z = self.W1 @ x + self.b1
+        W2 = self.W2[rows]
+        g = self.offset[rows] + self.scale[rows] * (W2 @ self.sigma(z))
+        J = (self.scale[rows][:, None] * W2) @ (self.dsigma(z)[:, None] * self.W1)
+        return g, J
+
+
+class EllDecoder:
+    """The same decoder g(x) = offset + scale o (W2 sigma(W1 x + b1)) (Sec. 5.1, Eq.
+    autoencoder_architecture b/d) with W2 kept in its ELL form (mask columns and values per output row),
+    for decoders whose dense W2 does not fit in memory.  Row r: g_r = offset_r + scale_r sum_k val_rk
+    sigma(z_{c_rk}), dg_r/dx = scale_r sum_k val_rk sigma'(z_{c_rk}) W1[c_rk, :]."""
+
+    def __init__(self, spec: dict):
+        self.N, self.w, self.n = spec["N"], spec["w"], spec["n"]
+        self.W1 = np.asarray(spec["W1"], dtype=np.float64)
+        self.b1 = np.asarray(spec["b1"], dtype=np.float64)
+        cols = np.asarray(spec["cols"], dtype=np.int64)
+        self.valid = cols >= 0
+        self.cols = np.where(self.valid, cols, 0)
+        self.vals = np.where(self.valid, np.asarray(spec["vals"], dtype=np.float64), 0.0)
+        self.scale = np.asarray(spec["scale"], dtype=np.float64)
+        self.offset = np.asarray(spec["offset"], dtype=np.float64)
+        self.act_name = spec.get("act", "swish")
+        self.sigma, self.dsigma = activation(self.act_name)
+
+    def value_jacobian_rows(self, x, rows):
+        z = self.W1 @ x + self.b1
+        c, v = self.cols[rows], self.vals[rows]
+        g = self.offset[rows] + self.scale[rows] * (v * self.sigma(z)[c]).sum(axis=1)
+        P = self.dsigma(z)[:, None] * self.W1                   # w x n: sigma'(z_c) W1[c, :]
+        J = self.scale[rows][:, None] * np.einsum("rk,rkn->rn", v, P[c])
+        return g, J
+
+    def value(self, x):
+        z = self.W1 @ x + self.b1
+        return self.offset + self.scale * (self.vals * self.sigma(z)[self.cols]).sum(axis=1)
+
+    def value_jacobian(self, x):
+        return self.value_jacobian_rows(x, np.arange(self.N))
+
 
 class Subnet:
     """g~(x) = W2~ sigma(W1~ x + b1~) over the hidden set I_h (Eq. subnet), de-normalised on I_o."""
@@ -107,6 +150,9 @@ class LinearDecoder:
 
     def value_jacobian(self, x):
         return self.value(x), self.Phi
+
+    def value_jacobian_rows(self, x, rows):
+        return self.Phi[rows] @ x + self.x_ref[rows], self.Phi[rows]
 
 
 class IdentityDecoder(LinearDecoder):

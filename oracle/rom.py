@@ -69,6 +69,13 @@ class SolveResult:
     n_evals: int
 
 
+def _value_jacobian_rows(dec, x, rows):
+    if hasattr(dec, "value_jacobian_rows"):
+        return dec.value_jacobian_rows(x, rows)
+    g, J = dec.value_jacobian(x)
+    return g[rows], J[rows]
+
+
 class DDROM:
     """decoders_O/decoders_G: objects with value_jacobian(x) -> (g, dg/dx);
     hr: per subdomain local residual-row ids (None = all rows, i.e. B_i = I);
@@ -79,11 +86,24 @@ class DDROM:
         self.dO, self.dG = list(decoders_O), list(decoders_G)
         self.C = np.asarray(C, dtype=np.float64).reshape(-1, dd.N_A) if dd.N_A else np.zeros((0, 0))
         self.n_C = self.C.shape[0]
-        self.CA = [self.C @ A.toarray() for A in dd.A] if dd.N_A else [np.zeros((0, sd.interface.size)) for sd in dd.subs]
+        # C A_i (n_C x N_i^G) through the sparse A_i
+        self.CA = [np.asarray((A.T @ self.C.T).T) for A in dd.A] if dd.N_A else \
+            [np.zeros((0, sd.interface.size)) for sd in dd.subs]
         self.rows = []
+        self.need = []
+        N = fom.N
         for i, sd in enumerate(dd.subs):
             loc = np.arange(sd.res_rows.size) if (hr is None or hr[i] is None) else np.asarray(hr[i])
-            self.rows.append(sd.res_rows[loc])          # global rows of Z_i P_i^r
+            rows = sd.res_rows[loc]
+            self.rows.append(rows)                      # global rows of Z_i P_i^r
+            # the interior outputs these rows' 5-point stencils touch (both components), as indices into
+            # x_i^Omega: no other interior output enters Z_i r_i (the set I_o of Sec. 5.4)
+            p = rows % N
+            ii, jj = p % fom.nx, p // fom.nx
+            q = np.concatenate([p, p[ii > 0] - 1, p[ii < fom.nx - 1] + 1, p[jj > 0] - fom.nx,
+                                p[jj < fom.ny - 1] + fom.nx])
+            self.need.append(np.flatnonzero(np.isin(sd.interior, np.concatenate([q, N + q]))))
+        self._x = np.zeros(2 * N)
         self.nO = [d.n for d in self.dO]
         self.nG = [d.n for d in self.dG]
         self.n_i = [a + b for a, b in zip(self.nO, self.nG)]
@@ -99,6 +119,40 @@ class DDROM:
         return out
 
     def evaluate(self, xh, lam, mu) -> Evaluation:
+        """Blocks of Eq. (sqp_system) at (xh, lam): for every subdomain the collocated residual Z_i r_i and
+        R_i = Z_i dr_i/dx_i dg_i/dxh_i (Eq. gauss_newton_hessian), from the decoder outputs the rows touch,
+        H_i = R_i^T R_i, rho_i = R_i^T r_i + E_i^T lam, D_i = C A_i dg_i^G; Atil = sum_i C A_i g_i^G."""
+        fom, dd = self.fom, self.dd
+        bvec = fom.boundary_vectors(mu)
+        ev = Evaluation([], [], [], [], [], np.zeros(self.n_C), [], None, 0.0)
+        x = self._x
+        for i, (xo, xg) in enumerate(self.split(xh)):
+            sd = dd.subs[i]
+            need = self.need[i]
+            gO, JO = _value_jacobian_rows(self.dO[i], xo, need)
+            gG, JG = self.dG[i].value_jacobian(xg)
+            x[sd.interior[need]] = gO                    # the touched part of P_i^O^T gO + P_i^G^T gG
+            x[sd.interface] = gG
+            rows = self.rows[i]
+            r = fom.residual_rows(x, mu, rows, bvec)
+            J = fom.jacobian_rows(x, mu, rows, bvec)
+            x[sd.interior[need]] = 0.0
+            x[sd.interface] = 0.0
+            R = np.hstack([J[:, sd.interior[need]] @ JO, J[:, sd.interface] @ JG])
+            D = self.CA[i] @ JG
+            grad = R.T @ r
+            rho = grad.copy()
+            rho[self.nO[i]:] += D.T @ lam
+            ev.r.append(r); ev.R.append(R); ev.H.append(R.T @ R); ev.grad.append(grad)
+            ev.D.append(D); ev.rho.append(rho); ev.gO.append(gO); ev.gG.append(gG)
+            ev.Atil = ev.Atil + self.CA[i] @ gG
+        ev.F = np.concatenate(ev.rho + [ev.Atil])
+        ev.phi = float(np.linalg.norm(ev.F))
+        return ev
+
+    def evaluate_dense(self, xh, lam, mu) -> Evaluation:
+        """evaluate() written on the whole state and the whole FOM residual and Jacobian (rows picked
+        afterwards): the plain form that pins the row-restricted one on small problems."""
         fom, dd = self.fom, self.dd
         bvec = fom.boundary_vectors(mu)
         ev = Evaluation([], [], [], [], [], np.zeros(self.n_C), [], None, 0.0)

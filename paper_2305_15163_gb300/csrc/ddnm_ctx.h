@@ -21,9 +21,10 @@ struct SubHost {
     std::vector<int> interior;   // global variable ids, ascending
     std::vector<int> interface;  // global variable ids, ascending
     std::vector<int> hr_rows;    // local residual-row ids
-    std::vector<int> hr_ops;     // HR_INTS per row
+    std::vector<int> hr_raw;     // HR_INTS per row: component, then 6 operands (global variable id, or
+                                 // -(2 * Dirichlet point + component) - 1)
     std::vector<int> need;       // interior outputs the stencils use (I_o), ascending local indices
-    std::vector<std::vector<int>> chunk_need;   // the same per chunk of HR_CHUNK collocation rows
+    std::vector<int> needG;      // interface outputs the stencils use, ascending local indices
     int nO = 0, nG = 0;
 };
 
@@ -92,7 +93,8 @@ struct ddnm_ctx {
     void* d_ws = nullptr;
     int* h_active = nullptr;     // pinned
 
-    std::vector<long long> nnzO, nnzG;   // mask nonzeros of the interior subnet rows / all interface rows
+    std::vector<long long> nnzO, nnzG, nnzGn;   // mask nonzeros: interior subnet rows, all interface rows,
+                                                // interface rows the stencils use
 
     WarmStart ws;
 

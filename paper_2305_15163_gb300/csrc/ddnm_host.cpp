@@ -206,47 +206,26 @@ extern "C" int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out) {
                 }
             }
         }
-        // interior outputs the stencils need: per chunk of HR_CHUNK rows (chunk-local slots) and in total (I_o)
-        const int nch = (nb + HR_CHUNK - 1) / HR_CHUNK;
-        sd.chunk_need.assign(nch, {});
+        // outputs the stencils use: interior (I_o of the interior subnet) and interface; the operand codes
+        // and the chunking of the collocation rows are made when the tables are uploaded
         for (int k = 0; k < nb; ++k)
             for (int o = 0; o < 6; ++o) {
-                int v = raw[k * HR_INTS + 1 + o];
-                if (v >= 0) {
-                    int li = find_sorted(sd.interior, v);
-                    if (li >= 0) {
-                        sd.need.push_back(li);
-                        sd.chunk_need[k / HR_CHUNK].push_back(li);
-                    }
-                }
-            }
-        std::sort(sd.need.begin(), sd.need.end());
-        sd.need.erase(std::unique(sd.need.begin(), sd.need.end()), sd.need.end());
-        for (auto& cn : sd.chunk_need) {
-            std::sort(cn.begin(), cn.end());
-            cn.erase(std::unique(cn.begin(), cn.end()), cn.end());
-        }
-        // second pass: operand codes
-        for (int k = 0; k < nb; ++k) {
-            sd.hr_ops.push_back(raw[k * HR_INTS]);
-            for (int o = 0; o < 6; ++o) {
-                int v = raw[k * HR_INTS + 1 + o];
-                int code;
-                if (v >= 0) {
-                    int li = find_sorted(sd.interior, v);
-                    if (li >= 0) {
-                        code = (OP_INTERIOR << OP_SHIFT) | find_sorted(sd.chunk_need[k / HR_CHUNK], li);
-                    } else {
-                        int gi = find_sorted(sd.interface, v);
-                        if (gi < 0) return bail(DDNM_E_INVALID, "internal: stencil operand outside the subdomain");
-                        code = (OP_INTERFACE << OP_SHIFT) | gi;
-                    }
+                const int v = raw[k * HR_INTS + 1 + o];
+                if (v < 0) continue;
+                const int li = find_sorted(sd.interior, v);
+                if (li >= 0) {
+                    sd.need.push_back(li);
                 } else {
-                    code = (OP_BOUNDARY << OP_SHIFT) | (-v - 1);
+                    const int gi = find_sorted(sd.interface, v);
+                    if (gi < 0) return bail(DDNM_E_INVALID, "internal: stencil operand outside the subdomain");
+                    sd.needG.push_back(gi);
                 }
-                sd.hr_ops.push_back(code);
             }
+        for (auto* v : {&sd.need, &sd.needG}) {
+            std::sort(v->begin(), v->end());
+            v->erase(std::unique(v->begin(), v->end()), v->end());
         }
+        sd.hr_raw = std::move(raw);
         ctx->sum_NB += nb;
         ctx->n_D += sd.nO + sd.nG;
     }
@@ -484,6 +463,57 @@ bool subnet_tiles(const DecoderHost& d, const std::vector<int>& rows, const std:
     }
     return true;
 }
+// Distinct mask columns over the outputs `rows` (the hidden width |I_h| of their subnet).
+int hidden_count(const DecoderHost& d, const std::vector<int>& rows) {
+    std::vector<char> used(d.w, 0);
+    int n = 0;
+    for (int r : rows)
+        for (int t = 0; t < d.K; ++t) {
+            const int c = d.cols[(size_t)r * d.K + t];
+            if (c >= 0 && !used[c]) {
+                used[c] = 1;
+                ++n;
+            }
+        }
+    return n;
+}
+
+// The collocation rows of a subdomain cut into chunks of hc rows: the interior outputs each chunk's
+// stencils use (chunk-local slots, ascending) and, with ops, the operand codes of every row (component,
+// then per operand: interior -> chunk slot, interface -> slot among the interface outputs the stencils
+// use, Dirichlet point -> 2 * point + component).
+void chunk_rows(const SubHost& sd, int hc, std::vector<std::vector<int>>& chunk_need, std::vector<int>* ops) {
+    const int nb = (int)sd.hr_rows.size();
+    chunk_need.assign((nb + hc - 1) / hc, {});
+    for (int k = 0; k < nb; ++k)
+        for (int o = 0; o < 6; ++o) {
+            const int v = sd.hr_raw[(size_t)k * HR_INTS + 1 + o];
+            if (v < 0) continue;
+            const int li = find_sorted(sd.interior, v);
+            if (li >= 0) chunk_need[k / hc].push_back(li);
+        }
+    for (auto& cn : chunk_need) {
+        std::sort(cn.begin(), cn.end());
+        cn.erase(std::unique(cn.begin(), cn.end()), cn.end());
+    }
+    if (!ops) return;
+    ops->clear();
+    for (int k = 0; k < nb; ++k) {
+        ops->push_back(sd.hr_raw[(size_t)k * HR_INTS]);
+        for (int o = 0; o < 6; ++o) {
+            const int v = sd.hr_raw[(size_t)k * HR_INTS + 1 + o];
+            int code;
+            if (v >= 0) {
+                const int li = find_sorted(sd.interior, v);
+                if (li >= 0) code = (OP_INTERIOR << OP_SHIFT) | find_sorted(chunk_need[k / hc], li);
+                else code = (OP_INTERFACE << OP_SHIFT) | find_sorted(sd.needG, find_sorted(sd.interface, v));
+            } else {
+                code = (OP_BOUNDARY << OP_SHIFT) | (-v - 1);
+            }
+            ops->push_back(code);
+        }
+    }
+}
 }  // namespace
 
 int ddnm_finalize(ddnm_ctx* ctx) {
@@ -505,6 +535,49 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     ctx->rec_smem = 0;
     ctx->nnzO.assign(ns, 0);
     ctx->nnzG.assign(ns, 0);
+    ctx->nnzGn.assign(ns, 0);
+    int dev_max = 0, sm_smem = 0;
+    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    // collocation rows per chunk, among 128, 64, ..., 8: the one that lets the most evaluation CTAs share
+    // an SM (shared memory against the register budget), the larger on a tie; it must fit one CTA
+    int hc = 0, need_bytes = 0;
+    {
+        std::vector<int> hO(ns), hG(ns);
+        for (int s = 0; s < ns; ++s) {
+            std::vector<int> allG(ctx->subs[s].interface.size());
+            for (size_t r = 0; r < allG.size(); ++r) allG[r] = (int)r;
+            hO[s] = hidden_count(ctx->decO[s], ctx->subs[s].need);
+            hG[s] = hidden_count(ctx->decG[s], allG);
+        }
+        int best_ctas = 0, smallest = 1 << 30;
+        for (int cand = HR_CHUNK; cand >= 8; cand /= 2) {
+            int bytes = 0, ctas = 1 << 30;
+            for (int s = 0; s < ns; ++s) {
+                const SubHost& sd = ctx->subs[s];
+                std::vector<std::vector<int>> cn;
+                chunk_rows(sd, cand, cn, nullptr);
+                SubDev T{};
+                T.nO = sd.nO; T.nG = sd.nG; T.ni = sd.nO + sd.nG; T.hO = hO[s]; T.hG = hG[s];
+                T.NG = (int)sd.interface.size(); T.NGn = (int)sd.needG.size(); T.hr_chunk = cand;
+                for (const auto& c : cn) T.mmax = std::max(T.mmax, (int)c.size());
+                const int b = eval_smem(T, nC, (int)tsize).bytes;
+                bytes = std::max(bytes, b);
+                const int by_smem = sm_smem / (b + 1024);      // 1 KB per CTA is the runtime's own
+                ctas = std::min(ctas, std::min(by_smem, eval_min_ctas((int)tsize, round4(T.nO + 1), round4(T.nG + 1))));
+            }
+            smallest = std::min(smallest, bytes);
+            if (bytes <= dev_max && ctas > best_ctas) {
+                best_ctas = ctas;
+                hc = cand;
+                need_bytes = bytes;
+            }
+        }
+        if (!hc)
+            return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain's evaluation needs " + std::to_string(smallest) +
+                                                          " bytes of shared memory (device limit " +
+                                                          std::to_string(dev_max) + ")");
+    }
     for (int s = 0; s < ns; ++s) {
         const SubHost& sd = ctx->subs[s];
         const DecoderHost &dO = ctx->decO[s], &dG = ctx->decG[s];
@@ -518,16 +591,20 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         // interior subnet over I_o = all outputs the stencils need; one slot-major table per HR chunk
         std::vector<int> posO, posG;
         subnet_hidden(dO, sd.need, P, S.w1O, S.b1O, S.hO, posO);
-        S.n_chunks = (int)sd.chunk_need.size();
+        std::vector<std::vector<int>> chunk_need;
+        std::vector<int> hr_ops;
+        chunk_rows(sd, hc, chunk_need, &hr_ops);
+        S.hr_chunk = hc;
+        S.n_chunks = (int)chunk_need.size();
         S.chunk0 = (int)ctx->hchunk.size();
         S.mmax = 0;
         for (int q = 0; q < S.n_chunks; ++q) {
             ChunkDev c{};
-            c.q0 = q * HR_CHUNK;
-            c.nq = std::min(HR_CHUNK, S.NB - c.q0);
-            c.m = (int)sd.chunk_need[q].size();
-            subnet_rows(dO, sd.chunk_need[q], posO, S.Kp, P, c.col, c.val, c.so);
-            if (!subnet_tiles(dO, sd.chunk_need[q], posO, S.hO, P, ctx->htiles, c.tile0, c.ntiles)) c.ntiles = 0;
+            c.q0 = q * hc;
+            c.nq = std::min(hc, S.NB - c.q0);
+            c.m = (int)chunk_need[q].size();
+            subnet_rows(dO, chunk_need[q], posO, S.Kp, P, c.col, c.val, c.so);
+            if (!subnet_tiles(dO, chunk_need[q], posO, S.hO, P, ctx->htiles, c.tile0, c.ntiles)) c.ntiles = 0;
             S.mmax = std::max(S.mmax, c.m);
             ctx->hchunk.push_back(c);
         }
@@ -540,7 +617,12 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         subnet_rows(dG, allG, posG, S.Kp, P, S.colG, S.valG, S.soG);
         if (!subnet_tiles(dG, allG, posG, S.hG, P, ctx->htiles, S.tileG0, S.ntilesG)) S.ntilesG = 0;
         for (int c : dG.cols) ctx->nnzG[s] += c >= 0;
-        // M_i = C A_i, stored N^G x n_C
+        // the interface outputs the stencils use, with Jacobian rows
+        S.NGn = (int)sd.needG.size();
+        subnet_rows(dG, sd.needG, posG, S.Kp, P, S.colGn, S.valGn, S.soGn);
+        for (int r : sd.needG)
+            for (int t = 0; t < dG.K; ++t) ctx->nnzGn[s] += dG.cols[(size_t)r * dG.K + t] >= 0;
+        // M_i = C A_i (N^G x n_C), then Q_i^T = (M_i^T diag(scale) W2~)^T (h_G x n_C): D_i = Q_i P_G
         std::vector<double> M((size_t)S.NG * nC, 0.0);
         for (int r = 0; r < ctx->N_A; ++r) {
             if (ctx->con_lo[r] == s) {
@@ -552,7 +634,16 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 for (int c = 0; c < nC; ++c) M[(size_t)li * nC + c] -= ctx->C[(size_t)c * ctx->N_A + r];
             }
         }
-        S.M = P.addv(M.data(), M.size());
+        std::vector<double> Qt((size_t)S.hG * nC, 0.0);
+        for (int r = 0; r < S.NG; ++r)
+            for (int t = 0; t < dG.K; ++t) {
+                const int col = dG.cols[(size_t)r * dG.K + t];
+                if (col < 0) continue;
+                const double coef = dG.scale[r] * dG.vals[(size_t)r * dG.K + t];
+                double* q = &Qt[(size_t)posG[col] * nC];
+                for (int c = 0; c < nC; ++c) q[c] += coef * M[(size_t)r * nC + c];
+            }
+        S.Qt = P.addv(Qt.data(), Qt.size());
         // full decoders and ownership for reconstruction
         S.NO_full = dO.N; S.wO_full = dO.w; S.wG_full = dG.w;
         std::vector<double> so(dO.scale);
@@ -577,7 +668,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         S.blk = blk;
         blk += blk_layout(S.ni, S.nG, nC).size;
         for (int o = 0; o < HR_INTS; ++o)            // operand-major: consecutive rows are consecutive ints
-            for (int q = 0; q < S.NB; ++q) hr_all.push_back(sd.hr_ops[(size_t)q * HR_INTS + o]);
+            for (int q = 0; q < S.NB; ++q) hr_all.push_back(hr_ops[(size_t)q * HR_INTS + o]);
         S.smem_bytes = eval_smem(S, nC, (int)tsize).bytes;
         ctx->eval_smem = std::max(ctx->eval_smem, S.smem_bytes);
         ctx->rec_smem = std::max(ctx->rec_smem, (int)(std::max(dO.w, dG.w) * tsize));
@@ -606,8 +697,6 @@ int ddnm_finalize(ddnm_ctx* ctx) {
             if (c.n) ctx->eval_classes.push_back(c);
         }
     if ((int)cls.size() != ns) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "latent dims outside the kernel classes");
-    int dev_max = 0;
-    CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (ctx->eval_smem > dev_max)
         return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain needs " + std::to_string(ctx->eval_smem) +
                                                       " bytes of shared memory (device limit " + std::to_string(dev_max) + ")");
@@ -778,13 +867,16 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         // hidden layers: z = W1 x + b1 (2 h n), P = sigma'(z) W1 (h n)
         f += 3.0 * (S.hO * nO + S.hG * nG);
         // outputs and Jacobian rows over the mask nonzeros, then de-normalisation
-        f += 2.0 * ctx->nnzO[s] * (nO + 1) + 2.0 * ctx->nnzG[s] * (nG + 1) + mO * (nO + 2) + S.NG * (nG + 2);
+        // (interior: values and Jacobian rows of the needed outputs; interface: values of every output,
+        // Jacobian rows of the needed ones)
+        f += 2.0 * ctx->nnzO[s] * (nO + 1) + 2.0 * ctx->nnzG[s] + 2.0 * ctx->nnzGn[s] * nG + mO * (nO + 2) +
+             2.0 * S.NG + S.NGn * nG;
         // residual row, 6 partials, chain rule R = sum_o d_o J_o
         f += S.NB * (30.0 + 12.0 * ni);
         // H = R^T R (upper triangle) and R^T r
         f += 2.0 * S.NB * (ni * (ni + 1) / 2 + ni);
-        // D_i = (C A_i) dg^G/dxh
-        f += 2.0 * nC * S.NG * nG;
+        // D_i = Q_i P_G over the interface hidden units
+        f += 2.0 * nC * S.hG * nG;
         // FP64 in the evaluation: rho += D^T lambda, ||rho_i||^2
         f64 += 2 * nC * nG + 2 * ni;
         // FP64 at an accepted point: L D L^T, t, W = L_GG^{-1} D^T, u (k_factor); lower triangle of
@@ -792,7 +884,7 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         fac += ni * ni * ni / 3.0 + ni * ni + nC * nG * nG + 3 * nC * nG + nC * (nC + 1) * nG + nC;
         // bytes: subnet weights, tables and M_i once; per instance latents, multipliers, block outputs
         bytes += tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] + 2.0 * (mO + S.NG) +
-                        S.NG * nC) +
+                        (double)S.hG * nC) +
                  4.0 * (mO * S.K + (double)S.NG * S.K + 7.0 * S.NB) +
                  8.0 * (blk_layout(S.ni, S.nG, ctx->n_C).size) + tsz * S.NG;
         // back-substitution per subdomain (in the next evaluation)

@@ -20,7 +20,7 @@ constexpr int CON_BLOCK = 512;  // constraint rows of one canonical partial of A
 constexpr int MIN_CON_SPLIT = CON_BLOCK, MAX_CON_SPLIT = 4 * CON_BLOCK;
 constexpr int MAX_CHAINS = 16; // instance groups iterating concurrently inside the solve graph
 constexpr int MAX_CLASSES = 12; // width classes (RO, RG) of the evaluation kernel
-constexpr int HR_CHUNK = 128;  // collocation rows per evaluation chunk (bounds shared memory)
+constexpr int HR_CHUNK = 128;  // largest collocation rows per evaluation chunk (the set-up may choose fewer)
 
 // HR stencil operand codes: (kind << 28) | index
 constexpr int OP_SHIFT = 28;
@@ -40,6 +40,12 @@ enum { XT_KEEP = 0, XT_NEWSTEP = 1, XT_BACKTRACK = 2 };
 enum { D_PHI0 = 0, D_ALPHA, D_PHI, D_ALPHA_LAST, INST_DBLS };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+
+// register budget of the evaluation kernel: 4 CTAs per SM for the narrow FP32 records, 3 or 2 for the wider
+// ones; FP64 records take twice the registers
+__host__ __device__ constexpr int eval_min_ctas(int tsize, int ro, int rg) {
+    return tsize == 8 ? 2 : (ro + rg <= 12 ? 4 : (ro + rg <= 20 ? 3 : 2));
+}
 
 // 32 consecutive output rows of a decoder subnet whose mask columns (in I_h numbering) all lie in the
 // window [c0, c0 + tw) (tw a multiple of 4, c0 + tw <= round4(|I_h|)): values dense over the window, zero
@@ -75,7 +81,9 @@ struct SubDev {
     long long w1G, b1G;            // interface subnet hidden layer: W1~ (hG x round4(nG)), b1~ (hG)
     long long colG, valG, soG;     // interface outputs, all rows: ELL slot-major (Kp x NG), scale/offset
     int tileG0, ntilesG;           // dense-window tiles of the interface outputs (0 tiles: ELL)
-    long long M;                   // M_i = C A_i stored N^G x n_C (row = interface output), value pool
+    int NGn, hr_chunk;             // interface outputs the stencils use; collocation rows per chunk
+    long long colGn, valGn, soGn;  // those outputs: ELL slot-major (Kp x NGn), scale/offset
+    long long Qt;                  // value pool: Q_i^T = (C A_i diag(scale) W2~)^T, h_G x n_C
     // full (not subnet) decoders for reconstruction
     int NO_full, wO_full, wG_full, K;
     long long fw1O, fb1O, fw2O, foutO, fcolO;
@@ -166,7 +174,7 @@ constexpr int CTL_INTS = MAX_CHAINS * (2 + MAX_CLASSES);
 
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {
-    int sx, hidO, hidG, outG, outO, Rr, red;   // value-type arrays
+    int sx, hidO, hidG, outGn, outO, Rr, red;  // value-type arrays
     int dlam, dH, drho, dD, dt;                // double arrays
     int bytes;
 };
@@ -180,10 +188,10 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.sx = o; o = align16(o + MAX_NI * tsize);
     e.hidO = o; o = align16(o + round4(s.hO) * rO * tsize);  // [sigma, sigma' W1 row] per hidden unit (+ zero rows)
     e.hidG = o; o = align16(o + round4(s.hG) * rG * tsize);
-    e.outG = o; o = align16(o + s.NG * rG * tsize);          // [y, Jacobian row] per interface output
+    e.outGn = o; o = align16(o + s.NGn * rG * tsize);        // [y, Jacobian row] per interface output the stencils use
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
-    e.Rr = o; o = align16(o + HR_CHUNK * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
-    e.red = o; o = align16(o + (EVAL_THREADS / 32) * nC * s.nG * tsize);   // D_i partials per warp
+    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
+    e.red = o; o = align16(o + (EVAL_THREADS / nC) * nC * s.nG * tsize);   // D_i partials per thread group
     e.dlam = o; o = align16(o + nC * 8);
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);

@@ -269,6 +269,46 @@ __device__ __forceinline__ void tile_accumulate(const TileDev& TD, const T* V, c
     }
 }
 
+// Values only (the first element of each hidden record, records STRIDE apart) of the 32 rows of a tile.
+template <typename T, int STRIDE>
+__device__ __forceinline__ T tile_values(const TileDev& TD, const T* V, const T* hid, int lane) {
+    const T* vp = V + TD.voff + lane * 4;
+    const T* h = hid + (size_t)TD.c0 * STRIDE;
+    const int tw = TD.tw;
+    T acc = T(0);
+    for (int j = 0; j < tw; j += 8) {        // two quads of window values in flight
+        T v[2][4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (j + 4 * q < tw) ld4(vp + (size_t)(j + 4 * q) * 32, v[q]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            if (j + 4 * q < tw) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc += v[q][u] * h[(size_t)(j + 4 * q + u) * STRIDE];
+            }
+    }
+    return acc;
+}
+
+// Values only of one ELL row (slot-major, Kp slots), records STRIDE apart.
+template <typename T, int STRIDE>
+__device__ __forceinline__ T ell_values(const int* col, const T* val, int stride, int Kp, const T* hid) {
+    T acc = T(0);
+    for (int t0 = 0; t0 < Kp; t0 += 8) {
+        int c[8];
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            c[u] = col[(size_t)(t0 + u) * stride];
+            v[u] = val[(size_t)(t0 + u) * stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u] * hid[(size_t)c[u] * STRIDE];
+    }
+    return acc;
+}
+
 // ------------------------------------------------------------------------ evaluation
 
 // stencil constants 1/(2h_x), 1/(2h_y), nu/h_x^2, nu/h_y^2 in the value type (precomputed on the host)
@@ -359,7 +399,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     T* sx = (T*)(smem + L.sx);
     T* hidO = (T*)(smem + L.hidO);
     T* hidG = (T*)(smem + L.hidG);
-    T* outG = (T*)(smem + L.outG);
+    T* outGn = (T*)(smem + L.outGn);
     T* outO = (T*)(smem + L.outO);
     T* Rr = (T*)(smem + L.Rr);
     T* red = (T*)(smem + L.red);
@@ -432,6 +472,80 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
     __syncthreads();
 
+    const int nwarp = nth >> 5;
+    const int w = tid >> 5, lane = tid & 31;
+
+    // interface decoder: values of every output (the constraint residual needs them all: Sec. 5.3's
+    // remark, the WFPC constraint is not hyper-reduced), from the first element of the hidden records
+    {
+        T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
+        const int tG = S.ntilesG;
+        for (int t = w; t < tG; t += nwarp) {
+            const T v = tile_values<T, RG>(P.tiles[S.tileG0 + t], V, hidG, lane);
+            const int r = t * 32 + lane;
+            if (r < NG) gout[r] = V[S.soG + NG + r] + V[S.soG + r] * v;
+        }
+        if (!tG)
+            for (int r = tid; r < NG; r += nth) {
+                const T v = ell_values<T, RG>(IP + S.colG + r, V + S.valG + r, NG, S.Kp, hidG);
+                gout[r] = V[S.soG + NG + r] + V[S.soG + r] * v;
+            }
+    }
+    // interface outputs the collocation stencils use: [y, Jacobian row] records
+    for (int r = tid; r < S.NGn; r += nth) {
+        T acc[RG];
+#pragma unroll
+        for (int k = 0; k < RG; ++k) acc[k] = T(0);
+        ell_accumulate<T, RG>(IP + S.colGn + r, V + S.valGn + r, S.NGn, S.Kp, hidG, acc);
+        const T sc = V[S.soGn + r], off = V[S.soGn + S.NGn + r];
+        acc[0] = off + sc * acc[0];
+#pragma unroll
+        for (int k = 1; k < RG; ++k) acc[k] *= sc;
+#pragma unroll
+        for (int k = 0; k < RG; k += 4) st4(outGn + (size_t)r * RG + k, acc + k);
+    }
+    // D_i = C A_i dg^G/dxh = Q_i P_G with Q_i = C A_i diag(scale) W2~ (n_C x h_G, precomputed, stored
+    // transposed) and P_G[h] = sigma'(z_h) W1~[h, :] (the hidden records): thread (group, c) sums the
+    // hidden units h = group, group + n_grp, ... for row c; the groups are added in order afterwards
+    {
+        const int ngrp = nth / nC;
+        const int c = tid % nC, grp = tid / nC;
+        if (grp < ngrp) {
+            T acc[RG - 1];
+#pragma unroll
+            for (int k = 0; k < RG - 1; ++k) acc[k] = T(0);
+            const T* Qt = V + S.Qt;
+            int h = grp;
+            for (; h + ngrp < S.hG; h += 2 * ngrp) {          // two loads in flight
+                T q[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) q[u] = Qt[(size_t)(h + u * ngrp) * nC + c];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const T* pr = hidG + (size_t)(h + u * ngrp) * RG + 1;
+#pragma unroll
+                    for (int k = 0; k < RG - 1; ++k) acc[k] += q[u] * pr[k];
+                }
+            }
+            for (; h < S.hG; h += ngrp) {
+                const T q = Qt[(size_t)h * nC + c];
+                const T* pr = hidG + (size_t)h * RG + 1;
+#pragma unroll
+                for (int k = 0; k < RG - 1; ++k) acc[k] += q * pr[k];
+            }
+#pragma unroll
+            for (int k = 0; k < RG - 1; ++k)
+                if (k < nG) red[((size_t)grp * nC + c) * nG + k] = acc[k];
+        }
+    }
+    __syncthreads();
+    for (int o = tid; o < nC * nG; o += nth) {
+        const int ngrp = nth / nC;
+        T acc = T(0);
+        for (int g = 0; g < ngrp; ++g) acc += red[(size_t)g * nC * nG + o];
+        dD[o] = (double)acc;
+    }
+
     // H_i = R^T R and R^T r: thread p owns one entry (a <= c), running sum over the chunks
     const int npair = ni * (ni + 1) / 2;
     int pa = 0, pc = 0;
@@ -448,174 +562,95 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
     T hacc = T(0);
     const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
-    const T* bnd = (const T*)P.bnd + (size_t)b * P.n_bnd * 2;
-    const T ax = cst<T>(P, 0), ay = cst<T>(P, 1), cx = cst<T>(P, 2), cy = cst<T>(P, 3);
-    T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
-    const int nout = nC * nG;
-    const int nwarp = nth >> 5;
     for (int q = 0; q < S.n_chunks; ++q) {
         const ChunkDev Cq = P.chunk[S.chunk0 + q];
-        // decoder outputs of this chunk's interior rows (and, with the first chunk, all interface rows):
-        // dense-window tiles, warp per tile, where the host built them; the ELL tables otherwise
+        // interior decoder outputs of this chunk's collocation rows: dense-window tiles, warp per tile,
+        // where the host built them; the ELL table otherwise
         {
-            const int tO = Cq.ntiles, tG = q == 0 ? S.ntilesG : 0;
-            const int w = tid >> 5, lane = tid & 31;
-            for (int t = w; t < tO + tG; t += nwarp) {
-                if (t < tO) {
-                    T acc[RO];
-                    tile_accumulate<T, RO>(P.tiles[Cq.tile0 + t], V, hidO, lane, acc);
-                    const int r = t * 32 + lane;
-                    if (r < Cq.m) {
-                        const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
-                        acc[0] = off + sc * acc[0];
-#pragma unroll
-                        for (int k = 1; k < RO; ++k) acc[k] *= sc;
-#pragma unroll
-                        for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
-                    }
-                } else {
-                    T acc[RG];
-                    tile_accumulate<T, RG>(P.tiles[S.tileG0 + t - tO], V, hidG, lane, acc);
-                    const int r = (t - tO) * 32 + lane;
-                    if (r < NG) {
-                        const T sc = V[S.soG + r], off = V[S.soG + NG + r];
-                        acc[0] = off + sc * acc[0];
-#pragma unroll
-                        for (int k = 1; k < RG; ++k) acc[k] *= sc;
-#pragma unroll
-                        for (int k = 0; k < RG; k += 4) st4(outG + (size_t)r * RG + k, acc + k);
-                        gout[r] = acc[0];
-                    }
-                }
-            }
-            const int mO = tO ? 0 : Cq.m;                 // rows left to the ELL tables
-            const int mG = (q == 0 && !S.ntilesG) ? NG : 0;
-            for (int it = tid; it < mO + mG; it += nth) {
-                if (it < mO) {
-                    const int r = it;
-                    T acc[RO];
-#pragma unroll
-                    for (int k = 0; k < RO; ++k) acc[k] = T(0);
-                    const int* col = IP + Cq.col + r;
-                    const T* val = V + Cq.val + r;
-                    ell_accumulate<T, RO>(col, val, Cq.m, S.Kp, hidO, acc);
+            const int tO = Cq.ntiles;
+            for (int t = w; t < tO; t += nwarp) {
+                T acc[RO];
+                tile_accumulate<T, RO>(P.tiles[Cq.tile0 + t], V, hidO, lane, acc);
+                const int r = t * 32 + lane;
+                if (r < Cq.m) {
                     const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
                     acc[0] = off + sc * acc[0];
 #pragma unroll
                     for (int k = 1; k < RO; ++k) acc[k] *= sc;
 #pragma unroll
                     for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
-                } else {
-                    const int r = it - mO;
-                    T acc[RG];
-#pragma unroll
-                    for (int k = 0; k < RG; ++k) acc[k] = T(0);
-                    const int* col = IP + S.colG + r;
-                    const T* val = V + S.valG + r;
-                    ell_accumulate<T, RG>(col, val, NG, S.Kp, hidG, acc);
-                    const T sc = V[S.soG + r], off = V[S.soG + NG + r];
-                    acc[0] = off + sc * acc[0];
-#pragma unroll
-                    for (int k = 1; k < RG; ++k) acc[k] *= sc;
-#pragma unroll
-                    for (int k = 0; k < RG; k += 4) st4(outG + (size_t)r * RG + k, acc + k);
-                    gout[r] = acc[0];
                 }
+            }
+            const int mO = tO ? 0 : Cq.m;                 // rows left to the ELL table
+            for (int r = tid; r < mO; r += nth) {
+                T acc[RO];
+#pragma unroll
+                for (int k = 0; k < RO; ++k) acc[k] = T(0);
+                ell_accumulate<T, RO>(IP + Cq.col + r, V + Cq.val + r, Cq.m, S.Kp, hidO, acc);
+                const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
+                acc[0] = off + sc * acc[0];
+#pragma unroll
+                for (int k = 1; k < RO; ++k) acc[k] *= sc;
+#pragma unroll
+                for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
             }
         }
         __syncthreads();
-        // D_i[c][k] = sum_rows M[row][c] dg^G[row][k] (M = C A_i, N^G x n_C): warp w takes rows w, w+8, ...,
-        // lane l the rows c = l, l+32, ... of C; partials per warp in `red`, summed after the barrier
-        if (q == 0) {
-            const int w = tid >> 5, lane = tid & 31;
-            const T* M = V + S.M;
-            for (int c0 = 0; c0 < nC; c0 += 32) {
-                const int c = c0 + lane;
-                T acc[RG - 1];
-#pragma unroll
-                for (int k = 0; k < RG - 1; ++k) acc[k] = T(0);
-                if (c < nC) {
-                    int row = w;
-                    for (; row + 3 * nwarp < NG; row += 4 * nwarp) {
-                        T m[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) m[u] = M[(size_t)(row + u * nwarp) * nC + c];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const T* j = outG + (size_t)(row + u * nwarp) * RG + 1;
-#pragma unroll
-                            for (int k = 0; k < RG - 1; ++k) acc[k] += m[u] * j[k];
-                        }
-                    }
-                    for (; row < NG; row += nwarp) {
-                        const T m = M[(size_t)row * nC + c];
-                        const T* j = outG + (size_t)row * RG + 1;
-#pragma unroll
-                        for (int k = 0; k < RG - 1; ++k) acc[k] += m * j[k];
-                    }
-#pragma unroll
-                    for (int k = 0; k < RG - 1; ++k)
-                        if (k < nG) red[((size_t)w * nC + c) * nG + k] = acc[k];
-                }
-            }
-        }
         // collocation rows of the chunk
-        {
-            for (int it = tid; it < Cq.nq; it += nth) {
-                {
-                    const int qq = Cq.q0 + it;
-                    const int comp = hr[qq];
-                    int code[6];
+        const T* bnd = (const T*)P.bnd + (size_t)b * P.n_bnd * 2;
+        const T ax = cst<T>(P, 0), ay = cst<T>(P, 1), cx = cst<T>(P, 2), cy = cst<T>(P, 3);
+        for (int it = tid; it < Cq.nq; it += nth) {
+            const int qq = Cq.q0 + it;
+            const int comp = hr[qq];
+            int code[6];
 #pragma unroll
-                    for (int o = 0; o < 6; ++o) code[o] = hr[(size_t)(o + 1) * S.NB + qq];
-                    T f[6];
+            for (int o = 0; o < 6; ++o) code[o] = hr[(size_t)(o + 1) * S.NB + qq];
+            T f[6];
 #pragma unroll
-                    for (int o = 0; o < 6; ++o) {
-                        const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
-                        f[o] = kind == OP_INTERIOR ? outO[(size_t)idx * RO]
-                                                   : (kind == OP_INTERFACE ? outG[(size_t)idx * RG] : bnd[idx]);
-                    }
-                    const T up = comp == 0 ? f[0] : f[5];
-                    const T vp = comp == 0 ? f[5] : f[0];
-                    const T dxf = f[1] - f[2], dyf = f[3] - f[4];
-                    const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
-                                cy * (f[3] - T(2) * f[0] + f[4]);
-                    T d[6];
-                    d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
-                    d[1] = -up * ax + cx;
-                    d[2] = up * ax + cx;
-                    d[3] = -vp * ay + cy;
-                    d[4] = vp * ay + cy;
-                    d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
-                    T RO_[RO - 1 > 0 ? RO - 1 : 1], RG_[RG - 1 > 0 ? RG - 1 : 1];
+            for (int o = 0; o < 6; ++o) {
+                const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
+                f[o] = kind == OP_INTERIOR ? outO[(size_t)idx * RO]
+                                           : (kind == OP_INTERFACE ? outGn[(size_t)idx * RG] : bnd[idx]);
+            }
+            const T up = comp == 0 ? f[0] : f[5];
+            const T vp = comp == 0 ? f[5] : f[0];
+            const T dxf = f[1] - f[2], dyf = f[3] - f[4];
+            const T r = -up * dxf * ax - vp * dyf * ay + cx * (f[1] - T(2) * f[0] + f[2]) +
+                        cy * (f[3] - T(2) * f[0] + f[4]);
+            T d[6];
+            d[0] = -T(2) * cx - T(2) * cy - (comp == 0 ? dxf * ax : dyf * ay);
+            d[1] = -up * ax + cx;
+            d[2] = up * ax + cx;
+            d[3] = -vp * ay + cy;
+            d[4] = vp * ay + cy;
+            d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
+            T RO_[RO - 1 > 0 ? RO - 1 : 1], RG_[RG - 1 > 0 ? RG - 1 : 1];
 #pragma unroll
-                    for (int k = 0; k < RO - 1; ++k) RO_[k] = T(0);
+            for (int k = 0; k < RO - 1; ++k) RO_[k] = T(0);
 #pragma unroll
-                    for (int k = 0; k < RG - 1; ++k) RG_[k] = T(0);
+            for (int k = 0; k < RG - 1; ++k) RG_[k] = T(0);
 #pragma unroll
-                    for (int o = 0; o < 6; ++o) {
-                        const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
-                        if (kind == OP_INTERIOR) {
-                            const T* j = outO + (size_t)idx * RO + 1;
+            for (int o = 0; o < 6; ++o) {
+                const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
+                if (kind == OP_INTERIOR) {
+                    const T* j = outO + (size_t)idx * RO + 1;
 #pragma unroll
-                            for (int k = 0; k < RO - 1; ++k) RO_[k] += d[o] * j[k];
-                        } else if (kind == OP_INTERFACE) {
-                            const T* j = outG + (size_t)idx * RG + 1;
+                    for (int k = 0; k < RO - 1; ++k) RO_[k] += d[o] * j[k];
+                } else if (kind == OP_INTERFACE) {
+                    const T* j = outGn + (size_t)idx * RG + 1;
 #pragma unroll
-                            for (int k = 0; k < RG - 1; ++k) RG_[k] += d[o] * j[k];
-                        }
-                    }
-                    T* row = Rr + (size_t)it * ld;
-#pragma unroll
-                    for (int k = 0; k < RO - 1; ++k)
-                        if (k < nO) row[k] = RO_[k];
-#pragma unroll
-                    for (int k = 0; k < RG - 1; ++k)
-                        if (k < nG) row[nO + k] = RG_[k];
-                    row[ni] = r;
-                    if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
+                    for (int k = 0; k < RG - 1; ++k) RG_[k] += d[o] * j[k];
                 }
             }
+            T* row = Rr + (size_t)it * ld;
+#pragma unroll
+            for (int k = 0; k < RO - 1; ++k)
+                if (k < nO) row[k] = RO_[k];
+#pragma unroll
+            for (int k = 0; k < RG - 1; ++k)
+                if (k < nG) row[nO + k] = RG_[k];
+            row[ni] = r;
+            if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
         }
         __syncthreads();
         if (tid < npair + ni) {
@@ -630,12 +665,6 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (; ql < Cq.nq; ++ql) h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
             hacc += (h0 + h1) + (h2 + h3);
         }
-        if (q == 0)
-            for (int o = tid; o < nout; o += nth) {
-                T acc = T(0);
-                for (int w = 0; w < nwarp; ++w) acc += red[(size_t)w * nout + o];
-                dD[o] = (double)acc;
-            }
         if (q + 1 < S.n_chunks) __syncthreads();   // outO / Rr reused by the next chunk
     }
     if (tid < npair) {
@@ -675,11 +704,8 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
 // subdomain of the class); item k is instance k % B of subdomain subs[k / B] (subs: the class's subdomains,
 // largest first).  With ctr == NULL CTA k takes item k; otherwise the grid is persistent and its CTAs claim
 // items from the counter *ctr (zero before the launch) until none are left.
-// register budget: 4 CTAs per SM for the narrow records, 3 or 2 for the wider ones (no spills)
-__host__ __device__ constexpr int eval_min_ctas(int ro, int rg) { return ro + rg <= 12 ? 4 : (ro + rg <= 20 ? 3 : 2); }
-
 template <typename T, int RO, int RG>
-__global__ void __launch_bounds__(EVAL_THREADS, eval_min_ctas(RO, RG)) k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr) {
+__global__ void __launch_bounds__(EVAL_THREADS, eval_min_ctas(sizeof(T), RO, RG)) k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int items = B * nsub;
     if (!ctr) {

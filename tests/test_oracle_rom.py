@@ -10,7 +10,7 @@ import inputs
 from oracle import setup
 from oracle.burgers import Burgers
 from oracle.dd import decompose
-from oracle.decoders import LinearDecoder, MaskedDecoder, activation, pod_basis, subnet
+from oracle.decoders import EllDecoder, LinearDecoder, MaskedDecoder, activation, pod_basis, subnet
 from oracle.rom import CONVERGED, MAX_ITER, DDROM, relative_error
 
 
@@ -229,3 +229,57 @@ def test_relative_error_formula():
     assert relative_error(ref, ref) == 0.0
     scaled = [(1.1 * a, 1.1 * b) for a, b in ref]
     assert np.isclose(relative_error(ref, scaled), 0.1)
+
+
+# ---- the row-restricted and ELL forms the large workloads need, pinned against the plain forms ----
+
+def test_residual_and_jacobian_rows_match_full():
+    """Burgers.residual_rows / jacobian_rows are exactly the picked rows of the full residual and
+    Jacobian (same operators, restricted before the products)."""
+    fom = Burgers(9, 7, 0.1)
+    r = np.random.default_rng(5)
+    x = r.standard_normal(2 * fom.N)
+    mu = (1.03, 0.95)
+    rows = np.sort(r.choice(2 * fom.N, size=40, replace=False))
+    assert np.allclose(fom.residual_rows(x, mu, rows), fom.residual(x, mu)[rows], rtol=0, atol=1e-13)
+    J = fom.jacobian(x, mu)[rows].toarray()
+    assert np.allclose(fom.jacobian_rows(x, mu, rows).toarray(), J, rtol=0, atol=1e-13)
+    with pytest.raises(ValueError):
+        fom.residual_rows(x, mu, rows[::-1])
+
+
+def test_ell_decoder_matches_dense_decoder():
+    """EllDecoder (W2 kept as mask columns and values) against MaskedDecoder (dense W2): values and
+    Jacobian rows at any output subset, for a three-band mask with clipped rows."""
+    spec = inputs.decoder(37, 48, 5, 4, (91, 1), offset=np.linspace(-1, 1, 37), scale=np.linspace(0.5, 2, 37))
+    dense, ell = MaskedDecoder(spec), EllDecoder(spec)
+    x = np.random.default_rng(6).standard_normal(5)
+    g, J = dense.value_jacobian(x)
+    g2, J2 = ell.value_jacobian(x)
+    assert np.allclose(g2, g, rtol=1e-14, atol=1e-14) and np.allclose(J2, J, rtol=1e-13, atol=1e-14)
+    assert np.allclose(ell.value(x), g, rtol=1e-14, atol=1e-14)
+    rows = np.array([0, 3, 17, 36])
+    g3, J3 = ell.value_jacobian_rows(x, rows)
+    g4, J4 = dense.value_jacobian_rows(x, rows)
+    assert np.allclose(g3, g[rows], rtol=1e-14, atol=1e-14) and np.allclose(J3, J[rows], rtol=1e-13, atol=1e-14)
+    assert np.allclose(g4, g[rows], rtol=1e-14, atol=1e-14) and np.allclose(J4, J[rows], rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["c1", "tiny12x10_2x2", "tiny13x9_3x2"])
+def test_restricted_evaluation_matches_dense(name):
+    """DDROM.evaluate (collocation rows and touched outputs only, sparse C A_i) equals the plain
+    whole-state evaluation, for dense and for ELL decoders."""
+    wl = inputs.workload(name)
+    fom, dd, rom, raw = setup.build(wl)
+    fom2, dd2, rom_ell, _ = setup.build(wl, ell=True)
+    r = np.random.default_rng(7)
+    x = 0.3 * r.standard_normal(rom.n_D)
+    lam = r.standard_normal(rom.n_C)
+    mu = inputs.mu_batch(1)[0]
+    a, b, c = rom.evaluate_dense(x, lam, mu), rom.evaluate(x, lam, mu), rom_ell.evaluate(x, lam, mu)
+    for e in (b, c):
+        assert np.allclose(e.F, a.F, rtol=1e-12, atol=1e-12)
+        for i in range(dd.n_sub):
+            assert np.allclose(e.H[i], a.H[i], rtol=1e-12, atol=1e-12)
+            assert np.allclose(e.D[i], a.D[i], rtol=1e-12, atol=1e-12)
+            assert np.allclose(e.r[i], a.r[i], rtol=1e-12, atol=1e-12)
