@@ -187,12 +187,12 @@ def workload_config(cfg):
 
 # ------------------------------------------------------------------------ learned warm start (c4)
 
-def run_warmstart(args, lib, torch):
-    """MLP 2 -> 256 -> 256 -> n_D trained on 4096 SQP solutions of the 128x128 4x4 setup (paper's stopping
-    rule, default start), judged on 1024 held-out mu: iterations the SQP needs from the learned start to
-    reach the merit the default start ends with after 15 iterations, final merits, and solves/s of the
-    warm-started solve (mixed precision) next to the plain FP64 solve."""
-    wl = inputs.workload("c2")
+def run_warmstart(args, lib, torch, name="c2", n_train=4096, n_test=1024, epochs=60):
+    """MLP 2 -> 256 -> 256 -> n_D trained on n_train SQP solutions of workload `name` (paper's stopping rule,
+    default start), judged on n_test held-out mu: iterations the SQP needs from the learned start to reach
+    the merit the default start ends with after 15 iterations, final merits, and solves/s of the
+    warm-started mixed-precision solve next to the plain mixed and the plain FP64 solves on the same GPU."""
+    wl = inputs.workload(name)
     B = wl.batch
     s = lib.Solver(wl)
     dec_o, dec_g = inputs.decoders_for(wl, [d["interior"] for d in s.subs], [d["interface"] for d in s.subs])
@@ -209,16 +209,17 @@ def run_warmstart(args, lib, torch):
             sts.append(st)
         return np.concatenate(xs), np.concatenate(sts)
 
+    plan, _ = lib.ddnm_autotune(s.ctx, inputs.mu_batch(B, seed=3003), max_iter=2, reps=1)
     t0 = time.perf_counter()
-    mu_tr = inputs.mu_batch(4096, seed=1001)
+    mu_tr = inputs.mu_batch(n_train, seed=1001)
     x_tr, _ = solve_all(s, mu_tr)
     t_data = time.perf_counter() - t0
-    H, epochs = 256, 60
+    H = 256
     lib.ddnm_ws_init(s.ctx, H, inputs.mlp_init(2, H, nD))
     t0 = time.perf_counter()
-    losses = lib.ddnm_ws_train(s.ctx, mu_tr, x_tr, epochs, 64, 2e-3, inputs.mlp_order(4096, epochs))
+    losses = lib.ddnm_ws_train(s.ctx, mu_tr, x_tr, epochs, 64, 2e-3, inputs.mlp_order(n_train, epochs))
     t_train = time.perf_counter() - t0
-    mu_te = inputs.mu_batch(1024, seed=2002)
+    mu_te = inputs.mu_batch(n_test, seed=2002)
 
     def timed(solver, mu):
         torch.cuda.synchronize()
@@ -233,7 +234,7 @@ def run_warmstart(args, lib, torch):
     lib.ddnm_ws_enable(s.ctx, True)
     v_ws, st_ws = timed(s, mu_te)
     reach = np.full(len(mu_te), -1)
-    for K in range(1, 16):
+    for K in (1, 2, 3, 4, 6, 8, 11, 15):
         s.options(tol=0.0, max_iter=K)
         _, st = solve_all(s, mu_te)
         newly = (st["merit"] <= st_plain["merit"]) & (reach < 0)
@@ -248,15 +249,19 @@ def run_warmstart(args, lib, torch):
     # plain FP64 solve of the same workload on the same GPU
     s64 = lib.Solver(wl, precision=lib.DDNM_FP64)
     s64.load(dec_o, dec_g, Cm)
+    lib.ddnm_set_tune(s64.ctx, **plan)
     s64.options()
     solve_all(s64, mu_te[:B])
-    v_fp64, st_fp64 = timed(s64, mu_te[:256])
+    n64 = max(B, len(mu_te) // 4)
+    v_fp64, st_fp64 = timed(s64, mu_te[:n64])
     reached = reach > 0
     line = {"metric": METRIC, "value": v_ws, "unit": UNIT, "n_gpus": 1, "steps": len(mu_te) // B, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 KKT",
             "data": "synthetic",
-            "config": {"workload": "c4: learned warm start on the 128x128 4x4 setup, MLP 2-256-256-144 (bf16 "
-                                   "weights, fp32 accumulation), 4096 training solutions, 1024 held-out mu"},
+            "config": {"workload": f"learned warm start on the {wl.nx}x{wl.ny} {wl.kx}x{wl.ky} setup ({name}), MLP "
+                                   f"2-256-256-{nD} (bf16 weights, fp32 accumulation), {n_train} training "
+                                   f"solutions, {n_test} held-out mu, batches of {B}",
+                       "launch_plan": plan, "fp64_timed_on": n64},
             "warm_start": {"train_seconds": t_train, "data_seconds": t_data, "epochs": epochs,
                            "loss_first_last": [float(losses[0]), float(losses[-1])],
                            "fraction_reaching_plain_final_merit": float(reached.mean()),
@@ -298,6 +303,9 @@ def main():
     if args.config == "c4":
         torch.cuda.set_device(0)
         return run_warmstart(args, lib, torch)
+    if args.config == "c5":
+        torch.cuda.set_device(0)
+        return run_warmstart(args, lib, torch, name="c5", n_train=2048, n_test=1024, epochs=60)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -335,9 +335,13 @@ typedef struct ddnm_tune {
     int chains;         /* instance groups iterating concurrently, 1..16 (capped at B) */
     int con_split;      /* constraint rows per constraint CTA: 512, 1024 or 2048 */
     int eval_persist;   /* persistent evaluation: CTAs per SM per width class (1..8), or 0 for one CTA per item */
+    int d_gemm;         /* D_i = C A_i dg_i^G: 1 in one GEMM launch per pass over all instances of a subdomain
+                           (they share the decoder); 0 inside each evaluation CTA; -1 (default) picks 1 when
+                           some subdomain has h^G n_C >= 65536 (hidden units of its interface decoder times n_C) */
 } ddnm_tune;
 
-/* Set / read the plan.  DDNM_E_INVALID outside the ranges above. */
+/* Set / read the plan (ddnm_get_tune reports d_gemm as given, -1 included).  DDNM_E_INVALID outside the
+ * ranges above. */
 int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t);
 int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t);
 
@@ -348,7 +352,8 @@ int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t);
  *  - The search is coordinate-wise:
  *      chains       in {1, 2, 4, 8, 16}, capped at B;
  *      eval_persist in {0, 1, 2, 4};
- *      con_split    in {512, 1024, 2048}.
+ *      con_split    in {512, 1024, 2048};
+ *      d_gemm       in {0, 1}.
  *    Each knob is swept with the best values found so far for the others.
  *  - max_iter > 0 caps the SQP iterations of the timed solves, to keep tuning
  *    short (the options are restored on return).

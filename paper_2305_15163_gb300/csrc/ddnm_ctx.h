@@ -73,7 +73,7 @@ struct ddnm_ctx {
     bool finalized = false;
     std::vector<ddnm::SubDev> hsub;
     ddnm::ProbDev pd{};
-    int eval_smem = 0, kkt_smem = 0, rec_smem = 0, ss_rows = 0;
+    int eval_smem = 0, kkt_smem = 0, rec_smem = 0, ss_rows = 0, max_nG = 1;
     void* d_vpool = nullptr;
     int* d_ipool = nullptr;
     int* d_hr = nullptr;
@@ -106,7 +106,8 @@ struct ddnm_ctx {
     size_t n_events = 0;               // pairs in use for the current call
 
     // launch plan and the captured solve graph (ddnm_kernels.cu)
-    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0};
+    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0, -1};
+    int dgemm_auto = 0;                // the d_gemm = -1 choice for these sizes (set with the tables)
     long long gen = 0;                 // bumped whenever device tables or workspace pointers change
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;

@@ -530,6 +530,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     ctx->hchunk.clear();
     ctx->htiles.clear();
     int xoff = 0, hr_off = 0, blk = 0;
+    long long pg_stride = 0;
+    ctx->max_nG = 1;
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
     ctx->eval_smem = 0;
     ctx->rec_smem = 0;
@@ -539,8 +541,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     int dev_max = 0, sm_smem = 0;
     CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-    // collocation rows per chunk, among 128, 64, ..., 8: the one that lets the most evaluation CTAs share
-    // an SM (shared memory against the register budget), the larger on a tie; it must fit one CTA
+    // collocation rows per chunk, among 128, 64, ..., 8: the largest whose evaluation CTAs per SM (shared
+    // memory against the register budget) come within a factor 1.5 of the best candidate's, since every chunk
+    // adds barriers and a round of table loads; it must fit one CTA
     int hc = 0, need_bytes = 0;
     {
         std::vector<int> hO(ns), hG(ns);
@@ -550,7 +553,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
             hO[s] = hidden_count(ctx->decO[s], ctx->subs[s].need);
             hG[s] = hidden_count(ctx->decG[s], allG);
         }
-        int best_ctas = 0, smallest = 1 << 30;
+        int smallest = 1 << 30;
+        std::vector<std::pair<int, int>> cands;     // (chunk, CTAs per SM) of the candidates that fit
         for (int cand = HR_CHUNK; cand >= 8; cand /= 2) {
             int bytes = 0, ctas = 1 << 30;
             for (int s = 0; s < ns; ++s) {
@@ -567,12 +571,16 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 ctas = std::min(ctas, std::min(by_smem, eval_min_ctas((int)tsize, round4(T.nO + 1), round4(T.nG + 1))));
             }
             smallest = std::min(smallest, bytes);
-            if (bytes <= dev_max && ctas > best_ctas) {
-                best_ctas = ctas;
-                hc = cand;
-                need_bytes = bytes;
-            }
+            if (bytes <= dev_max) cands.push_back({cand, ctas});
         }
+        int best = 0;
+        for (const auto& c : cands) best = std::max(best, c.second);
+        for (const auto& c : cands)                 // largest first
+            if (2 * c.second * 3 >= 2 * best * 2) {  // ctas >= best / 1.5
+                hc = c.first;
+                break;
+            }
+        need_bytes = smallest;
         if (!hc)
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain's evaluation needs " + std::to_string(smallest) +
                                                           " bytes of shared memory (device limit " +
@@ -644,6 +652,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 for (int c = 0; c < nC; ++c) q[c] += coef * M[(size_t)r * nC + c];
             }
         S.Qt = P.addv(Qt.data(), Qt.size());
+        S.pgoff = pg_stride;
+        pg_stride += (long long)S.hG * S.nG;
+        ctx->max_nG = std::max(ctx->max_nG, S.nG);
         // full decoders and ownership for reconstruction
         S.NO_full = dO.N; S.wO_full = dO.w; S.wG_full = dG.w;
         std::vector<double> so(dO.scale);
@@ -787,6 +798,12 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.cst[3] = ctx->nu / (ctx->hy * ctx->hy);
     for (int k = 0; k < 4; ++k) pd.cstf[k] = (float)pd.cst[k];
     pd.blk_stride = blk;
+    {
+        long long big = 0;
+        for (const SubDev& S : ctx->hsub) big = std::max(big, (long long)S.hG * nC);
+        ctx->dgemm_auto = big >= 65536 ? 1 : 0;
+    }
+    pd.pg_stride = std::max(pg_stride, 1LL);
     pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.tiles = ctx->d_tiles; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
     pd.hr = ctx->d_hr;
     pd.con_lo = ctx->d_con; pd.con_hi = ctx->d_con + ctx->N_A; pd.C = ctx->d_C; pd.bnd_ij = ctx->d_bnd_ij;
@@ -818,6 +835,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
     size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * tsize);
     size_t o_gG = o; o = al(o + (size_t)cap * pd.sum_NG * tsize);
+    size_t o_PG = o; o = al(o + (size_t)cap * pd.pg_stride * tsize);
     size_t o_blk = o; o = al(o + (size_t)cap * pd.blk_stride * 8);
     size_t o_act = o; o = al(o + (size_t)CTL_INTS * 4);
     cudaFree(ctx->d_ws);
@@ -841,6 +859,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     pd.ist = (int*)(base + o_ist);
     pd.bnd = (void*)(base + o_bnd);
     pd.gG = (void*)(base + o_gG);
+    pd.PG = (void*)(base + o_PG);
     pd.blk = (double*)(base + o_blk);
     pd.active = (int*)(base + o_act);
     pd.pass = pd.active + MAX_CHAINS;

@@ -32,6 +32,8 @@ constexpr int HR_INTS = 7;     // comp, then operands: centre, E, W, N, S (same 
 enum { MODE_INIT0 = 0, MODE_INIT1 = 1, MODE_LS = 2 };
 constexpr int ST_RUNNING = -1;
 enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_XTMODE, I_PAD, INST_INTS };
+constexpr int DG_THREADS = 256;    // k_dgemm
+constexpr int DG_KT = 32;          // interface hidden units per staged chunk of k_dgemm
 constexpr int KKT_THREADS = 512;   // k_kkt: one CTA per instance, a warp per subdomain factorisation
 constexpr int SS_ROWS_DBL = 4096;  // staged W rows (doubles) per Schur-sum chunk, each for W and D_G^{-1} W
 // how the next evaluation forms its trial point xt (ist[I_XTMODE]): unchanged (xt = x), a new SQP step
@@ -84,6 +86,7 @@ struct SubDev {
     int NGn, hr_chunk;             // interface outputs the stencils use; collocation rows per chunk
     long long colGn, valGn, soGn;  // those outputs: ELL slot-major (Kp x NGn), scale/offset
     long long Qt;                  // value pool: Q_i^T = (C A_i diag(scale) W2~)^T, h_G x n_C
+    long long pgoff;               // offset of this subdomain's P_G (h_G x n^G) in an instance's P_G area
     // full (not subnet) decoders for reconstruction
     int NO_full, wO_full, wG_full, K;
     long long fw1O, fb1O, fw2O, foutO, fcolO;
@@ -129,6 +132,7 @@ struct ProbDev {
     int ss_rows;                   // rows of W staged per Schur-sum chunk
     int n_ss_chunks;               // Schur-sum chunks: subdomains [ss_chunk[k], ss_chunk[k + 1])
     const int* ss_chunk;
+    int d_gemm;                    // 1: D_i by the batched k_dgemm; 0: inside the evaluation
     int n_split;                   // constraint CTAs per instance (ceil(N_A / con_split))
     int con_split;                 // constraint rows per constraint CTA
     double hx, hy, nu, bx0, by0;
@@ -161,6 +165,8 @@ struct ProbDev {
     int* ist;                      // INST_INTS per instance
     void* bnd;                     // B x n_bnd x 2 (u, v) Dirichlet data, value type
     void* gG;                      // B x sum_NG interface outputs (value type)
+    void* PG;                      // B x pg_stride: per subdomain sigma'(z_h) W1~[h, :], value type
+    long long pg_stride;
     double* blk;                   // B x blk_stride
     double* r_hr;                  // optional output B x sum_NB
     int* active;                   // count of running instances after a step pass
@@ -175,7 +181,7 @@ constexpr int CTL_INTS = MAX_CHAINS * (2 + MAX_CLASSES);
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {
     int sx, hidO, hidG, outGn, outO, Rr, red;  // value-type arrays
-    int dlam, dH, drho, dD, dt;                // double arrays
+    int dH, drho, dt, dD;                      // double arrays
     int bytes;
 };
 
@@ -192,11 +198,10 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
     e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
     e.red = o; o = align16(o + (EVAL_THREADS / nC) * nC * s.nG * tsize);   // D_i partials per thread group
-    e.dlam = o; o = align16(o + nC * 8);
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
-    e.dD = o; o = align16(o + nC * s.nG * 8);
     e.dt = o; o = align16(o + s.ni * 8);
+    e.dD = o; o = align16(o + nC * s.nG * 8);
     e.bytes = o;
     return e;
 }

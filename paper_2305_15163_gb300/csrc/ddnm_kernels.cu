@@ -402,12 +402,11 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     T* outGn = (T*)(smem + L.outGn);
     T* outO = (T*)(smem + L.outO);
     T* Rr = (T*)(smem + L.Rr);
-    T* red = (T*)(smem + L.red);
-    double* dlam = (double*)(smem + L.dlam);
     double* dH = (double*)(smem + L.dH);
     double* drho = (double*)(smem + L.drho);
-    double* dD = (double*)(smem + L.dD);
     double* dt = (double*)(smem + L.dt);
+    double* dD = (double*)(smem + L.dD);
+    T* red = (T*)(smem + L.red);
 
     const T* V = (const T*)P.vpool;
     const int* IP = P.ipool;
@@ -420,7 +419,6 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     // latent coordinates and multipliers of the trial point
     form_trial(P, S, b, dt);
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
-    for (int c = tid; c < nC; c += nth) dlam[c] = P.lamt[(size_t)b * nC + c];
     __syncthreads();
 
     // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]; the rows that pad each
@@ -505,9 +503,17 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         for (int k = 0; k < RG; k += 4) st4(outGn + (size_t)r * RG + k, acc + k);
     }
     // D_i = C A_i dg^G/dxh = Q_i P_G with Q_i = C A_i diag(scale) W2~ (n_C x h_G, precomputed, stored
-    // transposed) and P_G[h] = sigma'(z_h) W1~[h, :] (the hidden records): thread (group, c) sums the
-    // hidden units h = group, group + n_grp, ... for row c; the groups are added in order afterwards
-    {
+    // transposed) and P_G[h] = sigma'(z_h) W1~[h, :] (from the hidden records).  Either here, thread
+    // (group, c) summing the hidden units h = group, group + n_grp, ... for row c and the groups added in
+    // order afterwards, or batched over the instances that share the decoder (k_dgemm), for which P_G is
+    // written out.
+    if (P.d_gemm) {
+        T* pg = (T*)P.PG + (size_t)b * P.pg_stride + S.pgoff;
+        for (int e = tid; e < S.hG * nG; e += nth) {
+            const int h = e / nG, k = e - h * nG;
+            pg[e] = hidG[(size_t)h * RG + 1 + k];
+        }
+    } else {
         const int ngrp = nth / nC;
         const int c = tid % nC, grp = tid / nC;
         if (grp < ngrp) {
@@ -537,13 +543,12 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int k = 0; k < RG - 1; ++k)
                 if (k < nG) red[((size_t)grp * nC + c) * nG + k] = acc[k];
         }
-    }
-    __syncthreads();
-    for (int o = tid; o < nC * nG; o += nth) {
-        const int ngrp = nth / nC;
-        T acc = T(0);
-        for (int g = 0; g < ngrp; ++g) acc += red[(size_t)g * nC * nG + o];
-        dD[o] = (double)acc;
+        __syncthreads();
+        for (int o = tid; o < nC * nG; o += nth) {
+            T a = T(0);
+            for (int g = 0; g < ngrp; ++g) a += red[(size_t)g * nC * nG + o];
+            dD[o] = (double)a;
+        }
     }
 
     // H_i = R^T R and R^T r: thread p owns one entry (a <= c), running sum over the chunks
@@ -675,29 +680,29 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
     __syncthreads();
 
-    // rho_i = R^T r + E_i^T lambda in FP64 (E_i = [0, D_i]: only the interface entries get D_i^T lambda),
-    // warp k forming entry n^O + k with its lanes over the multipliers; then phi_i = ||rho_i||^2.  The
-    // factorisation of H_i is left to k_factor, which runs only at accepted points.
+    // H_i and rho_i = R_i^T r + E_i^T lambda (E_i = [0, D_i]) with phi_i = ||rho_i||^2 (in FP64: warp k forms
+    // entry n^O + k, lanes over the multipliers), or R_i^T r alone when k_dgemm forms D_i and the rest
     double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
     const BlkLayout BL = blk_layout(ni, nG, nC);
-    {
-        const int w = tid >> 5, lane = tid & 31;
-        for (int k = w; k < nG; k += nwarp) {
+    if (!P.d_gemm) {
+        const int w2 = tid >> 5, l2 = tid & 31;
+        const double* lam = P.lamt + (size_t)b * nC;
+        for (int k = w2; k < nG; k += nwarp) {
             double v = 0.0;
-            for (int c = lane; c < nC; c += 32) v += dD[c * nG + k] * dlam[c];
+            for (int c = l2; c < nC; c += 32) v += dD[c * nG + k] * lam[c];
             v = warp_sum(v);
-            if (lane == 0) drho[nO + k] += v;
+            if (l2 == 0) drho[nO + k] += v;
         }
-    }
-    __syncthreads();
-    if (tid < 32) {
-        const double r = tid < ni ? drho[tid] : 0.0;
-        const double ph = warp_sum(r * r);
-        if (tid == 0) blk[BL.phi] = ph;
+        __syncthreads();
+        if (tid < 32) {
+            const double r = tid < ni ? drho[tid] : 0.0;
+            const double ph = warp_sum(r * r);
+            if (tid == 0) blk[BL.phi] = ph;
+        }
+        for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
     }
     for (int e = tid; e < ni * ni; e += nth) blk[BL.H + e] = dH[e];
     if (tid < ni) blk[BL.rho + tid] = drho[tid];
-    for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
 }
 
 // One launch per class of subdomains sharing the padded record widths (RO, RG).  Items are (instance,
@@ -744,6 +749,123 @@ EvalKernel<T> eval_kernel(int ro, int rg) {
     DDNM_EVAL_CASE(16, 4) DDNM_EVAL_CASE(16, 8) DDNM_EVAL_CASE(16, 12)
 #undef DDNM_EVAL_CASE
     return nullptr;
+}
+
+// k_dgemm shared memory: the staging area (also the reduction area afterwards), then TB x n_C multipliers
+template <typename T, int CPT>
+__host__ __device__ constexpr int dg_smem_main(int ncp) {
+    return ((DG_KT * (ncp + (DG_THREADS / ncp) * CPT) > DG_THREADS * CPT ? DG_KT * (ncp + (DG_THREADS / ncp) * CPT)
+                                                                           : DG_THREADS * CPT) *
+                (int)sizeof(T) + 15) & ~15;
+}
+
+// D_i = C A_i dg_i^G/dxh = Q_i P_G (Eq. sqp_block_matrices) for the instances of one subdomain at once:
+// Q_i (n_C x h_G, stored transposed) is shared by every instance, so the product over a tile of TB instances
+// is a GEMM [n_C x h_G] x [h_G x (TB n^G)].  CTA (subdomain, instance tile); thread (c, g) owns row c of C;
+// the thread groups g are split into column groups (CPT consecutive columns (instance, k) each) and, when
+// the tile has few columns, into hidden-unit groups whose partial sums are added in order at the end.  h_G
+// is walked in chunks of DG_KT staged in shared memory (Q rows coalesced, each instance's P_G slice
+// contiguous).  Epilogue in FP64: D_i into the block, rho_i^G += D_i^T lambda (E_i = [0, D_i], Eq.
+// optimality_residuals_GN) and phi_i = ||rho_i||^2.
+template <typename T, int CPT>
+__global__ void __launch_bounds__(DG_THREADS) k_dgemm(ProbDev P, int B, int TB) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int si = blockIdx.x, tid = threadIdx.x;
+    const SubDev& S = P.sub[si];
+    const int nC = P.n_C, nG = S.nG, nO = S.nO, ni = S.ni, hG = S.hG;
+    const int ncp = (nC + 31) & ~31, ngrp = DG_THREADS / ncp;
+    const int cols = TB * nG;
+    const int cg = (cols + CPT - 1) / CPT;      // column groups (the host keeps cg <= ngrp)
+    const int kg = ngrp / cg;                   // hidden-unit groups
+    const int ncolp = cg * CPT;
+    const int b0 = blockIdx.y * TB;
+    if (b0 >= B) return;
+    T* Qs = (T*)dsm;                            // DG_KT x ncp
+    T* Ps = Qs + DG_KT * ncp;                   // DG_KT x ncolp
+    __shared__ unsigned char run[DG_THREADS];
+    for (int bl = tid; bl < TB; bl += DG_THREADS) {
+        const int b = b0 + bl;
+        run[bl] = b < B && P.ist[(size_t)b * INST_INTS + I_STATUS] == ST_RUNNING;
+    }
+    const int c = tid % ncp, g = tid / ncp;
+    const int colg = g % cg, kgr = g / cg;
+    const bool active = g < cg * kg;
+    T acc[CPT];
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[j] = T(0);
+    const T* Qt = (const T*)P.vpool + S.Qt;
+    for (int h0 = 0; h0 < hG; h0 += DG_KT) {
+        __syncthreads();
+        for (int e = tid; e < DG_KT * ncp; e += DG_THREADS) {
+            const int hh = e / ncp, cc = e - hh * ncp;
+            Qs[e] = (h0 + hh < hG && cc < nC) ? Qt[(size_t)(h0 + hh) * nC + cc] : T(0);
+        }
+        for (int e = tid; e < TB * DG_KT * nG; e += DG_THREADS) {
+            const int bl = e / (DG_KT * nG), rem = e - bl * DG_KT * nG;
+            const int hh = rem / nG, k = rem - hh * nG;
+            T v = T(0);
+            if (h0 + hh < hG && run[bl])
+                v = ((const T*)P.PG)[(size_t)(b0 + bl) * P.pg_stride + S.pgoff + (size_t)(h0 + hh) * nG + k];
+            Ps[hh * ncolp + bl * nG + k] = v;
+        }
+        for (int e = tid; e < DG_KT * (ncolp - cols); e += DG_THREADS) {   // padding columns
+            const int hh = e / (ncolp - cols), cc = e - hh * (ncolp - cols);
+            Ps[hh * ncolp + cols + cc] = T(0);
+        }
+        __syncthreads();
+        if (active) {
+            const T* pr = Ps + colg * CPT;
+            for (int hh = kgr; hh < DG_KT; hh += kg) {
+                const T q = Qs[hh * ncp + c];
+#pragma unroll
+                for (int j = 0; j < CPT; j += 4) {
+                    T pv[4];
+                    ld4(pr + hh * ncolp + j, pv);
+                    acc[j] += q * pv[0];
+                    acc[j + 1] += q * pv[1];
+                    acc[j + 2] += q * pv[2];
+                    acc[j + 3] += q * pv[3];
+                }
+            }
+        }
+    }
+    // partial sums of the hidden-unit groups, added in group order; multipliers of the tile's instances
+    __syncthreads();
+    T* red = (T*)dsm;                                            // kg x ncp x ncolp
+    double* lam_s = (double*)(dsm + dg_smem_main<T, CPT>(ncp));  // TB x nC
+    if (active)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) red[((size_t)kgr * ncp + c) * ncolp + colg * CPT + j] = acc[j];
+    for (int e = tid; e < TB * nC; e += DG_THREADS) {
+        const int b = b0 + e / nC;
+        lam_s[e] = b < B ? P.lamt[(size_t)b * nC + e % nC] : 0.0;
+    }
+    __syncthreads();
+    const BlkLayout BL = blk_layout(ni, nG, nC);
+    for (int e = tid; e < nC * cols; e += DG_THREADS) {
+        const int cc = e / cols, col = e - cc * cols;
+        T v = T(0);
+        for (int k = 0; k < kg; ++k) v += red[((size_t)k * ncp + cc) * ncolp + col];
+        red[(size_t)cc * ncolp + col] = v;                       // this (c, col) is read by this thread only
+        const int bl = col / nG, kk = col - bl * nG;
+        if (run[bl]) P.blk[(size_t)(b0 + bl) * P.blk_stride + S.blk + BL.D + cc * nG + kk] = (double)v;
+    }
+    __syncthreads();
+    for (int col = tid; col < cols; col += DG_THREADS) {
+        const int bl = col / nG, k = col - bl * nG;
+        if (!run[bl]) continue;
+        double v = 0.0;
+        for (int cc = 0; cc < nC; ++cc) v += (double)red[(size_t)cc * ncolp + col] * lam_s[bl * nC + cc];
+        P.blk[(size_t)(b0 + bl) * P.blk_stride + S.blk + BL.rho + nO + k] += v;
+    }
+    __syncthreads();
+    for (int bl = tid; bl < TB; bl += DG_THREADS) {
+        if (!run[bl]) continue;
+        double* blk = P.blk + (size_t)(b0 + bl) * P.blk_stride + S.blk;
+        double ph = 0.0;
+        for (int jj = 0; jj < ni; ++jj) ph += blk[BL.rho + jj] * blk[BL.rho + jj];
+        blk[BL.phi] = ph;
+    }
 }
 
 // Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
@@ -1452,11 +1574,34 @@ int set_smem_attrs(ddnm_ctx* ctx) {
     for (const auto& g : ctx->eval_classes)
         CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem));
     CK(cudaFuncSetAttribute(k_kkt, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->kkt_smem));
+    {
+        constexpr int CPT = sizeof(T) == 8 ? 16 : 32;
+        const int ncp = (ctx->n_C + 31) & ~31;
+        const int tb_max = std::max(1, (DG_THREADS / ncp) * CPT / ctx->max_nG);
+        const int smem = dg_smem_main<T, CPT>(ncp) + tb_max * ctx->n_C * 8;
+        CK(cudaFuncSetAttribute(k_dgemm<T, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
     CK(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(ctx->rec_smem, 16)));
     return DDNM_OK;
 }
 
-// One pass's evaluation (one launch per width class) and constraint launches for the B instances of P.
+// the batched D_i GEMM of one pass (after the evaluation launches): instance tiles of about
+// B n_sub / (2 SMs) instances, at most as many as the CTA's columns hold
+template <typename T>
+cudaError_t launch_dgemm(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st) {
+    constexpr int CPT = sizeof(T) == 8 ? 16 : 32;
+    const int ncp = (P.n_C + 31) & ~31, ncol = (DG_THREADS / ncp) * CPT;
+    const int tb_max = std::max(1, ncol / ctx->max_nG);
+    const int n_sm = ctx->n_sm > 0 ? ctx->n_sm : 148;
+    const long long want = ((long long)B * P.n_sub + 2LL * n_sm - 1) / (2LL * n_sm);
+    const int TB = (int)std::max(1LL, std::min<long long>(want, tb_max));
+    const size_t smem = (size_t)dg_smem_main<T, CPT>(ncp) + (size_t)TB * P.n_C * 8;
+    k_dgemm<T, CPT><<<dim3(P.n_sub, (B + TB - 1) / TB), DG_THREADS, smem, st>>>(P, B, TB);
+    return cudaGetLastError();
+}
+
+// One pass's evaluation (one launch per width class, then the batched D_i GEMM) and constraint launches for
+// the B instances of P.
 // persist: the evaluation launches are persistent; zero_ctr: clear their work counters first (the loop
 // kernel of the solve graph clears them otherwise).
 template <typename T>
@@ -1474,6 +1619,10 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
         }
         eval_kernel<T>(g.ro, g.rg)<<<grid, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, ctr);
         CK(cudaGetLastError());
+        ctx->tm.eval_launches++;
+    }
+    if (P.d_gemm) {
+        CK(launch_dgemm<T>(ctx, P, B, st));
         ctx->tm.eval_launches++;
     }
     tstop(ctx, k, st);
@@ -1517,6 +1666,7 @@ ProbDev group_view(const ProbDev& P, int b0, int c, size_t tsize) {
     Q.ist += b * INST_INTS;
     Q.bnd = (char*)P.bnd + b * P.n_bnd * 2 * tsize;
     Q.gG = (char*)P.gG + b * P.sum_NG * tsize;
+    Q.PG = (char*)P.PG + b * P.pg_stride * tsize;
     Q.blk += b * P.blk_stride;
     if (Q.r_hr) Q.r_hr += b * P.sum_NB;
     Q.active = P.active + c;
@@ -1577,11 +1727,13 @@ void fold_pending(ddnm_ctx* ctx) {
     if (cudaEventSynchronize(ctx->pass_ev) != cudaSuccess) return;
     long long passes = 0;
     for (int c = 0; c < ctx->pending_chains; ++c) passes += ctx->h_pass[c];
-    ctx->tm.eval_launches += passes * ctx->pending_classes;
+    ctx->tm.eval_launches += passes * ctx->pending_classes;   // with the D_i GEMM when it is used
     ctx->tm.constraint_launches += passes;
     ctx->tm.step_launches += passes;           // k_kkt
     ctx->tm.other_launches += passes;          // the loop kernel
 }
+
+int resolved_dgemm(const ddnm_ctx* ctx) { return ctx->tune.d_gemm < 0 ? ctx->dgemm_auto : ctx->tune.d_gemm; }
 
 void drop_graph(ddnm_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
@@ -1702,7 +1854,8 @@ int solve_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool ha
     const ddnm_options& o = ctx->opt;
     const std::vector<long long> key{ctx->gen, B, Bw, ws, has_x0, has_lam0, (long long)sizeof(T), max_passes,
                                      bits(o.tol), bits(o.armijo_c1), bits(o.beta), o.max_iter, o.max_backtracks,
-                                     ctx->tune.chains, ctx->tune.con_split, ctx->tune.eval_persist, ctx->n_sm};
+                                     ctx->tune.chains, ctx->tune.con_split, ctx->tune.eval_persist, ctx->n_sm,
+                                     P.d_gemm};
     if (!ctx->gexec || key != ctx->gkey) {
         const int rc = build_graph<T>(ctx, P, B, Bw, ws, has_x0, has_lam0, max_passes);
         if (rc) return rc;
@@ -1711,7 +1864,7 @@ int solve_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool ha
     if (!ctx->h_pass) CK(cudaMallocHost(&ctx->h_pass, MAX_CHAINS * sizeof(int)));
     if (!ctx->pass_ev) CK(cudaEventCreateWithFlags(&ctx->pass_ev, cudaEventDisableTiming));
     CK(cudaGraphLaunch(ctx->gexec, st));
-    const int cls = (int)ctx->eval_classes.size();
+    const int cls = (int)ctx->eval_classes.size() + (P.d_gemm ? 1 : 0);
     ctx->tm.other_launches += 1 + (ws ? 1 : 0);                // k_init, k_ws_select
     if (ws) {
         ctx->tm.eval_launches += 2 * cls;
@@ -1758,6 +1911,7 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
     P.max_bt = ctx->opt.max_backtracks;
     P.con_split = ctx->tune.con_split;
     P.n_split = (P.N_A + P.con_split - 1) / P.con_split;
+    P.d_gemm = resolved_dgemm(ctx);
     if (ctx->tune.graph && !ctx->timing) {
         rc = fp64 ? solve_graph<double>(ctx, P, B, Bw, ws, x0 != nullptr, lam0 != nullptr, max_passes, st)
                   : solve_graph<float>(ctx, P, B, Bw, ws, x0 != nullptr, lam0 != nullptr, max_passes, st);
@@ -1835,6 +1989,7 @@ int eval_once(ddnm_ctx* ctx, ProbDev& P, int B, const double* mu, const double* 
     CK(cudaGetLastError());
     ctx->tm.other_launches++;
     P.r_hr = r_hr_dev;
+    P.d_gemm = resolved_dgemm(ctx);
     return launch_eval<T>(ctx, P, B, st);
 }
 }  // namespace
@@ -1943,9 +2098,10 @@ extern "C" int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t) {
     if (!ctx || !t) return DDNM_E_INVALID;
     const bool pow2 = t->con_split > 0 && (t->con_split & (t->con_split - 1)) == 0;
     if (t->graph < 0 || t->graph > 1 || t->chains < 1 || t->chains > MAX_CHAINS || !pow2 ||
-        t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8)
+        t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8 ||
+        t->d_gemm < -1 || t->d_gemm > 1)
         return ddnm_fail(ctx, DDNM_E_INVALID,
-                         "tune: graph 0/1, chains 1..16, con_split 512, 1024 or 2048, eval_persist 0..8");
+                         "tune: graph 0/1, chains 1..16, con_split 512, 1024 or 2048, eval_persist 0..8, d_gemm -1..1");
     ctx->tune = *t;
     return DDNM_OK;
 }
@@ -2019,6 +2175,8 @@ extern "C" int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kin
     if ((rc = sweep(&ddnm_tune::chains, {1, 2, 4, 8, 16}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::eval_persist, {0, 1, 2, 4}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::con_split, {512, 1024, 2048}))) return finish(rc);
+    if (cur.d_gemm < 0) cur.d_gemm = ctx->dgemm_auto;
+    if ((rc = sweep(&ddnm_tune::d_gemm, {0, 1}))) return finish(rc);
     ctx->tune = cur;
     if (best) *best = cur;
     if (best_ms) *best_ms = cur_ms;
@@ -2100,6 +2258,10 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
     k_noalloc_init<<<B, 128, 0, st>>>(P, B, (int)(sizeof(T) == 8));
     for (const auto& g : ctx->eval_classes)
         eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, nullptr);
+    if (P.d_gemm) {
+        e = launch_dgemm<T>(ctx, P, B, st);
+        if (e != cudaSuccess) return cfail(ctx, e, "no-allocation D_i product launch");
+    }
     k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B);
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
@@ -2118,6 +2280,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
                          "the decoder and constraint tables are not on the device yet: make one allocating call "
                          "(ddnm_residual, ddnm_linearize or ddnm_solve_batch) first");
     ProbDev P = ctx->pd;
+    P.d_gemm = resolved_dgemm(ctx);
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
     auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
     size_t o = 0;
@@ -2125,6 +2288,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     const size_t o_dst = o; o = al(o + (size_t)B * INST_DBLS * 8);
     const size_t o_bnd = o; o = al(o + (size_t)B * std::max(P.n_bnd, 1) * 2 * 8);
     const size_t o_gG = o; o = al(o + (size_t)B * P.sum_NG * tsize);
+    const size_t o_PG = o; o = al(o + (size_t)B * P.pg_stride * tsize);
     const size_t o_blk = o; o = al(o + (size_t)B * P.blk_stride * 8);
     const size_t o_At = o; o = al(o + (size_t)B * P.n_split * P.n_C * 8);
     const size_t o_Ss = o; o = al(o + (size_t)B * ((size_t)P.n_C * P.n_C + P.n_C) * 8);
@@ -2149,6 +2313,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     P.dst = (double*)(s + o_dst);
     P.bnd = (void*)(s + o_bnd);
     P.gG = (void*)(s + o_gG);
+    P.PG = (void*)(s + o_PG);
     P.blk = (double*)(s + o_blk);
     P.Atil = (double*)(s + o_At);
     P.Ssum = (double*)(s + o_Ss);

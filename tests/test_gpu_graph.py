@@ -1,8 +1,9 @@
 """Launch plan of the batched solve: the graph-resident SQP loop (one CUDA graph launch with a device-side
 while loop per instance group), the persistent evaluation and the constraint-slice size change how the work
-is scheduled, never what is computed.  Every plan gives bit-identical iterates, multipliers and
-per-instance statistics to the host-driven loop; the autotuner returns a valid plan and the solve under it
-still matches the oracle."""
+is scheduled, never what is computed.  Every such plan gives bit-identical iterates, multipliers and
+per-instance statistics to the host-driven loop.  Where D_i is formed (inside the evaluation or in the
+batched GEMM) changes its summation order only: both match the oracle.  The autotuner returns a valid plan
+and the solve under it still matches the oracle."""
 import numpy as np
 import pytest
 
@@ -23,6 +24,7 @@ PLANS = [dict(graph=1, chains=1, con_split=512, eval_persist=0),
          dict(graph=1, chains=16, con_split=2048, eval_persist=1),
          dict(graph=1, chains=4, con_split=512, eval_persist=4),
          dict(graph=0, chains=1, con_split=2048, eval_persist=3)]
+TOL = {FP64: 1e-6, MIXED: 1e-4}
 
 
 def solver(name, prec):
@@ -41,23 +43,45 @@ def same(a, b):
         assert np.array_equal(sa[f], sb[f]), f
 
 
+@pytest.mark.parametrize("d_gemm", [0, 1])
 @pytest.mark.parametrize("name,prec,B", [("c2", MIXED, 13), ("c2", FP64, 5), ("c3", MIXED, 7), ("c1", FP64, 1),
                                          ("tiny13x9_3x2", MIXED, 4)])
-def test_plans_are_bit_identical(name, prec, B):
+def test_plans_are_bit_identical(name, prec, B, d_gemm):
     wl, s = solver(name, prec)
     mu = inputs.mu_batch(B, seed=31)
     s.options(tol=0.0, max_iter=4)
-    lib.ddnm_set_tune(s.ctx, **HOST)
+    lib.ddnm_set_tune(s.ctx, **HOST, d_gemm=d_gemm)
     ref = s.solve(mu)
     for plan in PLANS:
-        lib.ddnm_set_tune(s.ctx, **plan)
+        lib.ddnm_set_tune(s.ctx, **plan, d_gemm=d_gemm)
         same(s.solve(mu), ref)
         same(s.solve(mu), ref)                 # replay of the captured graph
     s.options()
-    lib.ddnm_set_tune(s.ctx, **HOST)
+    lib.ddnm_set_tune(s.ctx, **HOST, d_gemm=d_gemm)
     ref = s.solve(mu)                          # stopping rule active: groups finish at different passes
-    lib.ddnm_set_tune(s.ctx, graph=1, chains=min(B, 5), con_split=1024, eval_persist=2)
+    lib.ddnm_set_tune(s.ctx, graph=1, chains=min(B, 5), con_split=1024, eval_persist=2, d_gemm=d_gemm)
     same(s.solve(mu), ref)
+    s.close()
+
+
+@pytest.mark.parametrize("name,prec", [("c1", FP64), ("c1", MIXED), ("tiny13x9_3x2", FP64), ("c3", MIXED)])
+def test_both_d_forms_match_oracle(name, prec):
+    """D_i inside the evaluation and D_i from the batched GEMM: both against the FP64 oracle (3 SQP
+    iterations, same line-search decisions)."""
+    wl = inputs.workload(name)
+    fom, dd, rom, raw = setup.build(wl)
+    s = lib.Solver(wl, precision=prec)
+    s.load(raw["dec_o"], raw["dec_g"], raw["C"])
+    mu = inputs.mu_batch(3)
+    s.options(tol=0.0, max_iter=3)
+    refs = [rom.solve(mu[b], tol=0.0, max_iter=3) for b in range(3)]
+    for d_gemm in (0, 1):
+        lib.ddnm_set_tune(s.ctx, graph=1, chains=2, d_gemm=d_gemm)
+        x, lam, st = s.solve(mu)
+        for b in range(3):
+            assert st[b]["n_evals"] == refs[b].n_evals
+            assert np.linalg.norm(x[b] - refs[b].x) <= TOL[prec] * np.linalg.norm(refs[b].x)
+            assert np.linalg.norm(lam[b] - refs[b].lam) <= TOL[prec] * np.linalg.norm(refs[b].lam)
     s.close()
 
 
@@ -115,7 +139,7 @@ def test_autotune_then_parity_with_oracle():
     mu = inputs.mu_batch(3)
     plan, ms = lib.ddnm_autotune(s.ctx, mu, max_iter=2, reps=2)
     assert plan["graph"] == 1 and 1 <= plan["chains"] <= 3 and plan["con_split"] in (512, 1024, 2048)
-    assert plan["eval_persist"] in (0, 1, 2, 4) and ms > 0
+    assert plan["eval_persist"] in (0, 1, 2, 4) and plan["d_gemm"] in (0, 1) and ms > 0
     assert lib.ddnm_get_tune(s.ctx) == plan
     s.options(tol=0.0, max_iter=3)
     x, lam, st = s.solve(mu)
