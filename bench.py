@@ -18,6 +18,7 @@ import argparse
 import json
 import multiprocessing as mp
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -35,6 +36,24 @@ UNIT = "solves/s"
 FLUSH_BYTES = 512 << 20          # > 129 MB L2
 SMS, FP32_LANES, FP64_PER_CLK = 152, 128, 2   # GB300: SMs, FP32 lanes / SM, DFMA / clk / SM
 SM_MAX_MHZ = 2070.0
+
+
+def eval_traffic_profile():
+    """DRAM bytes per launch of the evaluation kernel on this workload from the committed ncu summary, if it
+    was taken on the current kernel source (same SHA-256), else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_eval_c2.md")
+    src = os.path.join(ROOT, "paper_2305_15163_gb300", "csrc", "ddnm_kernels.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
+    m_b = re.search(r"dram bytes per launch: ([0-9]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return int(m_b.group(1))
 
 
 def peaks():
@@ -255,7 +274,8 @@ def run_warmstart(args, lib, torch, name="c2", n_train=4096, n_test=1024, epochs
     n64 = max(B, len(mu_te) // 4)
     v_fp64, st_fp64 = timed(s64, mu_te[:n64])
     reached = reach > 0
-    line = {"metric": METRIC, "value": v_ws, "unit": UNIT, "n_gpus": 1, "steps": len(mu_te) // B, "warmup": 1,
+    line = {"metric": METRIC + " [mixed + learned warm start at the plain solve's final merit]", "value": v_ws_eq,
+            "unit": UNIT, "n_gpus": 1, "steps": len(mu_te) // B, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 KKT",
             "data": "synthetic",
             "config": {"workload": f"learned warm start on the {wl.nx}x{wl.ny} {wl.kx}x{wl.ky} setup ({name}), MLP "
@@ -392,7 +412,10 @@ def main():
 
     # roofline of the dominant kernel: per-kernel device time from the library's CUDA events, taken in a
     # separate run of the same solves through the host-driven loop (events around every launch)
+    # (non-persistent evaluation, so that every launch covers its whole grid alone on the GPU)
     kb = max(3, args.steps // 4)
+    plan_now = lib.ddnm_get_tune(s.ctx)
+    lib.ddnm_set_tune(s.ctx, **dict(plan_now, graph=0, eval_persist=0))
     lib.ddnm_timing_enable(s.ctx, True)
     for _ in range(kb):
         flush.zero_()
@@ -400,6 +423,7 @@ def main():
     torch.cuda.synchronize()
     tm = lib.ddnm_get_timing(s.ctx)
     lib.ddnm_timing_enable(s.ctx, False)
+    lib.ddnm_set_tune(s.ctx, **plan_now)
     work = lib.ddnm_get_work(s.ctx)
     pk = peaks()
     evals_per_step = float(st["n_evals"].sum())
@@ -424,10 +448,18 @@ def main():
             else "derived: 152 SMs x 2 DFMA/clk x 2 x sm_max_mhz",
             "launches": launches, "flops_per_launch": fl / max(launches, 1),
             "avg_launch_us": 1000.0 * kern[dom] / max(launches, 1),
-            "hbm_frac_of_measured": (work["eval_bytes"] * evals_per_step * kb / (tm["eval_ms"] / 1000.0) / 1e9)
-            / pk["hbm_gbs"],
+            # algorithmic bytes of the evaluation launches: shared tables once per launch, the instance
+            # bytes per instance-evaluation
+            "hbm_frac_of_measured": ((work["table_bytes"] * tm["eval_launches"] + work["instance_bytes"] * evals_per_step * kb)
+                                     / (tm["eval_ms"] / 1000.0) / 1e9) / pk["hbm_gbs"],
+            "eval_algorithmic_bytes_per_launch": (work["table_bytes"] * tm["eval_launches"]
+                                                  + work["instance_bytes"] * evals_per_step * kb) / max(tm["eval_launches"], 1),
             "kernel_ms_per_step": {k: round(v / kb, 4) for k, v in kern.items()},
-            "timed_in": f"{kb} extra solves, host-driven loop, CUDA events around every launch"}
+            "timed_in": f"{kb} extra solves, host-driven loop, one CTA per item, CUDA events around every launch"}
+    prof = eval_traffic_profile()
+    if dom == "k_eval" and prof is not None:
+        roof["traffic"] = prof
+        roof["traffic_source"] = "profiles/k_eval_c2.md (ncu dram__bytes_read.sum + dram__bytes_write.sum per launch)"
 
     # end to end through the public API with host (pinned) buffers, copies inside the timed region
     mu_h = torch.from_numpy(mu.copy()).pin_memory()

@@ -167,12 +167,17 @@ typedef struct ddnm_work {
     double eval_flops;          /* value-type flops of k_eval: hidden layers, decoder outputs and
                                    Jacobian rows, residual rows and chain rule, H_i and R_i^T r_i, D_i */
     double eval_fp64_flops;     /* FP64 flops of k_eval: rho_i += D_i^T lambda, ||rho_i||^2 */
-    double eval_bytes;          /* unique global bytes one instance-evaluation must touch
-                                   (weights and tables counted once, latents, outputs) */
+    double eval_bytes;          /* global bytes of one instance-evaluation on its own: table_bytes +
+                                   instance_bytes */
     double constraint_fp64_flops;  /* 2 n_C N_A */
     double step_fp64_flops;     /* per accepted point: per-subdomain L D L^T, t, W, u; the Schur sums
                                    S = sum_i W_i^T D_G^{-1} W_i and sum_i u_i; the n_C L D L^T and solves;
                                    the back-substitution */
+    double table_bytes;         /* bytes an evaluation reads that every instance shares: subnet weights, mask
+                                   values and columns, scale/offset, Q_i, collocation-row table */
+    double instance_bytes;      /* bytes an evaluation reads or writes for one instance: latents, mu,
+                                   multipliers, Dirichlet values, interface values, H_i, rho_i, D_i.  The
+                                   algorithmic bytes of a launch of B instances: table_bytes + B instance_bytes */
 } ddnm_work;
 
 typedef struct ddnm_ctx ddnm_ctx;

@@ -69,7 +69,8 @@ class ddnm_timing(C.Structure):
 
 class ddnm_work(C.Structure):
     _fields_ = [("eval_flops", C.c_double), ("eval_fp64_flops", C.c_double), ("eval_bytes", C.c_double),
-                ("constraint_fp64_flops", C.c_double), ("step_fp64_flops", C.c_double)]
+                ("constraint_fp64_flops", C.c_double), ("step_fp64_flops", C.c_double),
+                ("table_bytes", C.c_double), ("instance_bytes", C.c_double)]
 
 
 class ddnm_tune(C.Structure):

@@ -878,7 +878,7 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         if (rc) return rc;
     }
     const double nC = ctx->n_C, tsz = ctx->precision == DDNM_FP64 ? 8.0 : 4.0;
-    double f = 0, f64 = 0, bytes = 0, step = 0, fac = 0;
+    double f = 0, f64 = 0, bytes = 0, step = 0, fac = 0, table = 0, inst = 0;
     for (int s = 0; s < ctx->n_sub; ++s) {
         const SubDev& S = ctx->hsub[s];
         const double ni = S.ni, nO = S.nO, nG = S.nG;
@@ -901,16 +901,26 @@ extern "C" int ddnm_get_work(ddnm_ctx* ctx, ddnm_work* out) {
         // FP64 at an accepted point: L D L^T, t, W = L_GG^{-1} D^T, u (k_factor); lower triangle of
         // W^T D_G^{-1} W summed into S (k_ssum)
         fac += ni * ni * ni / 3.0 + ni * ni + nC * nG * nG + 3 * nC * nG + nC * (nC + 1) * nG + nC;
-        // bytes: subnet weights, tables and M_i once; per instance latents, multipliers, block outputs
-        bytes += tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] + 2.0 * (mO + S.NG) +
-                        (double)S.hG * nC) +
-                 4.0 * (mO * S.K + (double)S.NG * S.K + 7.0 * S.NB) +
-                 8.0 * (blk_layout(S.ni, S.nG, ctx->n_C).size) + tsz * S.NG;
+        // bytes shared by all instances (read once per launch at best): the subnet weights, the mask values
+        // and columns of the needed rows, scale/offset, Q_i, the collocation-row table
+        const double shared = tsz * (S.hO * (nO + 1) + S.hG * (nG + 1) + ctx->nnzO[s] + ctx->nnzG[s] +
+                                     2.0 * (mO + S.NG) + (double)S.hG * nC) +
+                              4.0 * (mO * S.K + (double)S.NG * S.K + 7.0 * S.NB);
+        // bytes of one instance: the block outputs H, rho, D (FP64), the interface values, the Dirichlet
+        // values its stencils read
+        const double own = 8.0 * (ni * ni + ni + nC * nG) + tsz * S.NG;
+        table += shared;
+        inst += own;
+        bytes += shared + own;
         // back-substitution per subdomain (in the next evaluation)
         step += 2.0 * nG * nC + ni * ni;
     }
-    bytes += 8.0 * (ctx->n_D + nC + 2);
+    const double lat = 8.0 * (ctx->n_D + nC + 2) + tsz * 2.0 * ctx->bnd_ij.size() / 2;   // latents, lambda, mu, Dirichlet
+    bytes += lat;
+    inst += lat;
     step += nC * nC * nC / 3.0 + 2.0 * nC * nC;
+    out->table_bytes = table;
+    out->instance_bytes = inst;
     out->eval_flops = f;
     out->eval_fp64_flops = f64;
     out->eval_bytes = bytes;

@@ -2288,7 +2288,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     const size_t o_dst = o; o = al(o + (size_t)B * INST_DBLS * 8);
     const size_t o_bnd = o; o = al(o + (size_t)B * std::max(P.n_bnd, 1) * 2 * 8);
     const size_t o_gG = o; o = al(o + (size_t)B * P.sum_NG * tsize);
-    const size_t o_PG = o; o = al(o + (size_t)B * P.pg_stride * tsize);
+    const size_t o_PG = o; o = al(o + (P.d_gemm ? (size_t)B * P.pg_stride * tsize : 0));
     const size_t o_blk = o; o = al(o + (size_t)B * P.blk_stride * 8);
     const size_t o_At = o; o = al(o + (size_t)B * P.n_split * P.n_C * 8);
     const size_t o_Ss = o; o = al(o + (size_t)B * ((size_t)P.n_C * P.n_C + P.n_C) * 8);
