@@ -268,7 +268,7 @@ int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, cons
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture.
- *  - B beyond what fits in 16 MiB (about 110 instances of the 128x128 4x4
+ *  - B beyond what fits in 16 MiB (about 210 instances of the 128x128 4x4
  *    workload) returns DDNM_E_UNSUPPORTED with the limit in the message.
  *  - All calls share the array and it keeps the last call's contents; calls
  *    that overlap on the GPU (two streams, or two threads) race on it and give
@@ -343,6 +343,9 @@ typedef struct ddnm_tune {
     int d_gemm;         /* D_i = C A_i dg_i^G: 1 in one GEMM launch per pass over all instances of a subdomain
                            (they share the decoder); 0 inside each evaluation CTA; -1 (default) picks 1 when
                            some subdomain has h^G n_C >= 65536 (hidden units of its interface decoder times n_C) */
+    int eval_groups;    /* 1 (default): one instance per evaluation CTA; 0: an evaluation CTA holds as many
+                           independent 256-thread groups as one-instance CTAs would fit an SM, on neighbouring
+                           instances of one subdomain (they share its tables through L1) */
 } ddnm_tune;
 
 /* Set / read the plan (ddnm_get_tune reports d_gemm as given, -1 included).  DDNM_E_INVALID outside the
@@ -358,7 +361,8 @@ int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t);
  *      chains       in {1, 2, 4, 8, 16}, capped at B;
  *      eval_persist in {0, 1, 2, 4};
  *      con_split    in {512, 1024, 2048};
- *      d_gemm       in {0, 1}.
+ *      d_gemm       in {0, 1};
+ *      eval_groups  in {0, 1}.
  *    Each knob is swept with the best values found so far for the others.
  *  - max_iter > 0 caps the SQP iterations of the timed solves, to keep tuning
  *    short (the options are restored on return).

@@ -75,7 +75,7 @@ class ddnm_work(C.Structure):
 
 class ddnm_tune(C.Structure):
     _fields_ = [("graph", C.c_int), ("chains", C.c_int), ("con_split", C.c_int), ("eval_persist", C.c_int),
-                ("d_gemm", C.c_int)]
+                ("d_gemm", C.c_int), ("eval_groups", C.c_int)]
 
 
 STATS_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("flags", np.int32),
@@ -330,8 +330,8 @@ def ddnm_get_work(ctx) -> dict:
     return {k: getattr(w, k) for k, _ in ddnm_work._fields_}
 
 
-def ddnm_set_tune(ctx, graph=1, chains=1, con_split=512, eval_persist=0, d_gemm=-1):
-    t = ddnm_tune(int(graph), int(chains), int(con_split), int(eval_persist), int(d_gemm))
+def ddnm_set_tune(ctx, graph=1, chains=1, con_split=512, eval_persist=0, d_gemm=-1, eval_groups=1):
+    t = ddnm_tune(int(graph), int(chains), int(con_split), int(eval_persist), int(d_gemm), int(eval_groups))
     _check(ctx, _lib.ddnm_set_tune(ctx, C.byref(t)))
 
 

@@ -50,7 +50,9 @@ struct WarmStart {
 struct EvalClass {
     int ro, rg;      // round4(n^O + 1), round4(n^G + 1)
     int off, n;      // range in the class index table
-    int smem;        // largest dynamic shared memory of its subdomains
+    int smem;        // largest dynamic shared memory of its subdomains (one instance)
+    int stride;      // smem rounded up to 128 bytes: one group's area in a grouped CTA
+    int groups;      // instances per CTA when grouped: the one-instance CTAs of this class that fit an SM
 };
 
 struct ddnm_ctx {
@@ -106,7 +108,7 @@ struct ddnm_ctx {
     size_t n_events = 0;               // pairs in use for the current call
 
     // launch plan and the captured solve graph (ddnm_kernels.cu)
-    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0, -1};
+    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0, -1, 1};
     int dgemm_auto = 0;                // the d_gemm = -1 choice for these sizes (set with the tables)
     long long gen = 0;                 // bumped whenever device tables or workspace pointers change
     cudaGraph_t graph = nullptr;

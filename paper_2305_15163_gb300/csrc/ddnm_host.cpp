@@ -689,7 +689,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     std::vector<int> cls;
     for (int ro = 4; ro <= 16; ro += 4)
         for (int rg = 4; rg <= 12; rg += 4) {
-            EvalClass c{ro, rg, (int)cls.size(), 0, 0};
+            EvalClass c{ro, rg, (int)cls.size(), 0, 0, 0, 1};
             for (int s = 0; s < ns; ++s) {
                 const SubDev& S = ctx->hsub[s];
                 if (round4(S.nO + 1) == ro && round4(S.nG + 1) == rg) {
@@ -705,6 +705,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                        (double)S.NB * S.ni * (S.ni + 6);
             };
             std::stable_sort(cls.begin() + c.off, cls.end(), [&](int a, int b) { return cost(a) > cost(b); });
+            c.stride = (c.smem + 127) & ~127;
+            c.groups = std::max(1, std::min({eval_min_ctas((int)tsize, ro, rg), sm_smem / (c.stride + 1024),
+                                             dev_max / std::max(c.stride, 1), 4}));
             if (c.n) ctx->eval_classes.push_back(c);
         }
     if ((int)cls.size() != ns) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "latent dims outside the kernel classes");

@@ -319,15 +319,21 @@ __device__ __forceinline__ float cst<float>(const ProbDev& P, int k) { return P.
 template <>
 __device__ __forceinline__ double cst<double>(const ProbDev& P, int k) { return P.cst[k]; }
 
+// Barrier of one EVAL_THREADS group of an evaluation CTA (named barrier `bar`; the groups of a CTA work on
+// different instances and never wait for each other).
+__device__ __forceinline__ void gsync(int bar) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(EVAL_THREADS) : "memory");
+}
+
 // Trial point of this subdomain for the coming evaluation (ist[I_XTMODE]).  On a new SQP step the
 // subdomain back-substitutes its own piece of the KKT solution of Eq. (sqp_system) from s_lambda, with the
 // L D L^T factors of the accepted evaluation: s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda]) when H_i is PD,
 // s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G) with s_G from the step kernel when H_i is singular in its G
 // block.  Then xt_i = x_i + alpha s_i (Eq. sqp_update); alpha = 1 on a new step.
-__device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z) {
+__device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, int tid, int bar) {
     const int xm = P.ist[(size_t)b * INST_INTS + I_XTMODE];
     if (xm == XT_KEEP) return;
-    const int tid = threadIdx.x, nC = P.n_C, ni = S.ni, nO = S.nO, nG = S.nG;
+    const int nC = P.n_C, ni = S.ni, nO = S.nO, nG = S.nG;
     const double* x = P.x + (size_t)b * P.n_D + S.xoff;
     double* xt = P.xt + (size_t)b * P.n_D + S.xoff;
     double* s = P.s + (size_t)b * P.n_D + S.xoff;
@@ -379,13 +385,13 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z) 
             __syncwarp();
             if (lane < nb) s[lane] = -z[lane];
         }
-        __syncthreads();
+        gsync(bar);
         if (tid < ni) xt[tid] = x[tid] + s[tid];
     } else {
         const double alpha = P.dst[(size_t)b * INST_DBLS + D_ALPHA];
         if (tid < ni) xt[tid] = x[tid] + alpha * s[tid];
     }
-    __syncthreads();
+    gsync(bar);
 }
 
 // One (instance, subdomain) evaluation.  RO = round4(n^O + 1) and RG = round4(n^G + 1) are the padded
@@ -394,7 +400,7 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z) 
 // bounded for any subdomain size; every decoder table is read slot-major (consecutive threads ->
 // consecutive addresses).
 template <typename T, int RO, int RG>
-__device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned char* smem) {
+__device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned char* smem, int tid, int bar) {
     const EvalSmem L = eval_smem(S, P.n_C, (int)sizeof(T));
     T* sx = (T*)(smem + L.sx);
     T* hidO = (T*)(smem + L.hidO);
@@ -410,16 +416,16 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
 
     const T* V = (const T*)P.vpool;
     const int* IP = P.ipool;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int nth = EVAL_THREADS;
     const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C, NG = S.NG;
     const int ld = ni + 1;
     constexpr int WO = RO - 1 > 0 ? ((RO - 1 + 3) & ~3) : 4;   // padded W1 row width of the interior subnet
     constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
     // latent coordinates and multipliers of the trial point
-    form_trial(P, S, b, dt);
+    form_trial(P, S, b, dt, tid, bar);
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
-    __syncthreads();
+    gsync(bar);
 
     // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]; the rows that pad each
     // record array to a multiple of 4 are zero (dense-window tiles may span them with zero values)
@@ -468,89 +474,125 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int k = 0; k < RG; k += 4) st4(hidG + (size_t)cc * RG + k, row + k);
         }
     }
-    __syncthreads();
+    gsync(bar);
 
     const int nwarp = nth >> 5;
     const int w = tid >> 5, lane = tid & 31;
 
-    // interface decoder: values of every output (the constraint residual needs them all: Sec. 5.3's
-    // remark, the WFPC constraint is not hyper-reduced), from the first element of the hidden records
-    {
-        T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
-        const int tG = S.ntilesG;
-        for (int t = w; t < tG; t += nwarp) {
-            const T v = tile_values<T, RG>(P.tiles[S.tileG0 + t], V, hidG, lane);
-            const int r = t * 32 + lane;
-            if (r < NG) gout[r] = V[S.soG + NG + r] + V[S.soG + r] * v;
-        }
-        if (!tG)
-            for (int r = tid; r < NG; r += nth) {
-                const T v = ell_values<T, RG>(IP + S.colG + r, V + S.valG + r, NG, S.Kp, hidG);
-                gout[r] = V[S.soG + NG + r] + V[S.soG + r] * v;
+    // The interface phase (values of every interface output, records of those the stencils use, D_i) and the
+    // interior outputs of a chunk, for threads t_ < n_ (warps w_ < nw_) of the group.
+    auto interface_phase = [&](int t_, int n_, int w_, int nw_) {
+        // interface decoder: values of every output (the constraint residual needs them all: Sec. 5.3's
+        // remark, the WFPC constraint is not hyper-reduced), from the first element of the hidden records
+        {
+            T* gout = (T*)P.gG + (size_t)b * P.sum_NG + S.goff;
+            const int tG = S.ntilesG;
+            for (int t = w_; t < tG; t += nw_) {
+                const T v = tile_values<T, RG>(P.tiles[S.tileG0 + t], V, hidG, lane);
+                const int r = t * 32 + lane;
+                if (r < NG) gout[r] = V[S.soG + NG + r] + V[S.soG + r] * v;
             }
-    }
-    // interface outputs the collocation stencils use: [y, Jacobian row] records
-    for (int r = tid; r < S.NGn; r += nth) {
-        T acc[RG];
-#pragma unroll
-        for (int k = 0; k < RG; ++k) acc[k] = T(0);
-        ell_accumulate<T, RG>(IP + S.colGn + r, V + S.valGn + r, S.NGn, S.Kp, hidG, acc);
-        const T sc = V[S.soGn + r], off = V[S.soGn + S.NGn + r];
-        acc[0] = off + sc * acc[0];
-#pragma unroll
-        for (int k = 1; k < RG; ++k) acc[k] *= sc;
-#pragma unroll
-        for (int k = 0; k < RG; k += 4) st4(outGn + (size_t)r * RG + k, acc + k);
-    }
-    // D_i = C A_i dg^G/dxh = Q_i P_G with Q_i = C A_i diag(scale) W2~ (n_C x h_G, precomputed, stored
-    // transposed) and P_G[h] = sigma'(z_h) W1~[h, :] (from the hidden records).  Either here, thread
-    // (group, c) summing the hidden units h = group, group + n_grp, ... for row c and the groups added in
-    // order afterwards, or batched over the instances that share the decoder (k_dgemm), for which P_G is
-    // written out.
-    if (P.d_gemm) {
-        T* pg = (T*)P.PG + (size_t)b * P.pg_stride + S.pgoff;
-        for (int e = tid; e < S.hG * nG; e += nth) {
-            const int h = e / nG, k = e - h * nG;
-            pg[e] = hidG[(size_t)h * RG + 1 + k];
-        }
-    } else {
-        const int ngrp = nth / nC;
-        const int c = tid % nC, grp = tid / nC;
-        if (grp < ngrp) {
-            T acc[RG - 1];
-#pragma unroll
-            for (int k = 0; k < RG - 1; ++k) acc[k] = T(0);
-            const T* Qt = V + S.Qt;
-            int h = grp;
-            for (; h + ngrp < S.hG; h += 2 * ngrp) {          // two loads in flight
-                T q[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) q[u] = Qt[(size_t)(h + u * ngrp) * nC + c];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const T* pr = hidG + (size_t)(h + u * ngrp) * RG + 1;
-#pragma unroll
-                    for (int k = 0; k < RG - 1; ++k) acc[k] += q[u] * pr[k];
+            if (!tG)
+                for (int r = t_; r < NG; r += n_) {
+                    const T v = ell_values<T, RG>(IP + S.colG + r, V + S.valG + r, NG, S.Kp, hidG);
+                    gout[r] = V[S.soG + NG + r] + V[S.soG + r] * v;
                 }
-            }
-            for (; h < S.hG; h += ngrp) {
-                const T q = Qt[(size_t)h * nC + c];
-                const T* pr = hidG + (size_t)h * RG + 1;
-#pragma unroll
-                for (int k = 0; k < RG - 1; ++k) acc[k] += q * pr[k];
-            }
-#pragma unroll
-            for (int k = 0; k < RG - 1; ++k)
-                if (k < nG) red[((size_t)grp * nC + c) * nG + k] = acc[k];
         }
-        __syncthreads();
-        for (int o = tid; o < nC * nG; o += nth) {
-            T a = T(0);
-            for (int g = 0; g < ngrp; ++g) a += red[(size_t)g * nC * nG + o];
-            dD[o] = (double)a;
+        // interface outputs the collocation stencils use: [y, Jacobian row] records
+        for (int r = t_; r < S.NGn; r += n_) {
+            T acc[RG];
+    #pragma unroll
+            for (int k = 0; k < RG; ++k) acc[k] = T(0);
+            ell_accumulate<T, RG>(IP + S.colGn + r, V + S.valGn + r, S.NGn, S.Kp, hidG, acc);
+            const T sc = V[S.soGn + r], off = V[S.soGn + S.NGn + r];
+            acc[0] = off + sc * acc[0];
+    #pragma unroll
+            for (int k = 1; k < RG; ++k) acc[k] *= sc;
+    #pragma unroll
+            for (int k = 0; k < RG; k += 4) st4(outGn + (size_t)r * RG + k, acc + k);
+        }
+        // D_i = C A_i dg^G/dxh = Q_i P_G with Q_i = C A_i diag(scale) W2~ (n_C x h_G, precomputed, stored
+        // transposed) and P_G[h] = sigma'(z_h) W1~[h, :] (from the hidden records).  Either here, thread
+        // (group, c) summing the hidden units h = group, group + n_grp, ... for row c and the groups added in
+        // order afterwards, or batched over the instances that share the decoder (k_dgemm), for which P_G is
+        // written out.
+        if (P.d_gemm) {
+            T* pg = (T*)P.PG + (size_t)b * P.pg_stride + S.pgoff;
+            for (int e = t_; e < S.hG * nG; e += n_) {
+                const int h = e / nG, k = e - h * nG;
+                pg[e] = hidG[(size_t)h * RG + 1 + k];
+            }
+        } else {
+            const int ngrp = n_ / nC;
+            const int c = t_ % nC, grp = t_ / nC;
+            if (grp < ngrp) {
+                T acc[RG - 1];
+    #pragma unroll
+                for (int k = 0; k < RG - 1; ++k) acc[k] = T(0);
+                const T* Qt = V + S.Qt;
+                int h = grp;
+                for (; h + ngrp < S.hG; h += 2 * ngrp) {          // two loads in flight
+                    T q[2];
+    #pragma unroll
+                    for (int u = 0; u < 2; ++u) q[u] = Qt[(size_t)(h + u * ngrp) * nC + c];
+    #pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const T* pr = hidG + (size_t)(h + u * ngrp) * RG + 1;
+    #pragma unroll
+                        for (int k = 0; k < RG - 1; ++k) acc[k] += q[u] * pr[k];
+                    }
+                }
+                for (; h < S.hG; h += ngrp) {
+                    const T q = Qt[(size_t)h * nC + c];
+                    const T* pr = hidG + (size_t)h * RG + 1;
+    #pragma unroll
+                    for (int k = 0; k < RG - 1; ++k) acc[k] += q * pr[k];
+                }
+    #pragma unroll
+                for (int k = 0; k < RG - 1; ++k)
+                    if (k < nG) red[((size_t)grp * nC + c) * nG + k] = acc[k];
+            }
+            gsync(bar);
+            for (int o = t_; o < nC * nG; o += n_) {
+                T a = T(0);
+                for (int g = 0; g < ngrp; ++g) a += red[(size_t)g * nC * nG + o];
+                dD[o] = (double)a;
+            }
+        }
+    };
+    auto interior_outputs = [&](const ChunkDev& Cq, int t_, int n_, int w_, int nw_) {
+    // interior decoder outputs of this chunk's collocation rows: dense-window tiles, warp per tile,
+    // where the host built them; the ELL table otherwise
+    {
+        const int tO = Cq.ntiles;
+        for (int t = w_; t < tO; t += nw_) {
+            T acc[RO];
+            tile_accumulate<T, RO>(P.tiles[Cq.tile0 + t], V, hidO, lane, acc);
+            const int r = t * 32 + lane;
+            if (r < Cq.m) {
+                const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
+                acc[0] = off + sc * acc[0];
+#pragma unroll
+                for (int k = 1; k < RO; ++k) acc[k] *= sc;
+#pragma unroll
+                for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
+            }
+        }
+        const int mO = tO ? 0 : Cq.m;                 // rows left to the ELL table
+        for (int r = t_; r < mO; r += n_) {
+            T acc[RO];
+#pragma unroll
+            for (int k = 0; k < RO; ++k) acc[k] = T(0);
+            ell_accumulate<T, RO>(IP + Cq.col + r, V + Cq.val + r, Cq.m, S.Kp, hidO, acc);
+            const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
+            acc[0] = off + sc * acc[0];
+#pragma unroll
+            for (int k = 1; k < RO; ++k) acc[k] *= sc;
+#pragma unroll
+            for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
         }
     }
-
+    };
     // H_i = R^T R and R^T r: thread p owns one entry (a <= c), running sum over the chunks
     const int npair = ni * (ni + 1) / 2;
     int pa = 0, pc = 0;
@@ -567,40 +609,11 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     }
     T hacc = T(0);
     const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
+    interface_phase(tid, nth, w, nwarp);
     for (int q = 0; q < S.n_chunks; ++q) {
         const ChunkDev Cq = P.chunk[S.chunk0 + q];
-        // interior decoder outputs of this chunk's collocation rows: dense-window tiles, warp per tile,
-        // where the host built them; the ELL table otherwise
-        {
-            const int tO = Cq.ntiles;
-            for (int t = w; t < tO; t += nwarp) {
-                T acc[RO];
-                tile_accumulate<T, RO>(P.tiles[Cq.tile0 + t], V, hidO, lane, acc);
-                const int r = t * 32 + lane;
-                if (r < Cq.m) {
-                    const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
-                    acc[0] = off + sc * acc[0];
-#pragma unroll
-                    for (int k = 1; k < RO; ++k) acc[k] *= sc;
-#pragma unroll
-                    for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
-                }
-            }
-            const int mO = tO ? 0 : Cq.m;                 // rows left to the ELL table
-            for (int r = tid; r < mO; r += nth) {
-                T acc[RO];
-#pragma unroll
-                for (int k = 0; k < RO; ++k) acc[k] = T(0);
-                ell_accumulate<T, RO>(IP + Cq.col + r, V + Cq.val + r, Cq.m, S.Kp, hidO, acc);
-                const T sc = V[Cq.so + r], off = V[Cq.so + Cq.m + r];
-                acc[0] = off + sc * acc[0];
-#pragma unroll
-                for (int k = 1; k < RO; ++k) acc[k] *= sc;
-#pragma unroll
-                for (int k = 0; k < RO; k += 4) st4(outO + (size_t)r * RO + k, acc + k);
-            }
-        }
-        __syncthreads();
+        interior_outputs(Cq, tid, nth, w, nwarp);
+        gsync(bar);
         // collocation rows of the chunk
         const T* bnd = (const T*)P.bnd + (size_t)b * P.n_bnd * 2;
         const T ax = cst<T>(P, 0), ay = cst<T>(P, 1), cx = cst<T>(P, 2), cy = cst<T>(P, 3);
@@ -657,7 +670,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             row[ni] = r;
             if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
         }
-        __syncthreads();
+        gsync(bar);
         if (tid < npair + ni) {
             T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
             int ql = 0;
@@ -670,7 +683,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (; ql < Cq.nq; ++ql) h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
             hacc += (h0 + h1) + (h2 + h3);
         }
-        if (q + 1 < S.n_chunks) __syncthreads();   // outO / Rr reused by the next chunk
+        if (q + 1 < S.n_chunks) gsync(bar);   // outO / Rr reused by the next chunk
     }
     if (tid < npair) {
         dH[pa * ni + pc] = (double)hacc;
@@ -678,7 +691,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     } else if (tid < npair + ni) {
         drho[pa] = (double)hacc;
     }
-    __syncthreads();
+    gsync(bar);
 
     // H_i and rho_i = R_i^T r + E_i^T lambda (E_i = [0, D_i]) with phi_i = ||rho_i||^2 (in FP64: warp k forms
     // entry n^O + k, lanes over the multipliers), or R_i^T r alone when k_dgemm forms D_i and the rest
@@ -693,7 +706,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             v = warp_sum(v);
             if (l2 == 0) drho[nO + k] += v;
         }
-        __syncthreads();
+        gsync(bar);
         if (tid < 32) {
             const double r = tid < ni ? drho[tid] : 0.0;
             const double ph = warp_sum(r * r);
@@ -707,37 +720,44 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
 
 // One launch per class of subdomains sharing the padded record widths (RO, RG).  Items are (instance,
 // subdomain of the class); item k is instance k % B of subdomain subs[k / B] (subs: the class's subdomains,
-// largest first).  With ctr == NULL CTA k takes item k; otherwise the grid is persistent and its CTAs claim
-// items from the counter *ctr (zero before the launch) until none are left.
+// largest first).  A CTA holds G = blockDim / EVAL_THREADS independent groups (each with its own named
+// barrier and shared-memory area of `stride` bytes) that take consecutive items, i.e. neighbouring
+// instances of one subdomain, whose decoder tables they then share through L1.  With ctr == NULL group g of
+// CTA c takes item c G + g; otherwise the grid is persistent and every group claims items from *ctr (zero
+// before the launch) until none are left.
 template <typename T, int RO, int RG>
-__global__ void __launch_bounds__(EVAL_THREADS, eval_min_ctas(sizeof(T), RO, RG)) k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr) {
+__global__ void __launch_bounds__(EVAL_THREADS * eval_min_ctas(sizeof(T), RO, RG), 1)
+    k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr, int stride) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const int G = blockDim.x / EVAL_THREADS, g = threadIdx.x / EVAL_THREADS;
+    const int tid = threadIdx.x - g * EVAL_THREADS, bar = g + 1;
+    unsigned char* gsm = smem + (size_t)g * stride;
     const int items = B * nsub;
     if (!ctr) {
-        const int k = blockIdx.x;
+        const int k = blockIdx.x * G + g;
         if (k >= items) return;
         const int b = k % B;
         if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
-        eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, smem);
+        eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, gsm, tid, bar);
         return;
     }
-    __shared__ int s_item;
+    __shared__ int s_item[4];
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
-        __syncthreads();
-        const int k = s_item;
-        __syncthreads();                  // every thread has its item before s_item is claimed again
+        if (tid == 0) s_item[g] = atomicAdd(ctr, 1);
+        gsync(bar);
+        const int k = s_item[g];
+        gsync(bar);                       // every thread has its item before s_item is claimed again
         if (k >= items) return;
         const int b = k % B;
         if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) continue;
-        eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, smem);
-        __syncthreads();                  // shared memory is reused by the next item
+        eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, gsm, tid, bar);
+        gsync(bar);                       // shared memory is reused by the next item
     }
 }
 
 // host side: the kernel of a width class
 template <typename T>
-using EvalKernel = void (*)(ProbDev, int, const int*, int, int*);
+using EvalKernel = void (*)(ProbDev, int, const int*, int, int*, int);
 
 template <typename T>
 EvalKernel<T> eval_kernel(int ro, int rg) {
@@ -1572,7 +1592,8 @@ int tflush(ddnm_ctx* ctx, cudaStream_t st) {
 template <typename T>
 int set_smem_attrs(ddnm_ctx* ctx) {
     for (const auto& g : ctx->eval_classes)
-        CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem));
+        CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                std::max(g.smem, g.groups * g.stride)));
     CK(cudaFuncSetAttribute(k_kkt, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->kkt_smem));
     {
         constexpr int CPT = sizeof(T) == 8 ? 16 : 32;
@@ -1610,14 +1631,16 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
     if (persist && zero_ctr) CK(cudaMemsetAsync(P.ctr, 0, MAX_CLASSES * sizeof(int), st));
     for (size_t ci = 0; ci < ctx->eval_classes.size(); ++ci) {
         const EvalClass& g = ctx->eval_classes[ci];
+        const int G = ctx->tune.eval_groups == 1 ? 1 : g.groups;
         const int items = B * g.n;
-        int grid = items;
+        int grid = (items + G - 1) / G;
         int* ctr = nullptr;
         if (persist) {
-            grid = std::min(items, ctx->n_sm * ctx->tune.eval_persist);
+            grid = std::min(grid, std::max(1, ctx->n_sm * ctx->tune.eval_persist / G));
             ctr = P.ctr + ci;
         }
-        eval_kernel<T>(g.ro, g.rg)<<<grid, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, ctr);
+        eval_kernel<T>(g.ro, g.rg)<<<grid, EVAL_THREADS * G, G == 1 ? g.smem : G * g.stride, st>>>(
+            P, B, ctx->d_classes + g.off, g.n, ctr, g.stride);
         CK(cudaGetLastError());
         ctx->tm.eval_launches++;
     }
@@ -1855,7 +1878,7 @@ int solve_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool ha
     const std::vector<long long> key{ctx->gen, B, Bw, ws, has_x0, has_lam0, (long long)sizeof(T), max_passes,
                                      bits(o.tol), bits(o.armijo_c1), bits(o.beta), o.max_iter, o.max_backtracks,
                                      ctx->tune.chains, ctx->tune.con_split, ctx->tune.eval_persist, ctx->n_sm,
-                                     P.d_gemm};
+                                     P.d_gemm, ctx->tune.eval_groups};
     if (!ctx->gexec || key != ctx->gkey) {
         const int rc = build_graph<T>(ctx, P, B, Bw, ws, has_x0, has_lam0, max_passes);
         if (rc) return rc;
@@ -2099,9 +2122,9 @@ extern "C" int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t) {
     const bool pow2 = t->con_split > 0 && (t->con_split & (t->con_split - 1)) == 0;
     if (t->graph < 0 || t->graph > 1 || t->chains < 1 || t->chains > MAX_CHAINS || !pow2 ||
         t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8 ||
-        t->d_gemm < -1 || t->d_gemm > 1)
-        return ddnm_fail(ctx, DDNM_E_INVALID,
-                         "tune: graph 0/1, chains 1..16, con_split 512, 1024 or 2048, eval_persist 0..8, d_gemm -1..1");
+        t->d_gemm < -1 || t->d_gemm > 1 || t->eval_groups < 0 || t->eval_groups > 1)
+        return ddnm_fail(ctx, DDNM_E_INVALID, "tune: graph 0/1, chains 1..16, con_split 512, 1024 or 2048, "
+                                              "eval_persist 0..8, d_gemm -1..1, eval_groups 0/1");
     ctx->tune = *t;
     return DDNM_OK;
 }
@@ -2177,6 +2200,7 @@ extern "C" int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kin
     if ((rc = sweep(&ddnm_tune::con_split, {512, 1024, 2048}))) return finish(rc);
     if (cur.d_gemm < 0) cur.d_gemm = ctx->dgemm_auto;
     if ((rc = sweep(&ddnm_tune::d_gemm, {0, 1}))) return finish(rc);
+    if ((rc = sweep(&ddnm_tune::eval_groups, {0, 1}))) return finish(rc);
     ctx->tune = cur;
     if (best) *best = cur;
     if (best_ms) *best_ms = cur_ms;
@@ -2257,7 +2281,8 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
     }
     k_noalloc_init<<<B, 128, 0, st>>>(P, B, (int)(sizeof(T) == 8));
     for (const auto& g : ctx->eval_classes)
-        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, nullptr);
+        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, nullptr,
+                                                                           g.stride);
     if (P.d_gemm) {
         e = launch_dgemm<T>(ctx, P, B, st);
         if (e != cudaSuccess) return cfail(ctx, e, "no-allocation D_i product launch");

@@ -18,12 +18,13 @@ if not torch.cuda.is_available():
 lib = pytest.importorskip("paper_2305_15163_gb300")
 
 FP64, MIXED = 0, 1
-HOST = dict(graph=0, chains=1, con_split=512, eval_persist=0)
+HOST = dict(graph=0, chains=1, con_split=512, eval_persist=0, eval_groups=1)
 PLANS = [dict(graph=1, chains=1, con_split=512, eval_persist=0),
-         dict(graph=1, chains=3, con_split=1024, eval_persist=2),
+         dict(graph=1, chains=3, con_split=1024, eval_persist=2, eval_groups=0),
          dict(graph=1, chains=16, con_split=2048, eval_persist=1),
-         dict(graph=1, chains=4, con_split=512, eval_persist=4),
-         dict(graph=0, chains=1, con_split=2048, eval_persist=3)]
+         dict(graph=1, chains=4, con_split=512, eval_persist=4, eval_groups=0),
+         dict(graph=0, chains=1, con_split=2048, eval_persist=3),
+         dict(graph=0, chains=1, con_split=512, eval_persist=0, eval_groups=0)]
 TOL = {FP64: 1e-6, MIXED: 1e-4}
 
 
@@ -139,7 +140,8 @@ def test_autotune_then_parity_with_oracle():
     mu = inputs.mu_batch(3)
     plan, ms = lib.ddnm_autotune(s.ctx, mu, max_iter=2, reps=2)
     assert plan["graph"] == 1 and 1 <= plan["chains"] <= 3 and plan["con_split"] in (512, 1024, 2048)
-    assert plan["eval_persist"] in (0, 1, 2, 4) and plan["d_gemm"] in (0, 1) and ms > 0
+    assert plan["eval_persist"] in (0, 1, 2, 4) and plan["d_gemm"] in (0, 1) and plan["eval_groups"] in (0, 1)
+    assert ms > 0
     assert lib.ddnm_get_tune(s.ctx) == plan
     s.options(tol=0.0, max_iter=3)
     x, lam, st = s.solve(mu)
