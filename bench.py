@@ -172,6 +172,30 @@ def oracle_sample(name: str, per_worker: int = 1, workers: int | None = None):
                        f"{wall:.1f} s wall with set-up")
 
 
+# ------------------------------------------------------------------------ replicas over ranks
+
+def shard(mu_all: np.ndarray, rank: int, world: int) -> np.ndarray:
+    """This rank's instances: the global batch cut into `world` equal consecutive pieces (replicas, weak
+    scaling: every rank solves its own piece, no collective on the data path)."""
+    B = len(mu_all) // world
+    return mu_all[rank * B:(rank + 1) * B]
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (the job's time), by an all-reduce MAX; the value itself on one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job units per second: the units all ranks processed over the slowest rank's time."""
+    return per_rank * world * steps / seconds
+
+
 # ------------------------------------------------------------------------ reference arm
 
 def run_reference(args):
@@ -347,8 +371,7 @@ def main():
     Cm = inputs.test_matrix(wl.n_c(), s.sizes.N_A)
     s.load(dec_o, dec_g, Cm)
     s.options()
-    mu_all = inputs.mu_batch(B * world)
-    mu = mu_all[rank * B:(rank + 1) * B]
+    mu = shard(inputs.mu_batch(B * world), rank, world)
     dev = torch.device("cuda", local)
     nD, nC = s.sizes.n_D, s.sizes.n_C
     mu_d = torch.from_numpy(mu).to(dev)
@@ -401,14 +424,10 @@ def main():
     launch_keys = ("eval_launches", "constraint_launches", "step_launches", "other_launches")
     gpu_launches = sum(tm1[k] - tm0[k] for k in launch_keys)
     t_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t_max = t_ms
-    if dist:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(t_ms, dist, dev)
     st = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=lib.STATS_DTYPE).copy()
     deterministic = bool(np.array_equal(st["n_evals"], st_warm["n_evals"]))
-    value = B * world * args.steps / (t_max / 1000.0)
+    value = job_throughput(B, world, args.steps, t_max / 1000.0)
 
     # roofline of the dominant kernel: per-kernel device time from the library's CUDA events, taken in a
     # separate run of the same solves through the host-driven loop (events around every launch)
@@ -474,12 +493,8 @@ def main():
     for _ in range(e2e_steps):
         lib.ddnm_solve_batch(s.ctx, B, mu_h.numpy(), None, None, x_h.numpy(), l_h.numpy(), None, st_h)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": B * world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(mu.nbytes),
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": job_throughput(B, world, e2e_steps, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(mu.nbytes),
            "d2h_bytes_per_step": int(x_h.numel() * 8 + l_h.numel() * 8 + st_h.nbytes)}
 
     cfg = workload_config(args.config)
