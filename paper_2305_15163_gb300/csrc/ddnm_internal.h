@@ -34,8 +34,9 @@ constexpr int ST_RUNNING = -1;
 enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_XTMODE, I_PAD, INST_INTS };
 constexpr int DG_THREADS = 256;    // k_dgemm
 constexpr int DG_KT = 32;          // interface hidden units per staged chunk of k_dgemm
-constexpr int KKT_THREADS = 512;   // k_kkt: one CTA per instance, a warp per subdomain factorisation
-constexpr int SS_ROWS_DBL = 4096;  // staged W rows (doubles) per Schur-sum chunk, each for W and D_G^{-1} W
+constexpr int KKT_THREADS = 512;   // k_kkt: one CTA per instance
+constexpr int KKT_SPW = 2;         // subdomains a warp factors at once (32 / KKT_SPW lanes each)
+constexpr int SS_ROWS_DBL = 3072;  // staged W rows (doubles) per Schur-sum chunk, each for W, D_G^{-1} W and u
 // how the next evaluation forms its trial point xt (ist[I_XTMODE]): unchanged (xt = x), a new SQP step
 // (each subdomain back-substitutes s_i from s_lambda, then xt = x + s), or a backtrack (xt = x + alpha s)
 enum { XT_KEEP = 0, XT_NEWSTEP = 1, XT_BACKTRACK = 2 };

@@ -66,14 +66,31 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ double tree_sum(const double* v, int n, size_t s) {
     double stk[33];
     int top = 0;
-    for (int i = 0; i < n; ++i) {
-        double x = v[(size_t)i * s];
-        for (int k = i; k & 1; k >>= 1) x = stk[--top] + x;
-        stk[top++] = x;
+    for (int i0 = 0; i0 < n; i0 += 8) {       // eight loads in flight, then merged in order
+        double x8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x8[u] = i0 + u < n ? v[(size_t)(i0 + u) * s] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u;
+            if (i >= n) break;
+            double x = x8[u];
+            for (int k = i; k & 1; k >>= 1) x = stk[--top] + x;
+            stk[top++] = x;
+        }
     }
     double acc = top ? stk[--top] : 0.0;
     while (top) acc = stk[--top] + acc;
     return acc;
+}
+
+// (row, column) of entry e of a lower triangle stored row by row: e = i (i + 1) / 2 + k, 0 <= k <= i
+__device__ __forceinline__ void tri_index(int e, int& i, int& k) {
+    int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > e) --r;
+    while ((r + 1) * (r + 2) / 2 <= e) ++r;
+    i = r;
+    k = e - r * (r + 1) / 2;
 }
 
 __device__ double block_sum(double v, double* scratch /* >= 32 */) {
@@ -108,22 +125,21 @@ __device__ bool block_ldl(double* A, double* rd, int n) {
         const double r = rd[j];
         const int m = n - j - 1;
         if (m > 0) {
-            if (tid == 0) {
-                const double l = A[(j + 1) * n + j];
-                const double a = A[(j + 1) * n + j + 1] - l * r * l;
-                A[(j + 1) * n + j + 1] = a;
-                const int ok = (a > 0.0) && isfinite(a);
-                s_ok = ok;
-                rd[j + 1] = ok ? 1.0 / a : 0.0;
-            } else {
+            if (tid < 32) {          // warp 0: the next pivot and its reciprocal (the critical path)
+                if (tid == 0) {
+                    const double l = A[(j + 1) * n + j];
+                    const double a = A[(j + 1) * n + j + 1] - l * r * l;
+                    A[(j + 1) * n + j + 1] = a;
+                    const int ok = (a > 0.0) && isfinite(a);
+                    s_ok = ok;
+                    rd[j + 1] = ok ? 1.0 / a : 0.0;
+                }
+            } else {                 // the other warps: the rest of the trailing triangle
                 const int ntri = m * (m + 1) / 2;
-                for (int e = tid; e < ntri; e += nth - 1) {
-                    int i = 0, rem = e;
-                    while (rem > i) {
-                        rem -= i + 1;
-                        ++i;
-                    }
-                    const int ii = j + 1 + i, kk = j + 1 + rem;
+                for (int e = tid - 32 + 1; e < ntri; e += nth - 32) {   // entry 0 is the pivot
+                    int i, k;
+                    tri_index(e, i, k);
+                    const int ii = j + 1 + i, kk = j + 1 + k;
                     A[ii * n + kk] -= A[ii * n + j] * r * A[kk * n + j];
                 }
             }
@@ -926,85 +942,114 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
 
 // ------------------------------------------------------------------------ SQP step
 
-// FP64 factorisation of the Gauss-Newton block of subdomain i of instance b at an accepted point, one
-// warp (scratch: fac_stride doubles): H_i = L D L^T (unit lower L, one reciprocal per pivot),
-// t = L^{-1} rho_i, W = L_GG^{-1} D_i^T (the Omega rows of L^{-1} E_i^T vanish), u_i = W^T D_G^{-1} t_G.
-// Lemma 1 only needs H_i PD on null(E_i): when the collocation rows miss an interface direction, H_i is
-// singular in its G block while H_i^{OO} is PD; the factorisation then stops after the O columns and the
-// subdomain is handled through G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).  Returns the
-// flag (FLAG_PD, FLAG_OMEGA_FAIL, FLAG_GAMMA_SING as 0, 1, 2), also stored in the block.
-__device__ int factor_sub(const ProbDev& P, const SubDev& S, double* blk, double* L, int lane) {
-    const int ni = S.ni, nO = S.nO, nG = S.nG, nC = P.n_C;
+// FP64 factorisation of the Gauss-Newton blocks of 32 / LG subdomains of one instance at an accepted point, one
+// warp, LG lanes for each (n_i <= 16): every FP64 instruction, the pivot reciprocals included, serves all of
+// them.  H_i = L D L^T (unit lower L, one reciprocal per pivot), t = L^{-1} rho_i, W = L_GG^{-1} D_i^T (the
+// Omega rows of L^{-1} E_i^T vanish), u_i = W^T D_G^{-1} t_G.  Lemma 1 only needs H_i PD on null(E_i): when the
+// collocation rows miss an interface direction, H_i is singular in its G block while H_i^{OO} is PD; the
+// factorisation of that subdomain then stops after the O columns and it is handled through
+// G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).  Subdomains i_first .. i_first + 32/LG - 1 below
+// ns; scratch (32 / LG) fs doubles; flags (FLAG_PD, FLAG_OMEGA_FAIL, FLAG_GAMMA_SING as 0, 1, 2) to fl[] and
+// the blocks.  A pivot is accepted when its bits are those of a positive finite double (integer tests).
+template <int LG>
+__device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, const unsigned char* s_nO,
+                             const unsigned char* s_nG, int i_first, int ns, double* scr, int fs, unsigned char* fl) {
+    const int lane = threadIdx.x & 31, half = lane / LG, hl = lane % LG, nC = P.n_C;
+    const int i = i_first + half < ns ? i_first + half : -1;
+    const bool on = i >= 0;
+    const int nO = on ? s_nO[i] : 0, nG = on ? s_nG[i] : 0, ni = nO + nG;
     const BlkLayout BL = blk_layout(ni, nG, nC);
+    double* bi = on ? blk + s_blk[i] : nullptr;
+    double* L = scr + (size_t)half * fs;
     double* t = L + ni * ni;
     double* rinv = t + ni;
     double* G = rinv + ni;
-    for (int e = lane; e < ni * ni; e += 32) L[e] = blk[BL.H + e];
-    if (lane < ni) t[lane] = blk[BL.rho + lane];
+    int nmax = 0;
+    for (int q = 0; q < 32 / LG && i_first + q < ns; ++q) nmax = max(nmax, (int)s_nO[i_first + q] + s_nG[i_first + q]);
+    if (on) {
+        for (int e = hl; e < ni * ni; e += LG) L[e] = bi[BL.H + e];
+        for (int e = hl; e < ni; e += LG) t[e] = bi[BL.rho + e];
+    }
     __syncwarp();
-    int flag = 0;
-    for (int j = 0; j < ni; ++j) {
-        if (j == nO) {
-            for (int e = lane; e < nG * nG; e += 32) G[e] = L[(nO + e / nG) * ni + nO + e % nG];
-            __syncwarp();
+    int flag = 0, nf = 0;                       // this half's subdomain: flag and factored columns
+    bool act = on;
+    for (int j = 0; j < nmax; ++j) {
+        if (act && j == nO)
+            for (int e = hl; e < nG * nG; e += LG) G[e] = L[(nO + e / nG) * ni + nO + e % nG];
+        __syncwarp();
+        double r = 0.0;
+        bool piv = false;
+        if (act && j < ni) {
+            const double d = L[j * ni + j];
+            const long long db = __double_as_longlong(d);
+            if (!(db > 0 && db < 0x7FF0000000000000LL)) {   // not positive and finite: the same for the lane group
+                flag = j < nO ? 1 : 2;
+                act = false;
+            } else {
+                r = 1.0 / d;
+                nf = j + 1;
+                piv = true;
+            }
         }
-        const double d = L[j * ni + j];
-        if (!(d > 0.0) || !isfinite(d)) {   // d is the same for every lane: a uniform branch
-            flag = j < nO ? 1 : 2;
-            break;
-        }
-        const double r = 1.0 / d;
         const int m = ni - j - 1;
-        for (int e = lane; e < m * (m + 1) / 2; e += 32) {     // trailing lower triangle, unscaled column j
-            int i = 0, rem = e;
-            while (rem > i) {
-                rem -= i + 1;
-                ++i;
+        if (piv && m > 0) {
+            for (int e = hl; e < m * (m + 1) / 2; e += LG) {     // trailing lower triangle, unscaled column j
+                int a, c;
+                tri_index(e, a, c);
+                const int ii = j + 1 + a, kk = j + 1 + c;
+                L[ii * ni + kk] -= L[ii * ni + j] * r * L[kk * ni + j];
             }
-            const int ii = j + 1 + i, kk = j + 1 + rem;
-            L[ii * ni + kk] -= L[ii * ni + j] * r * L[kk * ni + j];
         }
         __syncwarp();
-        for (int i = j + 1 + lane; i < ni; i += 32) L[i * ni + j] *= r;   // column j of L
-        if (lane == 0) rinv[j] = r;
+        if (piv) {
+            for (int ii = j + 1 + hl; ii < ni; ii += LG) L[ii * ni + j] *= r;   // column j of L
+            if (hl == 0) rinv[j] = r;
+        }
         __syncwarp();
     }
-    if (flag != 1) {
-        const int nf = flag == 0 ? ni : nO;       // unit forward substitution over the factored columns
-        for (int j = 0; j < nf; ++j) {
-            const double tj = t[j];
-            for (int i = j + 1 + lane; i < ni; i += 32) t[i] -= L[i * ni + j] * tj;
-            __syncwarp();
-        }
-        for (int e = lane; e < ni * ni; e += 32) blk[BL.L + e] = L[e];
-        if (lane < ni) {
-            blk[BL.t + lane] = t[lane];
-            blk[BL.rinv + lane] = rinv[lane];
-        }
+    // t = L^{-1} rho over the factored columns (n_f = n_i when PD, n^O when G-singular)
+    const int nft = flag == 0 ? ni : (flag == 2 ? nO : 0);
+    for (int j = 0; j < nmax; ++j) {
+        const double tj = j < nft ? t[j] : 0.0;
+        if (j < nft)
+            for (int ii = j + 1 + hl; ii < ni; ii += LG) t[ii] -= L[ii * ni + j] * tj;
+        __syncwarp();
     }
-    if (flag == 0) {
-        for (int c = lane; c < nC; c += 32) {
-            double wv[MAX_NG];
-            double uc = 0.0;
+    (void)nf;
+    if (on) {
+        if (flag != 1) {
+            for (int e = hl; e < ni * ni; e += LG) bi[BL.L + e] = L[e];
+            for (int e = hl; e < ni; e += LG) {
+                bi[BL.t + e] = t[e];
+                bi[BL.rinv + e] = rinv[e];
+            }
+        }
+        if (flag == 2)
+            for (int e = hl; e < nG * nG; e += LG) bi[BL.G + e] = G[e];
+        if (flag == 0) {
+            for (int c = hl; c < nC; c += LG) {
+                double wv[MAX_NG];
+                double uc = 0.0;
 #pragma unroll
-            for (int k = 0; k < MAX_NG; ++k) {
-                if (k < nG) {
-                    double v = blk[BL.D + c * nG + k];
+                for (int q = 0; q < MAX_NG; ++q) {
+                    if (q < nG) {
+                        double v = bi[BL.D + c * nG + q];
 #pragma unroll
-                    for (int m = 0; m < k; ++m) v -= L[(nO + k) * ni + nO + m] * wv[m];
-                    wv[k] = v;
-                    blk[BL.W + k * nC + c] = v;
-                    uc += v * rinv[nO + k] * t[nO + k];
+                        for (int mm = 0; mm < q; ++mm) v -= L[(nO + q) * ni + nO + mm] * wv[mm];
+                        wv[q] = v;
+                        bi[BL.W + q * nC + c] = v;
+                        uc += v * rinv[nO + q] * t[nO + q];
+                    }
                 }
+                bi[BL.u + c] = uc;
             }
-            blk[BL.u + c] = uc;
+        }
+        if (hl == 0) {
+            bi[BL.flag] = (double)flag;
+            fl[i] = (unsigned char)flag;
         }
     }
-    if (flag == 2)
-        for (int e = lane; e < nG * nG; e += 32) blk[BL.G + e] = G[e];
-    if (lane == 0) blk[BL.flag] = (double)flag;
     __syncwarp();
-    return flag;
 }
 
 // One SQP pass's work after the evaluation and the constraint residual, one CTA per instance:
@@ -1046,12 +1091,20 @@ __global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
     double* lamt = P.lamt + (size_t)b * nC;
     double* slam = P.slam + (size_t)b * nC;
 
+    // per-subdomain fields used below, in shared memory (one round of loads instead of a chain per use)
+    __shared__ int s_blk[MAX_SUB];
+    __shared__ unsigned char s_nO[MAX_SUB], s_nG[MAX_SUB];
+
     // ---- 1. merit, Armijo, update
     {
         double acc = 0.0;
         for (int i = tid; i < ns; i += nth) {
             const SubDev& S = P.sub[i];
-            acc += blk[S.blk + blk_layout(S.ni, S.nG, nC).phi];
+            const int bo = S.blk, nO = S.nO, nG = S.nG;
+            s_blk[i] = bo;
+            s_nO[i] = (unsigned char)nO;
+            s_nG[i] = (unsigned char)nG;
+            acc += blk[bo + blk_layout(nO + nG, nG, nC).phi];
         }
         for (int c = tid; c < nC; c += nth) {
             const double a = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
@@ -1143,12 +1196,11 @@ __global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
         }
     }
 
-    // ---- 2. factor the subdomain blocks, a warp per subdomain
-    for (int i = w; i < ns; i += nw) {
-        const SubDev& S = P.sub[i];
-        const int fl = factor_sub(P, S, blk + S.blk, work + (size_t)w * P.fac_stride, lane);
-        if (lane == 0) s_fl[i] = (unsigned char)fl;
-    }
+    // ---- 2. factor the subdomain blocks, a warp per group of KKT_SPW subdomains
+    __syncthreads();                                     // s_blk, s_nO, s_nG of every subdomain
+    for (int g = w; KKT_SPW * g < ns; g += nw)
+        factor_group<32 / KKT_SPW>(P, blk, s_blk, s_nO, s_nG, KKT_SPW * g, ns,
+                                   work + (size_t)w * KKT_SPW * P.fac_stride, P.fac_stride, s_fl);
     for (int e = tid; e < nC * nC; e += nth) Sm[e] = 0.0;
     for (int c = tid; c < nC; c += nth) us[c] = 0.0;
     __syncthreads();
@@ -1188,39 +1240,41 @@ __global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
         const int ntri = nC * (nC + 1) / 2, NE = ntri + nC;
         for (int ch = 0; ch < P.n_ss_chunks; ++ch) {
             const int i0 = P.ss_chunk[ch], i1 = P.ss_chunk[ch + 1];
-            int rows = 0;
-            for (int i = i0; i < i1; ++i) {
-                const SubDev& S = P.sub[i];
-                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-                const double* bi = blk + S.blk;
-                const bool pd = s_fl[i] == 0;
-                for (int e = tid; e < S.nG * nC; e += nth) {
-                    const int k = e / nC;
-                    const double wv = pd ? bi[BL.W + e] : 0.0;
-                    const double r = pd ? bi[BL.rinv + S.nO + k] : 0.0;
-                    Wsh[(size_t)rows * nC + e] = wv;
-                    Wr[(size_t)rows * nC + e] = wv * r;
+            // stage W_i, D_G^{-1} W_i and u_i of the chunk: thread e takes entry e of the chunk's rows
+            int tot = 0;
+            for (int i = i0; i < i1; ++i) tot += s_nG[i] * nC;
+            double* Us = Wr + (size_t)P.ss_rows * nC;          // (i1 - i0) x nC
+            for (int e = tid; e < tot + (i1 - i0) * nC; e += nth) {
+                if (e < tot) {
+                    int i = i0, off = e;
+                    while (off >= s_nG[i] * nC) off -= s_nG[i++] * nC;
+                    const int nG = s_nG[i], nO = s_nO[i];
+                    const BlkLayout BL = blk_layout(nO + nG, nG, nC);
+                    const double* bi = blk + s_blk[i];
+                    const bool pd = s_fl[i] == 0;
+                    const double wv = pd ? bi[BL.W + off] : 0.0;
+                    const double r = pd ? bi[BL.rinv + nO + off / nC] : 0.0;
+                    Wsh[e] = wv;
+                    Wr[e] = wv * r;
+                } else {
+                    const int f = e - tot, i = i0 + f / nC, c = f % nC;
+                    const int nG = s_nG[i];
+                    Us[f] = s_fl[i] == 0 ? blk[s_blk[i] + blk_layout(s_nO[i] + nG, nG, nC).u + c] : 0.0;
                 }
-                rows += S.nG;
             }
+            const int rows = tot / nC;
             __syncthreads();
             for (int e = tid; e < NE; e += nth) {
                 if (e < ntri) {
-                    int c1 = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-                    while (c1 * (c1 + 1) / 2 > e) --c1;
-                    while ((c1 + 1) * (c1 + 2) / 2 <= e) ++c1;
-                    const int c2 = e - c1 * (c1 + 1) / 2;
+                    int c1, c2;
+                    tri_index(e, c1, c2);
                     double v = Sm[c1 * nC + c2];
                     for (int r = 0; r < rows; ++r) v += Wr[r * nC + c1] * Wsh[r * nC + c2];
                     Sm[c1 * nC + c2] = v;
                 } else {
                     const int c = e - ntri;
                     double v = us[c];
-                    for (int i = i0; i < i1; ++i) {
-                        if (s_fl[i] != 0) continue;
-                        const SubDev& S = P.sub[i];
-                        v += blk[S.blk + blk_layout(S.ni, S.nG, nC).u + c];
-                    }
+                    for (int i = 0; i < i1 - i0; ++i) v += Us[i * nC + c];
                     us[c] = v;
                 }
             }
