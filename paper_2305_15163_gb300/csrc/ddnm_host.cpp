@@ -529,7 +529,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     ctx->hsub.assign(ns, SubDev{});
     ctx->hchunk.clear();
     ctx->htiles.clear();
-    int xoff = 0, hr_off = 0, blk = 0;
+    // an instance's block area: the n_sub merits ||rho_i||^2 (padded to an even count), then the blocks
+    int xoff = 0, hr_off = 0, blk = (ctx->n_sub + 1) & ~1;
     long long pg_stride = 0;
     ctx->max_nG = 1;
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
@@ -642,13 +643,14 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 for (int c = 0; c < nC; ++c) M[(size_t)li * nC + c] -= ctx->C[(size_t)c * ctx->N_A + r];
             }
         }
-        std::vector<double> Qt((size_t)S.hG * nC, 0.0);
+        const int qld = round4(nC);
+        std::vector<double> Qt((size_t)S.hG * qld, 0.0);
         for (int r = 0; r < S.NG; ++r)
             for (int t = 0; t < dG.K; ++t) {
                 const int col = dG.cols[(size_t)r * dG.K + t];
                 if (col < 0) continue;
                 const double coef = dG.scale[r] * dG.vals[(size_t)r * dG.K + t];
-                double* q = &Qt[(size_t)posG[col] * nC];
+                double* q = &Qt[(size_t)posG[col] * qld];
                 for (int c = 0; c < nC; ++c) q[c] += coef * M[(size_t)r * nC + c];
             }
         S.Qt = P.addv(Qt.data(), Qt.size());
@@ -677,6 +679,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         S.own = P.addi(own.data(), own.size());
         S.ids = P.addi(ids.data(), ids.size());
         S.blk = blk;
+        S.phio = s;
         blk += blk_layout(S.ni, S.nG, nC).size;
         for (int o = 0; o < HR_INTS; ++o)            // operand-major: consecutive rows are consecutive ints
             for (int q = 0; q < S.NB; ++q) hr_all.push_back(hr_ops[(size_t)q * HR_INTS + o]);
@@ -717,7 +720,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     if (ctx->rec_smem > dev_max) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "decoder too wide for reconstruction");
     int fac_stride = 0, sum_nG = 0;
     for (const SubDev& S : ctx->hsub) {
-        fac_stride = std::max(fac_stride, S.ni * S.ni + 2 * S.ni + S.nG * S.nG);
+        fac_stride = std::max(fac_stride, S.ni * S.ni + 3 * S.ni + S.nG * S.nG);
         sum_nG += S.nG;
     }
     fac_stride = (fac_stride + 1) & ~1;
@@ -801,6 +804,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.cst[3] = ctx->nu / (ctx->hy * ctx->hy);
     for (int k = 0; k < 4; ++k) pd.cstf[k] = (float)pd.cst[k];
     pd.blk_stride = blk;
+    pd.qld = round4(nC);
     {
         long long big = 0;
         for (const SubDev& S : ctx->hsub) big = std::max(big, (long long)S.hG * nC);

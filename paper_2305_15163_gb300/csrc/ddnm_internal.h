@@ -80,6 +80,7 @@ struct SubDev {
     int n_chunks, chunk0, mmax;    // HR chunks: count, first index in the chunk table, max outputs per chunk
     int smem_bytes;                // dynamic shared memory the evaluation of this subdomain needs
     int blk;                       // offset of this subdomain's block in an instance's block area
+    int phio;                      // offset of ||rho_i||^2 in an instance's block area (a header of n_sub doubles)
     long long w1O, b1O;            // interior subnet hidden layer: W1~ (hO x round4(nO)), b1~ (hO)
     long long w1G, b1G;            // interface subnet hidden layer: W1~ (hG x round4(nG)), b1~ (hG)
     long long colG, valG, soG;     // interface outputs, all rows: ELL slot-major (Kp x NG), scale/offset
@@ -98,7 +99,7 @@ struct SubDev {
 
 // per-subdomain block layout (doubles) inside an instance's block area
 struct BlkLayout {
-    int H, rho, D, L, rinv, t, W, u, G, phi, flag, size;
+    int H, rho, D, L, rinv, t, W, u, G, flag, size;
 };
 
 // per-subdomain flag values written by the factorisation
@@ -120,7 +121,6 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
     b.W = o; o += nG * nC;
     b.u = o; o += nC;
     b.G = o; o += nG * nG;         // Schur complement of H^{OO} in H_i (used when H_i is singular)
-    b.phi = o; o += 1;
     b.flag = o; o += 1;
     b.size = o;
     return b;
@@ -129,7 +129,7 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
 struct ProbDev {
     int n_sub, n_D, n_C, N_A, sum_NG, sum_NB, n_bnd, N_x;
     int nx, ny;
-    int fac_stride;                // factorisation scratch doubles per warp: max_i n_i^2 + 2 n_i + (n_i^G)^2
+    int fac_stride;                // factorisation scratch doubles per warp: max_i n_i^2 + 3 n_i + (n_i^G)^2
     int ss_rows;                   // rows of W staged per Schur-sum chunk
     int n_ss_chunks;               // Schur-sum chunks: subdomains [ss_chunk[k], ss_chunk[k + 1])
     const int* ss_chunk;
@@ -151,6 +151,7 @@ struct ProbDev {
     const int* con_lo;             // flat interface index (goff + local) of the +1 side of each constraint row
     const int* con_hi;             // ... of the -1 side
     const double* C;               // n_C x N_A
+    int qld;                       // row stride of every Q_i^T in the value pool: round4(n_C)
     const int* bnd_ij;             // n_bnd x 2 grid indices of the Dirichlet points the stencils touch
     // workspace (B instances)
     double* mu;

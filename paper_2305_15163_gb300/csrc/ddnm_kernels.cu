@@ -59,7 +59,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// sum over the CTA; every thread gets the result
 // v[0], v[s], ..., v[(n-1)s] summed as a pairwise tree over the values padded with zeros to a power of
 // two (adding the zero subtrees is exact, so a slice of the tree computed elsewhere can be passed in as
 // one value).  Streaming form: a stack of complete subtrees, merged like a binary counter.
@@ -93,15 +92,19 @@ __device__ __forceinline__ void tri_index(int e, int& i, int& k) {
     k = e - r * (r + 1) / 2;
 }
 
-__device__ double block_sum(double v, double* scratch /* >= 32 */) {
+// Barrier over the n threads (a multiple of 32) of a thread range; bar 0 with n = blockDim is __syncthreads.
+__device__ __forceinline__ void range_sync(int bar, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(n) : "memory");
+}
+
+// Sum over the threads t < n of a thread range (barrier bar); every thread of the range gets the result.
+__device__ double range_sum(double v, double* scratch /* >= 32 */, int t, int n, int bar) {
     v = warp_sum(v);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-    __syncthreads();
-    if (l == 0) scratch[w] = v;
-    __syncthreads();
-    double t = (l < nw) ? scratch[l] : 0.0;
-    t = warp_sum(t);
-    return t;
+    range_sync(bar, n);
+    if ((t & 31) == 0) scratch[t >> 5] = v;
+    range_sync(bar, n);
+    const double u = (t & 31) < (n >> 5) ? scratch[t & 31] : 0.0;
+    return warp_sum(u);
 }
 
 // In-place A = L D L^T of the n x n symmetric row-major matrix A in shared memory (whole CTA): the
@@ -528,10 +531,10 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int k = 0; k < RG; k += 4) st4(outGn + (size_t)r * RG + k, acc + k);
         }
         // D_i = C A_i dg^G/dxh = Q_i P_G with Q_i = C A_i diag(scale) W2~ (n_C x h_G, precomputed, stored
-        // transposed) and P_G[h] = sigma'(z_h) W1~[h, :] (from the hidden records).  Either here, thread
-        // (group, c) summing the hidden units h = group, group + n_grp, ... for row c and the groups added in
-        // order afterwards, or batched over the instances that share the decoder (k_dgemm), for which P_G is
-        // written out.
+        // transposed with rows of qld = round4(n_C) values) and P_G[h] = sigma'(z_h) W1~[h, :] (from the hidden
+        // records).  Either here, thread (group, c) summing the hidden units h = group, group + n_grp, ... for
+        // row c (eight Q loads in flight) and the groups added in order afterwards, or batched over the
+        // instances that share the decoder (k_dgemm), for which P_G is written out.
         if (P.d_gemm) {
             T* pg = (T*)P.PG + (size_t)b * P.pg_stride + S.pgoff;
             for (int e = t_; e < S.hG * nG; e += n_) {
@@ -546,20 +549,21 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     #pragma unroll
                 for (int k = 0; k < RG - 1; ++k) acc[k] = T(0);
                 const T* Qt = V + S.Qt;
+                constexpr int U = 8;                               // loads in flight
                 int h = grp;
-                for (; h + ngrp < S.hG; h += 2 * ngrp) {          // two loads in flight
-                    T q[2];
+                for (; h + (U - 1) * ngrp < S.hG; h += U * ngrp) {
+                    T q[U];
     #pragma unroll
-                    for (int u = 0; u < 2; ++u) q[u] = Qt[(size_t)(h + u * ngrp) * nC + c];
+                    for (int u = 0; u < U; ++u) q[u] = Qt[(size_t)(h + u * ngrp) * P.qld + c];
     #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
+                    for (int u = 0; u < U; ++u) {
                         const T* pr = hidG + (size_t)(h + u * ngrp) * RG + 1;
     #pragma unroll
                         for (int k = 0; k < RG - 1; ++k) acc[k] += q[u] * pr[k];
                     }
                 }
                 for (; h < S.hG; h += ngrp) {
-                    const T q = Qt[(size_t)h * nC + c];
+                    const T q = Qt[(size_t)h * P.qld + c];
                     const T* pr = hidG + (size_t)h * RG + 1;
     #pragma unroll
                     for (int k = 0; k < RG - 1; ++k) acc[k] += q * pr[k];
@@ -726,7 +730,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         if (tid < 32) {
             const double r = tid < ni ? drho[tid] : 0.0;
             const double ph = warp_sum(r * r);
-            if (tid == 0) blk[BL.phi] = ph;
+            if (tid == 0) P.blk[(size_t)b * P.blk_stride + S.phio] = ph;
         }
         for (int e = tid; e < nC * nG; e += nth) blk[BL.D + e] = dD[e];
     }
@@ -834,7 +838,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_dgemm(ProbDev P, int B, int TB) 
         __syncthreads();
         for (int e = tid; e < DG_KT * ncp; e += DG_THREADS) {
             const int hh = e / ncp, cc = e - hh * ncp;
-            Qs[e] = (h0 + hh < hG && cc < nC) ? Qt[(size_t)(h0 + hh) * nC + cc] : T(0);
+            Qs[e] = (h0 + hh < hG && cc < nC) ? Qt[(size_t)(h0 + hh) * P.qld + cc] : T(0);
         }
         for (int e = tid; e < TB * DG_KT * nG; e += DG_THREADS) {
             const int bl = e / (DG_KT * nG), rem = e - bl * DG_KT * nG;
@@ -897,10 +901,10 @@ __global__ void __launch_bounds__(DG_THREADS) k_dgemm(ProbDev P, int B, int TB) 
     __syncthreads();
     for (int bl = tid; bl < TB; bl += DG_THREADS) {
         if (!run[bl]) continue;
-        double* blk = P.blk + (size_t)(b0 + bl) * P.blk_stride + S.blk;
+        double* blk = P.blk + (size_t)(b0 + bl) * P.blk_stride;
         double ph = 0.0;
-        for (int jj = 0; jj < ni; ++jj) ph += blk[BL.rho + jj] * blk[BL.rho + jj];
-        blk[BL.phi] = ph;
+        for (int jj = 0; jj < ni; ++jj) ph += blk[S.blk + BL.rho + jj] * blk[S.blk + BL.rho + jj];
+        blk[S.phio] = ph;
     }
 }
 
@@ -963,12 +967,21 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     double* L = scr + (size_t)half * fs;
     double* t = L + ni * ni;
     double* rinv = t + ni;
-    double* G = rinv + ni;
+    double* ucol = rinv + ni;                   // column j before its scaling
+    double* G = ucol + ni;
     int nmax = 0;
     for (int q = 0; q < 32 / LG && i_first + q < ns; ++q) nmax = max(nmax, (int)s_nO[i_first + q] + s_nG[i_first + q]);
+    double dpre[MAX_NG];                        // D_i[c = hl][:], loaded ahead of the pivots for the W rows below
+#pragma unroll
+    for (int q = 0; q < MAX_NG; ++q) dpre[q] = 0.0;
     if (on) {
         for (int e = hl; e < ni * ni; e += LG) L[e] = bi[BL.H + e];
         for (int e = hl; e < ni; e += LG) t[e] = bi[BL.rho + e];
+        if (hl < nC) {
+#pragma unroll
+            for (int q = 0; q < MAX_NG; ++q)
+                if (q < nG) dpre[q] = bi[BL.D + hl * nG + q];
+        }
     }
     __syncwarp();
     int flag = 0, nf = 0;                       // this half's subdomain: flag and factored columns
@@ -992,18 +1005,22 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
             }
         }
         const int m = ni - j - 1;
+        if (piv) {                                           // column j of L, keeping the unscaled one
+            for (int ii = j + 1 + hl; ii < ni; ii += LG) {
+                const double a = L[ii * ni + j];
+                ucol[ii] = a;
+                L[ii * ni + j] = a * r;
+            }
+            if (hl == 0) rinv[j] = r;
+        }
+        __syncwarp();
         if (piv && m > 0) {
-            for (int e = hl; e < m * (m + 1) / 2; e += LG) {     // trailing lower triangle, unscaled column j
+            for (int e = hl; e < m * (m + 1) / 2; e += LG) {     // trailing lower triangle: (a_ij / d_j) a_kj
                 int a, c;
                 tri_index(e, a, c);
                 const int ii = j + 1 + a, kk = j + 1 + c;
-                L[ii * ni + kk] -= L[ii * ni + j] * r * L[kk * ni + j];
+                L[ii * ni + kk] -= L[ii * ni + j] * ucol[kk];
             }
-        }
-        __syncwarp();
-        if (piv) {
-            for (int ii = j + 1 + hl; ii < ni; ii += LG) L[ii * ni + j] *= r;   // column j of L
-            if (hl == 0) rinv[j] = r;
         }
         __syncwarp();
     }
@@ -1033,7 +1050,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
 #pragma unroll
                 for (int q = 0; q < MAX_NG; ++q) {
                     if (q < nG) {
-                        double v = bi[BL.D + c * nG + q];
+                        double v = c == hl ? dpre[q] : bi[BL.D + c * nG + q];
 #pragma unroll
                         for (int mm = 0; mm < q; ++mm) v -= L[(nO + q) * ni + nO + mm] * wv[mm];
                         wv[q] = v;
@@ -1052,12 +1069,87 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     __syncwarp();
 }
 
+enum { DEC_STEP = 0, DEC_DONE = 1, DEC_INIT0 = 2 };
+
+// Step 1 of k_kkt for one instance, by the threads t < n of a thread range (barrier bar): merit
+// phi = ||F||_2 with F = [rho_1 .. rho_n; Atil] (Sec. 4.1) from the merits ||rho_i||^2 (the header of the block
+// area, subdomain i's at index i) and the constraint partials (Atil to At), Armijo backtracking test, update and
+// stopping rule (Eq. sqp_update, Sec. 7.1).  Returns, the same to every thread of the range, DEC_DONE (a
+// rejected trial, whose backtrack is set up here, or a stop), DEC_INIT0 (the start-up pass: the least-squares
+// multiplier follows) or DEC_STEP (an accepted point that does not stop).  The accepted point's lambda <- lamt
+// is copied here, and x <- xt too when copy_x is set or the instance stops.
+__device__ int kkt_decide(const ProbDev& P, int b, const double* blk, double* At, double* scratch, int t, int n,
+                          int bar, bool copy_x) {
+    int* ist = P.ist + (size_t)b * INST_INTS;
+    double* dst = P.dst + (size_t)b * INST_DBLS;
+    const int nC = P.n_C, ns = P.n_sub, nD = P.n_D;
+    // one round of independent loads: the instance state, the merits and the constraint partial sums
+    const int mode = ist[I_MODE];
+    const int iters0 = ist[I_ITERS], nbt = ist[I_NBT];
+    const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
+    double acc = 0.0;
+    for (int i = t; i < ns; i += n) acc += blk[i];
+    for (int c = t; c < nC; c += n) {
+        const double a = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
+        At[c] = a;
+        acc += a * a;
+    }
+    const double phi2 = range_sum(acc, scratch, t, n, bar);   // barriers inside: the range has read ist and dst
+    const double phi = sqrt(phi2);
+    if (mode == MODE_INIT0) {
+        if (t == 0) ist[I_NEVALS] += 1;
+        return DEC_INIT0;
+    }
+    bool accept = true, lsfail = false;
+    if (mode == MODE_LS && !(phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0)) {
+        if (nbt < P.max_bt) accept = false;
+        else lsfail = true;
+    }
+    double* lam = P.lam + (size_t)b * nC;
+    double* lamt = P.lamt + (size_t)b * nC;
+    if (!accept) {
+        const double a = alpha * P.beta;
+        const double* slam = P.slam + (size_t)b * nC;
+        for (int c = t; c < nC; c += n) lamt[c] = lam[c] + a * slam[c];
+        if (t == 0) {
+            ist[I_NEVALS] += 1;
+            dst[D_ALPHA] = a;
+            ist[I_NBT] = nbt + 1;
+            ist[I_XTMODE] = XT_BACKTRACK;
+            atomicAdd(P.active, 1);
+        }
+        return DEC_DONE;
+    }
+    for (int c = t; c < nC; c += n) lam[c] = lamt[c];
+    const int iters = iters0 + (mode == MODE_LS ? 1 : 0);
+    int status = ST_RUNNING;
+    if (!isfinite(phi)) status = DDNM_NONFINITE;
+    else if (phi < P.tol) status = DDNM_CONVERGED;
+    else if (iters >= P.max_iter) status = DDNM_MAX_ITER;
+    if (copy_x || status != ST_RUNNING) {
+        double* x = P.x + (size_t)b * nD;
+        const double* xt = P.xt + (size_t)b * nD;
+        for (int k = t; k < nD; k += n) x[k] = xt[k];
+    }
+    if (t == 0) {
+        ist[I_NEVALS] += 1;
+        ist[I_ITERS] = iters;
+        dst[D_PHI0] = phi;
+        dst[D_PHI] = phi;
+        if (mode == MODE_LS) dst[D_ALPHA_LAST] = alpha;
+        if (lsfail) ist[I_FLAGS] |= DDNM_FLAG_LS_FAIL;
+        if (status != ST_RUNNING) ist[I_STATUS] = status;
+    }
+    return status == ST_RUNNING ? DEC_STEP : DEC_DONE;
+}
+
 // One SQP pass's work after the evaluation and the constraint residual, one CTA per instance:
 //  1. judge the evaluation: merit phi = ||F||_2 with F = [rho_1 .. rho_n; Atil] (Sec. 4.1), Armijo
 //     backtracking test, update and stopping rule (Eq. sqp_update, Sec. 7.1).  A rejected trial becomes
 //     the next backtrack (the evaluation forms xt = x + alpha beta s); the start-up pass solves for the
 //     least-squares multiplier (Sec. 7.2);
-//  2. at an accepted point that does not stop: factor every subdomain's block (a warp per subdomain);
+//  2. factor every subdomain's block (a warp per KKT_SPW subdomains): at an accepted point that does not
+//     stop, or side by side with step 1 when some warps have no subdomains;
 //  3. the border of the Schur complement of Eq. (sqp_system) over the subdomains with H_i PD,
 //       S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G,i^{-1} W_i,   r = Atil - sum_i u_i,
 //     each entry summed over the subdomains in index order (rows k ascending inside one), W_i and
@@ -1094,113 +1186,90 @@ __global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
     // per-subdomain fields used below, in shared memory (one round of loads instead of a chain per use)
     __shared__ int s_blk[MAX_SUB];
     __shared__ unsigned char s_nO[MAX_SUB], s_nG[MAX_SUB];
+    __shared__ int s_dec;
 
-    // ---- 1. merit, Armijo, update
-    {
-        double acc = 0.0;
+    // ---- 1 and 2: judge the trial point; factor the subdomain blocks, a warp per group of KKT_SPW subdomains.
+    // When some warps have no group, the two run side by side: the factor warps start at once and the others
+    // judge (at a rejected trial or a stop the factors are simply not used: a backtrack forms its trial point
+    // from s alone, and the next accepted point is factored afresh).  Otherwise every warp judges first.
+    double* x_ = P.x + (size_t)b * nD;
+    const double* xt = P.xt + (size_t)b * nD;
+    const int nfw = min(nw, (ns + KKT_SPW - 1) / KKT_SPW);   // warps with a group of subdomains
+    const bool side = nfw < nw;
+    if (side) {
+        if (w < nfw) {
+            for (int g = w; KKT_SPW * g < ns; g += nfw) {
+                const int i = KKT_SPW * g + lane;
+                if (lane < KKT_SPW && i < ns) {
+                    const SubDev& S = P.sub[i];
+                    s_blk[i] = S.blk;
+                    s_nO[i] = (unsigned char)S.nO;
+                    s_nG[i] = (unsigned char)S.nG;
+                }
+                __syncwarp();
+                factor_group<32 / KKT_SPW>(P, blk, s_blk, s_nO, s_nG, KKT_SPW * g, ns,
+                                           work + (size_t)w * KKT_SPW * P.fac_stride, P.fac_stride, s_fl);
+            }
+        } else {
+            const int dec = kkt_decide(P, b, blk, At, scratch, tid - 32 * nfw, nth - 32 * nfw, 1, true);
+            if (tid == 32 * nfw) s_dec = dec;
+        }
+    } else {
         for (int i = tid; i < ns; i += nth) {
             const SubDev& S = P.sub[i];
-            const int bo = S.blk, nO = S.nO, nG = S.nG;
-            s_blk[i] = bo;
-            s_nO[i] = (unsigned char)nO;
-            s_nG[i] = (unsigned char)nG;
-            acc += blk[bo + blk_layout(nO + nG, nG, nC).phi];
+            s_blk[i] = S.blk;
+            s_nO[i] = (unsigned char)S.nO;
+            s_nG[i] = (unsigned char)S.nG;
+        }
+        const int dec = kkt_decide(P, b, blk, At, scratch, tid, nth, 0, false);
+        if (tid == 0) s_dec = dec;
+    }
+    __syncthreads();
+    const int dec = s_dec;
+    if (dec == DEC_DONE) return;
+    if (dec == DEC_INIT0) {
+        // least-squares multiplier (Sec. 7.2): min_l sum_i ||rho_i^G + D_i^T l||^2 at lambda = 0,
+        // normal equations (sum_i D_i D_i^T) l = -sum_i D_i rho_i^G
+        for (int e = tid; e < nC * nC; e += nth) {
+            const int c1 = e / nC, c2 = e % nC;
+            double v = 0.0;
+            for (int i = 0; i < ns; ++i) {
+                const SubDev& S = P.sub[i];
+                const double* D = blk + S.blk + blk_layout(S.ni, S.nG, nC).D;
+                for (int k = 0; k < S.nG; ++k) v += D[c1 * S.nG + k] * D[c2 * S.nG + k];
+            }
+            Sm[e] = v;
         }
         for (int c = tid; c < nC; c += nth) {
-            const double a = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
-            At[c] = a;
-            acc += a * a;
+            double v = 0.0;
+            for (int i = 0; i < ns; ++i) {
+                const SubDev& S = P.sub[i];
+                const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
+                const double* D = blk + S.blk + BL.D;
+                const double* rho = blk + S.blk + BL.rho;
+                for (int k = 0; k < S.nG; ++k) v -= D[c * S.nG + k] * rho[S.nO + k];
+            }
+            rhs[c] = v;
         }
-        const double phi2 = block_sum(acc, scratch);   // barriers inside: every thread has read ist
-        const double phi = sqrt(phi2);
-        const int mode = ist[I_MODE];
-        const int iters0 = ist[I_ITERS], nbt = ist[I_NBT];
-        const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
-        __syncthreads();
-        if (mode == MODE_INIT0) {
-            if (tid == 0) ist[I_NEVALS] += 1;
-        } else {
-            bool accept = true, lsfail = false;
-            if (mode == MODE_LS && !(phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0)) {
-                if (nbt < P.max_bt) accept = false;
-                else lsfail = true;
-            }
-            if (!accept) {
-                const double a = alpha * P.beta;
-                for (int c = tid; c < nC; c += nth) lamt[c] = lam[c] + a * slam[c];
-                if (tid == 0) {
-                    ist[I_NEVALS] += 1;
-                    dst[D_ALPHA] = a;
-                    ist[I_NBT] = nbt + 1;
-                    ist[I_XTMODE] = XT_BACKTRACK;
-                    atomicAdd(P.active, 1);
-                }
-                return;
-            }
-            double* x_ = P.x + (size_t)b * nD;
-            const double* xt = P.xt + (size_t)b * nD;
-            for (int k = tid; k < nD; k += nth) x_[k] = xt[k];
-            for (int c = tid; c < nC; c += nth) lam[c] = lamt[c];
-            const int iters = iters0 + (mode == MODE_LS ? 1 : 0);
-            int status = ST_RUNNING;
-            if (!isfinite(phi)) status = DDNM_NONFINITE;
-            else if (phi < P.tol) status = DDNM_CONVERGED;
-            else if (iters >= P.max_iter) status = DDNM_MAX_ITER;
-            if (tid == 0) {
-                ist[I_NEVALS] += 1;
-                ist[I_ITERS] = iters;
-                dst[D_PHI0] = phi;
-                dst[D_PHI] = phi;
-                if (mode == MODE_LS) dst[D_ALPHA_LAST] = alpha;
-                if (lsfail) ist[I_FLAGS] |= DDNM_FLAG_LS_FAIL;
-                if (status != ST_RUNNING) ist[I_STATUS] = status;
-            }
-            if (status != ST_RUNNING) return;
-        }
-        if (mode == MODE_INIT0) {
-            // least-squares multiplier (Sec. 7.2): min_l sum_i ||rho_i^G + D_i^T l||^2 at lambda = 0,
-            // normal equations (sum_i D_i D_i^T) l = -sum_i D_i rho_i^G
-            for (int e = tid; e < nC * nC; e += nth) {
-                const int c1 = e / nC, c2 = e % nC;
-                double v = 0.0;
-                for (int i = 0; i < ns; ++i) {
-                    const SubDev& S = P.sub[i];
-                    const double* D = blk + S.blk + blk_layout(S.ni, S.nG, nC).D;
-                    for (int k = 0; k < S.nG; ++k) v += D[c1 * S.nG + k] * D[c2 * S.nG + k];
-                }
-                Sm[e] = v;
-            }
-            for (int c = tid; c < nC; c += nth) {
-                double v = 0.0;
-                for (int i = 0; i < ns; ++i) {
-                    const SubDev& S = P.sub[i];
-                    const BlkLayout BL = blk_layout(S.ni, S.nG, nC);
-                    const double* D = blk + S.blk + BL.D;
-                    const double* rho = blk + S.blk + BL.rho;
-                    for (int k = 0; k < S.nG; ++k) v -= D[c * S.nG + k] * rho[S.nO + k];
-                }
-                rhs[c] = v;
-            }
-            if (!block_ldl(Sm, rv, nC)) {
-                if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
-                return;
-            }
-            block_ldl_solve(Sm, rv, nC, rhs);
-            for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
-            if (tid == 0) {
-                ist[I_MODE] = MODE_INIT1;
-                ist[I_XTMODE] = XT_KEEP;
-                atomicAdd(P.active, 1);
-            }
+        if (!block_ldl(Sm, rv, nC)) {
+            if (tid == 0) ist[I_STATUS] = DDNM_KKT_FAIL;
             return;
         }
+        block_ldl_solve(Sm, rv, nC, rhs);
+        for (int c = tid; c < nC; c += nth) lamt[c] = rhs[c];
+        if (tid == 0) {
+            ist[I_MODE] = MODE_INIT1;
+            ist[I_XTMODE] = XT_KEEP;
+            atomicAdd(P.active, 1);
+        }
+        return;
     }
-
-    // ---- 2. factor the subdomain blocks, a warp per group of KKT_SPW subdomains
-    __syncthreads();                                     // s_blk, s_nO, s_nG of every subdomain
-    for (int g = w; KKT_SPW * g < ns; g += nw)
-        factor_group<32 / KKT_SPW>(P, blk, s_blk, s_nO, s_nG, KKT_SPW * g, ns,
-                                   work + (size_t)w * KKT_SPW * P.fac_stride, P.fac_stride, s_fl);
+    if (!side) {
+        for (int g = w; KKT_SPW * g < ns; g += nw)
+            factor_group<32 / KKT_SPW>(P, blk, s_blk, s_nO, s_nG, KKT_SPW * g, ns,
+                                       work + (size_t)w * KKT_SPW * P.fac_stride, P.fac_stride, s_fl);
+        for (int k = tid; k < nD; k += nth) x_[k] = xt[k];   // the accepted point
+    }
     for (int e = tid; e < nC * nC; e += nth) Sm[e] = 0.0;
     for (int c = tid; c < nC; c += nth) us[c] = 0.0;
     __syncthreads();
