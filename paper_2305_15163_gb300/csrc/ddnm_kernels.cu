@@ -124,10 +124,17 @@ __device__ bool block_ldl(double* A, double* rd, int n) {
     }
     __syncthreads();
     if (!s_ok) return false;
+    // Warps w with w % 4 == 0 share warp 0's scheduler (and FP64 unit) under the usual warp-to-scheduler
+    // assignment; while the trailing triangle fits the other warps in one pass they leave it to them, so that
+    // warp 0's pivot chain has its FP64 unit alone.  The column scaling is warp 1's.
+    const int w = tid >> 5, nw = nth >> 5;
+    const int nwo = nw - (nw + 3) / 4;                       // warps off warp 0's scheduler
+    const int wo = w - w / 4 - 1;                            // index among them (w % 4 != 0)
     for (int j = 0; j < n; ++j) {
         const double r = rd[j];
         const int m = n - j - 1;
         if (m > 0) {
+            const int ntri = m * (m + 1) / 2;
             if (tid < 32) {          // warp 0: the next pivot and its reciprocal (the critical path)
                 if (tid == 0) {
                     const double l = A[(j + 1) * n + j];
@@ -137,9 +144,18 @@ __device__ bool block_ldl(double* A, double* rd, int n) {
                     s_ok = ok;
                     rd[j + 1] = ok ? 1.0 / a : 0.0;
                 }
-            } else {                 // the other warps: the rest of the trailing triangle
-                const int ntri = m * (m + 1) / 2;
-                for (int e = tid - 32 + 1; e < ntri; e += nth - 32) {   // entry 0 is the pivot
+            } else if (ntri - 1 <= 32 * nwo) {               // one pass over the warps off warp 0's scheduler
+                if (w % 4 != 0) {
+                    const int e = 32 * wo + (tid & 31) + 1;     // entry 0 is the pivot
+                    if (e < ntri) {
+                        int i, k;
+                        tri_index(e, i, k);
+                        const int ii = j + 1 + i, kk = j + 1 + k;
+                        A[ii * n + kk] -= A[ii * n + j] * r * A[kk * n + j];
+                    }
+                }
+            } else {                 // all warps but warp 0
+                for (int e = tid - 32 + 1; e < ntri; e += nth - 32) {
                     int i, k;
                     tri_index(e, i, k);
                     const int ii = j + 1 + i, kk = j + 1 + k;
@@ -147,8 +163,8 @@ __device__ bool block_ldl(double* A, double* rd, int n) {
                 }
             }
         }
-        if (j > 0)
-            for (int i = j + tid; i < n; i += nth) A[i * n + j - 1] *= rd[j - 1];
+        if (j > 0 && w == 1)
+            for (int i = j + (tid & 31); i < n; i += 32) A[i * n + j - 1] *= rd[j - 1];
         __syncthreads();
         if (!s_ok) return false;
     }
@@ -159,21 +175,19 @@ __device__ bool block_ldl(double* A, double* rd, int n) {
 __device__ void block_ldl_solve(const double* A, const double* rd, int n, double* x) {
     const int tid = threadIdx.x, nth = blockDim.x;
     if (n <= 32) {
-        if (tid < 32) {
+        if (tid < 32) {              // lane i holds x_i; x_j of each step comes by a shuffle
             const int lane = tid;
+            double xv = lane < n ? x[lane] : 0.0;
             for (int j = 0; j < n; ++j) {
-                __syncwarp();
-                const double xj = x[j];
-                if (lane > j && lane < n) x[lane] -= A[lane * n + j] * xj;
+                const double xj = __shfl_sync(0xffffffffu, xv, j);
+                if (lane > j && lane < n) xv -= A[lane * n + j] * xj;
             }
-            __syncwarp();
-            if (lane < n) x[lane] *= rd[lane];
+            if (lane < n) xv *= rd[lane];
             for (int k = n - 1; k >= 0; --k) {
-                __syncwarp();
-                const double xk = x[k];
-                if (lane < k) x[lane] -= A[k * n + lane] * xk;
+                const double xk = __shfl_sync(0xffffffffu, xv, k);
+                if (lane < k) xv -= A[k * n + lane] * xk;
             }
-            __syncwarp();
+            if (lane < n) x[lane] = xv;
         }
         __syncthreads();
         return;
@@ -909,7 +923,8 @@ __global__ void __launch_bounds__(DG_THREADS) k_dgemm(ProbDev P, int B, int TB) 
 }
 
 // Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
-// Atil_c += sum_r C[c][r] jump_r, one warp per row c of C; partials per (instance, slice).
+// Atil_c += sum_r C[c][r] jump_r, one warp per row c of C; partials per (instance, slice).  The rows c of C
+// are split over gridDim.z CTAs (the same sums, more SMs, when the batch alone gives too few CTAs).
 template <typename T>
 __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
     extern __shared__ double jump[];      // con_split doubles
@@ -929,7 +944,9 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nb = P.con_split / CON_BLOCK;
     double* out = P.Atil + ((size_t)b * P.n_split + sp) * P.n_C;
-    for (int c = w; c < P.n_C; c += nw) {
+    const int rpg = (P.n_C + gridDim.z - 1) / gridDim.z;
+    const int c1 = min(P.n_C, ((int)blockIdx.z + 1) * rpg);
+    for (int c = (int)blockIdx.z * rpg + w; c < c1; c += nw) {
         const double* Cr = P.C + (size_t)c * P.N_A + r0;
         for (int k = 0; k < nb; ++k) {
             const int hi = min(nr, (k + 1) * CON_BLOCK);
@@ -942,6 +959,15 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
         if (lane == 0) out[c] = tree_sum(part[w], nb, 1);
         __syncwarp();
     }
+}
+
+// CTAs per (slice, instance) of k_constraint over the rows of C: about two CTAs per SM in all, at least one
+// row of C per warp
+int con_row_groups(const ddnm_ctx* ctx, const ProbDev& P, int B) {
+    const int base = std::max(1, B * P.n_split);
+    const int want = (2 * (ctx->n_sm > 0 ? ctx->n_sm : 148) + base - 1) / base;
+    const int most = (P.n_C + CON_THREADS / 32 - 1) / (CON_THREADS / 32);
+    return std::max(1, std::min(want, most));
 }
 
 // ------------------------------------------------------------------------ SQP step
@@ -1159,7 +1185,7 @@ __device__ int kkt_decide(const ProbDev& P, int b, const double* blk, double* At
 //     complements, (G_F + Z^T D_S^{-1} Z) s_F = -(rho_G - L_GO t_O)_F - Z^T D_S^{-1} q and
 //     s_lambda = L_S^{-T} D_S^{-1} (q + Z s_F).  Every other piece of s is back-substituted by the
 //     evaluation of its subdomain (form_trial).
-__global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
+__global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
     extern __shared__ __align__(16) double ksm[];
     __shared__ double scratch[32];
     __shared__ int s_mF, s_over, s_fail;
@@ -1273,27 +1299,33 @@ __global__ void __launch_bounds__(KKT_THREADS) k_kkt(ProbDev P, int B) {
     for (int e = tid; e < nC * nC; e += nth) Sm[e] = 0.0;
     for (int c = tid; c < nC; c += nth) us[c] = 0.0;
     __syncthreads();
-    if (tid == 0) {
-        int mF = 0, over = 0, fail = 0;
-        for (int i = 0; i < ns; ++i) {
-            const int fl = s_fl[i];
-            if (fl == 1) fail = 1;
-            if (fl == 2) {
-                const int nG = P.sub[i].nG;
-                if (mF + nG > MAX_MF) {
-                    over = 1;
-                    continue;
-                }
-                for (int k = 0; k < nG; ++k) {
-                    fcol_sub[mF] = i;
-                    fcol_k[mF] = k;
-                    ++mF;
+    if (w == 0) {                // flags: a vote first, the scan only when some block is not PD
+        int bad = 0;
+        for (int i = lane; i < ns; i += 32) bad |= s_fl[i];
+        if (!__any_sync(0xffffffffu, bad != 0)) {
+            if (lane == 0) s_mF = s_over = s_fail = 0;
+        } else if (lane == 0) {
+            int mF = 0, over = 0, fail = 0;
+            for (int i = 0; i < ns; ++i) {
+                const int fl = s_fl[i];
+                if (fl == 1) fail = 1;
+                if (fl == 2) {
+                    const int nG = P.sub[i].nG;
+                    if (mF + nG > MAX_MF) {
+                        over = 1;
+                        continue;
+                    }
+                    for (int k = 0; k < nG; ++k) {
+                        fcol_sub[mF] = i;
+                        fcol_k[mF] = k;
+                        ++mF;
+                    }
                 }
             }
+            s_mF = mF;
+            s_over = over;
+            s_fail = fail;
         }
-        s_mF = mF;
-        s_over = over;
-        s_fail = fail;
     }
     __syncthreads();
     const int mF = s_mF;
@@ -1773,7 +1805,8 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
     }
     tstop(ctx, k, st);
     k = tstart(ctx, 1, st);
-    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B);
+    k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B)), CON_THREADS, P.con_split * sizeof(double), st>>>(
+        P, B);
     CK(cudaGetLastError());
     tstop(ctx, k, st);
     ctx->tm.constraint_launches++;
@@ -2410,7 +2443,8 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
         e = launch_dgemm<T>(ctx, P, B, st);
         if (e != cudaSuccess) return cfail(ctx, e, "no-allocation D_i product launch");
     }
-    k_constraint<T><<<dim3(P.n_split, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B);
+    k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B)), CON_THREADS, P.con_split * sizeof(double), st>>>(
+        P, B);
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cfail(ctx, e, "no-allocation evaluation launch");
