@@ -151,9 +151,10 @@ typedef struct ddnm_stats {
  * stream around every launch of that kernel. */
 typedef struct ddnm_timing {
     double eval_ms;             /* k_eval: fused decoder / residual / Gauss-Newton blocks */
-    double constraint_ms;       /* k_constraint: FP64 weak-constraint residual */
-    double step_ms;             /* k_kkt: merit, Armijo, update; FP64 per-subdomain L D L^T, Schur sums and
-                                   border solve of the KKT system */
+    double constraint_ms;       /* k_constraint: FP64 weak-constraint residual (and, in a solve, the FP64
+                                   per-subdomain L D L^T of the Gauss-Newton blocks in CTAs of its own) */
+    double step_ms;             /* k_kkt: merit, Armijo, update; FP64 Schur sums and border solve of the
+                                   KKT system */
     long long eval_launches;
     long long constraint_launches;
     long long step_launches;

@@ -725,9 +725,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     }
     fac_stride = (fac_stride + 1) & ~1;
     ctx->ss_rows = std::min(sum_nG, std::max(MAX_NG, SS_ROWS_DBL / nC));   // staged rows of W per chunk
-    // k_kkt: S, rhs, Atil, pivots, sum u, then one area used in turn by the factorisation scratch of every
-    // warp, the staging of the Schur sums (W, D_G^{-1} W, u), and Z, T of the border solve
-    const size_t work = std::max({(size_t)(KKT_THREADS / 32) * KKT_SPW * fac_stride, (size_t)3 * ctx->ss_rows * nC,
+    // k_kkt: S, rhs, Atil, pivots, sum u, then one area used in turn by the staging of the Schur sums (W,
+    // D_G^{-1} W, u) and Z, T of the border solve (k_factor: fac_stride doubles per subdomain of a CTA)
+    const size_t work = std::max({(size_t)3 * ctx->ss_rows * nC,
                                   (size_t)nC * (MAX_MF + 1) + MAX_MF * MAX_MF + 2 * MAX_MF});
     ctx->kkt_smem = (int)(((size_t)nC * nC + 4 * nC + work) * 8);
     if (ctx->kkt_smem > dev_max)

@@ -8,6 +8,7 @@
 namespace ddnm {
 
 constexpr int MAX_NI = 16;     // n_i^O + n_i^G per subdomain
+constexpr int MAX_TRI = MAX_NI * (MAX_NI - 1) / 2;   // entries of the largest trailing triangle of an H_i
 constexpr int MAX_NG = 8;      // n_i^G
 constexpr int MAX_K = 64;      // ELL slots of a decoder output row
 constexpr int MAX_NC = 128;    // weak constraints
@@ -35,7 +36,8 @@ enum { I_STATUS = 0, I_MODE, I_ITERS, I_NBT, I_FLAGS, I_NEVALS, I_XTMODE, I_PAD,
 constexpr int DG_THREADS = 256;    // k_dgemm
 constexpr int DG_KT = 32;          // interface hidden units per staged chunk of k_dgemm
 constexpr int KKT_THREADS = 512;   // k_kkt: one CTA per instance
-constexpr int KKT_SPW = 2;         // subdomains a warp factors at once (32 / KKT_SPW lanes each)
+constexpr int FAC_WARPS = 4;       // factorisation CTAs of k_constraint: warps with a pair of subdomains each
+constexpr int KKT_DW = 4;          // k_kkt: warps that judge the trial point while the others form the Schur sums
 constexpr int SS_ROWS_DBL = 3072;  // staged W rows (doubles) per Schur-sum chunk, each for W, D_G^{-1} W and u
 // how the next evaluation forms its trial point xt (ist[I_XTMODE]): unchanged (xt = x), a new SQP step
 // (each subdomain back-substitutes s_i from s_lambda, then xt = x + s), or a backtrack (xt = x + alpha s)

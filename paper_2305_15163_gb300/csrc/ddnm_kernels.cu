@@ -922,15 +922,24 @@ __global__ void __launch_bounds__(DG_THREADS) k_dgemm(ProbDev P, int B, int TB) 
     }
 }
 
+__device__ void factor_cta(const ProbDev& P, int b, int f, double* scr);
+
 // Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
 // Atil_c += sum_r C[c][r] jump_r, one warp per row c of C; partials per (instance, slice).  The rows c of C
-// are split over gridDim.z CTAs (the same sums, more SMs, when the batch alone gives too few CTAs).
+// are split over gridDim.z - nfz CTAs (the same sums, more SMs, when the batch alone gives too few CTAs).
+// In the same launch, the last nfz z-indices factor the Gauss-Newton blocks of the evaluated point for the
+// step kernel (factor_cta), so that the two run side by side.
 template <typename T>
-__global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
-    extern __shared__ double jump[];      // con_split doubles
+__global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B, int nfz) {
+    extern __shared__ double jump[];      // con_split doubles (or the factorisation scratch)
     const int sp = blockIdx.x, b = blockIdx.y;
     if (b >= B) return;
     if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
+    const int nrg = (int)gridDim.z - nfz;
+    if ((int)blockIdx.z >= nrg) {
+        factor_cta(P, b, ((int)blockIdx.z - nrg) * (int)gridDim.x + sp, jump);
+        return;
+    }
     const int r0 = sp * P.con_split, nr = min(P.con_split, P.N_A - r0);
     const T* g = (const T*)P.gG + (size_t)b * P.sum_NG;
     for (int r = threadIdx.x; r < nr; r += blockDim.x)
@@ -944,7 +953,7 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nb = P.con_split / CON_BLOCK;
     double* out = P.Atil + ((size_t)b * P.n_split + sp) * P.n_C;
-    const int rpg = (P.n_C + gridDim.z - 1) / gridDim.z;
+    const int rpg = (P.n_C + nrg - 1) / nrg;
     const int c1 = min(P.n_C, ((int)blockIdx.z + 1) * rpg);
     for (int c = (int)blockIdx.z * rpg + w; c < c1; c += nw) {
         const double* Cr = P.C + (size_t)c * P.N_A + r0;
@@ -983,7 +992,8 @@ int con_row_groups(const ddnm_ctx* ctx, const ProbDev& P, int B) {
 // the blocks.  A pivot is accepted when its bits are those of a positive finite double (integer tests).
 template <int LG>
 __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, const unsigned char* s_nO,
-                             const unsigned char* s_nG, int i_first, int ns, double* scr, int fs, unsigned char* fl) {
+                             const unsigned char* s_nG, int i_first, int ns, double* scr, int fs, unsigned char* fl,
+                             const unsigned short* tri) {
     const int lane = threadIdx.x & 31, half = lane / LG, hl = lane % LG, nC = P.n_C;
     const int i = i_first + half < ns ? i_first + half : -1;
     const bool on = i >= 0;
@@ -997,17 +1007,19 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     double* G = ucol + ni;
     int nmax = 0;
     for (int q = 0; q < 32 / LG && i_first + q < ns; ++q) nmax = max(nmax, (int)s_nO[i_first + q] + s_nG[i_first + q]);
-    double dpre[MAX_NG];                        // D_i[c = hl][:], loaded ahead of the pivots for the W rows below
+    double dpre[2][MAX_NG];                     // D_i[c][:] for c = hl, hl + LG, loaded ahead of the pivots
 #pragma unroll
-    for (int q = 0; q < MAX_NG; ++q) dpre[q] = 0.0;
+    for (int q = 0; q < MAX_NG; ++q) dpre[0][q] = dpre[1][q] = 0.0;
     if (on) {
         for (int e = hl; e < ni * ni; e += LG) L[e] = bi[BL.H + e];
         for (int e = hl; e < ni; e += LG) t[e] = bi[BL.rho + e];
-        if (hl < nC) {
 #pragma unroll
-            for (int q = 0; q < MAX_NG; ++q)
-                if (q < nG) dpre[q] = bi[BL.D + hl * nG + q];
-        }
+        for (int u = 0; u < 2; ++u)
+            if (hl + u * LG < nC) {
+#pragma unroll
+                for (int q = 0; q < MAX_NG; ++q)
+                    if (q < nG) dpre[u][q] = bi[BL.D + (hl + u * LG) * nG + q];
+            }
     }
     __syncwarp();
     int flag = 0, nf = 0;                       // this half's subdomain: flag and factored columns
@@ -1042,8 +1054,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
         __syncwarp();
         if (piv && m > 0) {
             for (int e = hl; e < m * (m + 1) / 2; e += LG) {     // trailing lower triangle: (a_ij / d_j) a_kj
-                int a, c;
-                tri_index(e, a, c);
+                const int a = tri[e] >> 8, c = tri[e] & 255;
                 const int ii = j + 1 + a, kk = j + 1 + c;
                 L[ii * ni + kk] -= L[ii * ni + j] * ucol[kk];
             }
@@ -1076,7 +1087,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
 #pragma unroll
                 for (int q = 0; q < MAX_NG; ++q) {
                     if (q < nG) {
-                        double v = c == hl ? dpre[q] : bi[BL.D + c * nG + q];
+                        double v = c == hl ? dpre[0][q] : (c == hl + LG ? dpre[1][q] : bi[BL.D + c * nG + q]);
 #pragma unroll
                         for (int mm = 0; mm < q; ++mm) v -= L[(nO + q) * ni + nO + mm] * wv[mm];
                         wv[q] = v;
@@ -1095,6 +1106,96 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     __syncwarp();
 }
 
+// Factor CTA f of instance b (a role of k_constraint): the Gauss-Newton blocks of subdomains 8f .. 8f + 7 of
+// the evaluated point, FP64, one warp per pair (a half-warp each) on warps 0-3, i.e. one per scheduler and FP64
+// unit under the usual warp-to-scheduler assignment; the other warps idle.  The CTAs of an instance spread
+// over SMs, where the step kernel's one CTA would take the blocks on one SM's four FP64 units.  Every
+// evaluation is factored (the step kernel decides afterwards whether the point is accepted; a rejected
+// trial's factors are never read: a backtrack forms its trial point from s).  scr: 8 fac_stride doubles.
+__device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
+    constexpr int SPC = 2 * FAC_WARPS;                          // subdomains per CTA
+    __shared__ int s_blk[SPC];
+    __shared__ unsigned char s_nO[SPC], s_nG[SPC], s_fl[SPC];
+    __shared__ unsigned short tri[MAX_TRI];                     // (row << 8 | column) of triangle entry e
+    const int i0 = f * SPC, tid = threadIdx.x, w = tid >> 5;
+    if (i0 >= P.n_sub) return;
+    const int nrel = min(SPC, P.n_sub - i0);
+    for (int e = tid; e < MAX_TRI; e += blockDim.x) {
+        int a, c;
+        tri_index(e, a, c);
+        tri[e] = (unsigned short)(a << 8 | c);
+    }
+    if (tid < nrel) {
+        const SubDev& S = P.sub[i0 + tid];
+        s_blk[tid] = S.blk;
+        s_nO[tid] = (unsigned char)S.nO;
+        s_nG[tid] = (unsigned char)S.nG;
+    }
+    __syncthreads();
+    if (w < FAC_WARPS && 2 * w < nrel)
+        factor_group<16>(P, P.blk + (size_t)b * P.blk_stride, s_blk, s_nO, s_nG, 2 * w, nrel,
+                         scr + (size_t)w * 2 * P.fac_stride, P.fac_stride, s_fl, tri);
+}
+
+// Step 3 of k_kkt by the threads t < n of a thread range (barrier bar): the border of the Schur complement of
+// Eq. (sqp_system) over the subdomains with H_i PD (flag s_fl[i] == 0),
+//   S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G,i^{-1} W_i (lower triangle)   and   us = sum_i u_i,
+// each entry summed over the subdomains in index order (rows k ascending inside one), W_i, D_G^{-1} W_i and u_i
+// staged in shared memory a chunk of subdomains at a time (work: 2 ss_rows n_C + (chunk subdomains) n_C).
+__device__ __forceinline__ void kkt_schur_sums(const ProbDev& P, const double* blk, const int* s_blk,
+                                               const unsigned char* s_nO, const unsigned char* s_nG,
+                                               const unsigned char* s_fl, double* Sm, double* us, double* work,
+                                               int t, int n, int bar) {
+    const int nC = P.n_C;
+    for (int e = t; e < nC * nC; e += n) Sm[e] = 0.0;
+    for (int c = t; c < nC; c += n) us[c] = 0.0;
+    double* Wsh = work;                                  // ss_rows x nC
+    double* Wr = work + (size_t)P.ss_rows * nC;          // ss_rows x nC, row k scaled by 1 / D_kk
+    const int ntri = nC * (nC + 1) / 2, NE = ntri + nC;
+    for (int ch = 0; ch < P.n_ss_chunks; ++ch) {
+        const int i0 = P.ss_chunk[ch], i1 = P.ss_chunk[ch + 1];
+        // stage W_i, D_G^{-1} W_i and u_i of the chunk: thread e takes entry e of the chunk's rows
+        int tot = 0;
+        for (int i = i0; i < i1; ++i) tot += s_nG[i] * nC;
+        double* Us = Wr + (size_t)P.ss_rows * nC;          // (i1 - i0) x nC
+        for (int e = t; e < tot + (i1 - i0) * nC; e += n) {
+            if (e < tot) {
+                int i = i0, off = e;
+                while (off >= s_nG[i] * nC) off -= s_nG[i++] * nC;
+                const int nG = s_nG[i], nO = s_nO[i];
+                const BlkLayout BL = blk_layout(nO + nG, nG, nC);
+                const double* bi = blk + s_blk[i];
+                const bool pd = s_fl[i] == 0;
+                const double wv = pd ? bi[BL.W + off] : 0.0;
+                const double r = pd ? bi[BL.rinv + nO + off / nC] : 0.0;
+                Wsh[e] = wv;
+                Wr[e] = wv * r;
+            } else {
+                const int f = e - tot, i = i0 + f / nC, c = f % nC;
+                const int nG = s_nG[i];
+                Us[f] = s_fl[i] == 0 ? blk[s_blk[i] + blk_layout(s_nO[i] + nG, nG, nC).u + c] : 0.0;
+            }
+        }
+        const int rows = tot / nC;
+        range_sync(bar, n);
+        for (int e = t; e < NE; e += n) {
+            if (e < ntri) {
+                int c1, c2;
+                tri_index(e, c1, c2);
+                double v = Sm[c1 * nC + c2];
+                for (int r = 0; r < rows; ++r) v += Wr[r * nC + c1] * Wsh[r * nC + c2];
+                Sm[c1 * nC + c2] = v;
+            } else {
+                const int c = e - ntri;
+                double v = us[c];
+                for (int i = 0; i < i1 - i0; ++i) v += Us[i * nC + c];
+                us[c] = v;
+            }
+        }
+        range_sync(bar, n);
+    }
+}
+
 enum { DEC_STEP = 0, DEC_DONE = 1, DEC_INIT0 = 2 };
 
 // Step 1 of k_kkt for one instance, by the threads t < n of a thread range (barrier bar): merit
@@ -1104,7 +1205,7 @@ enum { DEC_STEP = 0, DEC_DONE = 1, DEC_INIT0 = 2 };
 // rejected trial, whose backtrack is set up here, or a stop), DEC_INIT0 (the start-up pass: the least-squares
 // multiplier follows) or DEC_STEP (an accepted point that does not stop).  The accepted point's lambda <- lamt
 // is copied here, and x <- xt too when copy_x is set or the instance stops.
-__device__ int kkt_decide(const ProbDev& P, int b, const double* blk, double* At, double* scratch, int t, int n,
+__device__ __forceinline__ int kkt_decide(const ProbDev& P, int b, const double* blk, double* At, double* scratch, int t, int n,
                           int bar, bool copy_x) {
     int* ist = P.ist + (size_t)b * INST_INTS;
     double* dst = P.dst + (size_t)b * INST_DBLS;
@@ -1169,17 +1270,14 @@ __device__ int kkt_decide(const ProbDev& P, int b, const double* blk, double* At
     return status == ST_RUNNING ? DEC_STEP : DEC_DONE;
 }
 
-// One SQP pass's work after the evaluation and the constraint residual, one CTA per instance:
+// One SQP pass's work after the evaluation, the constraint residual and the factorisation of the blocks
+// (both in k_constraint), one CTA per instance:
 //  1. judge the evaluation: merit phi = ||F||_2 with F = [rho_1 .. rho_n; Atil] (Sec. 4.1), Armijo
 //     backtracking test, update and stopping rule (Eq. sqp_update, Sec. 7.1).  A rejected trial becomes
 //     the next backtrack (the evaluation forms xt = x + alpha beta s); the start-up pass solves for the
 //     least-squares multiplier (Sec. 7.2);
-//  2. factor every subdomain's block (a warp per KKT_SPW subdomains): at an accepted point that does not
-//     stop, or side by side with step 1 when some warps have no subdomains;
-//  3. the border of the Schur complement of Eq. (sqp_system) over the subdomains with H_i PD,
-//       S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G,i^{-1} W_i,   r = Atil - sum_i u_i,
-//     each entry summed over the subdomains in index order (rows k ascending inside one), W_i and
-//     D_G^{-1} W_i staged in shared memory a chunk of subdomains at a time;
+//  3. (beside step 1) the border of the Schur complement of Eq. (sqp_system) over the subdomains with H_i PD,
+//       S = sum_i E_i H_i^{-1} E_i^T = sum_i W_i^T D_G,i^{-1} W_i,   r = Atil - sum_i u_i;
 //  4. S = L_S D_S L_S^T and s_lambda; the subdomains F whose H_i is singular in the G block keep their
 //     interface steps s_F as unknowns: with Z = L_S^{-1} D_F, q = L_S^{-1} r and G_F their Schur
 //     complements, (G_F + Z^T D_S^{-1} Z) s_F = -(rho_G - L_GO t_O)_F - Z^T D_S^{-1} q and
@@ -1204,7 +1302,7 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
     double* At = rhs + nC;            // nC: Atil
     double* rv = At + nC;             // nC: reciprocal pivots
     double* us = rv + nC;             // nC: sum_i u_i
-    double* work = us + nC;           // union: factor scratch | W staging | Z, T
+    double* work = us + nC;           // union: W staging | Z, T
     double* lam = P.lam + (size_t)b * nC;
     double* lamt = P.lamt + (size_t)b * nC;
     double* slam = P.slam + (size_t)b * nC;
@@ -1214,41 +1312,25 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
     __shared__ unsigned char s_nO[MAX_SUB], s_nG[MAX_SUB];
     __shared__ int s_dec;
 
-    // ---- 1 and 2: judge the trial point; factor the subdomain blocks, a warp per group of KKT_SPW subdomains.
-    // When some warps have no group, the two run side by side: the factor warps start at once and the others
-    // judge (at a rejected trial or a stop the factors are simply not used: a backtrack forms its trial point
-    // from s alone, and the next accepted point is factored afresh).  Otherwise every warp judges first.
-    double* x_ = P.x + (size_t)b * nD;
-    const double* xt = P.xt + (size_t)b * nD;
-    const int nfw = min(nw, (ns + KKT_SPW - 1) / KKT_SPW);   // warps with a group of subdomains
-    const bool side = nfw < nw;
-    if (side) {
-        if (w < nfw) {
-            for (int g = w; KKT_SPW * g < ns; g += nfw) {
-                const int i = KKT_SPW * g + lane;
-                if (lane < KKT_SPW && i < ns) {
-                    const SubDev& S = P.sub[i];
-                    s_blk[i] = S.blk;
-                    s_nO[i] = (unsigned char)S.nO;
-                    s_nG[i] = (unsigned char)S.nG;
-                }
-                __syncwarp();
-                factor_group<32 / KKT_SPW>(P, blk, s_blk, s_nO, s_nG, KKT_SPW * g, ns,
-                                           work + (size_t)w * KKT_SPW * P.fac_stride, P.fac_stride, s_fl);
+    // ---- 1 and 3: judge the trial point (the last KKT_DW warps) while the others form the Schur sums of step 3
+    // from the factors k_constraint left (sums formed beside a rejected trial or a stop are simply not used)
+    {
+        const int nst = nth - 32 * KKT_DW;                   // threads of the Schur sums
+        if (tid < nst) {
+            for (int i = tid; i < ns; i += nst) {
+                const SubDev& S = P.sub[i];
+                const int bo = S.blk, nO = S.nO, nG = S.nG;
+                s_blk[i] = bo;
+                s_nO[i] = (unsigned char)nO;
+                s_nG[i] = (unsigned char)nG;
+                s_fl[i] = (unsigned char)blk[bo + blk_layout(nO + nG, nG, nC).flag];
             }
+            range_sync(2, nst);
+            kkt_schur_sums(P, blk, s_blk, s_nO, s_nG, s_fl, Sm, us, work, tid, nst, 2);
         } else {
-            const int dec = kkt_decide(P, b, blk, At, scratch, tid - 32 * nfw, nth - 32 * nfw, 1, true);
-            if (tid == 32 * nfw) s_dec = dec;
+            const int dec = kkt_decide(P, b, blk, At, scratch, tid - nst, 32 * KKT_DW, 1, true);
+            if (tid == nst) s_dec = dec;
         }
-    } else {
-        for (int i = tid; i < ns; i += nth) {
-            const SubDev& S = P.sub[i];
-            s_blk[i] = S.blk;
-            s_nO[i] = (unsigned char)S.nO;
-            s_nG[i] = (unsigned char)S.nG;
-        }
-        const int dec = kkt_decide(P, b, blk, At, scratch, tid, nth, 0, false);
-        if (tid == 0) s_dec = dec;
     }
     __syncthreads();
     const int dec = s_dec;
@@ -1290,15 +1372,6 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
         }
         return;
     }
-    if (!side) {
-        for (int g = w; KKT_SPW * g < ns; g += nw)
-            factor_group<32 / KKT_SPW>(P, blk, s_blk, s_nO, s_nG, KKT_SPW * g, ns,
-                                       work + (size_t)w * KKT_SPW * P.fac_stride, P.fac_stride, s_fl);
-        for (int k = tid; k < nD; k += nth) x_[k] = xt[k];   // the accepted point
-    }
-    for (int e = tid; e < nC * nC; e += nth) Sm[e] = 0.0;
-    for (int c = tid; c < nC; c += nth) us[c] = 0.0;
-    __syncthreads();
     if (w == 0) {                // flags: a vote first, the scan only when some block is not PD
         int bad = 0;
         for (int i = lane; i < ns; i += 32) bad |= s_fl[i];
@@ -1334,55 +1407,7 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
         return;
     }
 
-    // ---- 3. Schur sums S (lower triangle) and sum_i u_i
-    {
-        double* Wsh = work;                                  // ss_rows x nC
-        double* Wr = work + (size_t)P.ss_rows * nC;          // ss_rows x nC, row k scaled by 1 / D_kk
-        const int ntri = nC * (nC + 1) / 2, NE = ntri + nC;
-        for (int ch = 0; ch < P.n_ss_chunks; ++ch) {
-            const int i0 = P.ss_chunk[ch], i1 = P.ss_chunk[ch + 1];
-            // stage W_i, D_G^{-1} W_i and u_i of the chunk: thread e takes entry e of the chunk's rows
-            int tot = 0;
-            for (int i = i0; i < i1; ++i) tot += s_nG[i] * nC;
-            double* Us = Wr + (size_t)P.ss_rows * nC;          // (i1 - i0) x nC
-            for (int e = tid; e < tot + (i1 - i0) * nC; e += nth) {
-                if (e < tot) {
-                    int i = i0, off = e;
-                    while (off >= s_nG[i] * nC) off -= s_nG[i++] * nC;
-                    const int nG = s_nG[i], nO = s_nO[i];
-                    const BlkLayout BL = blk_layout(nO + nG, nG, nC);
-                    const double* bi = blk + s_blk[i];
-                    const bool pd = s_fl[i] == 0;
-                    const double wv = pd ? bi[BL.W + off] : 0.0;
-                    const double r = pd ? bi[BL.rinv + nO + off / nC] : 0.0;
-                    Wsh[e] = wv;
-                    Wr[e] = wv * r;
-                } else {
-                    const int f = e - tot, i = i0 + f / nC, c = f % nC;
-                    const int nG = s_nG[i];
-                    Us[f] = s_fl[i] == 0 ? blk[s_blk[i] + blk_layout(s_nO[i] + nG, nG, nC).u + c] : 0.0;
-                }
-            }
-            const int rows = tot / nC;
-            __syncthreads();
-            for (int e = tid; e < NE; e += nth) {
-                if (e < ntri) {
-                    int c1, c2;
-                    tri_index(e, c1, c2);
-                    double v = Sm[c1 * nC + c2];
-                    for (int r = 0; r < rows; ++r) v += Wr[r * nC + c1] * Wsh[r * nC + c2];
-                    Sm[c1 * nC + c2] = v;
-                } else {
-                    const int c = e - ntri;
-                    double v = us[c];
-                    for (int i = 0; i < i1 - i0; ++i) v += Us[i * nC + c];
-                    us[c] = v;
-                }
-            }
-            __syncthreads();
-        }
-        for (int c = tid; c < nC; c += nth) rhs[c] = At[c] - us[c];
-    }
+    for (int c = tid; c < nC; c += nth) rhs[c] = At[c] - us[c];
 
     // ---- 4. the border system
     if (!block_ldl(Sm, rv, nC)) {
@@ -1781,7 +1806,8 @@ cudaError_t launch_dgemm(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st
 // persist: the evaluation launches are persistent; zero_ctr: clear their work counters first (the loop
 // kernel of the solve graph clears them otherwise).
 template <typename T>
-int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist = false, bool zero_ctr = true) {
+int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist = false, bool zero_ctr = true,
+                bool factor = false) {
     int k = tstart(ctx, 0, st);
     if (persist && zero_ctr) CK(cudaMemsetAsync(P.ctr, 0, MAX_CLASSES * sizeof(int), st));
     for (size_t ci = 0; ci < ctx->eval_classes.size(); ++ci) {
@@ -1805,8 +1831,13 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
     }
     tstop(ctx, k, st);
     k = tstart(ctx, 1, st);
-    k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B)), CON_THREADS, P.con_split * sizeof(double), st>>>(
-        P, B);
+    {
+        // with the factorisation CTAs of the step (8 subdomains each) when the pass goes on to a KKT step
+        const int nfc = factor ? (P.n_sub + 2 * FAC_WARPS - 1) / (2 * FAC_WARPS) : 0;
+        const int nfz = (nfc + P.n_split - 1) / P.n_split;
+        const size_t smem = std::max((size_t)P.con_split, nfc ? (size_t)2 * FAC_WARPS * P.fac_stride : 0) * 8;
+        k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B) + nfz), CON_THREADS, smem, st>>>(P, B, nfz);
+    }
     CK(cudaGetLastError());
     tstop(ctx, k, st);
     ctx->tm.constraint_launches++;
@@ -1817,7 +1848,7 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
 // running count before the step (the loop kernel of the solve graph does it otherwise).
 template <typename T>
 int run_pass(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist, bool host_style) {
-    int rc = launch_eval<T>(ctx, P, B, st, persist, host_style);
+    int rc = launch_eval<T>(ctx, P, B, st, persist, host_style, true);
     if (rc) return rc;
     if (host_style) CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
     const int k = tstart(ctx, 2, st);
@@ -2444,7 +2475,7 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
         if (e != cudaSuccess) return cfail(ctx, e, "no-allocation D_i product launch");
     }
     k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B)), CON_THREADS, P.con_split * sizeof(double), st>>>(
-        P, B);
+        P, B, 0);
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cfail(ctx, e, "no-allocation evaluation launch");
