@@ -53,6 +53,7 @@ struct EvalClass {
     int smem;        // largest dynamic shared memory of its subdomains (one instance)
     int stride;      // smem rounded up to 128 bytes: one group's area in a grouped CTA
     int groups;      // instances per CTA when grouped: the one-instance CTAs of this class that fit an SM
+    int nt;          // threads of one instance's evaluation (eval_threads)
 };
 
 struct ddnm_ctx {

@@ -569,7 +569,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 const int b = eval_smem(T, nC, (int)tsize).bytes;
                 bytes = std::max(bytes, b);
                 const int by_smem = sm_smem / (b + 1024);      // 1 KB per CTA is the runtime's own
-                ctas = std::min(ctas, std::min(by_smem, eval_min_ctas((int)tsize, round4(T.nO + 1), round4(T.nG + 1))));
+                ctas = std::min(ctas, std::min(by_smem, eval_ctas_by_regs((int)tsize, round4(T.nO + 1), round4(T.nG + 1))));
             }
             smallest = std::min(smallest, bytes);
             if (bytes <= dev_max) cands.push_back({cand, ctas});
@@ -709,8 +709,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
             };
             std::stable_sort(cls.begin() + c.off, cls.end(), [&](int a, int b) { return cost(a) > cost(b); });
             c.stride = (c.smem + 127) & ~127;
-            c.groups = std::max(1, std::min({eval_min_ctas((int)tsize, ro, rg), sm_smem / (c.stride + 1024),
-                                             dev_max / std::max(c.stride, 1), 4}));
+            c.nt = eval_threads((int)tsize, ro, rg);
+            c.groups = std::max(1, std::min({eval_ctas_by_regs((int)tsize, ro, rg), sm_smem / (c.stride + 1024),
+                                             dev_max / std::max(c.stride, 1), 1024 / c.nt}));
             if (c.n) ctx->eval_classes.push_back(c);
         }
     if ((int)cls.size() != ns) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "latent dims outside the kernel classes");

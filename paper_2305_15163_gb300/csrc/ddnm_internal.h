@@ -13,7 +13,7 @@ constexpr int MAX_NG = 8;      // n_i^G
 constexpr int MAX_K = 64;      // ELL slots of a decoder output row
 constexpr int MAX_NC = 128;    // weak constraints
 constexpr int MAX_SUB = 256;   // subdomains
-constexpr int EVAL_THREADS = 256;
+// threads of one evaluation group: eval_threads(...) below
 constexpr int STEP_THREADS = 256;
 constexpr int CON_THREADS = 256;
 constexpr int CON_SPLIT = 512; // default constraint rows per constraint CTA (the N_A axis is split)
@@ -46,10 +46,19 @@ enum { D_PHI0 = 0, D_ALPHA, D_PHI, D_ALPHA_LAST, INST_DBLS };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
-// register budget of the evaluation kernel: 4 CTAs per SM for the narrow FP32 records, 3 or 2 for the wider
-// ones; FP64 records take twice the registers
-__host__ __device__ constexpr int eval_min_ctas(int tsize, int ro, int rg) {
-    return tsize == 8 ? 2 : (ro + rg <= 12 ? 4 : (ro + rg <= 20 ? 3 : 2));
+// register budget of the evaluation kernel, as the threads per SM it is sized for: 1024 for the narrow FP32
+// records, 768 or 512 for the wider ones; FP64 records take twice the registers
+__host__ __device__ constexpr int eval_reg_threads(int tsize, int ro, int rg) {
+    return tsize == 8 ? 512 : (ro + rg <= 12 ? 1024 : (ro + rg <= 20 ? 768 : 512));
+}
+// threads of one (instance, subdomain) evaluation.  256 for every class: 512-thread CTAs of the narrow FP32
+// class (two per SM at the same budget) cut an evaluation's latency by a third on the 128 x 128 / 4 x 4
+// workload but lowered the SM's throughput by a quarter (half as many evaluations resident), a loss at 64
+// instances per batch.
+__host__ __device__ constexpr int eval_threads(int, int, int) { return 256; }
+// (instance, subdomain) evaluations per SM within the register budget
+__host__ __device__ constexpr int eval_ctas_by_regs(int tsize, int ro, int rg) {
+    return eval_reg_threads(tsize, ro, rg) / eval_threads(tsize, ro, rg);
 }
 
 // 32 consecutive output rows of a decoder subnet whose mask columns (in I_h numbering) all lie in the
@@ -201,7 +210,7 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.outGn = o; o = align16(o + s.NGn * rG * tsize);        // [y, Jacobian row] per interface output the stencils use
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
     e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
-    e.red = o; o = align16(o + (EVAL_THREADS / nC) * nC * s.nG * tsize);   // D_i partials per thread group
+    e.red = o; o = align16(o + (eval_threads(tsize, rO, rG) / nC) * nC * s.nG * tsize);   // D_i partials per thread group
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
     e.dt = o; o = align16(o + s.ni * 8);

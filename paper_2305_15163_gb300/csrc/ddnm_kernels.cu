@@ -140,7 +140,8 @@ __device__ bool block_ldl(double* A, double* rd, int n) {
                     const double l = A[(j + 1) * n + j];
                     const double a = A[(j + 1) * n + j + 1] - l * r * l;
                     A[(j + 1) * n + j + 1] = a;
-                    const int ok = (a > 0.0) && isfinite(a);
+                    const long long ab = __double_as_longlong(a);
+                    const int ok = ab > 0 && ab < 0x7FF0000000000000LL;   // positive and finite (integer test)
                     s_ok = ok;
                     rd[j + 1] = ok ? 1.0 / a : 0.0;
                 }
@@ -352,10 +353,11 @@ __device__ __forceinline__ float cst<float>(const ProbDev& P, int k) { return P.
 template <>
 __device__ __forceinline__ double cst<double>(const ProbDev& P, int k) { return P.cst[k]; }
 
-// Barrier of one EVAL_THREADS group of an evaluation CTA (named barrier `bar`; the groups of a CTA work on
+// Barrier of one NT-thread group of an evaluation CTA (named barrier `bar`; the groups of a CTA work on
 // different instances and never wait for each other).
+template <int NT>
 __device__ __forceinline__ void gsync(int bar) {
-    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(EVAL_THREADS) : "memory");
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory");
 }
 
 // Trial point of this subdomain for the coming evaluation (ist[I_XTMODE]).  On a new SQP step the
@@ -363,6 +365,7 @@ __device__ __forceinline__ void gsync(int bar) {
 // L D L^T factors of the accepted evaluation: s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda]) when H_i is PD,
 // s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G) with s_G from the step kernel when H_i is singular in its G
 // block.  Then xt_i = x_i + alpha s_i (Eq. sqp_update); alpha = 1 on a new step.
+template <int NT>
 __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, int tid, int bar) {
     const int xm = P.ist[(size_t)b * INST_INTS + I_XTMODE];
     if (xm == XT_KEEP) return;
@@ -418,13 +421,13 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, 
             __syncwarp();
             if (lane < nb) s[lane] = -z[lane];
         }
-        gsync(bar);
+        gsync<NT>(bar);
         if (tid < ni) xt[tid] = x[tid] + s[tid];
     } else {
         const double alpha = P.dst[(size_t)b * INST_DBLS + D_ALPHA];
         if (tid < ni) xt[tid] = x[tid] + alpha * s[tid];
     }
-    gsync(bar);
+    gsync<NT>(bar);
 }
 
 // One (instance, subdomain) evaluation.  RO = round4(n^O + 1) and RG = round4(n^G + 1) are the padded
@@ -434,6 +437,7 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, 
 // consecutive addresses).
 template <typename T, int RO, int RG>
 __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned char* smem, int tid, int bar) {
+    constexpr int NT = eval_threads(sizeof(T), RO, RG);
     const EvalSmem L = eval_smem(S, P.n_C, (int)sizeof(T));
     T* sx = (T*)(smem + L.sx);
     T* hidO = (T*)(smem + L.hidO);
@@ -449,16 +453,16 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
 
     const T* V = (const T*)P.vpool;
     const int* IP = P.ipool;
-    const int nth = EVAL_THREADS;
+    const int nth = NT;
     const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C, NG = S.NG;
     const int ld = ni + 1;
     constexpr int WO = RO - 1 > 0 ? ((RO - 1 + 3) & ~3) : 4;   // padded W1 row width of the interior subnet
     constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
     // latent coordinates and multipliers of the trial point
-    form_trial(P, S, b, dt, tid, bar);
+    form_trial<NT>(P, S, b, dt, tid, bar);
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
-    gsync(bar);
+    gsync<NT>(bar);
 
     // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]; the rows that pad each
     // record array to a multiple of 4 are zero (dense-window tiles may span them with zero values)
@@ -507,7 +511,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int k = 0; k < RG; k += 4) st4(hidG + (size_t)cc * RG + k, row + k);
         }
     }
-    gsync(bar);
+    gsync<NT>(bar);
 
     const int nwarp = nth >> 5;
     const int w = tid >> 5, lane = tid & 31;
@@ -586,7 +590,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
                 for (int k = 0; k < RG - 1; ++k)
                     if (k < nG) red[((size_t)grp * nC + c) * nG + k] = acc[k];
             }
-            gsync(bar);
+            gsync<NT>(bar);
             for (int o = t_; o < nC * nG; o += n_) {
                 T a = T(0);
                 for (int g = 0; g < ngrp; ++g) a += red[(size_t)g * nC * nG + o];
@@ -647,7 +651,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     for (int q = 0; q < S.n_chunks; ++q) {
         const ChunkDev Cq = P.chunk[S.chunk0 + q];
         interior_outputs(Cq, tid, nth, w, nwarp);
-        gsync(bar);
+        gsync<NT>(bar);
         // collocation rows of the chunk
         const T* bnd = (const T*)P.bnd + (size_t)b * P.n_bnd * 2;
         const T ax = cst<T>(P, 0), ay = cst<T>(P, 1), cx = cst<T>(P, 2), cy = cst<T>(P, 3);
@@ -704,7 +708,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             row[ni] = r;
             if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
         }
-        gsync(bar);
+        gsync<NT>(bar);
         if (tid < npair + ni) {
             T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
             int ql = 0;
@@ -717,7 +721,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (; ql < Cq.nq; ++ql) h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
             hacc += (h0 + h1) + (h2 + h3);
         }
-        if (q + 1 < S.n_chunks) gsync(bar);   // outO / Rr reused by the next chunk
+        if (q + 1 < S.n_chunks) gsync<NT>(bar);   // outO / Rr reused by the next chunk
     }
     if (tid < npair) {
         dH[pa * ni + pc] = (double)hacc;
@@ -725,7 +729,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     } else if (tid < npair + ni) {
         drho[pa] = (double)hacc;
     }
-    gsync(bar);
+    gsync<NT>(bar);
 
     // H_i and rho_i = R_i^T r + E_i^T lambda (E_i = [0, D_i]) with phi_i = ||rho_i||^2 (in FP64: warp k forms
     // entry n^O + k, lanes over the multipliers), or R_i^T r alone when k_dgemm forms D_i and the rest
@@ -740,7 +744,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             v = warp_sum(v);
             if (l2 == 0) drho[nO + k] += v;
         }
-        gsync(bar);
+        gsync<NT>(bar);
         if (tid < 32) {
             const double r = tid < ni ? drho[tid] : 0.0;
             const double ph = warp_sum(r * r);
@@ -754,17 +758,18 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
 
 // One launch per class of subdomains sharing the padded record widths (RO, RG).  Items are (instance,
 // subdomain of the class); item k is instance k % B of subdomain subs[k / B] (subs: the class's subdomains,
-// largest first).  A CTA holds G = blockDim / EVAL_THREADS independent groups (each with its own named
+// largest first).  A CTA holds G = blockDim / NT independent groups (NT = eval_threads) (each with its own named
 // barrier and shared-memory area of `stride` bytes) that take consecutive items, i.e. neighbouring
 // instances of one subdomain, whose decoder tables they then share through L1.  With ctr == NULL group g of
 // CTA c takes item c G + g; otherwise the grid is persistent and every group claims items from *ctr (zero
 // before the launch) until none are left.
 template <typename T, int RO, int RG>
-__global__ void __launch_bounds__(EVAL_THREADS * eval_min_ctas(sizeof(T), RO, RG), 1)
+__global__ void __launch_bounds__(eval_reg_threads(sizeof(T), RO, RG), 1)
     k_eval(ProbDev P, int B, const int* subs, int nsub, int* ctr, int stride) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int G = blockDim.x / EVAL_THREADS, g = threadIdx.x / EVAL_THREADS;
-    const int tid = threadIdx.x - g * EVAL_THREADS, bar = g + 1;
+    constexpr int NT = eval_threads(sizeof(T), RO, RG);
+    const int G = blockDim.x / NT, g = threadIdx.x / NT;
+    const int tid = threadIdx.x - g * NT, bar = g + 1;
     unsigned char* gsm = smem + (size_t)g * stride;
     const int items = B * nsub;
     if (!ctr) {
@@ -778,14 +783,14 @@ __global__ void __launch_bounds__(EVAL_THREADS * eval_min_ctas(sizeof(T), RO, RG
     __shared__ int s_item[4];
     for (;;) {
         if (tid == 0) s_item[g] = atomicAdd(ctr, 1);
-        gsync(bar);
+        gsync<NT>(bar);
         const int k = s_item[g];
-        gsync(bar);                       // every thread has its item before s_item is claimed again
+        gsync<NT>(bar);                       // every thread has its item before s_item is claimed again
         if (k >= items) return;
         const int b = k % B;
         if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) continue;
         eval_item<T, RO, RG>(P, P.sub[subs[k / B]], b, gsm, tid, bar);
-        gsync(bar);                       // shared memory is reused by the next item
+        gsync<NT>(bar);                       // shared memory is reused by the next item
     }
 }
 
@@ -1820,7 +1825,7 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
             grid = std::min(grid, std::max(1, ctx->n_sm * ctx->tune.eval_persist / G));
             ctr = P.ctr + ci;
         }
-        eval_kernel<T>(g.ro, g.rg)<<<grid, EVAL_THREADS * G, G == 1 ? g.smem : G * g.stride, st>>>(
+        eval_kernel<T>(g.ro, g.rg)<<<grid, g.nt * G, G == 1 ? g.smem : G * g.stride, st>>>(
             P, B, ctx->d_classes + g.off, g.n, ctr, g.stride);
         CK(cudaGetLastError());
         ctx->tm.eval_launches++;
@@ -2468,7 +2473,7 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
     }
     k_noalloc_init<<<B, 128, 0, st>>>(P, B, (int)(sizeof(T) == 8));
     for (const auto& g : ctx->eval_classes)
-        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, EVAL_THREADS, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, nullptr,
+        eval_kernel<T>(g.ro, g.rg)<<<B * g.n, g.nt, g.smem, st>>>(P, B, ctx->d_classes + g.off, g.n, nullptr,
                                                                            g.stride);
     if (P.d_gemm) {
         e = launch_dgemm<T>(ctx, P, B, st);
