@@ -77,6 +77,8 @@ struct ddnm_ctx {
     std::vector<ddnm::SubDev> hsub;
     ddnm::ProbDev pd{};
     int eval_smem = 0, kkt_smem = 0, rec_smem = 0, ss_rows = 0, max_nG = 1;
+    int fac_smem = 0;                  // dynamic shared memory of a factorisation CTA of k_constraint
+    bool fac_share = false;            // the factorisation CTAs form the Schur-sum shares (Spart)
     void* d_vpool = nullptr;
     int* d_ipool = nullptr;
     int* d_hr = nullptr;

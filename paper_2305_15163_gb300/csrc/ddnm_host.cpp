@@ -721,7 +721,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     if (ctx->rec_smem > dev_max) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "decoder too wide for reconstruction");
     int fac_stride = 0, sum_nG = 0;
     for (const SubDev& S : ctx->hsub) {
-        fac_stride = std::max(fac_stride, S.ni * S.ni + 3 * S.ni + S.nG * S.nG);
+        fac_stride = std::max(fac_stride, S.ni * S.ni + 4 * S.ni + S.nG * S.nG);
         sum_nG += S.nG;
     }
     fac_stride = (fac_stride + 1) & ~1;
@@ -796,6 +796,21 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.ss_rows = ctx->ss_rows;
     pd.n_ss_chunks = (int)ss_chunk.size() - 1;
     pd.ss_chunk = ctx->d_ipool + ss_chunk_off;
+    // factorisation CTAs of k_constraint (8 subdomains each): their Schur-sum shares when the staging of W,
+    // D_G^{-1} W and u fits FAC_SHARE_SMEM, else the KKT step sums the blocks
+    pd.nfc = (ns + 2 * FAC_WARPS - 1) / (2 * FAC_WARPS);
+    pd.fac_rows = 0;
+    for (int f = 0; f < pd.nfc; ++f) {
+        int rows = 0;
+        for (int i = 2 * FAC_WARPS * f; i < std::min(ns, 2 * FAC_WARPS * (f + 1)); ++i) rows += ctx->hsub[i].nG;
+        pd.fac_rows = std::max(pd.fac_rows, rows);
+    }
+    {
+        const size_t share = (size_t)(2 * pd.fac_rows + 2 * FAC_WARPS) * nC * 8;
+        ctx->fac_share = share <= (size_t)FAC_SHARE_SMEM;
+        ctx->fac_smem = (int)std::max((size_t)2 * FAC_WARPS * fac_stride * 8, ctx->fac_share ? share : 0);
+    }
+    pd.Spart = nullptr;            // set by ddnm_reserve when the shares are formed
     pd.con_split = CON_SPLIT;
     pd.n_split = (ctx->N_A + CON_SPLIT - 1) / CON_SPLIT;
     pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
@@ -838,7 +853,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     size_t o_slam = o; o = al(o + (size_t)cap * pd.n_C * 8);
     const size_t max_split = ((size_t)pd.N_A + MIN_CON_SPLIT - 1) / MIN_CON_SPLIT;   // any con_split of the plan
     size_t o_At = o; o = al(o + (size_t)cap * max_split * pd.n_C * 8);
-    size_t o_Ss = o; o = al(o + (size_t)cap * ((size_t)pd.n_C * pd.n_C + pd.n_C) * 8);
+    size_t o_Ss = o; o = al(o + (ctx->fac_share ? (size_t)cap * pd.nfc * ((size_t)pd.n_C * (pd.n_C + 1) / 2 + pd.n_C) * 8 : 0));
     size_t o_dst = o; o = al(o + (size_t)cap * INST_DBLS * 8);
     size_t o_ist = o; o = al(o + (size_t)cap * INST_INTS * 4);
     size_t o_bnd = o; o = al(o + (size_t)cap * std::max(pd.n_bnd, 1) * 2 * tsize);
@@ -862,7 +877,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     pd.s = (double*)(base + o_s);
     pd.slam = (double*)(base + o_slam);
     pd.Atil = (double*)(base + o_At);
-    pd.Ssum = (double*)(base + o_Ss);
+    pd.Spart = ctx->fac_share ? (double*)(base + o_Ss) : nullptr;
     pd.dst = (double*)(base + o_dst);
     pd.ist = (int*)(base + o_ist);
     pd.bnd = (void*)(base + o_bnd);

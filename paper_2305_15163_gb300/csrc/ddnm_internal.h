@@ -37,8 +37,9 @@ constexpr int DG_THREADS = 256;    // k_dgemm
 constexpr int DG_KT = 32;          // interface hidden units per staged chunk of k_dgemm
 constexpr int KKT_THREADS = 512;   // k_kkt: one CTA per instance
 constexpr int FAC_WARPS = 4;       // factorisation CTAs of k_constraint: warps with a pair of subdomains each
-constexpr int KKT_DW = 4;          // k_kkt: warps that judge the trial point while the others form the Schur sums
 constexpr int SS_ROWS_DBL = 3072;  // staged W rows (doubles) per Schur-sum chunk, each for W, D_G^{-1} W and u
+constexpr int FAC_SHARE_SMEM = 32768;   // largest staging (bytes) of a factorisation CTA's Schur-sum share
+constexpr int KKT_DW = 4;          // k_kkt: warps that judge the trial point while the others form the Schur sums
 // how the next evaluation forms its trial point xt (ist[I_XTMODE]): unchanged (xt = x), a new SQP step
 // (each subdomain back-substitutes s_i from s_lambda, then xt = x + s), or a backtrack (xt = x + alpha s)
 enum { XT_KEEP = 0, XT_NEWSTEP = 1, XT_BACKTRACK = 2 };
@@ -140,10 +141,7 @@ __host__ __device__ inline BlkLayout blk_layout(int ni, int nG, int nC) {
 struct ProbDev {
     int n_sub, n_D, n_C, N_A, sum_NG, sum_NB, n_bnd, N_x;
     int nx, ny;
-    int fac_stride;                // factorisation scratch doubles per warp: max_i n_i^2 + 3 n_i + (n_i^G)^2
-    int ss_rows;                   // rows of W staged per Schur-sum chunk
-    int n_ss_chunks;               // Schur-sum chunks: subdomains [ss_chunk[k], ss_chunk[k + 1])
-    const int* ss_chunk;
+    int fac_stride;                // factorisation scratch doubles per warp: max_i n_i^2 + 4 n_i + (n_i^G)^2
     int d_gemm;                    // 1: D_i by the batched k_dgemm; 0: inside the evaluation
     int n_split;                   // constraint CTAs per instance (ceil(N_A / con_split))
     int con_split;                 // constraint rows per constraint CTA
@@ -173,7 +171,14 @@ struct ProbDev {
     double* s;
     double* slam;
     double* Atil;                  // B x n_split x n_C partial sums of C * jump
-    double* Ssum;                  // B x (n_C^2 + n_C): sum over the PD subdomains of S_i (full) and u_i
+    double* Spart;                 // B x nfc x (n_C (n_C + 1) / 2 + n_C): per factorisation CTA, the sums over
+                                   // its PD subdomains of W_i^T D_G,i^{-1} W_i (lower triangle, row by row), u_i;
+                                   // null when the border is too wide for that (the KKT step sums the blocks)
+    int ss_rows;                   // rows of W staged per Schur-sum chunk of the KKT step
+    int n_ss_chunks;               // Schur-sum chunks: subdomains [ss_chunk[k], ss_chunk[k + 1])
+    const int* ss_chunk;
+    int nfc;                       // factorisation CTAs per instance: ceil(n_sub / (2 FAC_WARPS))
+    int fac_rows;                  // largest sum of n_i^G over the subdomains of one factorisation CTA
     double* dst;                   // INST_DBLS per instance
     int* ist;                      // INST_INTS per instance
     void* bnd;                     // B x n_bnd x 2 (u, v) Dirichlet data, value type

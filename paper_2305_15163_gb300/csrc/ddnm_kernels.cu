@@ -995,6 +995,7 @@ int con_row_groups(const ddnm_ctx* ctx, const ProbDev& P, int B) {
 // G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).  Subdomains i_first .. i_first + 32/LG - 1 below
 // ns; scratch (32 / LG) fs doubles; flags (FLAG_PD, FLAG_OMEGA_FAIL, FLAG_GAMMA_SING as 0, 1, 2) to fl[] and
 // the blocks.  A pivot is accepted when its bits are those of a positive finite double (integer tests).
+// Columns are taken two at a time where the lane groups allow (one reciprocal per pair), else one at a time.
 template <int LG>
 __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, const unsigned char* s_nO,
                              const unsigned char* s_nG, int i_first, int ns, double* scr, int fs, unsigned char* fl,
@@ -1009,7 +1010,8 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     double* t = L + ni * ni;
     double* rinv = t + ni;
     double* ucol = rinv + ni;                   // column j before its scaling
-    double* G = ucol + ni;
+    double* ucol2 = ucol + ni;                  // column j + 1 of a paired step, updated by column j, unscaled
+    double* G = ucol2 + ni;
     int nmax = 0;
     for (int q = 0; q < 32 / LG && i_first + q < ns; ++q) nmax = max(nmax, (int)s_nO[i_first + q] + s_nG[i_first + q]);
     double dpre[2][MAX_NG];                     // D_i[c][:] for c = hl, hl + LG, loaded ahead of the pivots
@@ -1029,16 +1031,69 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     __syncwarp();
     int flag = 0, nf = 0;                       // this half's subdomain: flag and factored columns
     bool act = on;
-    for (int j = 0; j < nmax; ++j) {
+    auto posfin = [](double v) {                // positive and finite (integer test)
+        const long long vb = __double_as_longlong(v);
+        return vb > 0 && vb < 0x7FF0000000000000LL;
+    };
+    for (int j = 0; j < nmax;) {
         if (act && j == nO)
             for (int e = hl; e < nG * nG; e += LG) G[e] = L[(nO + e / nG) * ni + nO + e % nG];
         __syncwarp();
+        // Two columns at once where every live lane group can: the 2 x 2 block [a b; b c] of columns j, j + 1
+        // (both in the O block or both in the G block) has a > 0 and det = a c - b^2 > 0.  One reciprocal
+        // q = 1 / (a det) gives both pivots' reciprocals: 1 / d_j = det q and 1 / d_{j+1} = a / det = a (a q).
+        const bool live = act && j < ni;
+        double pa = 0.0, pb = 0.0, pdet = 0.0;
+        bool pair_ok = false;
+        if (live && j + 1 < ni && !(j < nO && j + 1 >= nO)) {
+            pa = L[j * ni + j];
+            pb = L[(j + 1) * ni + j];
+            const double pc = L[(j + 1) * ni + j + 1];
+            pdet = fma(pa, pc, -(pb * pb));
+            pair_ok = posfin(pa) && posfin(pdet);
+        }
+        if (__all_sync(0xffffffffu, !live || pair_ok)) {
+            if (live) {
+                const double q = 1.0 / (pa * pdet);
+                const double ra = pdet * q, rdet = pa * q, r1 = pa * rdet;
+                for (int ii = j + 2 + hl; ii < ni; ii += LG) {   // columns j and j + 1 below the block
+                    const double u = L[ii * ni + j], v = L[ii * ni + j + 1];
+                    const double l0 = u * ra;
+                    const double v1 = v - l0 * pb;              // column j + 1 updated by column j
+                    ucol[ii] = u;
+                    ucol2[ii] = v1;
+                    L[ii * ni + j] = l0;
+                    L[ii * ni + j + 1] = v1 * r1;
+                }
+                if (hl == 0) {
+                    L[(j + 1) * ni + j] = pb * ra;
+                    L[(j + 1) * ni + j + 1] = pdet * ra;         // d_{j+1}
+                    rinv[j] = ra;
+                    rinv[j + 1] = r1;
+                }
+                nf = j + 2;
+            }
+            __syncwarp();
+            const int m = ni - j - 2;
+            if (live && m > 0) {
+                for (int e = hl; e < m * (m + 1) / 2; e += LG) {   // trailing triangle: columns j, then j + 1
+                    const int ta = tri[e] >> 8, tc = tri[e] & 255;
+                    const int ii = j + 2 + ta, kk = j + 2 + tc;
+                    double x = L[ii * ni + kk];
+                    x -= L[ii * ni + j] * ucol[kk];
+                    x -= L[ii * ni + j + 1] * ucol2[kk];
+                    L[ii * ni + kk] = x;
+                }
+            }
+            __syncwarp();
+            j += 2;
+            continue;
+        }
         double r = 0.0;
         bool piv = false;
-        if (act && j < ni) {
+        if (live) {
             const double d = L[j * ni + j];
-            const long long db = __double_as_longlong(d);
-            if (!(db > 0 && db < 0x7FF0000000000000LL)) {   // not positive and finite: the same for the lane group
+            if (!posfin(d)) {                   // not positive and finite: the same for the lane group
                 flag = j < nO ? 1 : 2;
                 act = false;
             } else {
@@ -1065,6 +1120,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
             }
         }
         __syncwarp();
+        ++j;
     }
     // t = L^{-1} rho over the factored columns (n_f = n_i when PD, n^O when G-singular)
     const int nft = flag == 0 ? ni : (flag == 2 ? nO : 0);
@@ -1116,7 +1172,9 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
 // unit under the usual warp-to-scheduler assignment; the other warps idle.  The CTAs of an instance spread
 // over SMs, where the step kernel's one CTA would take the blocks on one SM's four FP64 units.  Every
 // evaluation is factored (the step kernel decides afterwards whether the point is accepted; a rejected
-// trial's factors are never read: a backtrack forms its trial point from s).  scr: 8 fac_stride doubles.
+// trial's factors are never read: a backtrack forms its trial point from s).  Then, when the staging fits
+// (P.Spart set), the CTA's share of the Schur sums of the KKT step.  scr: ctx->fac_smem bytes, i.e.
+// 8 fac_stride doubles, or (2 fac_rows + 8) n_C doubles with the shares.
 __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
     constexpr int SPC = 2 * FAC_WARPS;                          // subdomains per CTA
     __shared__ int s_blk[SPC];
@@ -1137,9 +1195,51 @@ __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
         s_nG[tid] = (unsigned char)S.nG;
     }
     __syncthreads();
+    double* blk = P.blk + (size_t)b * P.blk_stride;
     if (w < FAC_WARPS && 2 * w < nrel)
-        factor_group<16>(P, P.blk + (size_t)b * P.blk_stride, s_blk, s_nO, s_nG, 2 * w, nrel,
-                         scr + (size_t)w * 2 * P.fac_stride, P.fac_stride, s_fl, tri);
+        factor_group<16>(P, blk, s_blk, s_nO, s_nG, 2 * w, nrel, scr + (size_t)w * 2 * P.fac_stride, P.fac_stride,
+                         s_fl, tri);
+    if (!P.Spart) return;          // the KKT step forms the Schur sums itself
+    __syncthreads();               // the CTA's blocks factored: W_i, 1 / D_jj, u_i and the flags written
+    // the CTA's share of the border of the Schur complement of Eq. (sqp_system): over its subdomains with H_i
+    // PD, sum W_i^T D_G,i^{-1} W_i (lower triangle) and sum u_i, rows in subdomain order (k ascending in one);
+    // the KKT step adds the shares of an instance in CTA order
+    const int nC = P.n_C, ntri = nC * (nC + 1) / 2;
+    int rows = 0;
+    for (int q = 0; q < nrel; ++q) rows += s_nG[q];
+    double* Wsh = scr;                          // rows x nC
+    double* Wr = Wsh + (size_t)rows * nC;       // rows x nC, row k scaled by 1 / D_kk
+    double* Us = Wr + (size_t)rows * nC;        // nrel x nC
+    for (int e = tid; e < (rows + nrel) * nC; e += blockDim.x) {
+        if (e < rows * nC) {
+            int q = 0, off = e;
+            while (off >= s_nG[q] * nC) off -= s_nG[q++] * nC;
+            const int nG = s_nG[q], nO = s_nO[q];
+            const BlkLayout BL = blk_layout(nO + nG, nG, nC);
+            const double* bi = blk + s_blk[q];
+            const bool pd = s_fl[q] == 0;
+            const double wv = pd ? bi[BL.W + off] : 0.0;
+            Wsh[e] = wv;
+            Wr[e] = wv * (pd ? bi[BL.rinv + nO + off / nC] : 0.0);
+        } else {
+            const int g = e - rows * nC, q = g / nC, c = g % nC;
+            const int nG = s_nG[q];
+            Us[g] = s_fl[q] == 0 ? blk[s_blk[q] + blk_layout(s_nO[q] + nG, nG, nC).u + c] : 0.0;
+        }
+    }
+    __syncthreads();
+    double* out = P.Spart + ((size_t)b * P.nfc + f) * (ntri + nC);
+    for (int e = tid; e < ntri + nC; e += blockDim.x) {
+        double v = 0.0;
+        if (e < ntri) {
+            int c1, c2;
+            tri_index(e, c1, c2);
+            for (int r = 0; r < rows; ++r) v += Wr[r * nC + c1] * Wsh[r * nC + c2];
+        } else {
+            for (int q = 0; q < nrel; ++q) v += Us[q * nC + e - ntri];
+        }
+        out[e] = v;
+    }
 }
 
 // Step 3 of k_kkt by the threads t < n of a thread range (barrier bar): the border of the Schur complement of
@@ -1307,7 +1407,7 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
     double* At = rhs + nC;            // nC: Atil
     double* rv = At + nC;             // nC: reciprocal pivots
     double* us = rv + nC;             // nC: sum_i u_i
-    double* work = us + nC;           // union: W staging | Z, T
+    double* work = us + nC;           // union: W staging (when summed here) | Z, T of the border solve
     double* lam = P.lam + (size_t)b * nC;
     double* lamt = P.lamt + (size_t)b * nC;
     double* slam = P.slam + (size_t)b * nC;
@@ -1317,8 +1417,8 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
     __shared__ unsigned char s_nO[MAX_SUB], s_nG[MAX_SUB];
     __shared__ int s_dec;
 
-    // ---- 1 and 3: judge the trial point (the last KKT_DW warps) while the others form the Schur sums of step 3
-    // from the factors k_constraint left (sums formed beside a rejected trial or a stop are simply not used)
+    // ---- 1 and 3: judge the trial point (the last KKT_DW warps) while the others add up the Schur sums of step 3
+    // from the shares k_constraint left (sums formed beside a rejected trial or a stop are simply not used)
     {
         const int nst = nth - 32 * KKT_DW;                   // threads of the Schur sums
         if (tid < nst) {
@@ -1330,8 +1430,25 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
                 s_nG[i] = (unsigned char)nG;
                 s_fl[i] = (unsigned char)blk[bo + blk_layout(nO + nG, nG, nC).flag];
             }
-            range_sync(2, nst);
-            kkt_schur_sums(P, blk, s_blk, s_nO, s_nG, s_fl, Sm, us, work, tid, nst, 2);
+            if (P.Spart) {
+                // S (lower triangle) and sum_i u_i: the shares of the factorisation CTAs added in CTA order
+                const int ntri = nC * (nC + 1) / 2;
+                const double* sp = P.Spart + (size_t)b * P.nfc * (ntri + nC);
+                for (int e = tid; e < ntri + nC; e += nst) {
+                    double v = 0.0;
+                    for (int f = 0; f < P.nfc; ++f) v += sp[(size_t)f * (ntri + nC) + e];
+                    if (e < ntri) {
+                        int c1, c2;
+                        tri_index(e, c1, c2);
+                        Sm[c1 * nC + c2] = v;
+                    } else {
+                        us[e - ntri] = v;
+                    }
+                }
+            } else {         // a border too wide for the factorisation CTAs' staging: summed here
+                range_sync(2, nst);
+                kkt_schur_sums(P, blk, s_blk, s_nO, s_nG, s_fl, Sm, us, work, tid, nst, 2);
+            }
         } else {
             const int dec = kkt_decide(P, b, blk, At, scratch, tid - nst, 32 * KKT_DW, 1, true);
             if (tid == nst) s_dec = dec;
@@ -1780,6 +1897,8 @@ int set_smem_attrs(ddnm_ctx* ctx) {
         CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 std::max(g.smem, g.groups * g.stride)));
     CK(cudaFuncSetAttribute(k_kkt, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->kkt_smem));
+    CK(cudaFuncSetAttribute(k_constraint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            std::max(MAX_CON_SPLIT * 8, ctx->fac_smem)));
     {
         constexpr int CPT = sizeof(T) == 8 ? 16 : 32;
         const int ncp = (ctx->n_C + 31) & ~31;
@@ -1840,7 +1959,9 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
         // with the factorisation CTAs of the step (8 subdomains each) when the pass goes on to a KKT step
         const int nfc = factor ? (P.n_sub + 2 * FAC_WARPS - 1) / (2 * FAC_WARPS) : 0;
         const int nfz = (nfc + P.n_split - 1) / P.n_split;
-        const size_t smem = std::max((size_t)P.con_split, nfc ? (size_t)2 * FAC_WARPS * P.fac_stride : 0) * 8;
+        const size_t smem = std::max((size_t)P.con_split * 8, nfc ? (size_t)ctx->fac_smem : 0);
+        if (smem > (size_t)std::max(MAX_CON_SPLIT * 8, ctx->fac_smem))     // beyond what set_smem_attrs allowed
+            return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "constraint launch: shared memory above its limit");
         k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B) + nfz), CON_THREADS, smem, st>>>(P, B, nfz);
     }
     CK(cudaGetLastError());
@@ -1876,7 +1997,7 @@ ProbDev group_view(const ProbDev& P, int b0, int c, size_t tsize) {
     Q.s += b * nD;
     Q.slam += b * nC;
     Q.Atil += b * P.n_split * nC;
-    Q.Ssum += b * (nC * nC + nC);
+    if (Q.Spart) Q.Spart += b * P.nfc * (nC * (nC + 1) / 2 + nC);
     Q.dst += b * INST_DBLS;
     Q.ist += b * INST_INTS;
     Q.bnd = (char*)P.bnd + b * P.n_bnd * 2 * tsize;
@@ -2509,7 +2630,6 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     const size_t o_PG = o; o = al(o + (P.d_gemm ? (size_t)B * P.pg_stride * tsize : 0));
     const size_t o_blk = o; o = al(o + (size_t)B * P.blk_stride * 8);
     const size_t o_At = o; o = al(o + (size_t)B * P.n_split * P.n_C * 8);
-    const size_t o_Ss = o; o = al(o + (size_t)B * ((size_t)P.n_C * P.n_C + P.n_C) * 8);
     const size_t o_lz = o; o = al(o + (size_t)B * P.n_C * 8);
     if (o > DDNM_NOALLOC_SCRATCH_BYTES) {
         const size_t per = o / B + 1;
@@ -2534,7 +2654,7 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     P.PG = (void*)(s + o_PG);
     P.blk = (double*)(s + o_blk);
     P.Atil = (double*)(s + o_At);
-    P.Ssum = (double*)(s + o_Ss);
+    P.Spart = nullptr;                     // no KKT step here
     P.r_hr = nullptr;
     if (lam) {
         P.lamt = const_cast<double*>(lam);  // read only by k_eval
