@@ -158,7 +158,7 @@ typedef struct ddnm_timing {
     long long eval_launches;
     long long constraint_launches;
     long long step_launches;
-    long long other_launches;   /* set-up, statistics, reconstruction, loop-control kernels */
+    long long other_launches;   /* set-up, statistics and reconstruction kernels */
 } ddnm_timing;
 
 /* Algorithmic work of ONE evaluation of ONE instance (all subdomains), counted

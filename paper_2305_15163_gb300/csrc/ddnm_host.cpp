@@ -887,6 +887,7 @@ int ddnm_reserve(ddnm_ctx* ctx, int B) {
     pd.active = (int*)(base + o_act);
     pd.pass = pd.active + MAX_CHAINS;
     pd.ctr = pd.pass + MAX_CHAINS;
+    pd.arrive = pd.ctr + MAX_CHAINS * MAX_CLASSES;
     ctx->cap_B = cap;
     ++ctx->gen;   // captured solve graphs hold workspace pointers
     return DDNM_OK;

@@ -20,6 +20,7 @@ constexpr int CON_SPLIT = 512; // default constraint rows per constraint CTA (th
 constexpr int CON_BLOCK = 512;  // constraint rows of one canonical partial of Atil (fixes the summation order)
 constexpr int MIN_CON_SPLIT = CON_BLOCK, MAX_CON_SPLIT = 4 * CON_BLOCK;
 constexpr int MAX_CHAINS = 16; // instance groups iterating concurrently inside the solve graph
+constexpr int PASSES_PER_BODY = 2;   // SQP passes per turn of an instance group's device-side loop
 constexpr int MAX_CLASSES = 12; // width classes (RO, RG) of the evaluation kernel
 constexpr int HR_CHUNK = 128;  // largest collocation rows per evaluation chunk (the set-up may choose fewer)
 
@@ -190,11 +191,12 @@ struct ProbDev {
     int* active;                   // count of running instances after a step pass
     int* pass;                     // loop passes of the solve graph's instance group
     int* ctr;                      // MAX_CLASSES work counters of the persistent evaluation
+    int* arrive;                   // step CTAs of the pass that have finished (the last one runs the loop control)
 };
 
-// Control area at the end of the workspace: per instance group, the running count, the loop passes and the
-// persistent evaluation's work counters.
-constexpr int CTL_INTS = MAX_CHAINS * (2 + MAX_CLASSES);
+// Control area at the end of the workspace: per instance group, the running count, the loop passes, the
+// persistent evaluation's work counters and the step kernel's arrival count.
+constexpr int CTL_INTS = MAX_CHAINS * (3 + MAX_CLASSES);
 
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {

@@ -1388,7 +1388,7 @@ __device__ __forceinline__ int kkt_decide(const ProbDev& P, int b, const double*
 //     complements, (G_F + Z^T D_S^{-1} Z) s_F = -(rho_G - L_GO t_O)_F - Z^T D_S^{-1} q and
 //     s_lambda = L_S^{-T} D_S^{-1} (q + Z s_F).  Every other piece of s is back-substituted by the
 //     evaluation of its subdomain (form_trial).
-__global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
+__device__ __forceinline__ void kkt_body(const ProbDev& P, int B) {
     extern __shared__ __align__(16) double ksm[];
     __shared__ double scratch[32];
     __shared__ int s_mF, s_over, s_fail;
@@ -1619,6 +1619,31 @@ __global__ void __maxnreg__(64) k_kkt(ProbDev P, int B) {
     }
 }
 
+// The step kernel: kkt_body for every instance, then, inside the solve graph (loop > 0), the loop control of
+// the instance group by the CTA that finishes last: count the pass, clear the running count, the arrival
+// count and the persistent evaluation's work counters, and (loop = 2, the last pass of the loop body) end
+// the group's device-side while loop when no instance is running or the pass bound is reached.  (Every
+// return of kkt_body is taken by a whole CTA.)
+__global__ void __maxnreg__(64) k_kkt(ProbDev P, int B, int loop, int p0, int max_passes,
+                                      cudaGraphConditionalHandle h) {
+    kkt_body(P, B);
+    if (!loop) return;
+    __shared__ int s_last;
+    __threadfence();                       // this CTA's running-count update before its arrival
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(P.arrive, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    const int a = atomicAdd(P.active, 0);
+    const int p = *P.pass + 1;
+    *P.pass = p;
+    *P.active = 0;
+    *P.arrive = 0;
+    for (int k = 0; k < MAX_CLASSES; ++k) P.ctr[k] = 0;
+    if (loop == 2 && (a == 0 || p0 + p >= max_passes)) cudaGraphSetConditional(h, 0);
+}
+
 // ------------------------------------------------------------------------ set-up / outputs
 
 // start state of every instance and its Dirichlet data
@@ -1828,18 +1853,6 @@ __global__ void k_ws_select(ProbDev P, int B) {
     }
 }
 
-// End of one pass of an instance group's loop in the solve graph: count the pass, clear the running
-// count and the evaluation counters for the next pass, and stop the loop (the conditional node's
-// handle) once no instance of the group is running or the pass limit is reached.  One thread.
-__global__ void k_loop(int* active, int* pass, int* ctr, int p0, int max_passes, cudaGraphConditionalHandle h) {
-    const int a = *active;
-    const int p = *pass + 1;
-    *pass = p;
-    *active = 0;
-    for (int k = 0; k < MAX_CLASSES; ++k) ctr[k] = 0;
-    if (a == 0 || p0 + p >= max_passes) cudaGraphSetConditional(h, 0);
-}
-
 // ------------------------------------------------------------------------ host drivers
 
 struct Launch {
@@ -1970,15 +1983,25 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
     return DDNM_OK;
 }
 
+// The device-side loop control of an instance group's pass inside the solve graph (k_kkt's last CTA):
+// on = 1 counts the pass and clears the counters, on = 2 (the last pass of the loop body) also decides
+// whether the loop goes on.
+struct LoopCtl {
+    int on = 0;
+    int p0 = 0, max_passes = 0;
+    cudaGraphConditionalHandle h = 0;
+};
+
 // One SQP pass (evaluation, constraint residual, KKT step) of the B instances of P.  host_style: clear the
-// running count before the step (the loop kernel of the solve graph does it otherwise).
+// running count before the step (the step's loop control in the solve graph does it otherwise).
 template <typename T>
-int run_pass(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist, bool host_style) {
+int run_pass(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool persist, bool host_style,
+             const LoopCtl& lc = LoopCtl{}) {
     int rc = launch_eval<T>(ctx, P, B, st, persist, host_style, true);
     if (rc) return rc;
     if (host_style) CK(cudaMemsetAsync(P.active, 0, sizeof(int), st));
     const int k = tstart(ctx, 2, st);
-    k_kkt<<<B, KKT_THREADS, ctx->kkt_smem, st>>>(P, B);
+    k_kkt<<<B, KKT_THREADS, ctx->kkt_smem, st>>>(P, B, lc.on, lc.p0, lc.max_passes, lc.h);
     CK(cudaGetLastError());
     tstop(ctx, k, st);
     ctx->tm.step_launches++;
@@ -2008,6 +2031,7 @@ ProbDev group_view(const ProbDev& P, int b0, int c, size_t tsize) {
     Q.active = P.active + c;
     Q.pass = P.pass + c;
     Q.ctr = P.ctr + (size_t)c * MAX_CLASSES;
+    Q.arrive = P.arrive + c;
     return Q;
 }
 
@@ -2066,7 +2090,6 @@ void fold_pending(ddnm_ctx* ctx) {
     ctx->tm.eval_launches += passes * ctx->pending_classes;   // with the D_i GEMM when it is used
     ctx->tm.constraint_launches += passes;
     ctx->tm.step_launches += passes;           // k_kkt
-    ctx->tm.other_launches += passes;          // the loop kernel
 }
 
 int resolved_dgemm(const ddnm_ctx* ctx) { return ctx->tune.d_gemm < 0 ? ctx->dgemm_auto : ctx->tune.d_gemm; }
@@ -2083,7 +2106,10 @@ int n_groups(const ddnm_ctx* ctx, int B) { return std::max(1, std::min(ctx->tune
 
 // Capture the solve of B instances (Bw with the warm-start shadow copies) as one graph:
 //   clear the control area -> k_init -> [warm start: two screening passes over Bw, k_ws_select]
-//   -> per instance group, a conditional while node whose body is one pass + k_loop.
+//   -> per instance group, a conditional while node whose body is PASSES_PER_BODY passes (each KKT step ends
+//      its pass with the loop control; the last one decides whether the loop goes on).  A body's later
+//      passes after the group has finished launch kernels that find no running instance and return: one
+//      loop turn (the conditional node's relaunch) per PASSES_PER_BODY passes instead of per pass.
 template <typename T>
 int build_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool has_x0, bool has_lam0,
                 int max_passes) {
@@ -2153,11 +2179,15 @@ int build_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool ha
         e = cudaStreamBeginCaptureToGraph(cb, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamBeginCaptureToGraph(body)"));
-        const int rc = run_pass<T>(ctx, Q, b1 - b0, cb, persist, false);
-        if (rc) return abort_capture(rc);
-        k_loop<<<1, 1, 0, cb>>>(Q.active, Q.pass, Q.ctr, p0, max_passes, h);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "capture: loop kernel"));
+        for (int u = 0; u < PASSES_PER_BODY; ++u) {
+            LoopCtl lc;
+            lc.on = u + 1 < PASSES_PER_BODY ? 1 : 2;
+            lc.p0 = p0;
+            lc.max_passes = max_passes;
+            lc.h = h;
+            const int rc = run_pass<T>(ctx, Q, b1 - b0, cb, persist, false, lc);
+            if (rc) return abort_capture(rc);
+        }
         cudaGraph_t body = nullptr;
         e = cudaStreamEndCapture(cb, &body);
         if (e != cudaSuccess) return abort_capture(cfail(ctx, e, "cudaStreamEndCapture(body)"));

@@ -114,7 +114,8 @@ def test_graph_with_warm_start_and_starts():
 
 def test_launch_counts_of_graph_solve():
     """The graph's loop passes are read back: per pass and instance group one launch per width class,
-    then the constraint (with the block factorisations), KKT-step and loop-control kernels."""
+    then the constraint (with the block factorisations) and KKT-step kernels (the step ends the pass with the
+    loop control)."""
     wl, s = solver("c3", MIXED)
     mu = inputs.mu_batch(6, seed=3)
     s.options(tol=0.0, max_iter=2)
