@@ -338,7 +338,7 @@ int ddnm_ws_load(ddnm_ctx* ctx, const char* path);
  * Per-kernel timing (ddnm_timing_enable) runs the host-driven loop instead. */
 typedef struct ddnm_tune {
     int graph;          /* 1: graph-resident loop (default); 0: host-driven passes */
-    int chains;         /* instance groups iterating concurrently, 1..16 (capped at B) */
+    int chains;         /* instance groups iterating concurrently, 1..64 (capped at B) */
     int con_split;      /* constraint rows per constraint CTA: 512, 1024 or 2048 */
     int eval_persist;   /* persistent evaluation: CTAs per SM per width class (1..8), or 0 for one CTA per item */
     int d_gemm;         /* D_i = C A_i dg_i^G: 1 in one GEMM launch per pass over all instances of a subdomain
@@ -359,7 +359,7 @@ int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t);
  *  - Each candidate gets one untimed solve, then `reps` solves timed with CUDA
  *    events on `stream`; the median decides.
  *  - The search is coordinate-wise:
- *      chains       in {1, 2, 4, 8, 16}, capped at B;
+ *      chains       in {1, 2, 4, 8, 16, 32, 64}, capped at B;
  *      eval_persist in {0, 1, 2, 4};
  *      con_split    in {512, 1024, 2048};
  *      d_gemm       in {0, 1};

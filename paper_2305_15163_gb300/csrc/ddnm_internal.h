@@ -19,7 +19,7 @@ constexpr int CON_THREADS = 256;
 constexpr int CON_SPLIT = 512; // default constraint rows per constraint CTA (the N_A axis is split)
 constexpr int CON_BLOCK = 512;  // constraint rows of one canonical partial of Atil (fixes the summation order)
 constexpr int MIN_CON_SPLIT = CON_BLOCK, MAX_CON_SPLIT = 4 * CON_BLOCK;
-constexpr int MAX_CHAINS = 16; // instance groups iterating concurrently inside the solve graph
+constexpr int MAX_CHAINS = 64; // instance groups iterating concurrently inside the solve graph
 constexpr int PASSES_PER_BODY = 2;   // SQP passes per turn of an instance group's device-side loop
 constexpr int MAX_CLASSES = 12; // width classes (RO, RG) of the evaluation kernel
 constexpr int HR_CHUNK = 128;  // largest collocation rows per evaluation chunk (the set-up may choose fewer)

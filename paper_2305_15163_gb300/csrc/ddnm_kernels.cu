@@ -2466,7 +2466,7 @@ extern "C" int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t) {
     if (t->graph < 0 || t->graph > 1 || t->chains < 1 || t->chains > MAX_CHAINS || !pow2 ||
         t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8 ||
         t->d_gemm < -1 || t->d_gemm > 1 || t->eval_groups < 0 || t->eval_groups > 1)
-        return ddnm_fail(ctx, DDNM_E_INVALID, "tune: graph 0/1, chains 1..16, con_split 512, 1024 or 2048, "
+        return ddnm_fail(ctx, DDNM_E_INVALID, "tune: graph 0/1, chains 1..64, con_split 512, 1024 or 2048, "
                                               "eval_persist 0..8, d_gemm -1..1, eval_groups 0/1");
     ctx->tune = *t;
     return DDNM_OK;
@@ -2538,7 +2538,7 @@ extern "C" int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kin
         }
         return DDNM_OK;
     };
-    if ((rc = sweep(&ddnm_tune::chains, {1, 2, 4, 8, 16}))) return finish(rc);
+    if ((rc = sweep(&ddnm_tune::chains, {1, 2, 4, 8, 16, 32, 64}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::eval_persist, {0, 1, 2, 4}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::con_split, {512, 1024, 2048}))) return finish(rc);
     if (cur.d_gemm < 0) cur.d_gemm = ctx->dgemm_auto;

@@ -95,15 +95,15 @@ def test_launch_plan_validation():
     s = lib.Solver(wl)
     assert lib.ddnm_get_tune(s.ctx) == {"graph": 1, "chains": 1, "con_split": 512, "eval_persist": 0, "d_gemm": -1,
                                         "eval_groups": 1}
-    lib.ddnm_set_tune(s.ctx, graph=0, chains=16, con_split=2048, eval_persist=8, d_gemm=1, eval_groups=0)
-    assert lib.ddnm_get_tune(s.ctx) == {"graph": 0, "chains": 16, "con_split": 2048, "eval_persist": 8, "d_gemm": 1,
+    lib.ddnm_set_tune(s.ctx, graph=0, chains=64, con_split=2048, eval_persist=8, d_gemm=1, eval_groups=0)
+    assert lib.ddnm_get_tune(s.ctx) == {"graph": 0, "chains": 64, "con_split": 2048, "eval_persist": 8, "d_gemm": 1,
                                         "eval_groups": 0}
     good = dict(graph=1, chains=2, con_split=1024, eval_persist=1, d_gemm=0, eval_groups=0)
-    for bad in (dict(graph=2), dict(graph=-1), dict(chains=0), dict(chains=17), dict(con_split=256),
+    for bad in (dict(graph=2), dict(graph=-1), dict(chains=0), dict(chains=65), dict(con_split=256),
                 dict(con_split=768), dict(con_split=4096), dict(eval_persist=-1), dict(eval_persist=9),
                 dict(d_gemm=2), dict(d_gemm=-2), dict(eval_groups=2), dict(eval_groups=-1)):
         with pytest.raises(lib.DDNMError) as e:
             lib.ddnm_set_tune(s.ctx, **{**good, **bad})
         assert e.value.code == lib.DDNM_E_INVALID
-    assert lib.ddnm_get_tune(s.ctx)["chains"] == 16      # a rejected plan leaves the old one
+    assert lib.ddnm_get_tune(s.ctx)["chains"] == 64      # a rejected plan leaves the old one
     s.close()

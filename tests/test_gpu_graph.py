@@ -22,6 +22,7 @@ HOST = dict(graph=0, chains=1, con_split=512, eval_persist=0, eval_groups=1)
 PLANS = [dict(graph=1, chains=1, con_split=512, eval_persist=0),
          dict(graph=1, chains=3, con_split=1024, eval_persist=2, eval_groups=0),
          dict(graph=1, chains=16, con_split=2048, eval_persist=1),
+         dict(graph=1, chains=64, con_split=512, eval_persist=0),
          dict(graph=1, chains=4, con_split=512, eval_persist=4, eval_groups=0),
          dict(graph=0, chains=1, con_split=2048, eval_persist=3),
          dict(graph=0, chains=1, con_split=512, eval_persist=0, eval_groups=0)]
