@@ -265,6 +265,7 @@ def run_warmstart(args, lib, torch, name="c2", n_train=4096, n_test=1024, epochs
     mu_te = inputs.mu_batch(n_test, seed=2002)
 
     def timed(solver, mu):
+        solve_all(solver, mu[:B])          # untimed: captures the solve graph for these options and this start
         torch.cuda.synchronize()
         t = time.perf_counter()
         _, st = solve_all(solver, mu)

@@ -1180,9 +1180,27 @@ __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
     __shared__ int s_blk[SPC];
     __shared__ unsigned char s_nO[SPC], s_nG[SPC], s_fl[SPC];
     __shared__ unsigned short tri[MAX_TRI];                     // (row << 8 | column) of triangle entry e
+    __shared__ int s_skip;
     const int i0 = f * SPC, tid = threadIdx.x, w = tid >> 5;
     if (i0 >= P.n_sub) return;
     const int nrel = min(SPC, P.n_sub - i0);
+    // A trial the step kernel is bound to reject needs no factors: phi^2 = ||F||^2 >= sum_i ||rho_i||^2, so
+    // when the subdomain residuals alone exceed the Armijo bound (with a relative margin of 1e-12 for the
+    // order of summation) the trial fails; so does the start-up pass, which only forms the multiplier.
+    if (w == 0) {
+        const int* ist = P.ist + (size_t)b * INST_INTS;
+        const double* dst = P.dst + (size_t)b * INST_DBLS;
+        const int mode = ist[I_MODE], nbt = ist[I_NBT];
+        const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
+        const double* hdr = P.blk + (size_t)b * P.blk_stride;   // the merits ||rho_i||^2, subdomain i at index i
+        double sphi = 0.0;
+        for (int i = tid; i < P.n_sub; i += 32) sphi += hdr[i];
+        sphi = warp_sum(sphi);
+        if (tid == 0)
+            s_skip = mode == MODE_INIT0 ||
+                     (mode == MODE_LS && nbt < P.max_bt &&
+                      sphi > (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0 * (1.0 + 1e-12));
+    }
     for (int e = tid; e < MAX_TRI; e += blockDim.x) {
         int a, c;
         tri_index(e, a, c);
@@ -1195,6 +1213,7 @@ __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
         s_nG[tid] = (unsigned char)S.nG;
     }
     __syncthreads();
+    if (s_skip) return;
     double* blk = P.blk + (size_t)b * P.blk_stride;
     if (w < FAC_WARPS && 2 * w < nrel)
         factor_group<16>(P, blk, s_blk, s_nO, s_nG, 2 * w, nrel, scr + (size_t)w * 2 * P.fac_stride, P.fac_stride,
