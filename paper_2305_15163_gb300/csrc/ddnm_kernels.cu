@@ -1437,7 +1437,9 @@ __device__ __forceinline__ void kkt_body(const ProbDev& P, int B) {
     __shared__ int s_dec;
 
     // ---- 1 and 3: judge the trial point (the last KKT_DW warps) while the others add up the Schur sums of step 3
-    // from the shares k_constraint left (sums formed beside a rejected trial or a stop are simply not used)
+    // from the shares k_constraint left (sums formed beside a rejected trial or a stop are simply not used).  A
+    // border too wide for the shares is summed here from the blocks, after the judgement: only at an accepted
+    // point, for those sums are the bulk of the step's FP64 work.
     {
         const int nst = nth - 32 * KKT_DW;                   // threads of the Schur sums
         if (tid < nst) {
@@ -1464,9 +1466,6 @@ __device__ __forceinline__ void kkt_body(const ProbDev& P, int B) {
                         us[e - ntri] = v;
                     }
                 }
-            } else {         // a border too wide for the factorisation CTAs' staging: summed here
-                range_sync(2, nst);
-                kkt_schur_sums(P, blk, s_blk, s_nO, s_nG, s_fl, Sm, us, work, tid, nst, 2);
             }
         } else {
             const int dec = kkt_decide(P, b, blk, At, scratch, tid - nst, 32 * KKT_DW, 1, true);
@@ -1513,6 +1512,7 @@ __device__ __forceinline__ void kkt_body(const ProbDev& P, int B) {
         }
         return;
     }
+    if (!P.Spart) kkt_schur_sums(P, blk, s_blk, s_nO, s_nG, s_fl, Sm, us, work, tid, nth, 0);
     if (w == 0) {                // flags: a vote first, the scan only when some block is not PD
         int bad = 0;
         for (int i = lane; i < ns; i += 32) bad |= s_fl[i];
