@@ -931,20 +931,20 @@ __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr);
 
 // Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
 // Atil_c += sum_r C[c][r] jump_r, one warp per row c of C; partials per (instance, slice).  The rows c of C
-// are split over gridDim.z - nfz CTAs (the same sums, more SMs, when the batch alone gives too few CTAs).
-// In the same launch, the last nfz z-indices factor the Gauss-Newton blocks of the evaluated point for the
-// step kernel (factor_cta), so that the two run side by side.
+// are split over nrg CTAs (the same sums, more SMs, when the batch alone gives too few CTAs).  CTA (x, b):
+// x < n_split nrg takes slice x % n_split, row group x / n_split; the CTAs after them factor the
+// Gauss-Newton blocks of the evaluated point for the step kernel (factor_cta), side by side in one launch.
 template <typename T>
-__global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B, int nfz) {
+__global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B, int nrg) {
     extern __shared__ double jump[];      // con_split doubles (or the factorisation scratch)
-    const int sp = blockIdx.x, b = blockIdx.y;
+    const int b = blockIdx.y, xi = blockIdx.x, ncon = P.n_split * nrg;
     if (b >= B) return;
     if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
-    const int nrg = (int)gridDim.z - nfz;
-    if ((int)blockIdx.z >= nrg) {
-        factor_cta(P, b, ((int)blockIdx.z - nrg) * (int)gridDim.x + sp, jump);
+    if (xi >= ncon) {
+        factor_cta(P, b, xi - ncon, jump);
         return;
     }
+    const int sp = xi % P.n_split, rg = xi / P.n_split;
     const int r0 = sp * P.con_split, nr = min(P.con_split, P.N_A - r0);
     const T* g = (const T*)P.gG + (size_t)b * P.sum_NG;
     for (int r = threadIdx.x; r < nr; r += blockDim.x)
@@ -959,8 +959,8 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B, in
     const int nb = P.con_split / CON_BLOCK;
     double* out = P.Atil + ((size_t)b * P.n_split + sp) * P.n_C;
     const int rpg = (P.n_C + nrg - 1) / nrg;
-    const int c1 = min(P.n_C, ((int)blockIdx.z + 1) * rpg);
-    for (int c = (int)blockIdx.z * rpg + w; c < c1; c += nw) {
+    const int c1 = min(P.n_C, (rg + 1) * rpg);
+    for (int c = rg * rpg + w; c < c1; c += nw) {
         const double* Cr = P.C + (size_t)c * P.N_A + r0;
         for (int k = 0; k < nb; ++k) {
             const int hi = min(nr, (k + 1) * CON_BLOCK);
@@ -1990,11 +1990,11 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
     {
         // with the factorisation CTAs of the step (8 subdomains each) when the pass goes on to a KKT step
         const int nfc = factor ? (P.n_sub + 2 * FAC_WARPS - 1) / (2 * FAC_WARPS) : 0;
-        const int nfz = (nfc + P.n_split - 1) / P.n_split;
+        const int nrg = con_row_groups(ctx, P, B);
         const size_t smem = std::max((size_t)P.con_split * 8, nfc ? (size_t)ctx->fac_smem : 0);
         if (smem > (size_t)std::max(MAX_CON_SPLIT * 8, ctx->fac_smem))     // beyond what set_smem_attrs allowed
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "constraint launch: shared memory above its limit");
-        k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B) + nfz), CON_THREADS, smem, st>>>(P, B, nfz);
+        k_constraint<T><<<dim3(P.n_split * nrg + nfc, B), CON_THREADS, smem, st>>>(P, B, nrg);
     }
     CK(cudaGetLastError());
     tstop(ctx, k, st);
@@ -2649,8 +2649,10 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
         e = launch_dgemm<T>(ctx, P, B, st);
         if (e != cudaSuccess) return cfail(ctx, e, "no-allocation D_i product launch");
     }
-    k_constraint<T><<<dim3(P.n_split, B, con_row_groups(ctx, P, B)), CON_THREADS, P.con_split * sizeof(double), st>>>(
-        P, B, 0);
+    {
+        const int nrg = con_row_groups(ctx, P, B);
+        k_constraint<T><<<dim3(P.n_split * nrg, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B, nrg);
+    }
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cfail(ctx, e, "no-allocation evaluation launch");
