@@ -21,7 +21,9 @@ def build(wl: inputs.Workload, act: str = "swish", denorm: bool = True, ell: boo
     dd = decompose(wl.nx, wl.ny, wl.xb, wl.yb)
     dec_o, dec_g = inputs.decoders_for(wl, [s.interior for s in dd.subs],
                                        [s.interface for s in dd.subs], act=act, denorm=denorm)
-    hr = inputs.hr_sets(wl)
+    hr = getattr(wl, "hr_override", None)      # explicit collocation rows of a test case, else the seeded draw
+    if hr is None:
+        hr = inputs.hr_sets(wl)
     C = inputs.test_matrix(wl.n_c(), dd.N_A, inputs.SEED_C + wl.seed_offset)
     if ell is None:
         ell = max(d["N"] * d["w"] for d in dec_o + dec_g) > 4_000_000

@@ -186,3 +186,23 @@ def test_batch_sizes_ragged():
     x7, l7, st7 = s.solve(mu)
     x1, l1, st1 = s.solve(mu[3:4])
     assert np.array_equal(x1[0], x7[3]) and np.array_equal(l1[0], l7[3])
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_gamma_singular_block_matches_oracle(prec):
+    """Subdomain 0 singular in its interface block (collocation rows that touch no interface state, see
+    tests/gamma_case.py): its factorisation stops after the Omega columns, the KKT step keeps its interface
+    steps as unknowns of the second Schur level, and 3 SQP iterations match the oracle's dense KKT solves."""
+    from gamma_case import gamma_singular_workload
+    wl = gamma_singular_workload()
+    fom, dd, rom, raw = setup.build(wl)
+    s = lib.Solver(wl, precision=prec)
+    s.load(raw["dec_o"], raw["dec_g"], raw["C"])
+    mu = inputs.mu_batch(3)
+    s.options(tol=0.0, max_iter=3)
+    x, lam, st = s.solve(mu)
+    for b in range(3):
+        ref = rom.solve(mu[b], tol=0.0, max_iter=3)
+        assert st[b]["status"] == lib.DDNM_MAX_ITER and st[b]["n_evals"] == ref.n_evals
+        assert rel(x[b], ref.x) < TOL[prec] and rel(lam[b], ref.lam) < TOL[prec]
+    s.close()

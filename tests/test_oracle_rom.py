@@ -283,3 +283,23 @@ def test_restricted_evaluation_matches_dense(name):
             assert np.allclose(e.H[i], a.H[i], rtol=1e-12, atol=1e-12)
             assert np.allclose(e.D[i], a.D[i], rtol=1e-12, atol=1e-12)
             assert np.allclose(e.r[i], a.r[i], rtol=1e-12, atol=1e-12)
+
+
+def test_gamma_singular_case_premise():
+    """The case of tests/gamma_case.py: subdomain 0's collocation rows touch no interface state, so R_0 has
+    zero interface columns and H_0 is singular in its Gamma block but PD on its Omega block; the KKT matrix of
+    Eq. (sqp_system) is still nonsingular (Lemma 1: H_i PD on null(E_i)), and the oracle's SQP runs."""
+    from gamma_case import gamma_singular_workload
+    wl = gamma_singular_workload()
+    fom, dd, rom, raw = setup.build(wl)
+    mu = inputs.mu_batch(1)[0]
+    ev = rom.evaluate(np.zeros(rom.n_D), np.zeros(rom.n_C), mu)
+    nO = rom.nO[0]
+    H0 = ev.H[0]
+    assert np.abs(ev.R[0][:, nO:]).max() == 0.0
+    assert np.abs(H0[nO:, :]).max() == 0.0 and np.abs(H0[:, nO:]).max() == 0.0
+    assert np.linalg.eigvalsh(H0[:nO, :nO]).min() > 0.0
+    K = rom.kkt_matrix(ev)
+    assert np.linalg.cond(K) < 1e12
+    res = rom.solve(mu, tol=0.0, max_iter=3)
+    assert np.all(np.isfinite(res.x)) and np.all(np.isfinite(res.lam)) and res.iters == 3
