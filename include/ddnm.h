@@ -323,17 +323,19 @@ int ddnm_ws_load(ddnm_ctx* ctx, const char* path);
  * graph launch.  The graph runs the start-up passes of Sec. 4.1 / 7.2 (and the
  * warm-start screening), then splits the batch into `chains` groups of
  * consecutive instances.  Each group iterates in its own device-side while
- * loop, a conditional graph node.  The loop stops when every instance of the
- * group has finished, and at the latest after 3 + max_iter * (max_backtracks
- * + 1) passes.  One group's small FP64 KKT kernels then overlap another
- * group's evaluation.
+ * loop, a conditional graph node whose body is two passes; the KKT kernel's
+ * last CTA counts each pass and ends the loop when every instance of the
+ * group has finished, or at the latest after 3 + max_iter * (max_backtracks
+ * + 1) passes (a guard the per-instance limits reach first; a body's second
+ * pass after the end finds no running instance).  One group's small FP64
+ * kernels then overlap another group's evaluation.
  * Inside a pass, each width class of subdomains (equal padded latent widths) is
  * one evaluation launch.  With eval_persist > 0 that launch is persistent:
  * eval_persist CTAs per SM claim (instance, subdomain) items from a device
  * counter, largest subdomains first.
- * Results do not depend on the plan, bit for bit: instances are independent, and every kernel sums in
- * a fixed order.  Atil in particular is one pairwise tree over 512-row blocks of the constraint rows,
- * whatever con_split is.  The graph is captured on first use and
+ * Results do not depend on the plan, bit for bit, apart from d_gemm (a different summation order of D_i):
+ * instances are independent, and every kernel sums in a fixed order.  Atil in particular is one pairwise
+ * tree over 512-row blocks of the constraint rows, whatever con_split is.  The graph is captured on first use and
  * re-captured when B, the options, the plan or the device tables change.
  * Per-kernel timing (ddnm_timing_enable) runs the host-driven loop instead. */
 typedef struct ddnm_tune {

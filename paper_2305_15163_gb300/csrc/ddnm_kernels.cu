@@ -1,18 +1,19 @@
 // sm_103a kernels of the batched Lagrange-Gauss-Newton SQP (Sec. 4.1) for the WFPC
 // DD-LSPG-ROM with collocation HR (Sec. 3.1, 5.3) on steady 2D Burgers (Sec. 7.1).
 //
-// One SQP "pass" over the batch is three launches:
-//   k_eval<T>       one CTA per (instance, subdomain): HR subnets of both decoders
-//                   (Eq. subnet) with Jacobians, the collocated Burgers residual and its
-//                   stencil partials (Eq. burgers_discretized), the chain rule
-//                   R_i = dr/dx dg/dxh (Eq. gauss_newton_hessian b), H_i = R_i^T R_i,
-//                   R_i^T r_i, D_i = C A_i dg^G/dxh, rho_i (Eq. optimality_residuals_GN),
-//                   and the subdomain's share of the Schur complement of the
-//                   block-arrowhead KKT matrix Eq. (sqp_system) in FP64.
-//   k_constraint<T> one CTA per (instance, row of C): Atil = C (sum_i A_i g_i^G) in FP64.
-//   k_step          one CTA per instance: merit ||F||_2, Armijo backtracking (Sec. 4.1),
-//                   least-squares multiplier start (Sec. 7.2), FP64 Schur solve of the KKT
-//                   system and the update Eq. (sqp_update).
+// One SQP "pass" over the batch (or over one instance group of it inside the solve graph) is:
+//   k_eval<T, RO, RG>  one CTA per (instance, subdomain), one launch per width class: the trial point,
+//                      HR subnets of both decoders (Eq. subnet) with Jacobians, the collocated Burgers
+//                      residual and its stencil partials (Eq. burgers_discretized), the chain rule
+//                      R_i = dr/dx dg/dxh (Eq. gauss_newton_hessian b), H_i = R_i^T R_i, R_i^T r_i,
+//                      D_i = C A_i dg^G/dxh, rho_i and ||rho_i||^2 (Eq. optimality_residuals_GN).
+//   [k_dgemm<T>]       D_i batched over the instances that share a subdomain's decoder.
+//   k_constraint<T>    Atil = C (sum_i A_i g_i^G) in FP64 over slices of the constraint rows, and in CTAs
+//                      of its own the FP64 L D L^T of every block H_i with the Schur-sum shares.
+//   k_kkt              one CTA per instance: merit ||F||_2, Armijo backtracking (Sec. 4.1),
+//                      least-squares multiplier start (Sec. 7.2), the border of the Schur complement of
+//                      Eq. (sqp_system), its FP64 solve and the update Eq. (sqp_update); in the solve graph
+//                      its last CTA also runs the instance group's loop control.
 // T is float (MIXED) or double (FP64).
 #include <cuda_runtime.h>
 
