@@ -35,7 +35,7 @@ SEED_GRID, SEED_HR, SEED_C, SEED_DEC, SEED_MU, SEED_MLP = 0, 1, 2, 3, 4, 5
 MU_LO, MU_HI = 0.9, 1.1
 
 # stream tags, so that each draw has its own independent generator
-_TAG = {"grid": 11, "hr": 12, "C": 13, "dec": 14, "mu": 15, "mlp": 16, "lat": 17}
+_TAG = {"grid": 11, "hr": 12, "C": 13, "dec": 14, "mu": 15, "mlp": 16, "lat": 17, "enc": 18, "ae": 19}
 
 
 def rng(kind: str, *key: int) -> np.random.Generator:
@@ -258,6 +258,51 @@ def decoders_for(wl: Workload, interior_ids: list, interface_ids: list, act: str
             out.append(decoder(len(ids), wl.width[i], n_lat, wl.band, (wl.seed_offset, i, kind),
                                off, sc, act=act))
     return dec_o, dec_g
+
+
+def transposed_mask(cols: np.ndarray, width: int) -> np.ndarray:
+    """The decoder output mask (ELL column ids per output row, -1 padding) transposed: per hidden unit, the
+    output rows whose mask holds it, ascending, as ELL (width x Kt, -1 padding).  The encoder input layer uses
+    this mask (Sec. 5.1: the encoder is symmetric to the decoder across the latent layer).  Index bookkeeping
+    only."""
+    cols = np.asarray(cols)
+    r, k = np.nonzero(cols >= 0)
+    j = cols[r, k].astype(np.int64)
+    order = np.lexsort((r, j))
+    j, r = j[order], r[order]
+    counts = np.bincount(j, minlength=width)
+    Kt = max(int(counts.max()) if counts.size else 0, 1)
+    out = np.full((width, Kt), -1, dtype=np.int32)
+    start = np.concatenate([[0], np.cumsum(counts)])
+    pos = np.arange(j.size) - start[j]
+    out[j, pos] = r
+    return out
+
+
+def encoder(n_in: int, width: int, n_lat: int, cols_t: np.ndarray, key: tuple, seed: int = SEED_DEC) -> dict:
+    """Random-init sparse-masked shallow encoder h(x) = W2 sigma(W1 x + b1) (Sec. 5.1, Eq.
+    autoencoder_architecture a/c) on the transposed decoder mask ``cols_t`` (width x Kt, -1 padding).
+    W1 values ~ N(0, 1/nnz_row), b1 = 0, W2 (n_lat x width) ~ N(0, 1/width)."""
+    r = rng("enc", seed, *key)
+    nnz = (cols_t >= 0).sum(axis=1)
+    vals = r.standard_normal(cols_t.shape) / np.sqrt(np.maximum(nnz, 1))[:, None]
+    vals[cols_t < 0] = 0.0
+    W2 = r.standard_normal((n_lat, width)) / math.sqrt(width)
+    return dict(N=n_in, w=width, n=n_lat, cols=np.asarray(cols_t, dtype=np.int32), vals=vals, b1=np.zeros(width),
+                W2=W2)
+
+
+def snapshot_mu(n_side: int) -> np.ndarray:
+    """Training parameters: an n_side x n_side uniform grid of mu over [0.9, 1.1]^2 (Sec. 7.2 samples its
+    training snapshots on a uniform (a, lambda) grid), shape (n_side^2, 2), a slowest."""
+    g = np.linspace(MU_LO, MU_HI, n_side)
+    return np.array([(a, l) for a in g for l in g])
+
+
+def ae_order(n: int, epochs: int, seed: int = SEED_DEC) -> np.ndarray:
+    """Sample order of each autoencoder training epoch (epochs x n, int32): one permutation per epoch."""
+    r = rng("ae", seed, n, epochs)
+    return np.stack([r.permutation(n) for _ in range(epochs)]).astype(np.int32)
 
 
 def hr_sets(wl: Workload) -> list[np.ndarray]:

@@ -4,8 +4,11 @@ Test infrastructure only (see ``oracle/__init__``).
 """
 from __future__ import annotations
 
+import numpy as np
+
 import inputs
 
+from .autoencoder import MaskedAutoencoder
 from .burgers import Burgers
 from .dd import decompose
 from .decoders import EllDecoder, MaskedDecoder
@@ -30,4 +33,45 @@ def build(wl: inputs.Workload, act: str = "swish", denorm: bool = True, ell: boo
     Dec = EllDecoder if ell else MaskedDecoder
     rom = DDROM(fom, dd, [Dec(d) for d in dec_o], [Dec(d) for d in dec_g], hr, C)
     raw = dict(dec_o=dec_o, dec_g=dec_g, hr=hr, C=C)
+    return fom, dd, rom, raw
+
+
+def snapshots(fom: Burgers, mus):
+    """FOM solutions at the parameters mus (n x 2), one per row (Sec. 7.2: monolithic solves, restricted to
+    the subdomain states afterwards); Newton from the exact solution sampled at the nodes."""
+    return np.array([fom.newton(m, x0=fom.exact_state(m))[0] for m in np.asarray(mus).reshape(-1, 2)])
+
+
+def train_autoencoders(wl: inputs.Workload, dd, X, epochs: int, batch: int = 32, lr: float = 1e-3,
+                       act: str = "swish"):
+    """Interior and interface autoencoders of every subdomain trained on the FOM snapshots X (n_snap x N_x)
+    restricted to each subdomain's interior / interface states (Sec. 7.2-7.3), from the seeded initial
+    weights.  Returns (autoencoders, decoder specs interior, decoder specs interface)."""
+    aes, dec_o, dec_g = [], [], []
+    order = inputs.ae_order(X.shape[0], epochs)
+    for i, sd in enumerate(dd.subs):
+        for kind, ids, n_lat, out in ((0, sd.interior, wl.n_omega[i], dec_o), (1, sd.interface, wl.n_gamma[i], dec_g)):
+            dec = inputs.decoder(len(ids), wl.width[i], n_lat, wl.band, (wl.seed_offset, i, kind), act=act)
+            enc = inputs.encoder(len(ids), wl.width[i], n_lat, inputs.transposed_mask(dec["cols"], wl.width[i]),
+                                 (wl.seed_offset, i, kind))
+            ae = MaskedAutoencoder(enc, dec, act)
+            ae.losses = ae.train(X[:, ids], epochs, batch, lr, order)
+            aes.append(ae)
+            out.append(ae.decoder_spec())
+    return aes, dec_o, dec_g
+
+
+def build_trained(wl: inputs.Workload, n_side: int = 8, epochs: int = 300, batch: int = 32, lr: float = 1e-3):
+    """(fom, dd, rom, raw) like build(), with decoders trained on FOM snapshots at an n_side x n_side grid of
+    mu instead of the random-init decoders."""
+    fom = Burgers(wl.nx, wl.ny, wl.nu)
+    dd = decompose(wl.nx, wl.ny, wl.xb, wl.yb)
+    X = snapshots(fom, inputs.snapshot_mu(n_side))
+    aes, dec_o, dec_g = train_autoencoders(wl, dd, X, epochs, batch, lr)
+    hr = getattr(wl, "hr_override", None)
+    if hr is None:
+        hr = inputs.hr_sets(wl)
+    C = inputs.test_matrix(wl.n_c(), dd.N_A, inputs.SEED_C + wl.seed_offset)
+    rom = DDROM(fom, dd, [MaskedDecoder(d) for d in dec_o], [MaskedDecoder(d) for d in dec_g], hr, C)
+    raw = dict(dec_o=dec_o, dec_g=dec_g, hr=hr, C=C, snapshots=X, autoencoders=aes)
     return fom, dd, rom, raw
