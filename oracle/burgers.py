@@ -149,7 +149,10 @@ class Burgers:
     # -- monolithic FOM solve ------------------------------------------------------------
     def newton(self, mu, x0=None, rtol=1e-12, max_iter=50):
         """Newton on r(x; mu) = 0 from x0 (default 0), sparse LU; stops at
-        ||r|| <= rtol * max(1, ||r(x0)||).  Returns (x, residual history)."""
+        ||r|| <= rtol * max(1, ||r(x0)||), or once a step fails to halve ||r||: in Newton's quadratic regime
+        that happens only at the rounding floor of the residual (a start close to the solution, e.g. the
+        exact solution at the nodes, can begin below rtol * max(1, ||r(x0)||) of nothing but that floor).
+        Returns (x, residual history)."""
         bvec = self.boundary_vectors(mu)
         x = np.zeros(2 * self.N) if x0 is None else np.array(x0, dtype=np.float64)
         r = self.residual(x, mu, bvec)
@@ -162,6 +165,8 @@ class Burgers:
             x = x + dx
             r = self.residual(x, mu, bvec)
             hist.append(np.linalg.norm(r))
+            if hist[-1] > 0.5 * hist[-2]:
+                break
         return x, hist
 
     def exact_state(self, mu):
