@@ -268,7 +268,14 @@ int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, cons
  *    first, else DDNM_E_STATE.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept per device and CUDA
+ *    context: after the application resets the device (cudaDeviceReset), the
+ *    next call is again a first call and looks it up anew.
+ *  - mu, x, lam and F_out must be device (or managed) memory of ctx's device;
+ *    any other pointer returns DDNM_E_INVALID before anything is queued
+ *    (checked with cudaPointerGetAttributes, which allocates nothing).  The
+ *    sizes of the arrays cannot be checked here: they must hold the counts
+ *    stated above.
  *  - B beyond what fits in 16 MiB (about 210 instances of the 128x128 4x4
  *    workload) returns DDNM_E_UNSUPPORTED with the limit in the message.
  *  - All calls share the array and it keeps the last call's contents; calls
@@ -374,6 +381,91 @@ int ddnm_get_tune(const ddnm_ctx* ctx, ddnm_tune* t);
  * No result of a tuning solve is returned. */
 int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kind, void* stream, int max_iter, int reps,
                   ddnm_tune* best, float* best_ms);
+
+/* ---- Offline: training the autoencoders (Sec. 3.4, 5.1, 7.2-7.3) ----
+ * Every subdomain has two sparse-masked shallow autoencoders, one for its interior states and one for its
+ * interface states.  The decoder g (ddnm_decoder, loaded with ddnm_load_decoders) carries the three-band
+ * mask on W2; the encoder h(x) = W2 sigma(W1 x + b1) carries the transposed mask on W1 (the encoder is
+ * symmetric to the decoder across the latent layer, Sec. 5.1).  Training minimises the mean squared error
+ * of Eq. (autoencoder_AbsMSE_loss) on snapshots normalised onto [-1, 1] (Sec. 7.3) by mini-batch Adam
+ * (beta 0.9 / 0.999, eps 1e-8, constant learning rate), in FP32 with FP32 master weights.  On return the
+ * trained decoders, with the normalisation as their de-normalisation layer (offset, scale), replace the
+ * context's decoders: the next solve uses them. */
+typedef struct ddnm_encoder {
+    int N;                  /* inputs (must equal N_i^O or N_i^G) */
+    int w;                  /* width (hidden units; must equal the decoder's) */
+    int n;                  /* latent dim (must equal n_i^O or n_i^G; <= 16) */
+    int Kt;                 /* ELL slots per hidden unit of W1 */
+    const int* cols;        /* w x Kt: the inputs of each hidden unit, ascending, -1 padding at the end;
+                               must be the transpose of the decoder's mask */
+    const double* vals;     /* w x Kt */
+    const double* b1;       /* w */
+    const double* W2;       /* n x w */
+} ddnm_encoder;
+
+/* Initial encoder of subdomain `sub`, kind DDNM_DECODER_INTERIOR / _INTERFACE (host arrays, copied). */
+int ddnm_load_encoder(ddnm_ctx* ctx, int sub, int kind, const ddnm_encoder* e);
+
+/* Train all 2 n_sub autoencoders together on n_snap snapshots X (n_snap x N_x full FOM states, restricted
+ * here to each subdomain's interior / interface states), starting from the loaded decoders and encoders.
+ * The normalisation (offset = (max+min)/2, scale = (max-min)/2 per state, 1 for a constant state) is taken
+ * over X.  Each epoch visits the snapshots in the order order[epoch * n_snap ..] (NULL: 0..n_snap-1) in
+ * mini-batches of `batch` (1..32; the last batch of an epoch may be smaller).  losses (epochs x 2 n_sub,
+ * may be NULL; autoencoder 2 s + kind) receives each epoch's mean batch loss.  X in host or device memory
+ * (mem_kind); the snapshots are copied to the device for the call. */
+int ddnm_ae_train(ddnm_ctx* ctx, int n_snap, const double* X, int epochs, int batch, double lr, const int* order,
+                  double* losses, int mem_kind, void* stream);
+
+/* Loss and gradient of one batch of normalised inputs Xt (nb x N, host FP32, nb <= 32) for the autoencoder
+ * (sub, kind) at the loaded weights, without an update (for checking the gradient).  grad receives the
+ * flat FP32 parameter block of that autoencoder; ddnm_ae_layout gives its layout: offsets[0..5] of W1 of
+ * the encoder (w x Kt, ELL), b1 of the encoder, W2 of the encoder (n x w), W1 of the decoder (w x n), b1 of
+ * the decoder, the decoder's W2 (N x K, ELL), and offsets[6] = the block's length. */
+int ddnm_ae_loss_grad(ddnm_ctx* ctx, int sub, int kind, int nb, const float* Xt, float* grad, double* loss);
+int ddnm_ae_layout(const ddnm_ctx* ctx, int sub, int kind, long long* offsets);
+
+/* Current decoder (sub, kind): W1 (w x n), b1 (w), vals (N x K, in the loaded decoder's mask), scale and
+ * offset (N); any may be NULL. */
+int ddnm_get_decoder(const ddnm_ctx* ctx, int sub, int kind, double* W1, double* b1, double* vals, double* scale,
+                     double* offset);
+
+/* ---- Full-order model (Sec. 7.1) ----
+ * Batched solve of the steady 2D Burgers finite-difference system r(x; mu) = 0 of
+ * Eq. (burgers_discretized) on ctx's grid (the monolithic FOM; the paper's ROM errors,
+ * Eq. relative_error, and speed-ups are measured against it, and its solutions are the
+ * snapshots the decoders are trained on, Sec. 7.2).  Needs only ddnm_setup: no decoders.
+ *
+ * Newton's method; each step J dx = -r solved by BiCGSTAB in FP64, right-preconditioned by
+ * the exact inverse of the diffusion part nu (D_xx + D_yy) per component (a sine transform in x
+ * and tridiagonal solves in y, in FP32).  Newton stops when ||r||_2 <= 1e-12 max(1, ||r(x0)||_2),
+ * or after a step that fails to halve ||r||_2 (the rounding floor; that step is kept), or after
+ * max_newton steps; each linear solve stops at ||J dx + r||_2 <= 1e-10 ||r||_2 or after
+ * max_krylov iterations.
+ *   mu     B x 2
+ *   x0     B x N_x start, or NULL for the exact solution Eq. (burgers_pde_exact_solution)
+ *          sampled at the grid nodes
+ *   x_out  B x N_x solution (ordering as everywhere: [u; v], x-fastest)
+ *   stats  B entries (host memory), or NULL
+ * mem_kind as in ddnm_solve_batch for mu, x0 and x_out.  Device memory: about 92 N_x bytes per
+ * instance, allocated on first use and kept with ctx.  Returns DDNM_E_NOMEM if it does not fit. */
+typedef struct ddnm_fom_stats {
+    int newton_iters;       /* Newton steps taken */
+    int krylov_iters;       /* BiCGSTAB iterations, summed over the Newton steps */
+    int status;             /* 0 converged, 1 no convergence (stall above the rounding floor, or
+                               max_newton reached), 2 non-finite residual */
+    int pad;
+    double res0;            /* ||r(x0)||_2 */
+    double res;             /* ||r(x)||_2 at the returned state */
+} ddnm_fom_stats;
+
+int ddnm_fom_solve(ddnm_ctx* ctx, int B, const double* mu, const double* x0, double* x_out, ddnm_fom_stats* stats,
+                   int max_newton, int max_krylov, int mem_kind, void* stream);
+
+/* Measured FP32 and FP64 fused multiply-add throughput of ctx's device (TFLOP/s, 2 flops per FMA): a
+ * grid of 8 CTAs x 256 threads per SM, every thread running 8 independent FMA chains, timed with CUDA
+ * events (best of 3 after a warm-up launch).  The paper has no counterpart: it is the denominator of the
+ * FP32 / FP64 roofline fractions that the benchmark reports.  Takes about a quarter of a second. */
+int ddnm_measure_peaks(ddnm_ctx* ctx, double* fp32_tflops, double* fp64_tflops);
 
 /* Turn per-kernel timing on (resets the counters) or off.  While on, every
  * compute call synchronises its stream before returning. */

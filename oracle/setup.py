@@ -42,20 +42,29 @@ def snapshots(fom: Burgers, mus):
     return np.array([fom.newton(m, x0=fom.exact_state(m))[0] for m in np.asarray(mus).reshape(-1, 2)])
 
 
+def train_autoencoder(wl: inputs.Workload, i: int, kind: int, Xs, epochs: int, batch: int = 32, lr: float = 1e-3,
+                      act: str = "swish") -> MaskedAutoencoder:
+    """The interior (kind 0) or interface (kind 1) autoencoder of subdomain i, from its seeded initial weights,
+    trained on Xs (n_snap x N: the snapshots restricted to those states; Sec. 7.2-7.3).  The epoch losses
+    are kept in ``.losses``."""
+    n_lat = (wl.n_omega if kind == 0 else wl.n_gamma)[i]
+    dec = inputs.decoder(Xs.shape[1], wl.width[i], n_lat, wl.band, (wl.seed_offset, i, kind), act=act)
+    enc = inputs.encoder(Xs.shape[1], wl.width[i], n_lat, inputs.transposed_mask(dec["cols"], wl.width[i]),
+                         (wl.seed_offset, i, kind))
+    ae = MaskedAutoencoder(enc, dec, act)
+    ae.losses = ae.train(Xs, epochs, batch, lr, inputs.ae_order(Xs.shape[0], epochs))
+    return ae
+
+
 def train_autoencoders(wl: inputs.Workload, dd, X, epochs: int, batch: int = 32, lr: float = 1e-3,
                        act: str = "swish"):
     """Interior and interface autoencoders of every subdomain trained on the FOM snapshots X (n_snap x N_x)
     restricted to each subdomain's interior / interface states (Sec. 7.2-7.3), from the seeded initial
     weights.  Returns (autoencoders, decoder specs interior, decoder specs interface)."""
     aes, dec_o, dec_g = [], [], []
-    order = inputs.ae_order(X.shape[0], epochs)
     for i, sd in enumerate(dd.subs):
-        for kind, ids, n_lat, out in ((0, sd.interior, wl.n_omega[i], dec_o), (1, sd.interface, wl.n_gamma[i], dec_g)):
-            dec = inputs.decoder(len(ids), wl.width[i], n_lat, wl.band, (wl.seed_offset, i, kind), act=act)
-            enc = inputs.encoder(len(ids), wl.width[i], n_lat, inputs.transposed_mask(dec["cols"], wl.width[i]),
-                                 (wl.seed_offset, i, kind))
-            ae = MaskedAutoencoder(enc, dec, act)
-            ae.losses = ae.train(X[:, ids], epochs, batch, lr, order)
+        for kind, ids, out in ((0, sd.interior, dec_o), (1, sd.interface, dec_g)):
+            ae = train_autoencoder(wl, i, kind, X[:, ids], epochs, batch, lr, act)
             aes.append(ae)
             out.append(ae.decoder_spec())
     return aes, dec_o, dec_g

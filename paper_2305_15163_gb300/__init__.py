@@ -51,6 +51,11 @@ class ddnm_decoder(C.Structure):
                 ("W1", _dp), ("b1", _dp), ("cols", _ip), ("vals", _dp), ("scale", _dp), ("offset", _dp)]
 
 
+class ddnm_encoder(C.Structure):
+    _fields_ = [("N", C.c_int), ("w", C.c_int), ("n", C.c_int), ("Kt", C.c_int), ("cols", _ip), ("vals", _dp),
+                ("b1", _dp), ("W2", _dp)]
+
+
 class ddnm_sizes(C.Structure):
     _fields_ = [("n_sub", C.c_int), ("N_x", C.c_int), ("n_D", C.c_int), ("n_C", C.c_int),
                 ("N_A", C.c_int), ("sum_hr", C.c_int), ("sum_gamma", C.c_int)]
@@ -77,6 +82,9 @@ class ddnm_tune(C.Structure):
     _fields_ = [("graph", C.c_int), ("chains", C.c_int), ("con_split", C.c_int), ("eval_persist", C.c_int),
                 ("d_gemm", C.c_int), ("eval_groups", C.c_int)]
 
+
+FOM_STATS_DTYPE = np.dtype([("newton_iters", np.int32), ("krylov_iters", np.int32), ("status", np.int32),
+                            ("pad", np.int32), ("res0", np.float64), ("res", np.float64)])
 
 STATS_DTYPE = np.dtype([("iters", np.int32), ("status", np.int32), ("flags", np.int32),
                         ("n_evals", np.int32), ("merit", np.float64), ("alpha_last", np.float64)])
@@ -105,6 +113,13 @@ _sig = {
     "ddnm_ws_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_ws_save": (C.c_int, [_vp, C.c_char_p]),
     "ddnm_ws_load": (C.c_int, [_vp, C.c_char_p]),
+    "ddnm_load_encoder": (C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(ddnm_encoder)]),
+    "ddnm_ae_train": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.c_double, _vp, _vp, C.c_int, _vp]),
+    "ddnm_ae_loss_grad": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "ddnm_ae_layout": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    "ddnm_get_decoder": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "ddnm_fom_solve": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
+    "ddnm_measure_peaks": (C.c_int, [_vp, _dp, _dp]),
     "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
     "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
@@ -251,9 +266,94 @@ def ddnm_residual_noalloc(ctx, B, mu, x, lam, F_out):
     """F at (x, lam) with no device allocation; all arrays are torch CUDA tensors (device memory),
     queued on the current torch stream.  For callers that cannot allocate device memory; the
     tables must already be on the device (one allocating call on ctx first).  Calls that overlap
-    on the GPU race on the library's shared static scratch."""
+    on the GPU race on the library's shared static scratch.
+
+    The C call dereferences raw pointers whose sizes it cannot see, so the tensors are checked here:
+    float64, contiguous, on one CUDA device, with shapes (B, 2), (B, n_D), (B, n_C) and (B, n_D + n_C)."""
+    sz = ddnm_get_sizes(ctx)
+    want = {"mu": (mu, (B, 2)), "x": (x, (B, sz.n_D)), "F_out": (F_out, (B, sz.n_D + sz.n_C))}
+    if lam is not None:
+        want["lam"] = (lam, (B, sz.n_C))
+    devs = set()
+    for name, (t, shape) in want.items():
+        if isinstance(t, np.ndarray) or not hasattr(t, "is_cuda") or not t.is_cuda:
+            raise TypeError(f"ddnm_residual_noalloc: {name} must be a torch CUDA tensor (device memory)")
+        import torch
+        if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != shape:
+            raise ValueError(f"ddnm_residual_noalloc: {name} must be a contiguous float64 tensor of shape {shape}, "
+                             f"got {t.dtype} {tuple(t.shape)}{'' if t.is_contiguous() else ' (strided)'}")
+        devs.add(t.device)
+    if len(devs) != 1:
+        raise ValueError(f"ddnm_residual_noalloc: tensors on several devices {sorted(map(str, devs))}")
     _check(ctx, _lib.ddnm_residual_noalloc(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(F_out),
                                            _stream(DDNM_MEM_DEVICE)))
+
+
+def ddnm_load_encoder(ctx, sub, kind, spec: dict):
+    """spec: the encoder dict of ``inputs.encoder`` (N, w, n, cols (w x Kt), vals, b1, W2)."""
+    cols, vals = _i32(spec["cols"]), _f64(spec["vals"])
+    b1, W2 = _f64(spec["b1"]), _f64(spec["W2"])
+    e = ddnm_encoder(spec["N"], spec["w"], spec["n"], cols.shape[1], cols.ctypes.data_as(_ip), vals.ctypes.data_as(_dp),
+                     b1.ctypes.data_as(_dp), W2.ctypes.data_as(_dp))
+    _check(ctx, _lib.ddnm_load_encoder(ctx, sub, kind, C.byref(e)))
+
+
+def ddnm_ae_train(ctx, X, epochs, batch, lr, order=None):
+    """Train every subdomain's autoencoders on the snapshots X (n_snap x N_x; numpy host or torch CUDA
+    tensor); returns the epoch losses (epochs x 2 n_sub)."""
+    kind = _mem_kind(X)
+    if kind == DDNM_MEM_HOST:
+        X = _f64(X)
+    n_snap = int(X.shape[0])
+    o = None if order is None else _i32(order)
+    losses = np.zeros((max(epochs, 1), 2 * ddnm_get_sizes(ctx).n_sub))
+    _check(ctx, _lib.ddnm_ae_train(ctx, n_snap, _ptr(X), int(epochs), int(batch), float(lr),
+                                   None if o is None else o.ctypes.data, losses.ctypes.data, kind, _stream(kind)))
+    return losses[:epochs]
+
+
+def ddnm_ae_layout(ctx, sub, kind):
+    off = np.zeros(7, dtype=np.int64)
+    _check(ctx, _lib.ddnm_ae_layout(ctx, sub, kind, off.ctypes.data))
+    return off
+
+
+def ddnm_ae_loss_grad(ctx, sub, kind, Xt):
+    """(loss, flat FP32 gradient, layout offsets) of one batch of normalised inputs Xt (nb x N)."""
+    Xt = np.ascontiguousarray(np.asarray(Xt, dtype=np.float32))
+    loss = C.c_double()
+    _check(ctx, _lib.ddnm_ae_loss_grad(ctx, sub, kind, Xt.shape[0], Xt.ctypes.data, None, C.byref(loss)))
+    off = ddnm_ae_layout(ctx, sub, kind)
+    g = np.zeros(int(off[6]), dtype=np.float32)
+    _check(ctx, _lib.ddnm_ae_loss_grad(ctx, sub, kind, Xt.shape[0], Xt.ctypes.data, g.ctypes.data, C.byref(loss)))
+    return loss.value, g, off
+
+
+def ddnm_get_decoder(ctx, sub, kind, like: dict):
+    """The context's current decoder (sub, kind) as a decoder dict shaped like ``like`` (same N, w, n, mask)."""
+    W1, b1 = np.zeros_like(_f64(like["W1"])), np.zeros(like["w"])
+    vals = np.zeros(np.asarray(like["cols"]).shape)
+    sc, off = np.zeros(like["N"]), np.zeros(like["N"])
+    _check(ctx, _lib.ddnm_get_decoder(ctx, sub, kind, W1.ctypes.data, b1.ctypes.data, vals.ctypes.data, sc.ctypes.data,
+                                      off.ctypes.data))
+    return dict(like, W1=W1, b1=b1, vals=vals, scale=sc, offset=off)
+
+
+def ddnm_fom_solve(ctx, mu, x0=None, x_out=None, max_newton=20, max_krylov=400):
+    """Batched FOM solve (Newton, preconditioned BiCGSTAB) on ctx's grid.  mu (B x 2) numpy -> returns
+    (x (B x N_x), stats) in host memory; or torch CUDA tensors mu, x0, x_out (device memory, current
+    stream), returning (x_out, stats)."""
+    kind = _mem_kind(mu, x0, x_out)
+    B = int(mu.shape[0])
+    Nx = ddnm_get_sizes(ctx).N_x
+    if kind == DDNM_MEM_HOST:
+        mu = _f64(mu).reshape(B, 2)
+        x0 = None if x0 is None else _f64(x0).reshape(B, Nx)
+        x_out = np.zeros((B, Nx)) if x_out is None else x_out
+    st = np.zeros(B, dtype=FOM_STATS_DTYPE)
+    _check(ctx, _lib.ddnm_fom_solve(ctx, B, _ptr(mu), _ptr(x0), _ptr(x_out), st.ctypes.data, int(max_newton),
+                                    int(max_krylov), kind, _stream(kind)))
+    return x_out, st
 
 
 def mlp_param_count(n_in, H, n_out):
@@ -312,6 +412,13 @@ def ddnm_ws_save(ctx, path):
 
 def ddnm_ws_load(ctx, path):
     _check(ctx, _lib.ddnm_ws_load(ctx, os.fsencode(path)))
+
+
+def ddnm_measure_peaks(ctx):
+    """(FP32, FP64) FMA throughput of ctx's device in TFLOP/s, measured."""
+    a, b = C.c_double(), C.c_double()
+    _check(ctx, _lib.ddnm_measure_peaks(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def ddnm_timing_enable(ctx, on=True):

@@ -103,6 +103,9 @@ struct ddnm_ctx {
 
     WarmStart ws;
 
+    void* fom = nullptr;               // batched FOM solver workspace (ddnm_fom.cu)
+    void* ae = nullptr;                // autoencoder training state (ddnm_ae.cu)
+
     // per-kernel timing (ddnm_timing_enable)
     bool timing = false;
     ddnm_timing tm{};
@@ -134,4 +137,6 @@ int ddnm_reserve(ddnm_ctx* ctx, int B);
 void ddnm_release_events(ddnm_ctx* ctx);
 void ddnm_release_graph(ddnm_ctx* ctx);
 void ddnm_ws_release(ddnm_ctx* ctx);
+void ddnm_fom_release(ddnm_ctx* ctx);
+void ddnm_ae_release(ddnm_ctx* ctx);
 int ddnm_ws_predict_dev(ddnm_ctx* ctx, int B, const double* mu_dev, double* x0_dev, int* fell_back, cudaStream_t st);

@@ -253,6 +253,8 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     ddnm_release_graph(ctx);
     ddnm_release_events(ctx);
     ddnm_ws_release(ctx);
+    ddnm_fom_release(ctx);
+    ddnm_ae_release(ctx);
     delete ctx;
 }
 
@@ -813,6 +815,10 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.Spart = nullptr;            // set by ddnm_reserve when the shares are formed
     pd.con_split = CON_SPLIT;
     pd.n_split = (ctx->N_A + CON_SPLIT - 1) / CON_SPLIT;
+    // A block pivot at or below piv_eps times the block's largest diagonal entry is a rounding remainder of a
+    // direction the collocation rows do not see: the block is treated as singular there.  The scale is the
+    // relative rounding of H_i (FP64 sums, or FP32 sums in the mixed path) times a safety factor.
+    pd.piv_eps = ctx->precision == DDNM_FP64 ? 1e-11 : 1e-5;
     pd.hx = ctx->hx; pd.hy = ctx->hy; pd.nu = ctx->nu; pd.bx0 = ctx->box[0]; pd.by0 = ctx->box[2];
     pd.cst[0] = 0.5 / ctx->hx;
     pd.cst[1] = 0.5 / ctx->hy;

@@ -150,6 +150,7 @@ struct ProbDev {
     double cst[4];                 // stencil constants 1/(2h_x), 1/(2h_y), nu/h_x^2, nu/h_y^2 (from the host)
     float cstf[4];                 // the same in FP32
     double tol, c1, beta;
+    double piv_eps;                // block pivots d_j <= piv_eps max_k H_kk count as zero (rank test)
     int max_iter, max_bt;
     int blk_stride;                // doubles per instance of the block area
     const SubDev* sub;

@@ -995,7 +995,9 @@ int con_row_groups(const ddnm_ctx* ctx, const ProbDev& P, int B) {
 // factorisation of that subdomain then stops after the O columns and it is handled through
 // G = H_GG - L_GO D_O L_GO^T (snapshot after the O columns).  Subdomains i_first .. i_first + 32/LG - 1 below
 // ns; scratch (32 / LG) fs doubles; flags (FLAG_PD, FLAG_OMEGA_FAIL, FLAG_GAMMA_SING as 0, 1, 2) to fl[] and
-// the blocks.  A pivot is accepted when its bits are those of a positive finite double (integer tests).
+// the blocks.  A pivot is accepted when its bits are those of a positive finite double (integer tests) and it
+// exceeds P.piv_eps times the block's largest diagonal entry (below that it is the rounding remainder of a
+// direction the collocation rows miss, and the block takes the second Schur level).
 // Columns are taken two at a time where the lane groups allow (one reciprocal per pair), else one at a time.
 template <int LG>
 __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, const unsigned char* s_nO,
@@ -1036,6 +1038,12 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
         const long long vb = __double_as_longlong(v);
         return vb > 0 && vb < 0x7FF0000000000000LL;
     };
+    // pivots at or below thr are rounding remainders (a direction no collocation row sees): rank test
+    double thr = 0.0;
+    if (on) {
+        for (int j = 0; j < ni; ++j) thr = fmax(thr, L[j * ni + j]);
+        thr *= P.piv_eps;
+    }
     for (int j = 0; j < nmax;) {
         if (act && j == nO)
             for (int e = hl; e < nG * nG; e += LG) G[e] = L[(nO + e / nG) * ni + nO + e % nG];
@@ -1051,7 +1059,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
             pb = L[(j + 1) * ni + j];
             const double pc = L[(j + 1) * ni + j + 1];
             pdet = fma(pa, pc, -(pb * pb));
-            pair_ok = posfin(pa) && posfin(pdet);
+            pair_ok = posfin(pa) && posfin(pdet) && pa > thr && pdet > thr * pa;
         }
         if (__all_sync(0xffffffffu, !live || pair_ok)) {
             if (live) {
@@ -1094,7 +1102,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
         bool piv = false;
         if (live) {
             const double d = L[j * ni + j];
-            if (!posfin(d)) {                   // not positive and finite: the same for the lane group
+            if (!posfin(d) || d <= thr) {       // not positive and finite, or numerically zero
                 flag = j < nO ? 1 : 2;
                 act = false;
             } else {
@@ -2589,23 +2597,76 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[DDNM_NOALLOC_SC
 
 namespace {
 
-// Device address of g_noalloc_scratch on each device, looked up once per device (with that device
-// current) on the first no-allocation call there.  The host-side name of the array is only a stand-in.
+// Device address of g_noalloc_scratch, looked up with cudaGetSymbolAddress once per device and CUDA context
+// (with that device current), on the first no-allocation call there.  The host-side name of the array is only
+// a stand-in.  The cache is keyed by the context's unique id (cuCtxGetId, reached through the runtime's
+// driver entry points, so the library does not link libcuda): after the application resets the device
+// (cudaDeviceReset) the primary context, and with it the array's address, is new, and the next call looks
+// the address up again.
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[128] = {};
+struct NoallocAddr {
+    void* p = nullptr;
+    unsigned long long ctx_id = 0;
+};
+NoallocAddr g_noalloc_addr[128];
+
+typedef int (*ctx_get_current_fn)(void** pctx);                    // cuCtxGetCurrent(CUcontext*)
+typedef int (*ctx_get_id_fn)(void* ctx, unsigned long long* id);   // cuCtxGetId(CUcontext, unsigned long long*)
+
+// unique id of the CUDA context current on this thread (0 if it cannot be read)
+unsigned long long current_ctx_id() {
+    static ctx_get_current_fn get_cur = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (ctx_get_current_fn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (ctx_get_id_fn)f;
+    }
+    void* c = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&c) == 0 && c && get_id(c, &id) == 0) return id;
+    return 0;
+}
 
 int noalloc_scratch(ddnm_ctx* ctx, void** out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (ctx->device < 0 || ctx->device >= 128) return ddnm_fail(ctx, DDNM_E_INVALID, "device ordinal out of range");
-    if (!g_noalloc_addr[ctx->device]) {
+    NoallocAddr& a = g_noalloc_addr[ctx->device];
+    const unsigned long long id = current_ctx_id();
+    if (!a.p || id == 0 || id != a.ctx_id) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return ddnm_fail(ctx, DDNM_E_CUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
                                                    cudaGetErrorString(e));
-        g_noalloc_addr[ctx->device] = p;
+        a.p = p;
+        a.ctx_id = id;
     }
-    *out = g_noalloc_addr[ctx->device];
+    *out = a.p;
+    return DDNM_OK;
+}
+
+// A caller's pointer must be device (or managed) memory of ctx's device: the kernels dereference it.
+int check_device_ptr(ddnm_ctx* ctx, const void* p, const char* what) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return ddnm_fail(ctx, DDNM_E_INVALID, std::string("ddnm_residual_noalloc: ") + what +
+                                                  " is not a pointer the CUDA runtime knows");
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+        (at.type == cudaMemoryTypeDevice && at.device != ctx->device))
+        return ddnm_fail(ctx, DDNM_E_INVALID, std::string("ddnm_residual_noalloc: ") + what +
+                                                  " must be device memory on device " + std::to_string(ctx->device));
     return DDNM_OK;
 }
 
@@ -2692,8 +2753,13 @@ extern "C" int ddnm_residual_noalloc(ddnm_ctx* ctx, int B, const double* mu, con
     }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cfail(ctx, e, "cudaSetDevice");
+    int rc = check_device_ptr(ctx, mu, "mu");
+    if (!rc) rc = check_device_ptr(ctx, x, "x");
+    if (!rc && lam) rc = check_device_ptr(ctx, lam, "lam");
+    if (!rc) rc = check_device_ptr(ctx, F_out, "F_out");
+    if (rc) return rc;
     void* base = nullptr;
-    int rc = noalloc_scratch(ctx, &base);
+    rc = noalloc_scratch(ctx, &base);
     if (rc) return rc;
     char* s = (char*)base;
     cudaStream_t st = (cudaStream_t)stream;

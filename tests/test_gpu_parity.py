@@ -1,16 +1,22 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded inputs.
 
-Tolerances (relative, in the 2-norm over the compared quantity):
-* FP64 path: 1e-6 on latent coordinates, multipliers and reconstructed state (1e-9 on one
-  evaluation's blocks, where only rounding order differs);
-* mixed path (FP32 evaluation, FP64 KKT): 1e-4 -- one evaluation carries ~1e-6 relative
-  FP32 rounding, which the Gauss-Newton steps of a few iterations amplify by at most ~10^2.
-Integer work (sizes, index maps, iteration and evaluation counts) must match exactly.
+Every comparison is per block and per element (``parity.close``): one subdomain's H_i, D_i, rho_i, Z_i r_i or
+xh_i, the multipliers, Atil, the reconstructed state; an entry passes when
+|gpu - ref| <= tol |ref| + tol max|ref over its block|.
+Tolerances:
+* FP64 path: 1e-6 on latent coordinates, multipliers, merit and reconstructed state after iterating (1e-9 on
+  one evaluation's blocks, where only the rounding order differs);
+* mixed path (FP32 evaluation, FP64 KKT): 1e-4 after iterating, 2e-5 on one evaluation -- one FP32
+  evaluation carries ~1e-6 relative rounding per entry, which a few Gauss-Newton steps amplify by at most
+  ~10^2.
+Integer results (iteration and evaluation counts, status, the LS_FAIL flag) and the last step length must
+match exactly: they show that both sides take the same line-search decisions.
 """
 import numpy as np
 import pytest
 
 import inputs
+import parity
 from oracle import setup
 
 pytestmark = pytest.mark.gpu
@@ -34,22 +40,18 @@ def case(name, precision):
     return _CACHE[key]
 
 
-def rel(a, b):
-    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
 FP64, MIXED = 0, 1
 TOL = {FP64: 1e-6, MIXED: 1e-4}
 TOL_EVAL = {FP64: 1e-9, MIXED: 2e-5}
 
 EVAL_CASES = [("c1", FP64), ("c1", MIXED), ("tiny12x10_2x2", FP64), ("tiny12x10_2x2", MIXED),
-              ("tiny13x9_3x2", FP64), ("tiny13x9_3x2", MIXED), ("c2", MIXED), ("c2", FP64), ("c3", MIXED)]
+              ("tiny13x9_3x2", FP64), ("tiny13x9_3x2", MIXED), ("c2", MIXED), ("c2", FP64), ("c3", MIXED),
+              ("c3", FP64)]
 
 
 @pytest.mark.parametrize("name,prec", EVAL_CASES)
 def test_one_evaluation(name, prec):
-    """H_i, D_i, Atil, F = [rho; Atil] and the collocated residuals at a random (xh, lambda)."""
+    """H_i, D_i, Atil, F = [rho; Atil] and the collocated residuals at a random (xh, lambda), block by block."""
     wl, fom, dd, rom, raw, s = case(name, prec)
     B = 3
     r = np.random.default_rng(10)
@@ -60,11 +62,8 @@ def test_one_evaluation(name, prec):
     F, rhr = s.residual(mu, x, lam)
     for b in range(B):
         ev = rom.evaluate(x[b], lam[b], mu[b])
-        assert rel(H[b], np.concatenate([h.ravel() for h in ev.H])) < TOL_EVAL[prec]
-        assert rel(D[b], np.concatenate([d.ravel() for d in ev.D])) < TOL_EVAL[prec]
-        assert rel(A[b], ev.Atil) < TOL_EVAL[prec]
-        assert rel(F[b], ev.F) < TOL_EVAL[prec]
-        assert rel(rhr[b], np.concatenate(ev.r)) < TOL_EVAL[prec]
+        parity.evaluation(rom, ev, TOL_EVAL[prec], H=H[b], D=D[b], A=A[b], F=F[b], rhr=rhr[b],
+                          what=f"{name} instance {b}")
 
 
 @pytest.mark.parametrize("name,prec,K", [("c1", FP64, 1), ("c1", FP64, 2), ("c1", FP64, 3), ("c1", FP64, 15),
@@ -80,23 +79,21 @@ def test_fixed_iterations(name, prec, K):
     for b in range(3):
         ref = rom.solve(mu[b], tol=0.0, max_iter=K)
         assert st[b]["iters"] == K and st[b]["status"] == lib.DDNM_MAX_ITER
-        assert st[b]["n_evals"] == ref.n_evals
-        assert rel(x[b], ref.x) < TOL[prec] and rel(lam[b], ref.lam) < TOL[prec]
-        assert abs(st[b]["merit"] - ref.phi) <= TOL[prec] * ref.phi
-        assert st[b]["alpha_last"] == ref.alpha_hist[-1]
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[prec], f"{name} K={K} instance {b}")
+    s.options()
 
 
 def test_default_options_c1_fp64():
-    """The paper's stopping rule (||F|| < 1e-4 or 15 iterations) on the 32x32 FP64 workload."""
+    """The paper's stopping rule (||F|| < 1e-4 or 15 iterations) on the 32x32 FP64 workload, with the
+    reconstructed state."""
     wl, fom, dd, rom, raw, s = case("c1", FP64)
     s.options()
     mu = inputs.mu_batch(4)
     x, lam, st, state = s.solve(mu, state=True)
     for b in range(4):
         ref = rom.solve(mu[b])
-        assert st[b]["status"] == ref.status and st[b]["iters"] == ref.iters
-        assert rel(x[b], ref.x) < TOL[FP64] and rel(lam[b], ref.lam) < TOL[FP64]
-        assert rel(state[b], rom.full_state(ref.x)) < TOL[FP64]
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[FP64], f"c1 instance {b}")
+        parity.close(state[b], rom.full_state(ref.x), TOL[FP64], f"c1 instance {b} state")
 
 
 def test_given_multiplier_start_and_x0():
@@ -109,22 +106,73 @@ def test_given_multiplier_start_and_x0():
     x, lam, st = s.solve(mu, x0=x0, lam0=l0)
     for b in range(2):
         ref = rom.solve(mu[b], x0=x0[b], lam0=l0[b], tol=0.0, max_iter=2)
-        assert rel(x[b], ref.x) < TOL[FP64] and rel(lam[b], ref.lam) < TOL[FP64]
-        assert st[b]["n_evals"] == ref.n_evals
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[FP64], f"explicit start instance {b}")
+    s.options()
 
 
-def test_c2_full_launch_sampled():
-    """The 128x128 4x4 workload as the benchmark launches it (64 instances, mixed path,
-    paper's stopping rule); instances 0 and 41 re-solved by the oracle."""
-    wl, fom, dd, rom, raw, s = case("c2", MIXED)
+_C2_REFS = {}
+
+
+def c2_refs():
+    """The oracle's solves of all 64 instances of the 128x128 4x4 batch under the paper's stopping rule."""
+    if not _C2_REFS:
+        wl = inputs.workload("c2")
+        _C2_REFS["refs"] = parity.oracle_solves("c2", inputs.mu_batch(wl.batch))
+    return _C2_REFS["refs"]
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_c2_full_launch_all_instances(prec):
+    """The 128x128 4x4 workload as the benchmark launches it (64 instances, paper's stopping rule), every
+    instance against the oracle's solve, in both precisions, with the reconstructed state."""
+    wl, fom, dd, rom, raw, s = case("c2", prec)
     s.options()
     mu = inputs.mu_batch(wl.batch)
+    x, lam, st, state = s.solve(mu, state=True)
+    refs = c2_refs()
+    for b, ref in enumerate(refs):
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[prec], f"c2 prec {prec} instance {b}")
+        parity.close(state[b], rom.full_state(ref.x), TOL[prec], f"c2 prec {prec} instance {b} state")
+
+
+@pytest.mark.parametrize("prec,K", [(FP64, 15), (MIXED, 5)])
+def test_c3_uneven_iterations(prec, K):
+    """The uneven 3x5 workload (differing sizes, latent dims, widths and collocation rows per subdomain), 16
+    instances of its 256-instance batch against the oracle: the FP64 path for the full 15 SQP iterations, the
+    mixed path for 5.  (With these random-init decoders the merit stays near 4e3 and the iteration does not
+    contract; over 15 such iterations the FP32 rounding of the mixed evaluation is amplified past the 1e-4
+    bound, whose derivation covers a few iterations, while the line-search decisions stay the same.  The
+    mixed path's full solves in the converging regime are checked with trained decoders.)"""
+    wl, fom, dd, rom, raw, s = case("c3", prec)
+    s.options(tol=0.0, max_iter=K)
+    mu = inputs.mu_batch(wl.batch)
     x, lam, st = s.solve(mu)
-    assert np.all((st["status"] == lib.DDNM_MAX_ITER) | (st["status"] == lib.DDNM_CONVERGED))
-    for b in (0, 41):
-        ref = rom.solve(mu[b])
-        assert st[b]["iters"] == ref.iters and st[b]["status"] == ref.status
-        assert rel(x[b], ref.x) < TOL[MIXED] and rel(lam[b], ref.lam) < TOL[MIXED]
+    pick = np.sort(np.random.default_rng(33).choice(wl.batch, 16, replace=False))
+    refs = parity.oracle_solves("c3", mu[pick], tol=0.0, max_iter=K)
+    for b, ref in zip(pick, refs):
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[prec], f"c3 prec {prec} instance {b}")
+    s.options()
+
+
+@pytest.mark.parametrize("prec,max_iter,max_bt", [(FP64, 30, 20), (FP64, 15, 3), (MIXED, 15, 3)])
+def test_line_search_failure_flags(prec, max_iter, max_bt):
+    """Line searches that run out of halvings: on the 12x10 2x2 workload, 30 iterations with the paper's 20
+    halvings leave two of four instances stalled (every trial fails Armijo, the last one is taken and the
+    instance is flagged LS_FAIL), and 3 halvings flag most instances within 15 iterations.  The flag, the
+    counts and the iterates match the oracle's."""
+    wl, fom, dd, rom, raw, s = case("tiny12x10_2x2", prec)
+    s.options(tol=0.0, max_iter=max_iter, max_backtracks=max_bt)
+    mu = inputs.mu_batch(6 if max_bt == 3 else 4)
+    x, lam, st = s.solve(mu)
+    flagged = 0
+    for b in range(len(mu)):
+        ref = rom.solve(mu[b], tol=0.0, max_iter=max_iter, max_bt=max_bt)
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[prec], f"LS case instance {b}")
+        flagged += ref.flags & 1
+    assert flagged > 0                                  # the case covers flagged instances ...
+    if max_bt == 20:
+        assert flagged < len(mu)                        # ... and, with the paper's halvings, unflagged ones
+    s.options()
 
 
 def test_reconstruction_and_full_residual():
@@ -135,7 +183,7 @@ def test_reconstruction_and_full_residual():
     F, rhr, rfull = s.residual(mu, x, None, full=True)
     for b in range(2):
         st = rom.full_state(x[b])
-        assert rel(rfull[b], fom.residual(st, mu[b])) < 1e-10
+        parity.close(rfull[b], fom.residual(st, mu[b]), 1e-10, f"FOM residual instance {b}")
 
 
 def test_device_memory_path_matches_host():
@@ -153,6 +201,7 @@ def test_device_memory_path_matches_host():
     assert np.array_equal(x_d.cpu().numpy(), x) and np.array_equal(l_d.cpu().numpy(), lam)
     st2 = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=lib.STATS_DTYPE)
     assert np.array_equal(st2["n_evals"], st["n_evals"])
+    s.options()
 
 
 def test_non_pd_hessian_reports_kkt_fail():
@@ -186,6 +235,7 @@ def test_batch_sizes_ragged():
     x7, l7, st7 = s.solve(mu)
     x1, l1, st1 = s.solve(mu[3:4])
     assert np.array_equal(x1[0], x7[3]) and np.array_equal(l1[0], l7[3])
+    s.options()
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
@@ -203,6 +253,6 @@ def test_gamma_singular_block_matches_oracle(prec):
     x, lam, st = s.solve(mu)
     for b in range(3):
         ref = rom.solve(mu[b], tol=0.0, max_iter=3)
-        assert st[b]["status"] == lib.DDNM_MAX_ITER and st[b]["n_evals"] == ref.n_evals
-        assert rel(x[b], ref.x) < TOL[prec] and rel(lam[b], ref.lam) < TOL[prec]
+        assert st[b]["status"] == lib.DDNM_MAX_ITER
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[prec], f"Gamma-singular instance {b}")
     s.close()

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import inputs
+import parity
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
@@ -47,11 +48,10 @@ def test_gradient_parity_with_oracle(c2):
     L, g_ref = omlp.loss_grad(p0.astype(np.float64), z.astype(np.float64), t.astype(np.float64), 2, H, nD)
     assert abs(loss - L) <= 1e-5 * L
     assert rel(g, g_ref) < 1e-4
-    # each parameter block separately (a transposed block would pass a norm test over everything)
-    o = 0
-    for n in (2 * H, H, H * H, H, nD * H, nD):
-        assert rel(g[o:o + n], g_ref[o:o + n]) < 1e-4
-        o += n
+    # each parameter block separately, element by element (a transposed block would pass a norm test)
+    for k, (gb, rb) in enumerate(zip(parity.split(g, [2 * H, H, H * H, H, nD * H, nD]),
+                                     parity.split(g_ref, [2 * H, H, H * H, H, nD * H, nD]))):
+        parity.close(gb, rb, 1e-4, f"gradient block {k}")
 
 
 def test_training_trajectory_matches_oracle(c2):
