@@ -1,20 +1,31 @@
 #!/usr/bin/env python
-"""Throughput of the batched DD NM-ROM-HR SQP solve (arXiv 2305.15163, Sec. 4.1) on GB300.
+"""Throughput of the batched DD NM-ROM-HR SQP solve (arXiv 2305.15163, Sec. 4.1) on GB300, at equal accuracy.
 
-Workload (default): 128x128 interior Burgers grid on [-1,1]^2, 4x4 equal subdomains, latent
-(n^O, n^G) = (6, 3), width 256, three-band masks with 8 nonzeros per band, collocation HR on 5 %
-of each subdomain's residual rows, Gaussian test matrix with n_C = 24, random-init decoders,
-64 parameter instances mu ~ U[0.9,1.1]^2 in one launch; FP32 evaluation, FP64 KKT / merit.
-One step = one ddnm_solve_batch of the 64 instances to the paper's stopping rule
-(||F||_2 < 1e-4 or 15 SQP iterations, Sec. 7.1).  metric = solves/s (instances per second).
+Workload (default, c5): steady 2D Burgers on a 1024x1024 interior grid on [-1,1]^2, 8x8 equal subdomains, latent
+(n^O, n^G) = (8, 4), width 1024, three-band masks with 8 nonzeros per band, collocation HR on 2 % of each
+subdomain's residual rows, Gaussian test matrix with n_C = 128, 1024 parameter instances mu ~ U[0.9,1.1]^2 per
+GPU.  Set-up on the GPU (untimed): FOM snapshots at a 12x12 grid of mu (ddnm_fom_solve), the 128 masked
+autoencoders trained on them (ddnm_ae_train, mini-batch Adam with a stepped learning rate), the learned warm
+start (MLP mu -> xh0) trained on mixed-precision ROM solutions.
 
-python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config c2]
-N > 1: launched by torchrun, one rank per GPU, each rank solving its own 64 instances
-(weak scaling, no collective on the data path; a barrier and a max-reduction of the time only).
+Accuracy criterion (the metric's "rel err <= 1e-4"): the reconstructed state g(xh) of an instance lies within
+1e-4 (relative 2-norm, Eq. relative_error) of the FP64 ROM solution of the same instance (40 FP64 SQP
+iterations).  Each method gets the smallest iteration budget for which every instance of a separate calibration
+batch meets it; the timed batch is then checked instance by instance and only the instances that meet it count.
+
+One step = one ddnm_solve_batch of the 1024 instances by the headline method: FP32 evaluation / FP64 KKT
+(mixed) with the learned warm start.  value = accurate solves per second.  Beside it, on the same GPU: the
+plain FP64 batched SQP from the default start at its own equal-accuracy budget, the plain mixed solve, and the
+FP64 solve under the paper's stopping rule (||F||_2 < 1e-4 or 15 iterations, Sec. 7.1).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config c5|c2|c3] [--peaks]
+N > 1: launched by torchrun, one rank per GPU, each rank solving its own instances (replicas, weak scaling;
+no collective on the data path, a barrier and a max-reduction of the time only).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import multiprocessing as mp
 import os
@@ -22,6 +33,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,39 +46,13 @@ import inputs  # noqa: E402
 METRIC = "DD NM-ROM-HR SQP solves/s at 1 GB300 (rel err ≤1e-4 vs FOM); % HBM roofline"
 UNIT = "solves/s"
 FLUSH_BYTES = 512 << 20          # > 129 MB L2
-SMS, FP32_LANES, FP64_PER_CLK = 152, 128, 2   # GB300: SMs, FP32 lanes / SM, DFMA / clk / SM
-SM_MAX_MHZ = 2070.0
-
-
-def eval_traffic_profile():
-    """DRAM bytes per launch of the evaluation kernel on this workload from the committed ncu summary, if it
-    was taken on the current kernel source (same SHA-256), else None."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_eval_c2.md")
-    src = os.path.join(ROOT, "paper_2305_15163_gb300", "csrc", "ddnm_kernels.cu")
-    try:
-        text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    m_sha = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
-    m_b = re.search(r"dram bytes per launch: ([0-9]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != sha:
-        return None
-    return int(m_b.group(1))
-
-
-def peaks():
-    p = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            p = json.load(f)
-    except OSError:
-        pass
-    mhz = float(p.get("sm_max_mhz", SM_MAX_MHZ))
-    return dict(hbm_gbs=float(p.get("hbm_gbs", 6800.0)), hbm_src="measured" if "hbm_gbs" in p else "fallback",
-                fp32_tflops=SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12,
-                fp64_tflops=SMS * FP64_PER_CLK * 2 * mhz * 1e6 / 1e12)
+ACC = 1e-4                       # accuracy criterion (relative 2-norm of the reconstructed state)
+K_REF = 40                       # FP64 SQP iterations of the reference ROM solution
+REF_ITERS = 15                   # SQP iterations of an oracle solve in the CPU throughput (the paper's cap)
+AE_STAGES = ((200, 3e-3), (200, 1e-3), (200, 3e-4), (200, 1e-4))   # (epochs, learning rate) of the AE training
+AE_SIDE, AE_BATCH = 12, 16
+WS_HIDDEN, WS_EPOCHS, WS_TRAIN = 256, 60, 2048
+SMS_FALLBACK = 152
 
 
 # ------------------------------------------------------------------------ clocks
@@ -130,46 +116,129 @@ def gpu_id_for(local_rank: int) -> str:
     return str(local_rank)
 
 
-# ------------------------------------------------------------------------ oracle (CPU) leg
-
-def _oracle_worker(args):
-    name, idx = args
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    from oracle import setup as osetup
-    wl = inputs.workload(name)
-    _, _, rom, _ = osetup.build(wl)
-    mu = inputs.mu_batch(wl.batch)
-    t0 = time.perf_counter()
-    res = [rom.solve(mu[i % wl.batch]) for i in idx]
-    return time.perf_counter() - t0, len(res), [r.n_evals for r in res]
-
-
-def oracle_sample(name: str, per_worker: int = 1, workers: int | None = None):
-    """Oracle solves of the same workload on the host cores: one spawn process per core, each
-    single-threaded (BLAS threads pinned to 1), each solving ``per_worker`` instances."""
-    workers = workers or max(1, min(os.cpu_count() or 1, 16))
-    env = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    old = {k: os.environ.get(k) for k in env}
-    os.environ.update(env)
+def measured_peaks():
     try:
-        ctx = mp.get_context("spawn")
-        jobs = [(name, [w * per_worker + k for k in range(per_worker)]) for w in range(workers)]
-        t0 = time.perf_counter()
-        with ctx.Pool(workers) as pool:
-            out = pool.map(_oracle_worker, jobs)
-        wall = time.perf_counter() - t0
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def traffic_profile(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, if it was taken on the
+    current kernel source (same SHA-256), else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    src = os.path.join(ROOT, "paper_2305_15163_gb300", "csrc", "ddnm_kernels.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
+    m_b = re.search(r"dram bytes per launch: ([0-9]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return int(m_b.group(1))
+
+
+# ------------------------------------------------------------------------ oracle (CPU) legs
+
+_W = {}
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _worker_init(name, dec_path):
+    """Pool initializer: the oracle's ROM of the workload, with the decoders stored at dec_path (the ones this
+    run trained) or, without it, the seeded random-init decoders."""
+    for k in _THREAD_VARS:
+        os.environ[k] = "1"
+    from oracle import setup as osetup
+    if dec_path is None:
+        _W["rom"] = osetup.build(inputs.workload(name))[2]
+        return
+    from oracle.burgers import Burgers
+    from oracle.dd import decompose
+    from oracle.decoders import EllDecoder
+    from oracle.rom import DDROM
+    wl = inputs.workload(name)
+    z = np.load(dec_path)
+    decs = {}
+    for kind in ("o", "g"):
+        decs[kind] = []
+        for i in range(wl.n_sub):
+            p = f"{kind}{i}_"
+            decs[kind].append(dict(N=int(z[p + "N"]), w=int(z[p + "w"]), n=int(z[p + "n"]), act="swish",
+                                   W1=z[p + "W1"].astype(np.float64), b1=z[p + "b1"].astype(np.float64),
+                                   cols=z[p + "cols"], vals=z[p + "vals"].astype(np.float64),
+                                   scale=z[p + "scale"], offset=z[p + "offset"]))
+    dd = decompose(wl.nx, wl.ny, wl.xb, wl.yb)
+    C = inputs.test_matrix(wl.n_c(), dd.N_A, inputs.SEED_C + wl.seed_offset)
+    _W["rom"] = DDROM(Burgers(wl.nx, wl.ny, wl.nu), dd, [EllDecoder(d) for d in decs["o"]],
+                      [EllDecoder(d) for d in decs["g"]], inputs.hr_sets(wl), C)
+
+
+def _worker_solve(job):
+    mu, kw = job
+    t0 = time.perf_counter()
+    r = _W["rom"].solve(mu, **kw)
+    return time.perf_counter() - t0, r.x, r.lam, r.n_evals
+
+
+def oracle_pool(name, dec_path, workers):
+    old = {k: os.environ.get(k) for k in _THREAD_VARS}
+    os.environ.update({k: "1" for k in _THREAD_VARS})
+    try:
+        return mp.get_context("spawn").Pool(workers, initializer=_worker_init, initargs=(name, dec_path))
     finally:
         for k, v in old.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    solved = sum(o[1] for o in out)
-    busy = max(o[0] for o in out)          # solve phase (after each worker's own set-up)
-    return dict(value=solved / busy, unit=UNIT, cores=workers, kind="oracle",
-                sample=f"{solved} instances of workload {name} (first {solved} mu), one spawn process per core, "
-                       f"single-threaded numpy/scipy FP64, paper's stopping rule; {busy:.1f} s solve phase, "
-                       f"{wall:.1f} s wall with set-up")
+
+
+def n_workers():
+    return max(1, min(os.cpu_count() or 1, 16))
+
+
+def oracle_sample(name, mu, dec_path=None, iters=2):
+    """The oracle's FP64 SQP on the host cores, one spawn process per core (single-threaded numpy/scipy),
+    each solving one instance of mu for `iters` iterations from the default start (tolerance 0).  Returns the
+    results and the solve-phase time (after each worker's set-up)."""
+    workers = min(n_workers(), len(mu))
+    t0 = time.perf_counter()
+    with oracle_pool(name, dec_path, workers) as pool:
+        out = pool.map(_worker_solve, [(m, dict(tol=0.0, max_iter=iters)) for m in mu[:workers]], chunksize=1)
+    wall = time.perf_counter() - t0
+    return out, workers, wall
+
+
+def cpu_throughput(out, workers, wall, name, iters, what):
+    """Oracle solves/s on `workers` cores from a sample of `iters` iterations per instance: a solve of
+    REF_ITERS iterations from the default start costs REF_ITERS + 2 evaluations and KKT steps where the sample
+    took iters + 2 (the multiplier start and the start point, then one trial per accepted step)."""
+    busy = max(o[0] for o in out)
+    evals = max(o[3] for o in out)
+    per_solve = busy * (REF_ITERS + 2) / evals
+    return dict(value=workers / per_solve, unit=UNIT, cores=workers, kind="oracle",
+                sample=f"{len(out)} instances of workload {name} ({what}), {iters} FP64 SQP iterations each from the "
+                       f"default start ({evals} evaluations), one spawn process per core, single-threaded numpy/scipy; "
+                       f"{busy:.1f} s solve phase ({wall:.1f} s wall with set-up), scaled to a solve of {REF_ITERS} "
+                       f"iterations ({REF_ITERS + 2} evaluations)")
+
+
+def save_decoders(path, dec_o, dec_g):
+    arrs = {}
+    for kind, decs in (("o", dec_o), ("g", dec_g)):
+        for i, d in enumerate(decs):
+            p = f"{kind}{i}_"
+            arrs.update({p + "N": np.int64(d["N"]), p + "w": np.int64(d["w"]), p + "n": np.int64(d["n"]),
+                         p + "W1": np.asarray(d["W1"], dtype=np.float32), p + "b1": np.asarray(d["b1"], dtype=np.float32),
+                         p + "cols": np.asarray(d["cols"], dtype=np.int32),
+                         p + "vals": np.asarray(d["vals"], dtype=np.float32),
+                         p + "scale": np.asarray(d["scale"], dtype=np.float64),
+                         p + "offset": np.asarray(d["offset"], dtype=np.float64)})
+    np.savez(path, **arrs)
 
 
 # ------------------------------------------------------------------------ replicas over ranks
@@ -191,166 +260,212 @@ def max_over_ranks(value: float, dist, device) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: int, dist, device) -> int:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(round(t.item()))
+
+
 def job_throughput(per_rank: int, world: int, steps: int, seconds: float) -> float:
     """Whole-job units per second: the units all ranks processed over the slowest rank's time."""
     return per_rank * world * steps / seconds
 
 
+def workload_config(cfg):
+    wl = inputs.workload(cfg)
+    return {"workload": f"{cfg}: steady Burgers {wl.nx}x{wl.ny} on [-1,1]^2, {wl.kx}x{wl.ky} subdomains, latent "
+                        f"({wl.n_omega[0]},{wl.n_gamma[0]}), width {wl.width[0]}, mask 3x{wl.band}, HR "
+                        f"{100 * wl.hr_frac[0]:.0f}% rows, n_C {wl.n_c()}, {wl.batch} mu per GPU",
+            "global_batch": wl.batch, "l2": "flushed (512 MiB write) before every timed step"}
+
+
 # ------------------------------------------------------------------------ reference arm
 
+def reference_sample(cfg, steps):
+    """`steps` samples of the oracle on the host cores (one instance per worker, one SQP iteration with the
+    first trial taken, i.e. 3 evaluations): per-step solves/s, step times and the last step's description."""
+    wl = inputs.workload(cfg)
+    workers = n_workers()
+    mu = inputs.mu_batch(wl.batch)
+    vals, times = [], []
+    with oracle_pool(cfg, None, workers) as pool:
+        for k in range(steps):
+            t0 = time.perf_counter()
+            out = pool.map(_worker_solve, [(mu[(k * workers + w) % len(mu)], dict(tol=0.0, max_iter=1, max_bt=0))
+                                           for w in range(workers)], chunksize=1)
+            times.append(time.perf_counter() - t0)
+            vals.append(cpu_throughput(out, workers, times[-1], cfg, 1, "seeded random-init decoders")["value"])
+    return vals, times, cpu_throughput(out, workers, times[-1], cfg, 1, "seeded random-init decoders")
+
+
 def run_reference(args):
+    """The oracle on the host cores, on this benchmark's workload (seeded random-init decoders: the GPU-trained
+    ones are not available without the GPU path; an SQP iteration costs the same).  One step: every worker
+    solves one instance for one SQP iteration (3 evaluations); throughput scaled to a solve of REF_ITERS
+    iterations."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     cfg = args.config
-    steps = max(1, min(args.steps, 3))
-    vals = []
-    base = None
-    for _ in range(steps):
-        base = oracle_sample(cfg)
-        vals.append(base["value"])
+    steps = max(1, min(args.steps, 4))
+    vals, times, base = reference_sample(cfg, steps)
     v = statistics.median(vals)
     base["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "steps_requested": args.steps, "warmup": 0, "ms_per_step": 1000.0 / v,
+            "steps": steps, "steps_requested": args.steps, "warmup": 0, "ms_per_step": 1000.0 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(cfg),
             "cpu_baseline": base, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def workload_config(cfg):
-    wl = inputs.workload(cfg)
-    return {"workload": f"{cfg}: Burgers {wl.nx}x{wl.ny} on [-1,1]^2, {wl.kx}x{wl.ky} subdomains, latent "
-                        f"({wl.n_omega[0]},{wl.n_gamma[0]}), width {wl.width[0]}, mask 3x{wl.band}, HR "
-                        f"{100 * wl.hr_frac[0]:.0f}% rows, n_C {wl.n_c()}, {wl.batch} mu per GPU, random-init decoders",
-            "global_batch": wl.batch, "l2": "flushed (512 MiB write) before every timed step",
-            "stopping": "||F||_2 < 1e-4 or 15 SQP iterations (Sec. 7.1)"}
+# ------------------------------------------------------------------------ the GPU arm
 
+class Rom:
+    """The workload on the GPU: a mixed-precision context (FP32 evaluation, FP64 KKT) and an FP64 context with
+    the same decoders, trained by the library on its own FOM snapshots."""
 
-# ------------------------------------------------------------------------ learned warm start (c4)
-
-def run_warmstart(args, lib, torch, name="c2", n_train=4096, n_test=1024, epochs=60):
-    """MLP 2 -> 256 -> 256 -> n_D trained on n_train SQP solutions of workload `name` (paper's stopping rule,
-    default start), judged on n_test held-out mu: iterations the SQP needs from the learned start to reach
-    the merit the default start ends with after 15 iterations, final merits, and solves/s of the
-    warm-started mixed-precision solve next to the plain mixed and the plain FP64 solves on the same GPU."""
-    wl = inputs.workload(name)
-    B = wl.batch
-    s = lib.Solver(wl)
-    dec_o, dec_g = inputs.decoders_for(wl, [d["interior"] for d in s.subs], [d["interface"] for d in s.subs])
-    Cm = inputs.test_matrix(wl.n_c(), s.sizes.N_A)
-    s.load(dec_o, dec_g, Cm)
-    s.options()
-    nD = s.sizes.n_D
-
-    def solve_all(solver, mu):
-        xs, sts = [], []
-        for b0 in range(0, len(mu), B):
-            x, lam, st = solver.solve(mu[b0:b0 + B])
-            xs.append(x)
-            sts.append(st)
-        return np.concatenate(xs), np.concatenate(sts)
-
-    plan, _ = lib.ddnm_autotune(s.ctx, inputs.mu_batch(B, seed=3003), max_iter=2, reps=1)
-    t0 = time.perf_counter()
-    mu_tr = inputs.mu_batch(n_train, seed=1001)
-    x_tr, _ = solve_all(s, mu_tr)
-    t_data = time.perf_counter() - t0
-    H = 256
-    lib.ddnm_ws_init(s.ctx, H, inputs.mlp_init(2, H, nD))
-    t0 = time.perf_counter()
-    losses = lib.ddnm_ws_train(s.ctx, mu_tr, x_tr, epochs, 64, 2e-3, inputs.mlp_order(n_train, epochs))
-    t_train = time.perf_counter() - t0
-    mu_te = inputs.mu_batch(n_test, seed=2002)
-
-    def timed(solver, mu):
-        solve_all(solver, mu[:B])          # untimed: captures the solve graph for these options and this start
+    def __init__(self, lib, torch, wl, device):
+        self.lib, self.torch, self.wl = lib, torch, wl
+        self.dev = torch.device("cuda", device)
+        s = lib.Solver(wl, precision=lib.DDNM_MIXED, device=device)
+        specs = {}
+        for i, d in enumerate(s.subs):
+            for kind, ids in ((0, d["interior"]), (1, d["interface"])):
+                n_lat = (wl.n_omega if kind == 0 else wl.n_gamma)[i]
+                dec = inputs.decoder(len(ids), wl.width[i], n_lat, wl.band, (wl.seed_offset, i, kind))
+                enc = inputs.encoder(len(ids), wl.width[i], n_lat, inputs.transposed_mask(dec["cols"], wl.width[i]),
+                                     (wl.seed_offset, i, kind))
+                lib.ddnm_load_decoders(s.ctx, i, kind, dec)
+                lib.ddnm_load_encoder(s.ctx, i, kind, enc)
+                specs[(i, kind)] = dec
+        self.Cm = inputs.test_matrix(wl.n_c(), s.sizes.N_A)
+        lib.ddnm_set_test_matrix(s.ctx, self.Cm)
         torch.cuda.synchronize()
-        t = time.perf_counter()
-        _, st = solve_all(solver, mu)
+        t0 = time.perf_counter()
+        X, fst = lib.ddnm_fom_solve(s.ctx, inputs.snapshot_mu(AE_SIDE))
         torch.cuda.synchronize()
-        return len(mu) / (time.perf_counter() - t), st
+        self.t_fom = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.loss_first = self.loss_last = None
+        for k, (ep, lr) in enumerate(AE_STAGES):
+            losses = lib.ddnm_ae_train(s.ctx, X, ep, AE_BATCH, lr, inputs.ae_order(X.shape[0], ep, seed=100 + k))
+            if self.loss_first is None:
+                self.loss_first = losses[0]
+            self.loss_last = losses[-1]
+        torch.cuda.synchronize()
+        self.t_train = time.perf_counter() - t0
+        self.n_snap = X.shape[0]
+        self.fom_newton = float(np.mean(fst["newton_iters"]))
+        del X
+        self.dec_o = [lib.ddnm_get_decoder(s.ctx, i, 0, specs[(i, 0)]) for i in range(len(s.subs))]
+        self.dec_g = [lib.ddnm_get_decoder(s.ctx, i, 1, specs[(i, 1)]) for i in range(len(s.subs))]
+        s64 = lib.Solver(wl, precision=lib.DDNM_FP64, device=device)
+        s64.load(self.dec_o, self.dec_g, self.Cm)
+        self.s, self.s64 = s, s64
+        self.nD, self.nC, self.Nx = s.sizes.n_D, s.sizes.n_C, s.sizes.N_x
 
-    lib.ddnm_ws_enable(s.ctx, False)
-    solve_all(s, mu_te[:B])
-    v_plain, st_plain = timed(s, mu_te)
-    lib.ddnm_ws_enable(s.ctx, True)
-    v_ws, st_ws = timed(s, mu_te)
-    reach = np.full(len(mu_te), -1)
-    for K in (1, 2, 3, 4, 6, 8, 11, 15):
-        s.options(tol=0.0, max_iter=K)
-        _, st = solve_all(s, mu_te)
-        newly = (st["merit"] <= st_plain["merit"]) & (reach < 0)
-        reach[newly] = K
-    # throughput at equal final merit: the learned start with the iteration budget that reaches the
-    # default start's 15-iteration merit for every held-out instance
-    k_eq = int(reach.max()) if (reach > 0).all() else 15
-    s.options(tol=0.0, max_iter=k_eq)
-    v_ws_eq, st_ws_eq = timed(s, mu_te)
-    s.options()
-    lib.ddnm_ws_enable(s.ctx, False)
-    # plain FP64 solve of the same workload on the same GPU
-    s64 = lib.Solver(wl, precision=lib.DDNM_FP64)
-    s64.load(dec_o, dec_g, Cm)
-    lib.ddnm_set_tune(s64.ctx, **plan)
-    s64.options()
-    solve_all(s64, mu_te[:B])
-    n64 = max(B, len(mu_te) // 4)
-    v_fp64, st_fp64 = timed(s64, mu_te[:n64])
-    reached = reach > 0
-    line = {"metric": METRIC + " [mixed + learned warm start at the plain solve's final merit]", "value": v_ws_eq,
-            "unit": UNIT, "n_gpus": 1, "steps": len(mu_te) // B, "warmup": 1,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 KKT",
-            "data": "synthetic",
-            "config": {"workload": f"learned warm start on the {wl.nx}x{wl.ny} {wl.kx}x{wl.ky} setup ({name}), MLP "
-                                   f"2-256-256-{nD} (bf16 weights, fp32 accumulation), {n_train} training "
-                                   f"solutions, {n_test} held-out mu, batches of {B}",
-                       "launch_plan": plan, "fp64_timed_on": n64},
-            "warm_start": {"train_seconds": t_train, "data_seconds": t_data, "epochs": epochs,
-                           "loss_first_last": [float(losses[0]), float(losses[-1])],
-                           "fraction_reaching_plain_final_merit": float(reached.mean()),
-                           "mean_iters_to_plain_final_merit": float(reach[reached].mean()) if reached.any() else None,
-                           "plain_iters": float(st_plain["iters"].mean()),
-                           "median_final_merit_plain": float(np.median(st_plain["merit"])),
-                           "median_final_merit_warm": float(np.median(st_ws["merit"])),
-                           "fallback_fraction": float(np.mean(st_ws["flags"] & lib.DDNM_FLAG_WS_FALLBACK > 0)),
-                           "solves_per_s_plain_mixed": v_plain, "solves_per_s_warm_mixed": v_ws,
-                           "equal_merit_iters": k_eq, "solves_per_s_warm_mixed_equal_merit": v_ws_eq,
-                           "equal_merit_holds": bool(np.all(st_ws_eq["merit"] <= st_plain["merit"])),
-                           "solves_per_s_plain_fp64": v_fp64,
-                           "median_final_merit_plain_fp64": float(np.median(st_fp64["merit"]))}}
-    print(json.dumps(line))
+    def solve(self, solver, mu, K, tol=0.0):
+        solver.options(tol=tol, max_iter=K)
+        x, lam, st = solver.solve(mu)
+        solver.options()
+        return x, lam, st
+
+    def state_errors(self, x, x_ref, chunk=64):
+        """Relative 2-norm distance of g(x) from g(x_ref) per instance (FP64 decoders, on the device)."""
+        torch, lib = self.torch, self.lib
+        out = []
+        for b0 in range(0, len(x), chunk):
+            n = min(chunk, len(x) - b0)
+            xa = torch.from_numpy(np.ascontiguousarray(x[b0:b0 + n])).to(self.dev)
+            xr = torch.from_numpy(np.ascontiguousarray(x_ref[b0:b0 + n])).to(self.dev)
+            ga = torch.empty((n, self.Nx), dtype=torch.float64, device=self.dev)
+            gr = torch.empty((n, self.Nx), dtype=torch.float64, device=self.dev)
+            lib.ddnm_reconstruct(self.s64.ctx, n, xa, ga)
+            lib.ddnm_reconstruct(self.s64.ctx, n, xr, gr)
+            out.append(((ga - gr).norm(dim=1) / gr.norm(dim=1)).cpu().numpy())
+            del ga, gr
+        return np.concatenate(out)
+
+    def fom_errors(self, x, mu, chunk=32):
+        """Relative 2-norm distance of g(x) from the FOM solution (GPU FOM) per instance."""
+        torch, lib = self.torch, self.lib
+        out = []
+        for b0 in range(0, len(x), chunk):
+            n = min(chunk, len(x) - b0)
+            xa = torch.from_numpy(np.ascontiguousarray(x[b0:b0 + n])).to(self.dev)
+            ga = torch.empty((n, self.Nx), dtype=torch.float64, device=self.dev)
+            lib.ddnm_reconstruct(self.s64.ctx, n, xa, ga)
+            xf = torch.empty((n, self.Nx), dtype=torch.float64, device=self.dev)
+            lib.ddnm_fom_solve(self.s.ctx, torch.from_numpy(np.ascontiguousarray(mu[b0:b0 + n])).to(self.dev), x_out=xf)
+            out.append(((ga - xf).norm(dim=1) / xf.norm(dim=1)).cpu().numpy())
+            del ga, xf
+        return np.concatenate(out)
+
+    def train_warm_start(self, mu_tr, K):
+        lib = self.lib
+        B = self.wl.batch
+        xs = []
+        for b0 in range(0, len(mu_tr), B):
+            xs.append(self.solve(self.s, mu_tr[b0:b0 + B], K)[0])
+        x_tr = np.concatenate(xs)
+        lib.ddnm_ws_init(self.s.ctx, WS_HIDDEN, inputs.mlp_init(2, WS_HIDDEN, self.nD))
+        t0 = time.perf_counter()
+        losses = lib.ddnm_ws_train(self.s.ctx, mu_tr, x_tr, WS_EPOCHS, 64, 2e-3, inputs.mlp_order(len(mu_tr), WS_EPOCHS))
+        self.torch.cuda.synchronize()
+        return time.perf_counter() - t0, losses
+
+
+def smallest_k(run, x_ref, Ks, errf):
+    """The smallest K of the increasing list Ks whose solve meets the accuracy criterion on every instance
+    (bisection; the error falls with K).  run(K) -> x.  Returns (K, max error at K)."""
+    lo, hi = 0, len(Ks) - 1
+    best = (Ks[-1], float(errf(run(Ks[-1]), x_ref).max()))
+    while lo < hi:
+        mid = (lo + hi) // 2
+        e = float(errf(run(Ks[mid]), x_ref).max())
+        if e <= ACC:
+            hi = mid
+            best = (Ks[mid], e)
+        else:
+            lo = mid + 1
+    if Ks[lo] != best[0]:
+        best = (Ks[lo], float(errf(run(Ks[lo]), x_ref).max()))
+    return best
+
+
+def run_peaks(args):
+    import torch
+    import paper_2305_15163_gb300 as lib
+    torch.cuda.set_device(0)
+    s = lib.Solver(inputs.workload("c1"))
+    f32, f64 = lib.ddnm_measure_peaks(s.ctx)
     s.close()
-    s64.close()
+    print(json.dumps({"fp32_tflops": f32, "fp64_tflops": f64, "how": "ddnm_measure_peaks: 8 CTAs x 256 threads per SM, "
+                      "8 independent FMA chains per thread, best of 3 CUDA-event timed launches"}))
 
-
-# ------------------------------------------------------------------------ our arm
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plan", default="auto",
-                    help="launch plan: auto (autotuned on the workload), host (host-driven passes), "
-                         "or chains,con_split,eval_persist for the graph-resident loop")
+    ap.add_argument("--peaks", action="store_true", help="print the measured FP32 / FP64 FMA peaks and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.peaks:
+        return run_peaks(args)
 
     import torch
     import paper_2305_15163_gb300 as lib
 
-    if args.config == "c4":
-        torch.cuda.set_device(0)
-        return run_warmstart(args, lib, torch)
-    if args.config == "c5":
-        torch.cuda.set_device(0)
-        return run_warmstart(args, lib, torch, name="c5", n_train=2048, n_test=1024, epochs=60)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -359,49 +474,76 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-
-    # CPU baseline first (spawn pool, before heavy GPU work), rank 0 at N = 1 only
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.config)
-
+    dev = torch.device("cuda", local)
     wl = inputs.workload(args.config)
     B = wl.batch
-    s = lib.Solver(wl, device=local)
-    dec_o, dec_g = inputs.decoders_for(wl, [d["interior"] for d in s.subs], [d["interface"] for d in s.subs])
-    Cm = inputs.test_matrix(wl.n_c(), s.sizes.N_A)
-    s.load(dec_o, dec_g, Cm)
-    s.options()
+    t_setup = time.perf_counter()
+
+    # ---- set-up on the GPU: FOM snapshots, autoencoders, the warm start (untimed)
+    R = Rom(lib, torch, wl, local)
+    s, s64 = R.s, R.s64
+    mu_tr = inputs.mu_batch(WS_TRAIN, seed=1001)
+    t_ws, ws_losses = R.train_warm_start(mu_tr, 30)
+    mu_cal = inputs.mu_batch(min(256, B), seed=3003)
     mu = shard(inputs.mu_batch(B * world), rank, world)
-    dev = torch.device("cuda", local)
-    nD, nC = s.sizes.n_D, s.sizes.n_C
+
+    # ---- references: the FP64 ROM solutions (K_REF iterations)
+    x_cal_ref = R.solve(s64, mu_cal, K_REF)[0]
+    x_ref, lam_ref, st_ref = R.solve(s64, mu, K_REF)
+
+    # ---- calibration: each method's smallest iteration budget meeting the accuracy criterion on mu_cal
+    lib.ddnm_ws_enable(s.ctx, False)
+    k64, e64 = smallest_k(lambda K: R.solve(s64, mu_cal, K)[0], x_cal_ref, [8, 10, 12, 14, 16, 18, 20, 22, 24, 28, 32, 40],
+                          R.state_errors)
+    kmp, emp = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32, 40],
+                          R.state_errors)
+    lib.ddnm_ws_enable(s.ctx, True)
+    kws, ews = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 20, 25, 30],
+                          R.state_errors)
+
+    # ---- launch plan of the headline solve: autotuned on this batch with the timed iteration budget
+    s.options(tol=0.0, max_iter=kws)
+    plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, max_iter=kws, reps=3)
+
+    # ---- CPU baseline (rank 0, N = 1): the oracle with this run's decoders, and its parity with both GPU paths
+    cpu, parity = None, None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        fd, dec_path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        try:
+            save_decoders(dec_path, R.dec_o, R.dec_g)
+            mu_o = inputs.mu_batch(n_workers(), seed=5005)
+            out, workers, wall = oracle_sample(args.config, mu_o, dec_path, iters=2)
+        finally:
+            os.unlink(dec_path)
+        cpu = cpu_throughput(out, workers, wall, args.config, 2, "the decoders this run trained")
+        lib.ddnm_ws_enable(s.ctx, False)
+        parity = {}
+        for name, solver in (("fp64", s64), ("mixed", s)):
+            x2, l2, _ = R.solve(solver, mu_o[:workers], 2)
+            ex = max(float(np.max(np.abs(x2[b] - o[1])) / max(np.max(np.abs(o[1])), 1e-300)) for b, o in enumerate(out))
+            el = max(float(np.max(np.abs(l2[b] - o[2])) / max(np.max(np.abs(o[2])), 1e-300)) for b, o in enumerate(out))
+            eg = float(R.state_errors(x2, np.array([o[1] for o in out])).max())
+            parity[name] = {"xh_max_rel": ex, "lambda_max_rel": el, "state_max_rel": eg}
+        parity["what"] = (f"{workers} instances, 2 SQP iterations from the default start, GPU path vs the FP64 oracle "
+                          f"(largest entry error over the largest entry of each vector; state: relative 2-norm)")
+        lib.ddnm_ws_enable(s.ctx, True)
+
+    # ---- the timed headline: mixed + learned warm start, kws iterations, device-resident
     mu_d = torch.from_numpy(mu).to(dev)
-    x_d = torch.zeros((B, nD), dtype=torch.float64, device=dev)
-    l_d = torch.zeros((B, nC), dtype=torch.float64, device=dev)
+    x_d = torch.zeros((B, R.nD), dtype=torch.float64, device=dev)
+    l_d = torch.zeros((B, R.nC), dtype=torch.float64, device=dev)
     st_d = torch.zeros(B * 32, dtype=torch.uint8, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s.options(tol=0.0, max_iter=kws)
 
     def step():
         lib.ddnm_solve_batch(s.ctx, B, mu_d, None, None, x_d, l_d, None, st_d)
-
-    # launch plan: the autotuner times candidate plans on this very batch (untimed here)
-    if args.plan == "auto":
-        plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, reps=3)
-        plan_info = dict(plan, source="autotuned on this workload", tune_median_ms_per_solve=round(tune_ms, 4))
-    elif args.plan == "host":
-        lib.ddnm_set_tune(s.ctx, graph=0)
-        plan_info = dict(lib.ddnm_get_tune(s.ctx), source="host-driven passes")
-    else:
-        ch, sp, pe = (int(v) for v in args.plan.split(","))
-        lib.ddnm_set_tune(s.ctx, graph=1, chains=ch, con_split=sp, eval_persist=pe)
-        plan_info = dict(lib.ddnm_get_tune(s.ctx), source="--plan")
 
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    st_warm = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=lib.STATS_DTYPE).copy()
-
     clocks = Clocks(gpu_id_for(local))
     time.sleep(0.3)
     tm0 = lib.ddnm_get_timing(s.ctx)
@@ -426,14 +568,44 @@ def main():
     gpu_launches = sum(tm1[k] - tm0[k] for k in launch_keys)
     t_ms = sum(a.elapsed_time(b) for a, b in evs)
     t_max = max_over_ranks(t_ms, dist, dev)
+    x_h = x_d.cpu().numpy()
+    lam_h = l_d.cpu().numpy()
     st = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=lib.STATS_DTYPE).copy()
-    deterministic = bool(np.array_equal(st["n_evals"], st_warm["n_evals"]))
-    value = job_throughput(B, world, args.steps, t_max / 1000.0)
+    err = R.state_errors(x_h, x_ref)
+    n_ok = int(np.sum(err <= ACC))
+    n_ok_all = sum_over_ranks(n_ok, dist, dev)                  # accurate instances of all ranks
+    value = n_ok_all * args.steps / (t_max / 1000.0)
+    lam_err = np.abs(lam_h - lam_ref).max(axis=1) / np.abs(lam_ref).max(axis=1)
+    xh_err = np.abs(x_h - x_ref).max(axis=1) / np.abs(x_ref).max(axis=1)
 
-    # roofline of the dominant kernel: per-kernel device time from the library's CUDA events, taken in a
-    # separate run of the same solves through the host-driven loop (events around every launch)
-    # (non-persistent evaluation, so that every launch covers its whole grid alone on the GPU)
-    kb = max(3, args.steps // 4)
+    # ---- the other methods on the same batch and GPU (one timed solve each after an untimed one)
+    def timed_once(solver, K, tol=0.0):
+        solver.options(tol=tol, max_iter=K)
+        solver.solve(mu)
+        torch.cuda.synchronize()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xs, ls, sts = solver.solve(mu)
+        dt = time.perf_counter() - t0
+        solver.options()
+        return xs, sts, dt
+
+    lib.ddnm_ws_enable(s.ctx, False)
+    x64, st64, t64 = timed_once(s64, k64)
+    e64t = R.state_errors(x64, x_ref)
+    xmp, stmp, tmp_ = timed_once(s, kmp)
+    emp_t = R.state_errors(xmp, x_ref)
+    xpr, stpr, tpr = timed_once(s64, 15, tol=1e-4)
+    epr = R.state_errors(xpr, x_ref)
+    lib.ddnm_ws_enable(s.ctx, True)
+    nfo = min(64, B)
+    fom_rom = R.fom_errors(x_ref[:nfo], mu[:nfo])
+    fom_head = R.fom_errors(x_h[:nfo], mu[:nfo])
+
+    # ---- roofline of the dominant kernel: per-kernel device time from the library's CUDA events, in a
+    # separate run of the headline solve through the host-driven loop (events around every launch)
+    kb = 3
     plan_now = lib.ddnm_get_tune(s.ctx)
     lib.ddnm_set_tune(s.ctx, **dict(plan_now, graph=0, eval_persist=0))
     lib.ddnm_timing_enable(s.ctx, True)
@@ -444,76 +616,114 @@ def main():
     tm = lib.ddnm_get_timing(s.ctx)
     lib.ddnm_timing_enable(s.ctx, False)
     lib.ddnm_set_tune(s.ctx, **plan_now)
+    st_k = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=lib.STATS_DTYPE).copy()
     work = lib.ddnm_get_work(s.ctx)
-    pk = peaks()
-    evals_per_step = float(st["n_evals"].sum())
+    f32_peak, f64_peak = lib.ddnm_measure_peaks(s.ctx)
+    pk = measured_peaks()
+    evals = float(st_k["n_evals"].sum()) * kb            # instance-evaluations in the timed kb solves
     kern = {"k_eval": tm["eval_ms"], "k_constraint": tm["constraint_ms"], "k_kkt": tm["step_ms"]}
     dom = max(kern, key=kern.get)
     if dom == "k_eval":
-        fl = work["eval_flops"] * evals_per_step * kb
-        peak, bound, unit = pk["fp32_tflops"], "alu", "TFLOP/s"
-        launches = tm["eval_launches"]
+        fl, peak, launches = work["eval_flops"] * evals, f32_peak, tm["eval_launches"]
+        note = "FP32 flops of the evaluation (ddnm_get_work) / summed launch time; peak: measured FFMA rate"
     elif dom == "k_constraint":
-        fl = work["constraint_fp64_flops"] * evals_per_step * kb
-        peak, bound, unit = pk["fp64_tflops"], "alu", "TFLOP/s"
-        launches = tm["constraint_launches"]
+        fl, peak, launches = work["constraint_fp64_flops"] * evals, f64_peak, tm["constraint_launches"]
+        note = "FP64-accurate flops 2 n_C N_A per evaluation; peak: measured DFMA rate"
     else:
-        fl = work["step_fp64_flops"] * float(st["iters"].sum()) * kb
-        peak, bound, unit = pk["fp64_tflops"], "alu", "TFLOP/s"
-        launches = tm["step_launches"]
+        fl, peak, launches = work["step_fp64_flops"] * float(st_k["iters"].sum()) * kb, f64_peak, tm["step_launches"]
+        note = "FP64 flops of the KKT step per accepted point; peak: measured DFMA rate"
     achieved = fl / (kern[dom] / 1000.0) / 1e12
-    roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None,
-            "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz" if dom == "k_eval"
-            else "derived: 152 SMs x 2 DFMA/clk x 2 x sm_max_mhz",
+    eval_bytes = work["table_bytes"] * tm["eval_launches"] + work["instance_bytes"] * evals
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_note": note + " (of measured)",
             "launches": launches, "flops_per_launch": fl / max(launches, 1),
             "avg_launch_us": 1000.0 * kern[dom] / max(launches, 1),
-            # algorithmic bytes of the evaluation launches: shared tables once per launch, the instance
-            # bytes per instance-evaluation
-            "hbm_frac_of_measured": ((work["table_bytes"] * tm["eval_launches"] + work["instance_bytes"] * evals_per_step * kb)
-                                     / (tm["eval_ms"] / 1000.0) / 1e9) / pk["hbm_gbs"],
-            "eval_algorithmic_bytes_per_launch": (work["table_bytes"] * tm["eval_launches"]
-                                                  + work["instance_bytes"] * evals_per_step * kb) / max(tm["eval_launches"], 1),
-            "kernel_ms_per_step": {k: round(v / kb, 4) for k, v in kern.items()},
-            "timed_in": f"{kb} extra solves, host-driven loop, one CTA per item, CUDA events around every launch"}
-    prof = eval_traffic_profile()
-    if dom == "k_eval" and prof is not None:
+            "hbm_frac_of_measured": (eval_bytes / (tm["eval_ms"] / 1000.0) / 1e9) / float(pk.get("hbm_gbs", 6800.0)),
+            "eval_algorithmic_bytes_per_launch": eval_bytes / max(tm["eval_launches"], 1),
+            "kernel_ms_per_solve": {k: round(v / kb, 3) for k, v in kern.items()},
+            "measured_peaks_tflops": {"fp32": f32_peak, "fp64": f64_peak},
+            "timed_in": f"{kb} extra headline solves, host-driven loop, one CTA per item, CUDA events around every launch"}
+    prof = traffic_profile(dom, args.config)
+    if prof is not None:
         roof["traffic"] = prof
-        roof["traffic_source"] = "profiles/k_eval_c2.md (ncu dram__bytes_read.sum + dram__bytes_write.sum per launch)"
+        roof["traffic_source"] = f"profiles/{dom}_{args.config}.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
 
-    # end to end through the public API with host (pinned) buffers, copies inside the timed region
+    # ---- end to end through the public API with host (pinned) buffers, copies inside the timed region
     mu_h = torch.from_numpy(mu.copy()).pin_memory()
-    x_h = torch.zeros((B, nD), dtype=torch.float64).pin_memory()
-    l_h = torch.zeros((B, nC), dtype=torch.float64).pin_memory()
+    xh_h = torch.zeros((B, R.nD), dtype=torch.float64).pin_memory()
+    lh_h = torch.zeros((B, R.nC), dtype=torch.float64).pin_memory()
     st_h = np.zeros(B, dtype=lib.STATS_DTYPE)
+    s.options(tol=0.0, max_iter=kws)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        lib.ddnm_solve_batch(s.ctx, B, mu_h.numpy(), None, None, x_h.numpy(), l_h.numpy(), None, st_h)
+        lib.ddnm_solve_batch(s.ctx, B, mu_h.numpy(), None, None, xh_h.numpy(), lh_h.numpy(), None, st_h)
     torch.cuda.synchronize()
     t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
-    e2e = {"value": job_throughput(B, world, e2e_steps, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(mu.nbytes),
-           "d2h_bytes_per_step": int(x_h.numel() * 8 + l_h.numel() * 8 + st_h.nbytes)}
+    e2e_ok = int(np.sum(R.state_errors(xh_h.numpy(), x_ref) <= ACC))
+    e2e = {"value": sum_over_ranks(e2e_ok, dist, dev) * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(mu.nbytes),
+           "d2h_bytes_per_step": int(xh_h.numel() * 8 + lh_h.numel() * 8 + st_h.nbytes),
+           "accurate_fraction": e2e_ok / B}
+    s.options()
+
+    def q(a):
+        return {"median": float(np.median(a)), "max": float(np.max(a))}
 
     cfg = workload_config(args.config)
-    cfg["launch_plan"] = plan_info
-    cfg.update({"converged_fraction": float(np.mean(st["status"] == lib.DDNM_CONVERGED)),
-                "mean_iters": float(st["iters"].mean()), "mean_evals": float(st["n_evals"].mean()),
-                "median_final_merit": float(np.median(st["merit"])), "deterministic_across_steps": deterministic,
-                "parallelism": f"replicas: {world} GPU(s), {B} mu each"})
+    cfg.update({
+        "method": f"mixed precision (FP32 evaluation, FP64 KKT / merit / constraint residual) + learned warm start, "
+                  f"{kws} SQP iterations (the smallest budget meeting the accuracy criterion on a calibration batch)",
+        "accuracy_criterion": f"relative 2-norm of g(xh) - g(xh_ref) <= {ACC:g}, xh_ref: FP64 ROM solution "
+                              f"({K_REF} SQP iterations); only instances that meet it are counted",
+        "accurate_fraction": n_ok / B,
+        "launch_plan": dict(plan, source="autotuned on this batch with the timed iteration budget",
+                            tune_median_ms_per_solve=round(tune_ms, 3)),
+        "parallelism": f"replicas: {world} GPU(s), {B} mu each",
+        "setup_seconds": round(time.perf_counter() - t_setup, 1)})
+    accuracy = {
+        "headline_state_rel_err": q(err), "headline_xh_rel_err": q(xh_err), "headline_lambda_rel_err": q(lam_err),
+        "rom_vs_fom_state_rel_err": q(fom_rom), "headline_vs_fom_state_rel_err": q(fom_head),
+        "fom_sample": nfo, "vs_oracle": parity,
+        "reference_final_merit": q(st_ref["merit"]),
+        "headline_final_merit": q(st["merit"]),
+    }
+    comparison = {
+        "fp64_plain_default_start": {"iters": k64, "solves_per_s": n_ok_fp(e64t) * 1.0 / t64,
+                                     "accurate_fraction": n_ok_fp(e64t) / B, "calibration_max_err": e64},
+        "mixed_plain_default_start": {"iters": kmp, "solves_per_s": n_ok_fp(emp_t) * 1.0 / tmp_,
+                                      "accurate_fraction": n_ok_fp(emp_t) / B, "calibration_max_err": emp},
+        "mixed_warm_start": {"iters": kws, "calibration_max_err": ews},
+        "fp64_paper_rule": {"converged_fraction": float(np.mean(stpr["status"] == lib.DDNM_CONVERGED)),
+                            "mean_iters": float(stpr["iters"].mean()), "solves_per_s_all": B / tpr,
+                            "accurate_fraction": n_ok_fp(epr) / B},
+        "speedup_vs_fp64_plain": value / world / max(n_ok_fp(e64t) / t64, 1e-300),
+        "timing": "one solve of the timed batch after an untimed one with the same options (host timer)",
+    }
+    training = {"fom_snapshots": R.n_snap, "fom_seconds": round(R.t_fom, 2), "fom_mean_newton": R.fom_newton,
+                "ae_stages": AE_STAGES, "ae_seconds": round(R.t_train, 1),
+                "ae_loss_interior_median_first_last": [float(np.median(R.loss_first[0::2])), float(np.median(R.loss_last[0::2]))],
+                "ae_loss_interior_max_last": float(np.max(R.loss_last[0::2])),
+                "ws_train_seconds": round(t_ws, 2), "ws_loss_first_last": [float(ws_losses[0]), float(ws_losses[-1])],
+                "ws_fallback_fraction": float(np.mean(st["flags"] & lib.DDNM_FLAG_WS_FALLBACK > 0))}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 KKT", "data": "synthetic",
             "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(gpu_launches),
-            "clocks": clk}
+            "clocks": clk, "accuracy": accuracy, "comparison": comparison, "training": training}
     if rank == 0:
         print(json.dumps(line))
     s.close()
+    s64.close()
     if dist:
         dist.destroy_process_group()
+
+
+def n_ok_fp(errs):
+    return int(np.sum(np.asarray(errs) <= ACC))
 
 
 if __name__ == "__main__":

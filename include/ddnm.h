@@ -237,6 +237,14 @@ int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const double* x0, c
                      double* x_out, double* lam_out, double* state_out, ddnm_stats* stats,
                      int mem_kind, void* stream);
 
+/* Reconstructed states g(xh) of B latent vectors (the state the relative error of Eq. relative_error
+ * measures, Sec. 7.1): every variable from its owning subdomain's interior or interface decoder.
+ *   x          B x n_D latent coordinates
+ *   state_out  B x N_x
+ * Host or device memory (mem_kind), queued on stream; with host memory the call returns once the state is
+ * copied back. */
+int ddnm_reconstruct(ddnm_ctx* ctx, int B, const double* x, double* state_out, int mem_kind, void* stream);
+
 /* One evaluation at (x, lam) without iterating.
  *   F_out      B x (n_D + n_C) KKT right-hand side F (NULL to skip)
  *   r_hr_out   B x sum(N_i^B) collocation residuals Z_i r_i (NULL to skip)
@@ -356,6 +364,12 @@ typedef struct ddnm_tune {
     int eval_groups;    /* 1 (default): one instance per evaluation CTA; 0: an evaluation CTA holds as many
                            independent 256-thread groups as one-instance CTAs would fit an SM, on neighbouring
                            instances of one subdomain (they share its tables through L1) */
+    int atil;           /* the constraint residual Atil = C jump of the mixed path: 1 over tiles of instances
+                           (C read once per tile) on the FP32 pipe in double-float arithmetic (C split into two
+                           floats; each jump, a difference of two FP32 outputs, held exactly as two floats;
+                           FP64 folds every 64 rows), accurate to about 2^-48 of sum_l |C_kl jump_l|;
+                           0 per instance in FP64; -1 (default) picks 1 when n_C N_A >= 2^20.  The FP64 path
+                           always takes 0. */
 } ddnm_tune;
 
 /* Set / read the plan (ddnm_get_tune reports d_gemm as given, -1 included).  DDNM_E_INVALID outside the

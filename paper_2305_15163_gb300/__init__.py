@@ -80,7 +80,7 @@ class ddnm_work(C.Structure):
 
 class ddnm_tune(C.Structure):
     _fields_ = [("graph", C.c_int), ("chains", C.c_int), ("con_split", C.c_int), ("eval_persist", C.c_int),
-                ("d_gemm", C.c_int), ("eval_groups", C.c_int)]
+                ("d_gemm", C.c_int), ("eval_groups", C.c_int), ("atil", C.c_int)]
 
 
 FOM_STATS_DTYPE = np.dtype([("newton_iters", np.int32), ("krylov_iters", np.int32), ("status", np.int32),
@@ -103,6 +103,7 @@ _sig = {
     "ddnm_solve_batch": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_linearize": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
+    "ddnm_reconstruct": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp]),
     "ddnm_residual_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "ddnm_ws_init": (C.c_int, [_vp, C.c_int, _vp]),
     "ddnm_ws_set_norm": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -254,6 +255,12 @@ def ddnm_residual(ctx, B, mu, x, lam, F_out, r_hr_out, r_full_out):
     kind = _mem_kind(mu, x, lam, F_out, r_hr_out, r_full_out)
     _check(ctx, _lib.ddnm_residual(ctx, B, _ptr(mu), _ptr(x), _ptr(lam), _ptr(F_out), _ptr(r_hr_out),
                                    _ptr(r_full_out), kind, _stream(kind)))
+
+
+def ddnm_reconstruct(ctx, B, x, state_out):
+    """g(xh) of B latent vectors into state_out (B x N_x): numpy host arrays or torch CUDA tensors."""
+    kind = _mem_kind(x, state_out)
+    _check(ctx, _lib.ddnm_reconstruct(ctx, int(B), _ptr(x), _ptr(state_out), kind, _stream(kind)))
 
 
 def ddnm_linearize(ctx, B, mu, x, lam, H_out, D_out, Atil_out):
@@ -437,8 +444,9 @@ def ddnm_get_work(ctx) -> dict:
     return {k: getattr(w, k) for k, _ in ddnm_work._fields_}
 
 
-def ddnm_set_tune(ctx, graph=1, chains=1, con_split=512, eval_persist=0, d_gemm=-1, eval_groups=1):
-    t = ddnm_tune(int(graph), int(chains), int(con_split), int(eval_persist), int(d_gemm), int(eval_groups))
+def ddnm_set_tune(ctx, graph=1, chains=1, con_split=512, eval_persist=0, d_gemm=-1, eval_groups=1, atil=-1):
+    t = ddnm_tune(int(graph), int(chains), int(con_split), int(eval_persist), int(d_gemm), int(eval_groups),
+                  int(atil))
     _check(ctx, _lib.ddnm_set_tune(ctx, C.byref(t)))
 
 

@@ -84,6 +84,7 @@ struct ddnm_ctx {
     int* d_hr = nullptr;
     int* d_con = nullptr;
     double* d_C = nullptr;
+    float* d_Ct = nullptr;             // mixed path: C transposed, split into FP32 hi and lo parts (2 N_A ldct)
     int* d_bnd_ij = nullptr;
     ddnm::SubDev* d_sub = nullptr;
     ddnm::ChunkDev* d_chunk = nullptr;
@@ -114,8 +115,9 @@ struct ddnm_ctx {
     size_t n_events = 0;               // pairs in use for the current call
 
     // launch plan and the captured solve graph (ddnm_kernels.cu)
-    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0, -1, 1};
+    ddnm_tune tune{1, 1, ddnm::CON_SPLIT, 0, -1, 1, -1};
     int dgemm_auto = 0;                // the d_gemm = -1 choice for these sizes (set with the tables)
+    int atil_auto = 0;                 // the atil = -1 choice
     long long gen = 0;                 // bumped whenever device tables or workspace pointers change
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;

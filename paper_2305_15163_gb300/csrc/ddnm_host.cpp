@@ -243,6 +243,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_hr);
     cudaFree(ctx->d_con);
     cudaFree(ctx->d_C);
+    cudaFree(ctx->d_Ct);
     cudaFree(ctx->d_bnd_ij);
     cudaFree(ctx->d_sub);
     cudaFree(ctx->d_chunk);
@@ -773,6 +774,24 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_con, con.data(), con.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_C, std::max<size_t>(ctx->C.size(), 1) * 8));
     CK(cudaMemcpy(ctx->d_C, ctx->C.data(), ctx->C.size() * 8, cudaMemcpyHostToDevice));
+    // mixed path: C transposed (constraint row l, then test-matrix row c) and split into two floats per entry,
+    // hi = fl32(C) and lo = fl32(C - hi), rows padded with zeros to ldct (the double-float Atil of k_atil_df)
+    cudaFree(ctx->d_Ct);
+    ctx->d_Ct = nullptr;
+    const int ldct = nC <= 32 ? 32 : (nC <= 64 ? 64 : (nC + 127) / 128 * 128);
+    if (tsize == 4 && nC > 0) {
+        std::vector<float> ct((size_t)2 * ctx->N_A * ldct, 0.f);
+        float* lo = ct.data() + (size_t)ctx->N_A * ldct;
+        for (int c = 0; c < nC; ++c)
+            for (int l = 0; l < ctx->N_A; ++l) {
+                const double v = ctx->C[(size_t)c * ctx->N_A + l];
+                const float h = (float)v;
+                ct[(size_t)l * ldct + c] = h;
+                lo[(size_t)l * ldct + c] = (float)(v - (double)h);
+            }
+        CK(cudaMalloc(&ctx->d_Ct, ct.size() * 4));
+        CK(cudaMemcpy(ctx->d_Ct, ct.data(), ct.size() * 4, cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc(&ctx->d_bnd_ij, std::max<size_t>(ctx->bnd_ij.size(), 1) * 4));
     CK(cudaMemcpy(ctx->d_bnd_ij, ctx->bnd_ij.data(), ctx->bnd_ij.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_sub, ns * sizeof(SubDev)));
@@ -832,6 +851,11 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         for (const SubDev& S : ctx->hsub) big = std::max(big, (long long)S.hG * nC);
         ctx->dgemm_auto = big >= 65536 ? 1 : 0;
     }
+    ctx->atil_auto = (long long)nC * ctx->N_A >= (1LL << 20) ? 1 : 0;
+    pd.ldct = ldct;
+    pd.Cthi = ctx->d_Ct;
+    pd.Ctlo = ctx->d_Ct ? ctx->d_Ct + (size_t)ctx->N_A * ldct : nullptr;
+    pd.atil_df = 0;
     pd.pg_stride = std::max(pg_stride, 1LL);
     pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.tiles = ctx->d_tiles; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
     pd.hr = ctx->d_hr;

@@ -19,6 +19,9 @@ constexpr int CON_THREADS = 256;
 constexpr int CON_SPLIT = 512; // default constraint rows per constraint CTA (the N_A axis is split)
 constexpr int CON_BLOCK = 512;  // constraint rows of one canonical partial of Atil (fixes the summation order)
 constexpr int MIN_CON_SPLIT = CON_BLOCK, MAX_CON_SPLIT = 4 * CON_BLOCK;
+// double-float Atil of the mixed path (k_atil_df): constraint rows staged per chunk, rows between the FP64 folds
+// of a double-float sum, constraint rows per slice (one Atil partial per slice and instance)
+constexpr int ATIL_KC = 32, ATIL_FOLD = 64, ATIL_KS = MAX_CON_SPLIT;
 constexpr int MAX_CHAINS = 64; // instance groups iterating concurrently inside the solve graph
 constexpr int PASSES_PER_BODY = 2;   // SQP passes per turn of an instance group's device-side loop
 constexpr int MAX_CLASSES = 12; // width classes (RO, RG) of the evaluation kernel
@@ -162,6 +165,10 @@ struct ProbDev {
     const int* con_lo;             // flat interface index (goff + local) of the +1 side of each constraint row
     const int* con_hi;             // ... of the -1 side
     const double* C;               // n_C x N_A
+    const float* Cthi;             // N_A x ldct: C transposed and split, C[c][l] = Cthi[l][c] + Ctlo[l][c] (to
+    const float* Ctlo;             // 2^-48), zero for c >= n_C; mixed path only
+    int ldct;                      // row stride of Cthi / Ctlo: n_C rounded up to 32, 64 or a multiple of 128
+    int atil_df;                   // 1: Atil by k_atil_df (instance tiles, double-float); 0: FP64 slices
     int qld;                       // row stride of every Q_i^T in the value pool: round4(n_C)
     const int* bnd_ij;             // n_bnd x 2 grid indices of the Dirichlet points the stencils touch
     // workspace (B instances)

@@ -976,6 +976,150 @@ __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B, in
     }
 }
 
+// ------------------------------------------------------------------------ Atil in double-float (mixed path)
+
+// a + b = s + e exactly (Knuth's TwoSum; the _rn intrinsics keep the compiler from contracting or reordering)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Atil partials of one slice of the constraint rows for a tile of instances, on the FP32 pipe, accurate to
+// about 2^-48 of sum_l |C_kl jump_l| (Sec. 3.1: Atil = C sum_i A_i g_i^G = C jump).  C is shared by every
+// instance, so a CTA stages a chunk of it once for TBI instances.  C is held split, C = C_hi + C_lo (two
+// floats, transposed: Ct[l][c]); jump_l = g_lo - g_hi, the difference of two FP32 interface outputs, is held
+// exactly as j_hi + j_lo (TwoSum).  A term C_kl jump_l is C_hi j_hi, exact as p + e with e from an FMA, plus
+// the cross terms C_hi j_lo + C_lo j_hi (C_lo j_lo, below 2^-48 of the term, is left out).  p joins a running
+// FP32 sum s through TwoSum, whose error, e and the cross terms join a second FP32 sum c: the accumulation of
+// Ogita, Rump and Oishi's Dot2.  Every ATIL_FOLD rows s + c is added to an FP64 accumulator, which bounds the
+// second-order error of Dot2 by that block length (about (64 u)^2 = 2^-36 in the worst case, u = 2^-24,
+// typically near u^2).  CTA (slice, instance tile, row tile); thread: RM consecutive rows of C (by lane) x IM
+// instances (by warp).  The partial of (instance, slice) goes where the FP64 slices put theirs.
+template <int RM, int IM>
+__global__ void __launch_bounds__(256) k_atil_df(ProbDev P, int B) {
+    constexpr int RT = 32 * RM, TBI = 8 * IM, KC = ATIL_KC, JS = TBI + 1;
+    __shared__ __align__(16) float Ch[KC * RT];
+    __shared__ __align__(16) float Cl[KC * RT];
+    __shared__ float Jh[KC * JS], Jl[KC * JS];
+    __shared__ int s_run[TBI];
+    __shared__ int s_any;
+    const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
+    const int sl = blockIdx.x, b0 = blockIdx.y * TBI, c0 = blockIdx.z * RT;
+    const int k0 = sl * P.con_split, k1 = min(P.N_A, k0 + P.con_split);
+    if (tid == 0) s_any = 0;
+    __syncthreads();
+    if (tid < TBI) {
+        const int b = b0 + tid;
+        const int r = b < B && P.ist[(size_t)b * INST_INTS + I_STATUS] == ST_RUNNING;
+        s_run[tid] = r;
+        if (r) s_any = 1;
+    }
+    __syncthreads();
+    if (!s_any) return;
+    const float* g = (const float*)P.gG;
+    float s[RM][IM], c[RM][IM];
+    double acc[RM][IM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < IM; ++j) {
+            s[i][j] = c[i][j] = 0.f;
+            acc[i][j] = 0.0;
+        }
+    for (int k = k0; k < k1; k += KC) {
+        __syncthreads();
+        for (int e = tid; e < KC * RT / 4; e += 256) {          // C chunk: KC rows of Ct, RT values each
+            const int kk = e / (RT / 4), q = e - kk * (RT / 4);
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+            if (k + kk < k1) {
+                const size_t o = (size_t)(k + kk) * P.ldct + c0 + 4 * q;
+                h = *reinterpret_cast<const float4*>(P.Cthi + o);
+                l = *reinterpret_cast<const float4*>(P.Ctlo + o);
+            }
+            reinterpret_cast<float4*>(Ch)[e] = h;
+            reinterpret_cast<float4*>(Cl)[e] = l;
+        }
+        for (int e = tid; e < KC * TBI; e += 256) {             // jumps of the tile's instances, exact
+            const int inst = e / KC, kk = e - inst * KC;
+            float hi = 0.f, lo = 0.f;
+            if (k + kk < k1 && s_run[inst]) {
+                const float* gb = g + (size_t)(b0 + inst) * P.sum_NG;
+                two_sum(gb[P.con_lo[k + kk]], -gb[P.con_hi[k + kk]], hi, lo);
+            }
+            Jh[kk * JS + inst] = hi;
+            Jl[kk * JS + inst] = lo;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int kk = 0; kk < KC; ++kk) {
+            float ch[RM], cl[RM], jh[IM], jl[IM];
+            if constexpr (RM == 4) {
+                const float4 a = reinterpret_cast<const float4*>(Ch + kk * RT)[lane];
+                const float4 b = reinterpret_cast<const float4*>(Cl + kk * RT)[lane];
+                ch[0] = a.x; ch[1] = a.y; ch[2] = a.z; ch[3] = a.w;
+                cl[0] = b.x; cl[1] = b.y; cl[2] = b.z; cl[3] = b.w;
+            } else if constexpr (RM == 2) {
+                const float2 a = reinterpret_cast<const float2*>(Ch + kk * RT)[lane];
+                const float2 b = reinterpret_cast<const float2*>(Cl + kk * RT)[lane];
+                ch[0] = a.x; ch[1] = a.y;
+                cl[0] = b.x; cl[1] = b.y;
+            } else {
+                ch[0] = Ch[kk * RT + lane];
+                cl[0] = Cl[kk * RT + lane];
+            }
+#pragma unroll
+            for (int j = 0; j < IM; ++j) {
+                jh[j] = Jh[kk * JS + wq * IM + j];
+                jl[j] = Jl[kk * JS + wq * IM + j];
+            }
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < IM; ++j) {
+                    const float p = __fmul_rn(ch[i], jh[j]);
+                    const float e = __fmaf_rn(ch[i], jh[j], -p);        // ch jh - p, exactly
+                    float t, q;
+                    two_sum(s[i][j], p, t, q);
+                    s[i][j] = t;
+                    float cc = __fadd_rn(c[i][j], __fadd_rn(q, e));
+                    cc = __fmaf_rn(ch[i], jl[j], cc);
+                    c[i][j] = __fmaf_rn(cl[i], jh[j], cc);
+                }
+        }
+        if ((k - k0 + KC) % ATIL_FOLD == 0 || k + KC >= k1) {
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < IM; ++j) {
+                    acc[i][j] += (double)s[i][j] + (double)c[i][j];
+                    s[i][j] = c[i][j] = 0.f;
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < IM; ++j) {
+            const int cr = c0 + RM * lane + i, inst = wq * IM + j;
+            if (cr < P.n_C && s_run[inst]) P.Atil[((size_t)(b0 + inst) * P.n_split + sl) * P.n_C + cr] = acc[i][j];
+        }
+}
+
+// the double-float Atil launch of a pass: instance tiles of 32, 16 or 8 (by batch), row tiles of ldct rows up to
+// 128; the summation order of an entry does not depend on either, so the result does not depend on the plan
+cudaError_t launch_atil(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st) {
+    const int RT = std::min(P.ldct, 128), IM = B >= 32 ? 4 : (B >= 16 ? 2 : 1), TBI = 8 * IM;
+    const dim3 grid(P.n_split, (B + TBI - 1) / TBI, P.ldct / RT);
+#define DDNM_ATIL(R, I) \
+    if (RT == 32 * R && IM == I) k_atil_df<R, I><<<grid, 256, 0, st>>>(P, B);
+    DDNM_ATIL(1, 1) DDNM_ATIL(1, 2) DDNM_ATIL(1, 4) DDNM_ATIL(2, 1) DDNM_ATIL(2, 2) DDNM_ATIL(2, 4)
+    DDNM_ATIL(4, 1) DDNM_ATIL(4, 2) DDNM_ATIL(4, 4)
+#undef DDNM_ATIL
+    (void)ctx;
+    return cudaGetLastError();
+}
+
 // CTAs per (slice, instance) of k_constraint over the rows of C: about two CTAs per SM in all, at least one
 // row of C per warp
 int con_row_groups(const ddnm_ctx* ctx, const ProbDev& P, int B) {
@@ -1997,13 +2141,18 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
     tstop(ctx, k, st);
     k = tstart(ctx, 1, st);
     {
-        // with the factorisation CTAs of the step (8 subdomains each) when the pass goes on to a KKT step
+        // with the factorisation CTAs of the step (8 subdomains each) when the pass goes on to a KKT step; the
+        // double-float Atil (mixed path) in a launch of its own, the constraint launch then only factorises
         const int nfc = factor ? (P.n_sub + 2 * FAC_WARPS - 1) / (2 * FAC_WARPS) : 0;
-        const int nrg = con_row_groups(ctx, P, B);
+        const int nrg = P.atil_df ? 0 : con_row_groups(ctx, P, B);
+        if constexpr (sizeof(T) == 4) {
+            if (P.atil_df) CK(launch_atil(ctx, P, B, st));
+        }
         const size_t smem = std::max((size_t)P.con_split * 8, nfc ? (size_t)ctx->fac_smem : 0);
         if (smem > (size_t)std::max(MAX_CON_SPLIT * 8, ctx->fac_smem))     // beyond what set_smem_attrs allowed
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "constraint launch: shared memory above its limit");
-        k_constraint<T><<<dim3(P.n_split * nrg + nfc, B), CON_THREADS, smem, st>>>(P, B, nrg);
+        if (P.n_split * nrg + nfc > 0)
+            k_constraint<T><<<dim3(P.n_split * nrg + nfc, B), CON_THREADS, smem, st>>>(P, B, nrg);
     }
     CK(cudaGetLastError());
     tstop(ctx, k, st);
@@ -2121,6 +2270,17 @@ void fold_pending(ddnm_ctx* ctx) {
 }
 
 int resolved_dgemm(const ddnm_ctx* ctx) { return ctx->tune.d_gemm < 0 ? ctx->dgemm_auto : ctx->tune.d_gemm; }
+
+// the Atil form of the plan (double-float instance tiles only in the mixed path, with the split C uploaded);
+// sets the slices of the constraint rows that the Atil partials cover
+void resolve_atil(const ddnm_ctx* ctx, ProbDev& P) {
+    const int want = ctx->tune.atil < 0 ? ctx->atil_auto : ctx->tune.atil;
+    P.atil_df = (ctx->precision == DDNM_MIXED && want == 1 && P.Cthi) ? 1 : 0;
+    if (P.atil_df) {
+        P.con_split = ATIL_KS;
+        P.n_split = (P.N_A + ATIL_KS - 1) / ATIL_KS;
+    }
+}
 
 void drop_graph(ddnm_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
@@ -2249,7 +2409,7 @@ int solve_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool ha
     const std::vector<long long> key{ctx->gen, B, Bw, ws, has_x0, has_lam0, (long long)sizeof(T), max_passes,
                                      bits(o.tol), bits(o.armijo_c1), bits(o.beta), o.max_iter, o.max_backtracks,
                                      ctx->tune.chains, ctx->tune.con_split, ctx->tune.eval_persist, ctx->n_sm,
-                                     P.d_gemm, ctx->tune.eval_groups};
+                                     P.d_gemm, ctx->tune.eval_groups, P.atil_df};
     if (!ctx->gexec || key != ctx->gkey) {
         const int rc = build_graph<T>(ctx, P, B, Bw, ws, has_x0, has_lam0, max_passes);
         if (rc) return rc;
@@ -2306,6 +2466,7 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
     P.con_split = ctx->tune.con_split;
     P.n_split = (P.N_A + P.con_split - 1) / P.con_split;
     P.d_gemm = resolved_dgemm(ctx);
+    resolve_atil(ctx, P);
     if (ctx->tune.graph && !ctx->timing) {
         rc = fp64 ? solve_graph<double>(ctx, P, B, Bw, ws, x0 != nullptr, lam0 != nullptr, max_passes, st)
                   : solve_graph<float>(ctx, P, B, Bw, ws, x0 != nullptr, lam0 != nullptr, max_passes, st);
@@ -2384,6 +2545,7 @@ int eval_once(ddnm_ctx* ctx, ProbDev& P, int B, const double* mu, const double* 
     ctx->tm.other_launches++;
     P.r_hr = r_hr_dev;
     P.d_gemm = resolved_dgemm(ctx);
+    resolve_atil(ctx, P);
     return launch_eval<T>(ctx, P, B, st);
 }
 }  // namespace
@@ -2426,6 +2588,32 @@ extern "C" int ddnm_residual(ddnm_ctx* ctx, int B, const double* mu, const doubl
     if (host && r_hr_out) CK(cudaMemcpyAsync(r_hr_out, dR, (size_t)B * P.sum_NB * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));   // temporaries are freed on return
     return tflush(ctx, st);
+}
+
+extern "C" int ddnm_reconstruct(ddnm_ctx* ctx, int B, const double* x, double* state_out, int mem_kind, void* stream) {
+    int rc = prepare(ctx, B, mem_kind);
+    if (rc) return rc;
+    if (!x || !state_out) return ddnm_fail(ctx, DDNM_E_INVALID, "x and state_out are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ProbDev& P = ctx->pd;
+    const bool host = mem_kind == DDNM_MEM_HOST;
+    Tmp tS;
+    const double* dx = x;
+    double* dS = state_out;
+    if (host) {
+        if ((rc = copy_in(ctx, P.x, x, (size_t)B * P.n_D, mem_kind, st))) return rc;
+        dx = P.x;
+        CK(cudaMalloc(&tS.p, (size_t)B * P.N_x * 8));
+        dS = (double*)tS.p;
+    }
+    rc = ctx->precision == DDNM_FP64 ? reconstruct<double>(ctx, P, B, dx, dS, st)
+                                     : reconstruct<float>(ctx, P, B, dx, dS, st);
+    if (rc) return rc;
+    if (host) {
+        CK(cudaMemcpyAsync(state_out, dS, (size_t)B * P.N_x * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));   // the temporary is freed on return
+    }
+    return DDNM_OK;
 }
 
 extern "C" int ddnm_linearize(ddnm_ctx* ctx, int B, const double* mu, const double* x, const double* lam, double* H_out,
@@ -2493,9 +2681,9 @@ extern "C" int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t) {
     const bool pow2 = t->con_split > 0 && (t->con_split & (t->con_split - 1)) == 0;
     if (t->graph < 0 || t->graph > 1 || t->chains < 1 || t->chains > MAX_CHAINS || !pow2 ||
         t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8 ||
-        t->d_gemm < -1 || t->d_gemm > 1 || t->eval_groups < 0 || t->eval_groups > 1)
+        t->d_gemm < -1 || t->d_gemm > 1 || t->eval_groups < 0 || t->eval_groups > 1 || t->atil < -1 || t->atil > 1)
         return ddnm_fail(ctx, DDNM_E_INVALID, "tune: graph 0/1, chains 1..64, con_split 512, 1024 or 2048, "
-                                              "eval_persist 0..8, d_gemm -1..1, eval_groups 0/1");
+                                              "eval_persist 0..8, d_gemm -1..1, eval_groups 0/1, atil -1..1");
     ctx->tune = *t;
     return DDNM_OK;
 }
@@ -2572,6 +2760,10 @@ extern "C" int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kin
     if (cur.d_gemm < 0) cur.d_gemm = ctx->dgemm_auto;
     if ((rc = sweep(&ddnm_tune::d_gemm, {0, 1}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::eval_groups, {0, 1}))) return finish(rc);
+    if (ctx->precision == DDNM_MIXED) {
+        if (cur.atil < 0) cur.atil = ctx->atil_auto;
+        if ((rc = sweep(&ddnm_tune::atil, {0, 1}))) return finish(rc);
+    }
     ctx->tune = cur;
     if (best) *best = cur;
     if (best_ms) *best_ms = cur_ms;

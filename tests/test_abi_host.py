@@ -94,14 +94,15 @@ def test_launch_plan_validation():
     wl = inputs.workload("tiny12x10_2x2")
     s = lib.Solver(wl)
     assert lib.ddnm_get_tune(s.ctx) == {"graph": 1, "chains": 1, "con_split": 512, "eval_persist": 0, "d_gemm": -1,
-                                        "eval_groups": 1}
-    lib.ddnm_set_tune(s.ctx, graph=0, chains=64, con_split=2048, eval_persist=8, d_gemm=1, eval_groups=0)
+                                        "eval_groups": 1, "atil": -1}
+    lib.ddnm_set_tune(s.ctx, graph=0, chains=64, con_split=2048, eval_persist=8, d_gemm=1, eval_groups=0, atil=1)
     assert lib.ddnm_get_tune(s.ctx) == {"graph": 0, "chains": 64, "con_split": 2048, "eval_persist": 8, "d_gemm": 1,
-                                        "eval_groups": 0}
-    good = dict(graph=1, chains=2, con_split=1024, eval_persist=1, d_gemm=0, eval_groups=0)
+                                        "eval_groups": 0, "atil": 1}
+    good = dict(graph=1, chains=2, con_split=1024, eval_persist=1, d_gemm=0, eval_groups=0, atil=0)
     for bad in (dict(graph=2), dict(graph=-1), dict(chains=0), dict(chains=65), dict(con_split=256),
                 dict(con_split=768), dict(con_split=4096), dict(eval_persist=-1), dict(eval_persist=9),
-                dict(d_gemm=2), dict(d_gemm=-2), dict(eval_groups=2), dict(eval_groups=-1)):
+                dict(d_gemm=2), dict(d_gemm=-2), dict(eval_groups=2), dict(eval_groups=-1), dict(atil=2),
+                dict(atil=-2)):
         with pytest.raises(lib.DDNMError) as e:
             lib.ddnm_set_tune(s.ctx, **{**good, **bad})
         assert e.value.code == lib.DDNM_E_INVALID

@@ -180,11 +180,16 @@ def test_rom_with_oracle_trained_decoders_fp64(name):
     s.close()
 
 
+MERIT_FLOOR = {"c1": 1e-4, "c2": 1e-2}
+
+
 @pytest.mark.parametrize("name", ["c1", "c2"])
 def test_rom_with_oracle_trained_decoders_mixed(name):
     """The same decoders in the mixed path.
-    * Two SQP iterations (the merit far above the FP32 rounding floor): the iterates, counts and step
-      lengths match the oracle's two iterations (1e-4).
+    * Two SQP iterations (the merit above the FP32 rounding floor): the iterates, counts and step lengths
+      match the oracle's two iterations (1e-4); the merit within 1e-4 plus the floor of the FP32 rounding of
+      rho (MERIT_FLOOR: the merit the mixed path stalls at under the paper's rule, about 1e-5 on the 32 x 32
+      grid and 5e-3 on 128 x 128, where the stencil weights nu / h^2 are 16 times larger), checked below.
     * Under the paper's stopping rule: the final latent coordinates and the reconstructed state are within
       1e-4 of the oracle's converged solution (tolerance 1e-9, up to 40 iterations).  The multipliers are
       within 1e-2: near the solution rho_i = R_i^T r_i + E_i^T lambda carries the FP32 rounding of the
@@ -201,9 +206,11 @@ def test_rom_with_oracle_trained_decoders_mixed(name):
     x, lam, st = s.solve(mu)
     refs = parity.oracle_solves(name, mu, raw=raw, tol=0.0, max_iter=2)
     for b, ref in enumerate(refs):
-        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[MIXED], f"{name} trained mixed K=2 instance {b}")
+        parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[MIXED], f"{name} trained mixed K=2 instance {b}",
+                            merit_atol=MERIT_FLOOR[name])
     s.options()
     x, lam, st, state = s.solve(mu, state=True)
+    assert np.all(st["merit"] < MERIT_FLOOR[name])
     conv = parity.oracle_solves(name, mu, raw=raw, tol=1e-9, max_iter=40)
     for b, ref in enumerate(conv):
         assert ref.status == 0

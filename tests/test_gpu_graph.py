@@ -46,24 +46,47 @@ def same(a, b):
         assert np.array_equal(sa[f], sb[f]), f
 
 
-@pytest.mark.parametrize("d_gemm", [0, 1])
+@pytest.mark.parametrize("d_gemm,atil", [(0, 0), (1, 0), (0, 1)])
 @pytest.mark.parametrize("name,prec,B", [("c2", MIXED, 13), ("c2", FP64, 5), ("c3", MIXED, 7), ("c1", FP64, 1),
-                                         ("tiny13x9_3x2", MIXED, 4)])
-def test_plans_are_bit_identical(name, prec, B, d_gemm):
+                                         ("tiny13x9_3x2", MIXED, 4), ("c2", MIXED, 40)])
+def test_plans_are_bit_identical(name, prec, B, d_gemm, atil):
+    """Every launch plan gives the same bits (the double-float Atil of the mixed path too: its summation order
+    does not depend on the instance tiles, whose size follows the instance group's)."""
     wl, s = solver(name, prec)
     mu = inputs.mu_batch(B, seed=31)
     s.options(tol=0.0, max_iter=4)
-    lib.ddnm_set_tune(s.ctx, **HOST, d_gemm=d_gemm)
+    lib.ddnm_set_tune(s.ctx, **HOST, d_gemm=d_gemm, atil=atil)
     ref = s.solve(mu)
     for plan in PLANS:
-        lib.ddnm_set_tune(s.ctx, **plan, d_gemm=d_gemm)
+        lib.ddnm_set_tune(s.ctx, **plan, d_gemm=d_gemm, atil=atil)
         same(s.solve(mu), ref)
         same(s.solve(mu), ref)                 # replay of the captured graph
     s.options()
-    lib.ddnm_set_tune(s.ctx, **HOST, d_gemm=d_gemm)
+    lib.ddnm_set_tune(s.ctx, **HOST, d_gemm=d_gemm, atil=atil)
     ref = s.solve(mu)                          # stopping rule active: groups finish at different passes
-    lib.ddnm_set_tune(s.ctx, graph=1, chains=min(B, 5), con_split=1024, eval_persist=2, d_gemm=d_gemm)
+    lib.ddnm_set_tune(s.ctx, graph=1, chains=min(B, 5), con_split=1024, eval_persist=2, d_gemm=d_gemm, atil=atil)
     same(s.solve(mu), ref)
+    s.close()
+
+
+@pytest.mark.parametrize("name,B", [("c2", 40), ("c3", 19), ("tiny13x9_3x2", 5), ("c5", 33)])
+def test_double_float_atil_matches_fp64(name, B):
+    """The mixed path's Atil = C jump on the FP32 pipe in double-float arithmetic (atil = 1) against the same
+    product in FP64 (atil = 0) on the same FP32 interface outputs: within 1e-10 of the larger entries, per
+    entry (the double-float sum carries about 2^-48 of sum_l |C_kl jump_l|, which the cancellation in C jump
+    raises relative to |Atil| by about sqrt(N_A)).  The evaluation's other outputs are bit-identical."""
+    wl, s = solver(name, MIXED)
+    r = np.random.default_rng(5)
+    mu = inputs.mu_batch(B, seed=41)
+    x = 0.3 * r.standard_normal((B, s.sizes.n_D))
+    lam = r.standard_normal((B, s.sizes.n_C))
+    lib.ddnm_set_tune(s.ctx, atil=0)
+    H0, D0, A0 = s.linearize(mu, x, lam)
+    lib.ddnm_set_tune(s.ctx, atil=1)
+    H1, D1, A1 = s.linearize(mu, x, lam)
+    assert np.array_equal(H0, H1) and np.array_equal(D0, D1)
+    for b in range(B):
+        parity.close(A1[b], A0[b], 1e-10, f"{name} Atil instance {b}")
     s.close()
 
 

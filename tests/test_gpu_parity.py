@@ -186,6 +186,30 @@ def test_reconstruction_and_full_residual():
         parity.close(rfull[b], fom.residual(st, mu[b]), 1e-10, f"FOM residual instance {b}")
 
 
+@pytest.mark.parametrize("name,prec", [("tiny12x10_2x2", FP64), ("tiny13x9_3x2", MIXED), ("c2", MIXED)])
+def test_reconstruct_matches_oracle_state(name, prec):
+    """ddnm_reconstruct: g(xh) with every variable from its owning subdomain's decoder, against the oracle's
+    full_state, per u / v block and element (FP64: 1e-10; mixed: FP32 decoder outputs, 1e-6 of the block), in
+    host and in device memory."""
+    wl, fom, dd, rom, raw, s = case(name, prec)
+    r = np.random.default_rng(8)
+    B = 3
+    x = 0.3 * r.standard_normal((B, rom.n_D))
+    st = np.zeros((B, s.sizes.N_x))
+    lib.ddnm_reconstruct(s.ctx, B, x, st)
+    dev = torch.device("cuda:0")
+    st_d = torch.zeros((B, s.sizes.N_x), dtype=torch.float64, device=dev)
+    lib.ddnm_reconstruct(s.ctx, B, torch.from_numpy(x).to(dev), st_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(st_d.cpu().numpy(), st)
+    tol = 1e-10 if prec == FP64 else 1e-6
+    N = fom.N
+    for b in range(B):
+        ref = rom.full_state(x[b])
+        parity.close(st[b][:N], ref[:N], tol, f"{name} state u instance {b}")
+        parity.close(st[b][N:], ref[N:], tol, f"{name} state v instance {b}")
+
+
 def test_device_memory_path_matches_host():
     wl, fom, dd, rom, raw, s = case("tiny12x10_2x2", MIXED)
     s.options(tol=0.0, max_iter=3)

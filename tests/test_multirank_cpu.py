@@ -66,8 +66,8 @@ def _reference_rank(rank, world, port, q):
     import contextlib
     import bench
     called = []
-    bench.oracle_sample = lambda *a, **k: called.append(1) or dict(value=1.0, unit="solves/s", cores=1, kind="oracle",
-                                                                    sample="stub")
+    bench.reference_sample = lambda *a, **k: called.append(1) or ([1.0], [1.0], dict(
+        value=1.0, unit="solves/s", cores=1, kind="oracle", sample="stub"))
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
         bench.run_reference(type("A", (), dict(config="c1", steps=1, warmup=0, gpus=world))())
