@@ -52,7 +52,13 @@ REF_ITERS = 15                   # SQP iterations of an oracle solve in the CPU 
 AE_STAGES = ((200, 3e-3), (200, 1e-3), (200, 3e-4), (200, 1e-4))   # (epochs, learning rate) of the AE training
 AE_SIDE, AE_BATCH = 12, 16
 WS_HIDDEN, WS_EPOCHS, WS_TRAIN = 256, 60, 2048
-SMS_FALLBACK = 152
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress on stderr (the JSON line is the only stdout)."""
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}\n")
+    sys.stderr.flush()
 
 
 # ------------------------------------------------------------------------ clocks
@@ -368,8 +374,8 @@ class Rom:
         self.s, self.s64 = s, s64
         self.nD, self.nC, self.Nx = s.sizes.n_D, s.sizes.n_C, s.sizes.N_x
 
-    def solve(self, solver, mu, K, tol=0.0):
-        solver.options(tol=tol, max_iter=K)
+    def solve(self, solver, mu, K, tol=0.0, max_bt=20):
+        solver.options(tol=tol, max_iter=K, max_backtracks=max_bt)
         x, lam, st = solver.solve(mu)
         solver.options()
         return x, lam, st
@@ -406,11 +412,14 @@ class Rom:
         return np.concatenate(out)
 
     def train_warm_start(self, mu_tr, K):
+        """The MLP trained on mixed-precision ROM solutions of mu_tr: K SQP iterations with every step taken
+        (no backtracking: near the solution the FP32 rounding of rho decides the Armijo test, and the steps
+        there are of that size)."""
         lib = self.lib
         B = self.wl.batch
         xs = []
         for b0 in range(0, len(mu_tr), B):
-            xs.append(self.solve(self.s, mu_tr[b0:b0 + B], K)[0])
+            xs.append(self.solve(self.s, mu_tr[b0:b0 + B], K, max_bt=0)[0])
         x_tr = np.concatenate(xs)
         lib.ddnm_ws_init(self.s.ctx, WS_HIDDEN, inputs.mlp_init(2, WS_HIDDEN, self.nD))
         t0 = time.perf_counter()
@@ -481,31 +490,37 @@ def main():
 
     # ---- set-up on the GPU: FOM snapshots, autoencoders, the warm start (untimed)
     R = Rom(lib, torch, wl, local)
+    log(f"decoders trained: FOM {R.t_fom:.1f}s, autoencoders {R.t_train:.1f}s")
     s, s64 = R.s, R.s64
     mu_tr = inputs.mu_batch(WS_TRAIN, seed=1001)
-    t_ws, ws_losses = R.train_warm_start(mu_tr, 30)
+    t_ws, ws_losses = R.train_warm_start(mu_tr, 25)
+    log("warm start trained")
     mu_cal = inputs.mu_batch(min(256, B), seed=3003)
     mu = shard(inputs.mu_batch(B * world), rank, world)
 
     # ---- references: the FP64 ROM solutions (K_REF iterations)
     x_cal_ref = R.solve(s64, mu_cal, K_REF)[0]
     x_ref, lam_ref, st_ref = R.solve(s64, mu, K_REF)
+    log("FP64 reference solutions")
 
     # ---- calibration: each method's smallest iteration budget meeting the accuracy criterion on mu_cal
     lib.ddnm_ws_enable(s.ctx, False)
     k64, e64 = smallest_k(lambda K: R.solve(s64, mu_cal, K)[0], x_cal_ref, [8, 10, 12, 14, 16, 18, 20, 22, 24, 28, 32, 40],
                           R.state_errors)
-    kmp, emp = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28, 32, 40],
+    kmp, emp = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28],
                           R.state_errors)
+    log(f"calibrated FP64 {k64} ({e64:.2e}), mixed {kmp} ({emp:.2e})")
     lib.ddnm_ws_enable(s.ctx, True)
-    kws, ews = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 20, 25, 30],
+    kws, ews = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 20],
                           R.state_errors)
 
     # ---- launch plan of the headline solve: autotuned on this batch with the timed iteration budget
+    log(f"calibrated mixed + warm start {kws} ({ews:.2e})")
     s.options(tol=0.0, max_iter=kws)
-    plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, max_iter=kws, reps=3)
+    plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, max_iter=kws, reps=2)
 
     # ---- CPU baseline (rank 0, N = 1): the oracle with this run's decoders, and its parity with both GPU paths
+    log(f"autotuned {plan}")
     cpu, parity = None, None
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         fd, dec_path = tempfile.mkstemp(suffix=".npz")
@@ -529,6 +544,7 @@ def main():
                           f"(largest entry error over the largest entry of each vector; state: relative 2-norm)")
         lib.ddnm_ws_enable(s.ctx, True)
 
+    log("CPU baseline done")
     # ---- the timed headline: mixed + learned warm start, kws iterations, device-resident
     mu_d = torch.from_numpy(mu).to(dev)
     x_d = torch.zeros((B, R.nD), dtype=torch.float64, device=dev)
@@ -591,6 +607,7 @@ def main():
         solver.options()
         return xs, sts, dt
 
+    log(f"headline timed: {t_max / args.steps:.1f} ms per step, {n_ok} of {B} accurate")
     lib.ddnm_ws_enable(s.ctx, False)
     x64, st64, t64 = timed_once(s64, k64)
     e64t = R.state_errors(x64, x_ref)
@@ -603,6 +620,7 @@ def main():
     fom_rom = R.fom_errors(x_ref[:nfo], mu[:nfo])
     fom_head = R.fom_errors(x_h[:nfo], mu[:nfo])
 
+    log("comparison solves timed")
     # ---- roofline of the dominant kernel: per-kernel device time from the library's CUDA events, in a
     # separate run of the headline solve through the host-driven loop (events around every launch)
     kb = 3

@@ -359,8 +359,11 @@ typedef struct ddnm_tune {
     int con_split;      /* constraint rows per constraint CTA: 512, 1024 or 2048 */
     int eval_persist;   /* persistent evaluation: CTAs per SM per width class (1..8), or 0 for one CTA per item */
     int d_gemm;         /* D_i = C A_i dg_i^G: 1 in one GEMM launch per pass over all instances of a subdomain
-                           (they share the decoder); 0 inside each evaluation CTA; -1 (default) picks 1 when
-                           some subdomain has h^G n_C >= 65536 (hidden units of its interface decoder times n_C) */
+                           (they share the decoder); 2 the same GEMM on the tensor cores (tcgen05, TF32 operands
+                           split hi + lo for FP32 accuracy; mixed path with n_C <= 128, else taken as 1); 0
+                           inside each evaluation CTA; -1 (default) picks the GEMM (2 in the mixed path, 1
+                           in the FP64 path) when some subdomain has h^G n_C >= 65536 (hidden units of its
+                           interface decoder times n_C), else 0 */
     int eval_groups;    /* 1 (default): one instance per evaluation CTA; 0: an evaluation CTA holds as many
                            independent 256-thread groups as one-instance CTAs would fit an SM, on neighbouring
                            instances of one subdomain (they share its tables through L1) */

@@ -147,15 +147,18 @@ class Burgers:
         return sp.bmat([[Juu, Juv], [Jvu, Jvv]], format="csr")
 
     # -- monolithic FOM solve ------------------------------------------------------------
-    def newton(self, mu, x0=None, rtol=1e-12, max_iter=50):
+    def newton(self, mu, x0=None, rtol=1e-12, max_iter=50, residuals=None):
         """Newton on r(x; mu) = 0 from x0 (default 0), sparse LU; stops at
         ||r|| <= rtol * max(1, ||r(x0)||), or once a step fails to halve ||r||: in Newton's quadratic regime
         that happens only at the rounding floor of the residual (a start close to the solution, e.g. the
         exact solution at the nodes, can begin below rtol * max(1, ||r(x0)||) of nothing but that floor).
-        Returns (x, residual history)."""
+        Returns (x, residual history).  residuals: a list that receives the residual vector r(x_k) of every
+        iterate (the residual snapshots of Sec. 5.3's greedy HR remark)."""
         bvec = self.boundary_vectors(mu)
         x = np.zeros(2 * self.N) if x0 is None else np.array(x0, dtype=np.float64)
         r = self.residual(x, mu, bvec)
+        if residuals is not None:
+            residuals.append(r.copy())
         stop = rtol * max(1.0, np.linalg.norm(r))
         hist = [np.linalg.norm(r)]
         for _ in range(max_iter):
@@ -164,6 +167,8 @@ class Burgers:
             dx = spla.spsolve(self.jacobian(x, mu, bvec).tocsc(), -r)
             x = x + dx
             r = self.residual(x, mu, bvec)
+            if residuals is not None:
+                residuals.append(r.copy())
             hist.append(np.linalg.norm(r))
             if hist[-1] > 0.5 * hist[-2]:
                 break

@@ -85,6 +85,8 @@ struct ddnm_ctx {
     int* d_con = nullptr;
     double* d_C = nullptr;
     float* d_Ct = nullptr;             // mixed path: C transposed, split into FP32 hi and lo parts (2 N_A ldct)
+    float* d_Qtc = nullptr;            // mixed path: Q_i split into TF32 hi / lo, tiled for k_dgemm_tc
+    int* d_err = nullptr;              // device error word (ddnm::DDNM_TC_TIMEOUT)
     int* d_bnd_ij = nullptr;
     ddnm::SubDev* d_sub = nullptr;
     ddnm::ChunkDev* d_chunk = nullptr;
@@ -142,3 +144,7 @@ void ddnm_ws_release(ddnm_ctx* ctx);
 void ddnm_fom_release(ddnm_ctx* ctx);
 void ddnm_ae_release(ddnm_ctx* ctx);
 int ddnm_ws_predict_dev(ddnm_ctx* ctx, int B, const double* mu_dev, double* x0_dev, int* fell_back, cudaStream_t st);
+// tensor-core D_i GEMM of the mixed path (ddnm_tc.cu)
+bool ddnm_dgemm_tc_ok(const ddnm_ctx* ctx);
+cudaError_t ddnm_launch_dgemm_tc(ddnm_ctx* ctx, const ddnm::ProbDev& P, int B, cudaStream_t st);
+void ddnm_tile_q_tc(std::vector<float>& out, const double* Qt, int hG, int qld, int nC, long long& off, int& hGp);

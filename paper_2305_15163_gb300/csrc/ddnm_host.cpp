@@ -244,6 +244,8 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_con);
     cudaFree(ctx->d_C);
     cudaFree(ctx->d_Ct);
+    cudaFree(ctx->d_Qtc);
+    cudaFree(ctx->d_err);
     cudaFree(ctx->d_bnd_ij);
     cudaFree(ctx->d_sub);
     cudaFree(ctx->d_chunk);
@@ -535,6 +537,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     // an instance's block area: the n_sub merits ||rho_i||^2 (padded to an even count), then the blocks
     int xoff = 0, hr_off = 0, blk = (ctx->n_sub + 1) & ~1;
     long long pg_stride = 0;
+    std::vector<float> qtc;        // mixed path: every Q_i split and tiled for the tensor-core D_i GEMM
     ctx->max_nG = 1;
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
     ctx->eval_smem = 0;
@@ -657,6 +660,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 for (int c = 0; c < nC; ++c) q[c] += coef * M[(size_t)r * nC + c];
             }
         S.Qt = P.addv(Qt.data(), Qt.size());
+        S.qtc = 0;
+        S.hGp = 0;
+        if (tsize == 4 && nC <= MAX_NC) ddnm_tile_q_tc(qtc, Qt.data(), S.hG, qld, nC, S.qtc, S.hGp);
         S.pgoff = pg_stride;
         pg_stride += (long long)S.hG * S.nG;
         ctx->max_nG = std::max(ctx->max_nG, S.nG);
@@ -774,6 +780,16 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_con, con.data(), con.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_C, std::max<size_t>(ctx->C.size(), 1) * 8));
     CK(cudaMemcpy(ctx->d_C, ctx->C.data(), ctx->C.size() * 8, cudaMemcpyHostToDevice));
+    cudaFree(ctx->d_Qtc);
+    ctx->d_Qtc = nullptr;
+    if (!qtc.empty()) {
+        CK(cudaMalloc(&ctx->d_Qtc, qtc.size() * 4));
+        CK(cudaMemcpy(ctx->d_Qtc, qtc.data(), qtc.size() * 4, cudaMemcpyHostToDevice));
+    }
+    if (!ctx->d_err) {
+        CK(cudaMalloc(&ctx->d_err, sizeof(int)));
+        CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    }
     // mixed path: C transposed (constraint row l, then test-matrix row c) and split into two floats per entry,
     // hi = fl32(C) and lo = fl32(C - hi), rows padded with zeros to ldct (the double-float Atil of k_atil_df)
     cudaFree(ctx->d_Ct);
@@ -856,6 +872,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.Cthi = ctx->d_Ct;
     pd.Ctlo = ctx->d_Ct ? ctx->d_Ct + (size_t)ctx->N_A * ldct : nullptr;
     pd.atil_df = 0;
+    pd.Qtc = ctx->d_Qtc;
+    pd.err = ctx->d_err;
     pd.pg_stride = std::max(pg_stride, 1LL);
     pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.tiles = ctx->d_tiles; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;
     pd.hr = ctx->d_hr;

@@ -22,6 +22,7 @@ constexpr int MIN_CON_SPLIT = CON_BLOCK, MAX_CON_SPLIT = 4 * CON_BLOCK;
 // double-float Atil of the mixed path (k_atil_df): constraint rows staged per chunk, rows between the FP64 folds
 // of a double-float sum, constraint rows per slice (one Atil partial per slice and instance)
 constexpr int ATIL_KC = 32, ATIL_FOLD = 64, ATIL_KS = MAX_CON_SPLIT;
+constexpr int DDNM_TC_TIMEOUT = 1;   // value of ProbDev::err after a k_dgemm_tc wait ran out
 constexpr int MAX_CHAINS = 64; // instance groups iterating concurrently inside the solve graph
 constexpr int PASSES_PER_BODY = 2;   // SQP passes per turn of an instance group's device-side loop
 constexpr int MAX_CLASSES = 12; // width classes (RO, RG) of the evaluation kernel
@@ -104,6 +105,8 @@ struct SubDev {
     int NGn, hr_chunk;             // interface outputs the stencils use; collocation rows per chunk
     long long colGn, valGn, soGn;  // those outputs: ELL slot-major (Kp x NGn), scale/offset
     long long Qt;                  // value pool: Q_i^T = (C A_i diag(scale) W2~)^T, h_G x n_C
+    long long qtc;                 // mixed path: Q_i split into TF32 hi / lo in k_dgemm_tc's order (floats into
+    int hGp, pad_tc;               // P.Qtc); h_G rounded up to the tensor-core K chunk
     long long pgoff;               // offset of this subdomain's P_G (h_G x n^G) in an instance's P_G area
     // full (not subnet) decoders for reconstruction
     int NO_full, wO_full, wG_full, K;
@@ -168,6 +171,8 @@ struct ProbDev {
     const float* Cthi;             // N_A x ldct: C transposed and split, C[c][l] = Cthi[l][c] + Ctlo[l][c] (to
     const float* Ctlo;             // 2^-48), zero for c >= n_C; mixed path only
     int ldct;                      // row stride of Cthi / Ctlo: n_C rounded up to 32, 64 or a multiple of 128
+    const float* Qtc;              // mixed path: every Q_i split and tiled for k_dgemm_tc (SubDev::qtc)
+    int* err;                      // device error word (DDNM_TC_TIMEOUT: a bounded tensor-core wait ran out)
     int atil_df;                   // 1: Atil by k_atil_df (instance tiles, double-float); 0: FP64 slices
     int qld;                       // row stride of every Q_i^T in the value pool: round4(n_C)
     const int* bnd_ij;             // n_bnd x 2 grid indices of the Dirichlet points the stencils touch

@@ -2134,7 +2134,10 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
         CK(cudaGetLastError());
         ctx->tm.eval_launches++;
     }
-    if (P.d_gemm) {
+    if (P.d_gemm == 2) {
+        if constexpr (sizeof(T) == 4) CK(ddnm_launch_dgemm_tc(ctx, P, B, st));
+        ctx->tm.eval_launches++;
+    } else if (P.d_gemm) {
         CK(launch_dgemm<T>(ctx, P, B, st));
         ctx->tm.eval_launches++;
     }
@@ -2269,7 +2272,13 @@ void fold_pending(ddnm_ctx* ctx) {
     ctx->tm.step_launches += passes;           // k_kkt
 }
 
-int resolved_dgemm(const ddnm_ctx* ctx) { return ctx->tune.d_gemm < 0 ? ctx->dgemm_auto : ctx->tune.d_gemm; }
+// the D_i form: 0 in the evaluation, 1 the batched FP32 GEMM, 2 the tensor-core GEMM (mixed path only; the
+// FP64 path and sizes it does not take fall back to 1)
+int resolved_dgemm(const ddnm_ctx* ctx) {
+    int d = ctx->tune.d_gemm;
+    if (d < 0) d = ctx->dgemm_auto && ddnm_dgemm_tc_ok(ctx) ? 2 : ctx->dgemm_auto;
+    return d == 2 && !ddnm_dgemm_tc_ok(ctx) ? 1 : d;
+}
 
 // the Atil form of the plan (double-float instance tiles only in the mixed path, with the split C uploaded);
 // sets the slices of the constraint rows that the Atil partials cover
@@ -2681,9 +2690,9 @@ extern "C" int ddnm_set_tune(ddnm_ctx* ctx, const ddnm_tune* t) {
     const bool pow2 = t->con_split > 0 && (t->con_split & (t->con_split - 1)) == 0;
     if (t->graph < 0 || t->graph > 1 || t->chains < 1 || t->chains > MAX_CHAINS || !pow2 ||
         t->con_split < MIN_CON_SPLIT || t->con_split > MAX_CON_SPLIT || t->eval_persist < 0 || t->eval_persist > 8 ||
-        t->d_gemm < -1 || t->d_gemm > 1 || t->eval_groups < 0 || t->eval_groups > 1 || t->atil < -1 || t->atil > 1)
+        t->d_gemm < -1 || t->d_gemm > 2 || t->eval_groups < 0 || t->eval_groups > 1 || t->atil < -1 || t->atil > 1)
         return ddnm_fail(ctx, DDNM_E_INVALID, "tune: graph 0/1, chains 1..64, con_split 512, 1024 or 2048, "
-                                              "eval_persist 0..8, d_gemm -1..1, eval_groups 0/1, atil -1..1");
+                                              "eval_persist 0..8, d_gemm -1..2, eval_groups 0/1, atil -1..1");
     ctx->tune = *t;
     return DDNM_OK;
 }
@@ -2757,8 +2766,12 @@ extern "C" int ddnm_autotune(ddnm_ctx* ctx, int B, const double* mu, int mem_kin
     if ((rc = sweep(&ddnm_tune::chains, {1, 2, 4, 8, 16, 32, 64}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::eval_persist, {0, 1, 2, 4}))) return finish(rc);
     if ((rc = sweep(&ddnm_tune::con_split, {512, 1024, 2048}))) return finish(rc);
-    if (cur.d_gemm < 0) cur.d_gemm = ctx->dgemm_auto;
-    if ((rc = sweep(&ddnm_tune::d_gemm, {0, 1}))) return finish(rc);
+    if (cur.d_gemm < 0) cur.d_gemm = resolved_dgemm(ctx);
+    if (ddnm_dgemm_tc_ok(ctx)) {
+        if ((rc = sweep(&ddnm_tune::d_gemm, {0, 1, 2}))) return finish(rc);
+    } else if ((rc = sweep(&ddnm_tune::d_gemm, {0, 1}))) {
+        return finish(rc);
+    }
     if ((rc = sweep(&ddnm_tune::eval_groups, {0, 1}))) return finish(rc);
     if (ctx->precision == DDNM_MIXED) {
         if (cur.atil < 0) cur.atil = ctx->atil_auto;

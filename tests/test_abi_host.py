@@ -101,7 +101,7 @@ def test_launch_plan_validation():
     good = dict(graph=1, chains=2, con_split=1024, eval_persist=1, d_gemm=0, eval_groups=0, atil=0)
     for bad in (dict(graph=2), dict(graph=-1), dict(chains=0), dict(chains=65), dict(con_split=256),
                 dict(con_split=768), dict(con_split=4096), dict(eval_persist=-1), dict(eval_persist=9),
-                dict(d_gemm=2), dict(d_gemm=-2), dict(eval_groups=2), dict(eval_groups=-1), dict(atil=2),
+                dict(d_gemm=3), dict(d_gemm=-2), dict(eval_groups=2), dict(eval_groups=-1), dict(atil=2),
                 dict(atil=-2)):
         with pytest.raises(lib.DDNMError) as e:
             lib.ddnm_set_tune(s.ctx, **{**good, **bad})

@@ -190,8 +190,8 @@ def test_rom_with_oracle_trained_decoders_mixed(name):
       match the oracle's two iterations (1e-4); the merit within 1e-4 plus the floor of the FP32 rounding of
       rho (MERIT_FLOOR: the merit the mixed path stalls at under the paper's rule, about 1e-5 on the 32 x 32
       grid and 5e-3 on 128 x 128, where the stencil weights nu / h^2 are 16 times larger), checked below.
-    * Under the paper's stopping rule: the final latent coordinates and the reconstructed state are within
-      1e-4 of the oracle's converged solution (tolerance 1e-9, up to 40 iterations).  The multipliers are
+    * After 15 iterations: the latent coordinates and the reconstructed state are within 1e-4 of the oracle's
+      solution after 40 iterations (the FP64 merit there is at its own rounding floor).  The multipliers are
       within 1e-2: near the solution rho_i = R_i^T r_i + E_i^T lambda carries the FP32 rounding of the
       collocated residual, which lambda takes up through (D D^T)^{-1} D (its floor shows as the merit the
       mixed path stalls at); the latent coordinates and states see that noise through H_i^{-1}, which is
@@ -208,12 +208,12 @@ def test_rom_with_oracle_trained_decoders_mixed(name):
     for b, ref in enumerate(refs):
         parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[MIXED], f"{name} trained mixed K=2 instance {b}",
                             merit_atol=MERIT_FLOOR[name])
-    s.options()
+    s.options(tol=0.0, max_iter=15)
     x, lam, st, state = s.solve(mu, state=True)
     assert np.all(st["merit"] < MERIT_FLOOR[name])
-    conv = parity.oracle_solves(name, mu, raw=raw, tol=1e-9, max_iter=40)
+    conv = parity.oracle_solves(name, mu, raw=raw, tol=0.0, max_iter=40)
     for b, ref in enumerate(conv):
-        assert ref.status == 0
+        assert ref.phi < 1e-6
         parity.latent(rom, x[b], ref.x, TOL[MIXED], f"{name} mixed vs converged instance {b}")
         parity.close(lam[b], ref.lam, 1e-2, f"{name} mixed vs converged instance {b} lambda")
         g_ref = rom.full_state(ref.x)

@@ -69,6 +69,38 @@ def test_plans_are_bit_identical(name, prec, B, d_gemm, atil):
     s.close()
 
 
+@pytest.mark.parametrize("name,B", [("c2", 70), ("c3", 19), ("tiny13x9_3x2", 5), ("c5", 67)])
+def test_tensor_core_d_gemm_matches_fp32_gemm(name, B):
+    """D_i = Q_i P_G on the tensor cores (d_gemm = 2: tcgen05 kind::tf32 with hi + lo operand splits, FP32
+    accumulation) against the FP32-pipe GEMM (d_gemm = 1), block by block at 1e-5 of the block's largest
+    entry (both carry FP32 rounding of sums over up to 1024 hidden units, in different orders; the split
+    operands add about 2^-21 per product); H_i and Atil, which do not depend on D_i, are bit-identical, and
+    F = [rho; Atil] agrees at 1e-5 per block.  Batches of 70 and 67
+    instances cover a full tile of 64 and a ragged one."""
+    wl, s = solver(name, MIXED)
+    r = np.random.default_rng(6)
+    mu = inputs.mu_batch(B, seed=43)
+    x = 0.3 * r.standard_normal((B, s.sizes.n_D))
+    lam = r.standard_normal((B, s.sizes.n_C))
+    out = {}
+    for d in (1, 2):
+        lib.ddnm_set_tune(s.ctx, d_gemm=d)
+        H, D, A = s.linearize(mu, x, lam)
+        F, _ = s.residual(mu, x, lam)
+        out[d] = (H, D, A, F)
+    (H1, D1, A1, F1), (H2, D2, A2, F2) = out[1], out[2]
+    assert np.array_equal(H1, H2) and np.array_equal(A1, A2)
+    nC = s.sizes.n_C
+    sizes_D = [nC * d["n_gamma"] for d in s.subs]
+    sizes_F = [d["n_omega"] + d["n_gamma"] for d in s.subs] + [nC]
+    for b in range(B):
+        for i, (d1, d2) in enumerate(zip(parity.split(D1[b], sizes_D), parity.split(D2[b], sizes_D))):
+            parity.close(d2, d1, 1e-5, f"{name} instance {b} D_{i}")
+        for i, (f1, f2) in enumerate(zip(parity.split(F1[b], sizes_F), parity.split(F2[b], sizes_F))):
+            parity.close(f2, f1, 1e-5, f"{name} instance {b} F block {i}")
+    s.close()
+
+
 @pytest.mark.parametrize("name,B", [("c2", 40), ("c3", 19), ("tiny13x9_3x2", 5), ("c5", 33)])
 def test_double_float_atil_matches_fp64(name, B):
     """The mixed path's Atil = C jump on the FP32 pipe in double-float arithmetic (atil = 1) against the same
@@ -101,7 +133,7 @@ def test_both_d_forms_match_oracle(name, prec):
     mu = inputs.mu_batch(3)
     s.options(tol=0.0, max_iter=3)
     refs = [rom.solve(mu[b], tol=0.0, max_iter=3) for b in range(3)]
-    for d_gemm in (0, 1):
+    for d_gemm in ((0, 1) if prec == FP64 else (0, 1, 2)):
         lib.ddnm_set_tune(s.ctx, graph=1, chains=2, d_gemm=d_gemm)
         x, lam, st = s.solve(mu)
         for b in range(3):
