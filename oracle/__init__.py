@@ -15,7 +15,10 @@ float64, the formulas written in the paper's matrix notation.
   matrices A_i (Eq. compatibility_conditions_mat).
 * ``decoders`` -- Sec. 5.1/5.4: masked shallow decoder, its Jacobian, the HR subnet;
   Sec. 3.3: linear (LS-ROM) decoder and POD with the energy criterion.
-* ``rom``      -- Sec. 3.1/4.1: WFPC DD-LSPG-ROM with collocation HR, Gauss-Newton
+* ``hr``       -- Sec. 3.1/5.3: gappy-POD hyper-reduction: residual snapshots from Newton's history,
+  the residual POD basis, greedy row sampling, the projector (Z_i Phi_i^r)^+.
+* ``autoencoder`` -- Sec. 5.1, 7.2-7.3: masked shallow autoencoders trained by mini-batch Adam.
+* ``rom``      -- Sec. 3.1/4.1: WFPC DD-LSPG-ROM with collocation or gappy-POD HR, Gauss-Newton
   blocks, the KKT system Eq. (sqp_system) solved densely, Armijo backtracking on the
   norm of the KKT right-hand side, least-squares multiplier start, Eq. (relative_error).
 

@@ -8,11 +8,12 @@ Problem, Eq. (dd_lspg_NLP) / (dd_lspg_NLP_general) with the WFPC constraint (Sec
     s.t. sum_i C A_i g_i^G(xh_i^G) = 0
 
 with r_i(xO, xG) = P_i^r r(P_i^O^T xO + P_i^G^T xG)  (Eq. subdomain_residual_def) and
-collocation HR B_i = Z_i (Sec. 3.1 / 5.3), or B_i = I when no HR rows are given.
+collocation HR B_i = Z_i (Sec. 3.1 / 5.3), B_i = I when no HR rows are given, or gappy-POD HR
+B_i = (Z_i Phi_i^r)^+ Z_i when the projector (Z_i Phi_i^r)^+ is given (``hr_proj``, see ``oracle.hr``).
 
 One evaluation builds, per subdomain (Sec. 4.1):
-    R_i   = [dr_i/dxO dg^O/dxh^O , dr_i/dxG dg^G/dxh^G]       rows sampled by Z_i (Eq. gauss_newton_hessian b)
-    H_i   = R_i^T R_i                                          (Eq. gauss_newton_hessian a, B^T B = I on samples)
+    R_i   = B_i [dr_i/dxO dg^O/dxh^O , dr_i/dxG dg^G/dxh^G]   (Eq. gauss_newton_hessian b)
+    H_i   = R_i^T R_i                                          (Eq. gauss_newton_hessian a)
     E_i   = [0, D_i],  D_i = C A_i dg^G/dxh^G                  (Eq. sqp_block_matrices)
     rho_i = R_i^T r_i + E_i^T lambda                           (Eq. optimality_residuals_GN)
 and Atil = sum_i C A_i g_i^G.  The KKT matrix of Eq. (sqp_system) is assembled densely and
@@ -43,8 +44,8 @@ FLAG_LS_FAIL = 1
 
 @dataclass
 class Evaluation:
-    r: list            # Z_i r_i
-    R: list            # Z_i R_i
+    r: list            # Z_i r_i (the sampled rows, before a gappy projection)
+    R: list            # Z_i [dr_i/dx dg_i/dxh] (the same rows)
     H: list            # H_i
     grad: list         # R_i^T r_i
     D: list            # D_i = C A_i dg_i^G
@@ -79,9 +80,11 @@ def _value_jacobian_rows(dec, x, rows):
 class DDROM:
     """decoders_O/decoders_G: objects with value_jacobian(x) -> (g, dg/dx);
     hr: per subdomain local residual-row ids (None = all rows, i.e. B_i = I);
-    C: n_C x N_A test matrix."""
+    C: n_C x N_A test matrix;
+    hr_proj: per subdomain (Z_i Phi_i^r)^+ (n_r x N_B, columns in the order of hr[i]) for gappy-POD HR,
+    or None (collocation)."""
 
-    def __init__(self, fom: Burgers, dd: Decomposition, decoders_O, decoders_G, hr, C):
+    def __init__(self, fom: Burgers, dd: Decomposition, decoders_O, decoders_G, hr, C, hr_proj=None):
         self.fom, self.dd = fom, dd
         self.dO, self.dG = list(decoders_O), list(decoders_G)
         self.C = np.asarray(C, dtype=np.float64).reshape(-1, dd.N_A) if dd.N_A else np.zeros((0, 0))
@@ -89,6 +92,8 @@ class DDROM:
         # C A_i (n_C x N_i^G) through the sparse A_i
         self.CA = [np.asarray((A.T @ self.C.T).T) for A in dd.A] if dd.N_A else \
             [np.zeros((0, sd.interface.size)) for sd in dd.subs]
+        self.proj = [None] * len(dd.subs) if hr_proj is None else \
+            [None if p is None else np.asarray(p, dtype=np.float64) for p in hr_proj]
         self.rows = []
         self.need = []
         N = fom.N
@@ -140,10 +145,12 @@ class DDROM:
             x[sd.interface] = 0.0
             R = np.hstack([J[:, sd.interior[need]] @ JO, J[:, sd.interface] @ JG])
             D = self.CA[i] @ JG
-            grad = R.T @ r
+            Pg = self.proj[i]
+            Rb, rb = (R, r) if Pg is None else (Pg @ R, Pg @ r)      # B_i applied (gappy POD) or Z_i alone
+            grad = Rb.T @ rb
             rho = grad.copy()
             rho[self.nO[i]:] += D.T @ lam
-            ev.r.append(r); ev.R.append(R); ev.H.append(R.T @ R); ev.grad.append(grad)
+            ev.r.append(r); ev.R.append(R); ev.H.append(Rb.T @ Rb); ev.grad.append(grad)
             ev.D.append(D); ev.rho.append(rho); ev.gO.append(gO); ev.gG.append(gG)
             ev.Atil = ev.Atil + self.CA[i] @ gG
         ev.F = np.concatenate(ev.rho + [ev.Atil])
@@ -168,10 +175,12 @@ class DDROM:
             J = fom.jacobian(x, mu, bvec)[rows]
             R = np.hstack([J[:, sd.interior] @ JO, J[:, sd.interface] @ JG])
             D = self.CA[i] @ JG
-            grad = R.T @ r
+            Pg = self.proj[i]
+            Rb, rb = (R, r) if Pg is None else (Pg @ R, Pg @ r)      # B_i applied (gappy POD) or Z_i alone
+            grad = Rb.T @ rb
             rho = grad.copy()
             rho[self.nO[i]:] += D.T @ lam
-            ev.r.append(r); ev.R.append(R); ev.H.append(R.T @ R); ev.grad.append(grad)
+            ev.r.append(r); ev.R.append(R); ev.H.append(Rb.T @ Rb); ev.grad.append(grad)
             ev.D.append(D); ev.rho.append(rho); ev.gO.append(gO); ev.gG.append(gG)
             ev.Atil = ev.Atil + self.CA[i] @ gG
         ev.F = np.concatenate(ev.rho + [ev.Atil])
