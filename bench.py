@@ -49,9 +49,12 @@ FLUSH_BYTES = 512 << 20          # > 129 MB L2
 ACC = 1e-4                       # accuracy criterion (relative 2-norm of the reconstructed state)
 K_REF = 40                       # FP64 SQP iterations of the reference ROM solution
 REF_ITERS = 15                   # SQP iterations of an oracle solve in the CPU throughput (the paper's cap)
+CAL_SHARE = 0.99                 # share of calibration instances a fixed iteration budget must make accurate
 AE_STAGES = ((200, 3e-3), (200, 1e-3), (200, 3e-4), (200, 1e-4))   # (epochs, learning rate) of the AE training
 AE_SIDE, AE_BATCH = 12, 16
 WS_HIDDEN, WS_EPOCHS, WS_TRAIN = 256, 60, 2048
+# the mixed solves: the paper's stopping rule (Sec. 7.1) plus the stop at the FP32 rounding floor of the merit
+HEADLINE_OPTS = dict(tol=1e-4, max_iter=15, floor_stop=1)
 _T0 = time.perf_counter()
 
 
@@ -428,21 +431,24 @@ class Rom:
         return time.perf_counter() - t0, losses
 
 
-def smallest_k(run, x_ref, Ks, errf):
-    """The smallest K of the increasing list Ks whose solve meets the accuracy criterion on every instance
-    (bisection; the error falls with K).  run(K) -> x.  Returns (K, max error at K)."""
+def smallest_k(run, x_ref, Ks, errf, share=CAL_SHARE):
+    """The smallest K of the increasing list Ks whose solve meets the accuracy criterion on at least `share` of
+    the instances (bisection; the error falls with K; the last K is taken when none does).  run(K) -> x.
+    Returns (K, share of instances meeting the criterion at K)."""
+    def frac(K):
+        return float(np.mean(errf(run(K), x_ref) <= ACC))
     lo, hi = 0, len(Ks) - 1
-    best = (Ks[-1], float(errf(run(Ks[-1]), x_ref).max()))
+    best = None
     while lo < hi:
         mid = (lo + hi) // 2
-        e = float(errf(run(Ks[mid]), x_ref).max())
-        if e <= ACC:
+        f = frac(Ks[mid])
+        if f >= share:
             hi = mid
-            best = (Ks[mid], e)
+            best = (Ks[mid], f)
         else:
             lo = mid + 1
-    if Ks[lo] != best[0]:
-        best = (Ks[lo], float(errf(run(Ks[lo]), x_ref).max()))
+    if best is None or best[0] != Ks[lo]:
+        best = (Ks[lo], frac(Ks[lo]))
     return best
 
 
@@ -503,21 +509,22 @@ def main():
     x_ref, lam_ref, st_ref = R.solve(s64, mu, K_REF)
     log("FP64 reference solutions")
 
-    # ---- calibration: each method's smallest iteration budget meeting the accuracy criterion on mu_cal
+    # ---- calibration of the plain FP64 solve: the smallest fixed iteration budget making CAL_SHARE of mu_cal
+    # accurate (the FP64 merit keeps falling to its own rounding floor, so a budget is its stopping rule)
     lib.ddnm_ws_enable(s.ctx, False)
-    k64, e64 = smallest_k(lambda K: R.solve(s64, mu_cal, K)[0], x_cal_ref, [8, 10, 12, 14, 16, 18, 20, 22, 24, 28, 32, 40],
+    k64, f64 = smallest_k(lambda K: R.solve(s64, mu_cal, K)[0], x_cal_ref, [8, 10, 12, 14, 16, 18, 20, 22, 24, 28, 32, 40],
                           R.state_errors)
-    kmp, emp = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [4, 6, 8, 10, 12, 14, 16, 18, 20, 24, 28],
-                          R.state_errors)
-    log(f"calibrated FP64 {k64} ({e64:.2e}), mixed {kmp} ({emp:.2e})")
+    log(f"calibrated FP64 budget {k64} ({f64:.3f} of the calibration batch accurate)")
+    # the mixed solves stop by themselves: the paper's rule plus the FP32 rounding floor of the merit
     lib.ddnm_ws_enable(s.ctx, True)
-    kws, ews = smallest_k(lambda K: R.solve(s, mu_cal, K)[0], x_cal_ref, [1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 15, 20],
-                          R.state_errors)
+    s.options(**HEADLINE_OPTS)
+    _, _, st_cal = s.solve(mu_cal)
+    x_cal = s.solve(mu_cal)[0]
+    f_cal = float(np.mean(R.state_errors(x_cal, x_cal_ref) <= ACC))
+    log(f"mixed + warm start on the calibration batch: {f_cal:.3f} accurate, {st_cal['iters'].mean():.2f} iterations")
 
-    # ---- launch plan of the headline solve: autotuned on this batch with the timed iteration budget
-    log(f"calibrated mixed + warm start {kws} ({ews:.2e})")
-    s.options(tol=0.0, max_iter=kws)
-    plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, max_iter=kws, reps=2)
+    # ---- launch plan of the headline solve: autotuned on this batch with its options
+    plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, max_iter=0, reps=2)
 
     # ---- CPU baseline (rank 0, N = 1): the oracle with this run's decoders, and its parity with both GPU paths
     log(f"autotuned {plan}")
@@ -545,13 +552,13 @@ def main():
         lib.ddnm_ws_enable(s.ctx, True)
 
     log("CPU baseline done")
-    # ---- the timed headline: mixed + learned warm start, kws iterations, device-resident
+    # ---- the timed headline: mixed + learned warm start, stopping by itself, device-resident
     mu_d = torch.from_numpy(mu).to(dev)
     x_d = torch.zeros((B, R.nD), dtype=torch.float64, device=dev)
     l_d = torch.zeros((B, R.nC), dtype=torch.float64, device=dev)
     st_d = torch.zeros(B * 32, dtype=torch.uint8, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    s.options(tol=0.0, max_iter=kws)
+    s.options(**HEADLINE_OPTS)
 
     def step():
         lib.ddnm_solve_batch(s.ctx, B, mu_d, None, None, x_d, l_d, None, st_d)
@@ -595,8 +602,8 @@ def main():
     xh_err = np.abs(x_h - x_ref).max(axis=1) / np.abs(x_ref).max(axis=1)
 
     # ---- the other methods on the same batch and GPU (one timed solve each after an untimed one)
-    def timed_once(solver, K, tol=0.0):
-        solver.options(tol=tol, max_iter=K)
+    def timed_once(solver, **opts):
+        solver.options(**opts)
         solver.solve(mu)
         torch.cuda.synchronize()
         flush.zero_()
@@ -609,11 +616,11 @@ def main():
 
     log(f"headline timed: {t_max / args.steps:.1f} ms per step, {n_ok} of {B} accurate")
     lib.ddnm_ws_enable(s.ctx, False)
-    x64, st64, t64 = timed_once(s64, k64)
+    x64, st64, t64 = timed_once(s64, tol=0.0, max_iter=k64)
     e64t = R.state_errors(x64, x_ref)
-    xmp, stmp, tmp_ = timed_once(s, kmp)
+    xmp, stmp, tmp_ = timed_once(s, **HEADLINE_OPTS)
     emp_t = R.state_errors(xmp, x_ref)
-    xpr, stpr, tpr = timed_once(s64, 15, tol=1e-4)
+    xpr, stpr, tpr = timed_once(s64, tol=1e-4, max_iter=15)
     epr = R.state_errors(xpr, x_ref)
     lib.ddnm_ws_enable(s.ctx, True)
     nfo = min(64, B)
@@ -624,6 +631,7 @@ def main():
     # ---- roofline of the dominant kernel: per-kernel device time from the library's CUDA events, in a
     # separate run of the headline solve through the host-driven loop (events around every launch)
     kb = 3
+    s.options(**HEADLINE_OPTS)
     plan_now = lib.ddnm_get_tune(s.ctx)
     lib.ddnm_set_tune(s.ctx, **dict(plan_now, graph=0, eval_persist=0))
     lib.ddnm_timing_enable(s.ctx, True)
@@ -671,7 +679,7 @@ def main():
     xh_h = torch.zeros((B, R.nD), dtype=torch.float64).pin_memory()
     lh_h = torch.zeros((B, R.nC), dtype=torch.float64).pin_memory()
     st_h = np.zeros(B, dtype=lib.STATS_DTYPE)
-    s.options(tol=0.0, max_iter=kws)
+    s.options(**HEADLINE_OPTS)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
     if dist:
@@ -693,12 +701,12 @@ def main():
 
     cfg = workload_config(args.config)
     cfg.update({
-        "method": f"mixed precision (FP32 evaluation, FP64 KKT / merit / constraint residual) + learned warm start, "
-                  f"{kws} SQP iterations (the smallest budget meeting the accuracy criterion on a calibration batch)",
+        "method": "mixed precision (FP32 evaluation, FP64 KKT / merit / constraint residual) + learned warm start; "
+                  "stop at ||F||_2 < 1e-4, at the FP32 rounding floor of ||F||_2, or after 15 SQP iterations",
         "accuracy_criterion": f"relative 2-norm of g(xh) - g(xh_ref) <= {ACC:g}, xh_ref: FP64 ROM solution "
                               f"({K_REF} SQP iterations); only instances that meet it are counted",
         "accurate_fraction": n_ok / B,
-        "launch_plan": dict(plan, source="autotuned on this batch with the timed iteration budget",
+        "launch_plan": dict(plan, source="autotuned on this batch with the headline options",
                             tune_median_ms_per_solve=round(tune_ms, 3)),
         "parallelism": f"replicas: {world} GPU(s), {B} mu each",
         "setup_seconds": round(time.perf_counter() - t_setup, 1)})
@@ -708,13 +716,20 @@ def main():
         "fom_sample": nfo, "vs_oracle": parity,
         "reference_final_merit": q(st_ref["merit"]),
         "headline_final_merit": q(st["merit"]),
+        "headline_iters": {"mean": float(st["iters"].mean()), "max": int(st["iters"].max())},
+        "headline_stopped_at_floor": float(np.mean(st["flags"] & lib.DDNM_FLAG_FLOOR > 0)),
+        "headline_converged_below_tol": float(np.mean((st["status"] == lib.DDNM_CONVERGED) &
+                                                      (st["flags"] & lib.DDNM_FLAG_FLOOR == 0))),
     }
     comparison = {
         "fp64_plain_default_start": {"iters": k64, "solves_per_s": n_ok_fp(e64t) * 1.0 / t64,
-                                     "accurate_fraction": n_ok_fp(e64t) / B, "calibration_max_err": e64},
-        "mixed_plain_default_start": {"iters": kmp, "solves_per_s": n_ok_fp(emp_t) * 1.0 / tmp_,
-                                      "accurate_fraction": n_ok_fp(emp_t) / B, "calibration_max_err": emp},
-        "mixed_warm_start": {"iters": kws, "calibration_max_err": ews},
+                                     "accurate_fraction": n_ok_fp(e64t) / B, "calibration_accurate_fraction": f64,
+                                     "budget": f"the smallest fixed iteration count making {CAL_SHARE:g} of a "
+                                               f"calibration batch accurate"},
+        "mixed_plain_default_start": {"mean_iters": float(stmp["iters"].mean()),
+                                      "solves_per_s": n_ok_fp(emp_t) * 1.0 / tmp_,
+                                      "accurate_fraction": n_ok_fp(emp_t) / B},
+        "mixed_warm_start_calibration_batch": {"accurate_fraction": f_cal, "mean_iters": float(st_cal["iters"].mean())},
         "fp64_paper_rule": {"converged_fraction": float(np.mean(stpr["status"] == lib.DDNM_CONVERGED)),
                             "mean_iters": float(stpr["iters"].mean()), "solves_per_s_all": B / tpr,
                             "accurate_fraction": n_ok_fp(epr) / B},

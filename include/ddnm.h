@@ -82,6 +82,7 @@ enum {
 /* per-instance flags (ddnm_stats.flags, bit mask) */
 #define DDNM_FLAG_LS_FAIL 1   /* some line search took its last trial without passing Armijo */
 #define DDNM_FLAG_WS_FALLBACK 2 /* learned warm start enabled, but the default start had the smaller merit */
+#define DDNM_FLAG_FLOOR 4     /* stopped at the FP32 rounding floor of the merit (options.floor_stop) */
 
 /* Problem statement (Sec. 2, 3.1, 7.1). */
 typedef struct ddnm_problem {
@@ -107,6 +108,13 @@ typedef struct ddnm_options {
     double armijo_c1;       /* accept alpha when phi(alpha)^2 <= (1 - 2 c1 alpha) phi(0)^2 */
     double beta;            /* backtracking factor */
     int max_backtracks;     /* after this many halvings the last trial is taken (flag LS_FAIL) */
+    int floor_stop;         /* mixed path only (0 = off, the default, the paper's rule alone): with the FP32
+                               evaluation, ||F||_2 cannot fall below the rounding of rho_i = R_i^T r_i, whose
+                               bound phi_u = 2^-24 ||sum_k |R_i,k| rabs_k|| (rabs_k: the sum of the magnitudes
+                               of the terms of the collocated residual r_k) every evaluation also forms.  With
+                               floor_stop = 1 a trial at phi <= phi_u is accepted and the instance stops there
+                               (status CONVERGED, flag DDNM_FLAG_FLOOR) instead of backtracking on rounding
+                               noise.  Ignored by the FP64 path. */
 } ddnm_options;
 
 /* One sparse-masked shallow decoder g(x) = offset + scale o (W2 sigma(W1 x + b1))
@@ -218,6 +226,27 @@ int ddnm_set_test_matrix(ddnm_ctx* ctx, const double* C);
  * stencils (interior) or the constraint (interface, all rows; Sec. 5.3 remark)
  * need.  DDNM_E_INVALID on size mismatch or a column outside [-1, w). */
 int ddnm_load_decoders(ddnm_ctx* ctx, int sub, int kind, const ddnm_decoder* d);
+
+/* Gappy-POD hyper-reduction for subdomain `sub` (Sec. 3.1, Eq. dd_lspg_NLP with B_i = (Z_i Phi_i^r)^+ Z_i):
+ * proj = (Z_i Phi_i^r)^+, nr x N_i^B row-major, its columns in the order of the subdomain's HR rows given to
+ * ddnm_setup (Z_i), Phi_i^r the subdomain's residual basis (nr columns).  The evaluation then forms
+ * R_i = proj Z_i dr_i/dxh and r~_i = proj Z_i r_i, H_i = R_i^T R_i and R_i^T r~_i from them.  nr = 0 returns
+ * to collocation (B_i = Z_i).  1 <= nr <= min(64, N_i^B); host memory, copied; takes effect at the next
+ * compute call.  DDNM_E_INVALID for sizes out of range or non-finite entries. */
+int ddnm_set_hr_projection(ddnm_ctx* ctx, int sub, int nr, const double* proj);
+
+/* Offline choice of the gappy-POD sample rows and projectors (Sec. 5.3, greedy-sampling remark) from residual
+ * snapshots snaps (n_snap x N_x host array: FOM residuals at Newton iterates, e.g. from ddnm_fom_residual).
+ * Per subdomain i: the residual basis Phi_i^r = the leading nr[i] left singular vectors of its rows of the
+ * snapshots; n_samples[i] rows chosen greedily (interpolation error of basis vector k for the first nr[i]
+ * rows, then the row of largest leverage against the rows taken); the projector (Z_i Phi_i^r)^+.
+ *   rows_out  sum_i n_samples[i] ascending local residual-row ids per subdomain, in subdomain order (the
+ *             hr_rows of a new ddnm_setup)
+ *   proj_out  sum_i nr[i] n_samples[i]: per subdomain the nr[i] x n_samples[i] projector, row-major (for
+ *             ddnm_set_hr_projection on that new context)
+ * Host computation (no device); 1 <= nr[i] <= min(64, n_snap), nr[i] <= n_samples[i] <= N_i^r. */
+int ddnm_hr_select(ddnm_ctx* ctx, int n_snap, const double* snaps, const int* nr, const int* n_samples, int* rows_out,
+                   double* proj_out);
 
 /* Replace the SQP options. */
 int ddnm_set_options(ddnm_ctx* ctx, const ddnm_options* opt);
@@ -477,6 +506,13 @@ typedef struct ddnm_fom_stats {
 
 int ddnm_fom_solve(ddnm_ctx* ctx, int B, const double* mu, const double* x0, double* x_out, ddnm_fom_stats* stats,
                    int max_newton, int max_krylov, int mem_kind, void* stream);
+
+/* FOM residual r(x; mu) of Eq. (burgers_discretized) at B given full states x (B x N_x, ordering [u; v],
+ * x-fastest), into r_out (B x N_x).  Used to collect residual snapshots along Newton's iterations for the
+ * gappy-POD basis (Sec. 5.3, greedy-sampling remark).  mem_kind as in ddnm_solve_batch; with host memory the
+ * call returns once r_out is written. */
+int ddnm_fom_residual(ddnm_ctx* ctx, int B, const double* mu, const double* x, double* r_out, int mem_kind,
+                      void* stream);
 
 /* Measured FP32 and FP64 fused multiply-add throughput of ctx's device (TFLOP/s, 2 flops per FMA): a
  * grid of 8 CTAs x 256 threads per SM, every thread running 8 independent FMA chains, timed with CUDA

@@ -28,7 +28,7 @@ DDNM_ACT = {"swish": 0, "sigmoid": 1, "identity": 2}
 DDNM_MEM_HOST, DDNM_MEM_DEVICE = 0, 1
 DDNM_DECODER_INTERIOR, DDNM_DECODER_INTERFACE = 0, 1
 DDNM_CONVERGED, DDNM_MAX_ITER, DDNM_NONFINITE, DDNM_KKT_FAIL = 0, 1, 2, 3
-DDNM_FLAG_LS_FAIL, DDNM_FLAG_WS_FALLBACK = 1, 2
+DDNM_FLAG_LS_FAIL, DDNM_FLAG_WS_FALLBACK, DDNM_FLAG_FLOOR = 1, 2, 4
 
 _ip = C.POINTER(C.c_int)
 _dp = C.POINTER(C.c_double)
@@ -43,7 +43,7 @@ class ddnm_problem(C.Structure):
 
 class ddnm_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("armijo_c1", C.c_double),
-                ("beta", C.c_double), ("max_backtracks", C.c_int)]
+                ("beta", C.c_double), ("max_backtracks", C.c_int), ("floor_stop", C.c_int)]
 
 
 class ddnm_decoder(C.Structure):
@@ -121,6 +121,9 @@ _sig = {
     "ddnm_get_decoder": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "ddnm_fom_solve": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "ddnm_measure_peaks": (C.c_int, [_vp, _dp, _dp]),
+    "ddnm_fom_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
+    "ddnm_set_hr_projection": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    "ddnm_hr_select": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
     "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
@@ -213,8 +216,8 @@ def ddnm_set_test_matrix(ctx, Cmat):
     _check(ctx, _lib.ddnm_set_test_matrix(ctx, Cm.ctypes.data))
 
 
-def ddnm_set_options(ctx, tol=1e-4, max_iter=15, armijo_c1=1e-4, beta=0.5, max_backtracks=20):
-    o = ddnm_options(tol, max_iter, armijo_c1, beta, max_backtracks)
+def ddnm_set_options(ctx, tol=1e-4, max_iter=15, armijo_c1=1e-4, beta=0.5, max_backtracks=20, floor_stop=0):
+    o = ddnm_options(tol, max_iter, armijo_c1, beta, max_backtracks, int(floor_stop))
     _check(ctx, _lib.ddnm_set_options(ctx, C.byref(o)))
 
 
@@ -361,6 +364,44 @@ def ddnm_fom_solve(ctx, mu, x0=None, x_out=None, max_newton=20, max_krylov=400):
     _check(ctx, _lib.ddnm_fom_solve(ctx, B, _ptr(mu), _ptr(x0), _ptr(x_out), st.ctypes.data, int(max_newton),
                                     int(max_krylov), kind, _stream(kind)))
     return x_out, st
+
+
+def ddnm_fom_residual(ctx, mu, x, r_out=None):
+    """FOM residual r(x; mu) of B full states: numpy (returns r) or torch CUDA tensors (fills r_out)."""
+    kind = _mem_kind(mu, x, r_out)
+    B = int(mu.shape[0])
+    if kind == DDNM_MEM_HOST:
+        mu, x = _f64(mu).reshape(B, 2), _f64(x).reshape(B, -1)
+        r_out = np.zeros_like(x) if r_out is None else r_out
+    _check(ctx, _lib.ddnm_fom_residual(ctx, B, _ptr(mu), _ptr(x), _ptr(r_out), kind, _stream(kind)))
+    return r_out
+
+
+def ddnm_set_hr_projection(ctx, sub, proj):
+    """Gappy-POD projector (Z_i Phi_i^r)^+ (nr x N_B numpy array) of subdomain sub; None returns to collocation."""
+    if proj is None:
+        _check(ctx, _lib.ddnm_set_hr_projection(ctx, int(sub), 0, None))
+        return
+    p = _f64(proj)
+    _check(ctx, _lib.ddnm_set_hr_projection(ctx, int(sub), int(p.shape[0]), p.ctypes.data))
+
+
+def ddnm_hr_select(ctx, snaps, nr, n_samples):
+    """Gappy-POD rows and projectors from residual snapshots (n_snap x N_x numpy): returns (rows per subdomain,
+    projectors per subdomain (nr_i x n_samples_i))."""
+    S = _f64(snaps)
+    nr, ns = _i32(nr), _i32(n_samples)
+    rows = np.zeros(int(ns.sum()), dtype=np.int32)
+    proj = np.zeros(int((nr.astype(np.int64) * ns).sum()))
+    _check(ctx, _lib.ddnm_hr_select(ctx, S.shape[0], S.ctypes.data, nr.ctypes.data, ns.ctypes.data, rows.ctypes.data,
+                                    proj.ctypes.data))
+    out_r, out_p, r0, p0 = [], [], 0, 0
+    for a, b in zip(nr, ns):
+        out_r.append(rows[r0:r0 + b].copy())
+        out_p.append(proj[p0:p0 + a * b].reshape(a, b).copy())
+        r0 += b
+        p0 += a * b
+    return out_r, out_p
 
 
 def mlp_param_count(n_in, H, n_out):

@@ -26,6 +26,8 @@ struct SubHost {
     std::vector<int> need;       // interior outputs the stencils use (I_o), ascending local indices
     std::vector<int> needG;      // interface outputs the stencils use, ascending local indices
     int nO = 0, nG = 0;
+    int nr = 0;                  // gappy-POD HR: rows of the projector (Z_i Phi_i^r)^+ (0: collocation)
+    std::vector<double> proj;    // nr x N_B, columns in the order of hr_rows
 };
 
 // learned warm start (ddnm_mlp.cu): MLP mu -> xh0 with FP32 master weights and a bfloat16 copy
@@ -61,7 +63,7 @@ struct ddnm_ctx {
     int nx = 0, ny = 0, kx = 0, ky = 0, n_sub = 0, N = 0, n_C = 0, N_A = 0;
     int precision = DDNM_MIXED, device = 0;
     double nu = 0.1, box[4] = {-1, 1, -1, 1}, hx = 0, hy = 0;
-    ddnm_options opt{1e-4, 15, 1e-4, 0.5, 20};
+    ddnm_options opt{1e-4, 15, 1e-4, 0.5, 20, 0};
     std::vector<int> xb, yb;
     std::vector<SubHost> subs;
     std::vector<int> con_var, con_lo, con_hi, con_lo_flat, con_hi_flat;

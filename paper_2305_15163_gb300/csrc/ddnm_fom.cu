@@ -678,6 +678,40 @@ int time_peak(ddnm_ctx* ctx, int n_sm, int iters, double* tflops) {
 }
 }  // namespace
 
+extern "C" int ddnm_fom_residual(ddnm_ctx* ctx, int B, const double* mu, const double* x, double* r_out, int mem_kind,
+                                 void* stream) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (B < 1 || !mu || !x || !r_out) return ddnm_fail(ctx, DDNM_E_INVALID, "ddnm_fom_residual: B >= 1, mu, x, r_out");
+    if (mem_kind != DDNM_MEM_HOST && mem_kind != DDNM_MEM_DEVICE) return ddnm_fail(ctx, DDNM_E_INVALID, "bad mem_kind");
+    FK(cudaSetDevice(ctx->device));
+    FomWork* W = nullptr;
+    int rc = fom_reserve(ctx, W, B);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = ctx->nx, ny = ctx->ny, N = nx * ny, Nx = 2 * N;
+    const size_t stride = (size_t)NV * Nx;
+    const cudaMemcpyKind in = mem_kind == DDNM_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind out = mem_kind == DDNM_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    FK(cudaMemcpyAsync(W->mu, mu, (size_t)B * 16, in, st));
+    FomDev F;
+    F.nx = nx; F.ny = ny; F.N = N; F.Nx = Nx;
+    F.hx = ctx->hx; F.hy = ctx->hy; F.nu = ctx->nu; F.bx0 = ctx->box[0]; F.by0 = ctx->box[2];
+    F.ihx2 = 1.0 / (2.0 * F.hx); F.ihy2 = 1.0 / (2.0 * F.hy);
+    F.lx = F.nu / (F.hx * F.hx); F.ly = F.nu / (F.hy * F.hy);
+    F.mu = W->mu;
+    F.bnd = W->bnd;
+    const int nb = 2 * (nx + ny);
+    k_fom_bnd<<<dim3((nb + FT - 1) / FT, B), FT, 0, st>>>(F, B);
+    double* X = W->vec + V_X * (size_t)Nx;
+    double* R = W->vec + V_R * (size_t)Nx;
+    for (int b = 0; b < B; ++b) FK(cudaMemcpyAsync(X + (size_t)b * stride, x + (size_t)b * Nx, (size_t)Nx * 8, in, st));
+    k_fom_res<<<dim3((N + FT - 1) / FT, B), FT, 0, st>>>(F, B, X, R, stride, nullptr);
+    FK(cudaGetLastError());
+    for (int b = 0; b < B; ++b) FK(cudaMemcpyAsync(r_out + (size_t)b * Nx, R + (size_t)b * stride, (size_t)Nx * 8, out, st));
+    if (mem_kind == DDNM_MEM_HOST) FK(cudaStreamSynchronize(st));
+    return DDNM_OK;
+}
+
 extern "C" int ddnm_measure_peaks(ddnm_ctx* ctx, double* fp32_tflops, double* fp64_tflops) {
     if (!ctx || !fp32_tflops || !fp64_tflops) return DDNM_E_INVALID;
     FK(cudaSetDevice(ctx->device));

@@ -314,9 +314,25 @@ extern "C" int ddnm_set_test_matrix(ddnm_ctx* ctx, const double* C) {
 extern "C" int ddnm_set_options(ddnm_ctx* ctx, const ddnm_options* o) {
     if (!ctx || !o) return DDNM_E_INVALID;
     if (!(o->tol >= 0) || o->max_iter < 0 || !(o->armijo_c1 >= 0 && o->armijo_c1 < 0.5) || !(o->beta > 0 && o->beta < 1) ||
-        o->max_backtracks < 0 || o->max_iter > 100000 || o->max_backtracks > 60)
+        o->max_backtracks < 0 || o->max_iter > 100000 || o->max_backtracks > 60 || o->floor_stop < 0 ||
+        o->floor_stop > 1)
         return ddnm_fail(ctx, DDNM_E_INVALID, "options out of range");
     ctx->opt = *o;
+    return DDNM_OK;
+}
+
+extern "C" int ddnm_set_hr_projection(ddnm_ctx* ctx, int sub, int nr, const double* proj) {
+    if (!ctx) return DDNM_E_INVALID;
+    if (sub < 0 || sub >= ctx->n_sub || nr < 0 || nr > MAX_NR || (nr && !proj))
+        return ddnm_fail(ctx, DDNM_E_INVALID, "hr projection: sub in range, 0 <= nr <= 64, proj given when nr > 0");
+    SubHost& sd = ctx->subs[sub];
+    const size_t nb = sd.hr_rows.size();
+    if ((size_t)nr > nb) return ddnm_fail(ctx, DDNM_E_INVALID, "hr projection: nr above the subdomain's HR rows");
+    for (size_t k = 0; k < (size_t)nr * nb; ++k)
+        if (!std::isfinite(proj[k])) return ddnm_fail(ctx, DDNM_E_INVALID, "hr projection: non-finite entry");
+    sd.nr = nr;
+    sd.proj.assign(proj, proj + (size_t)nr * nb);
+    ctx->finalized = false;      // the next compute call uploads it
     return DDNM_OK;
 }
 
@@ -534,8 +550,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     ctx->hsub.assign(ns, SubDev{});
     ctx->hchunk.clear();
     ctx->htiles.clear();
-    // an instance's block area: the n_sub merits ||rho_i||^2 (padded to an even count), then the blocks
-    int xoff = 0, hr_off = 0, blk = (ctx->n_sub + 1) & ~1;
+    // an instance's block area: the n_sub merits ||rho_i||^2, the n_sub squared rounding bounds of rho_i (mixed
+    // path; zero in FP64), padded to an even count, then the blocks
+    int xoff = 0, hr_off = 0, blk = (2 * ctx->n_sub + 1) & ~1;
     long long pg_stride = 0;
     std::vector<float> qtc;        // mixed path: every Q_i split and tiled for the tensor-core D_i GEMM
     ctx->max_nG = 1;
@@ -600,6 +617,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         SubDev& S = ctx->hsub[s];
         S.nO = sd.nO; S.nG = sd.nG; S.ni = sd.nO + sd.nG; S.xoff = xoff; xoff += S.ni;
         S.NB = (int)sd.hr_rows.size(); S.hr_off = hr_off; hr_off += S.NB;
+        S.nr = sd.nr;
+        S.gp = sd.nr ? P.addv(sd.proj.data(), sd.proj.size()) : 0;
         S.K = dO.K; S.Kp = (dO.K + 7) & ~7; S.actO = dO.act; S.actG = dG.act;
         S.goff = ctx->goff[s];
         S.NG = (int)sd.interface.size();

@@ -13,6 +13,7 @@ constexpr int MAX_NG = 8;      // n_i^G
 constexpr int MAX_K = 64;      // ELL slots of a decoder output row
 constexpr int MAX_NC = 128;    // weak constraints
 constexpr int MAX_SUB = 256;   // subdomains
+constexpr int MAX_NR = 64;     // rows of a gappy-POD projector (Z_i Phi_i^r)^+
 // threads of one evaluation group: eval_threads(...) below
 constexpr int STEP_THREADS = 256;
 constexpr int CON_THREADS = 256;
@@ -105,6 +106,8 @@ struct SubDev {
     int NGn, hr_chunk;             // interface outputs the stencils use; collocation rows per chunk
     long long colGn, valGn, soGn;  // those outputs: ELL slot-major (Kp x NGn), scale/offset
     long long Qt;                  // value pool: Q_i^T = (C A_i diag(scale) W2~)^T, h_G x n_C
+    int nr, pad_nr;                // gappy-POD HR: rows of (Z_i Phi_i^r)^+ (0: collocation, B_i = Z_i)
+    long long gp;                  // value pool: (Z_i Phi_i^r)^+, nr x N_B row-major
     long long qtc;                 // mixed path: Q_i split into TF32 hi / lo in k_dgemm_tc's order (floats into
     int hGp, pad_tc;               // P.Qtc); h_G rounded up to the tensor-core K chunk
     long long pgoff;               // offset of this subdomain's P_G (h_G x n^G) in an instance's P_G area
@@ -158,6 +161,7 @@ struct ProbDev {
     double tol, c1, beta;
     double piv_eps;                // block pivots d_j <= piv_eps max_k H_kk count as zero (rank test)
     int max_iter, max_bt;
+    int floor_stop;                // mixed path: accept and stop at the FP32 rounding floor of the merit
     int blk_stride;                // doubles per instance of the block area
     const SubDev* sub;
     const ChunkDev* chunk;
@@ -213,6 +217,7 @@ constexpr int CTL_INTS = MAX_CHAINS * (3 + MAX_CLASSES);
 
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {
+    int Rt;
     int sx, hidO, hidG, outGn, outO, Rr, red;  // value-type arrays
     int dH, drho, dt, dD;                      // double arrays
     int bytes;
@@ -229,8 +234,9 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.hidG = o; o = align16(o + round4(s.hG) * rG * tsize);
     e.outGn = o; o = align16(o + s.NGn * rG * tsize);        // [y, Jacobian row] per interface output the stencils use
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
-    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
+    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 2) * tsize); // [R row, r, rabs] per collocation row (chunk)
     e.red = o; o = align16(o + (eval_threads(tsize, rO, rG) / nC) * nC * s.nG * tsize);   // D_i partials per thread group
+    e.Rt = o; o = align16(o + s.nr * (s.ni + 2) * tsize);  // gappy POD: (Z Phi)^+ [R, r, rabs] over the rows
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
     e.dt = o; o = align16(o + s.ni * 8);
