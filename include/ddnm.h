@@ -82,7 +82,7 @@ enum {
 /* per-instance flags (ddnm_stats.flags, bit mask) */
 #define DDNM_FLAG_LS_FAIL 1   /* some line search took its last trial without passing Armijo */
 #define DDNM_FLAG_WS_FALLBACK 2 /* learned warm start enabled, but the default start had the smaller merit */
-#define DDNM_FLAG_FLOOR 4     /* stopped at the FP32 rounding floor of the merit (options.floor_stop) */
+#define DDNM_FLAG_STEP 4      /* stopped on a step below options.step_tol (mixed path) */
 
 /* Problem statement (Sec. 2, 3.1, 7.1). */
 typedef struct ddnm_problem {
@@ -108,13 +108,12 @@ typedef struct ddnm_options {
     double armijo_c1;       /* accept alpha when phi(alpha)^2 <= (1 - 2 c1 alpha) phi(0)^2 */
     double beta;            /* backtracking factor */
     int max_backtracks;     /* after this many halvings the last trial is taken (flag LS_FAIL) */
-    int floor_stop;         /* mixed path only (0 = off, the default, the paper's rule alone): with the FP32
-                               evaluation, ||F||_2 cannot fall below the rounding of rho_i = R_i^T r_i, whose
-                               bound phi_u = 2^-24 ||sum_k |R_i,k| rabs_k|| (rabs_k: the sum of the magnitudes
-                               of the terms of the collocated residual r_k) every evaluation also forms.  With
-                               floor_stop = 1 a trial at phi <= phi_u is accepted and the instance stops there
-                               (status CONVERGED, flag DDNM_FLAG_FLOOR) instead of backtracking on rounding
-                               noise.  Ignored by the FP64 path. */
+    double step_tol;        /* mixed path only (0 = off, the default: the paper's rule alone).  With the FP32
+                               evaluation ||F||_2 stalls near the solution at the rounding level of rho_i, where
+                               the Armijo test compares rounding noise and backtracks.  With step_tol > 0, the
+                               first trial of a step with ||s||_2 <= step_tol ||xh||_2 (the Gauss-Newton step of
+                               the latent coordinates) is accepted and the instance stops there (status
+                               CONVERGED, flag DDNM_FLAG_STEP).  Ignored by the FP64 path; 0 <= step_tol < 1. */
 } ddnm_options;
 
 /* One sparse-masked shallow decoder g(x) = offset + scale o (W2 sigma(W1 x + b1))

@@ -28,7 +28,7 @@ DDNM_ACT = {"swish": 0, "sigmoid": 1, "identity": 2}
 DDNM_MEM_HOST, DDNM_MEM_DEVICE = 0, 1
 DDNM_DECODER_INTERIOR, DDNM_DECODER_INTERFACE = 0, 1
 DDNM_CONVERGED, DDNM_MAX_ITER, DDNM_NONFINITE, DDNM_KKT_FAIL = 0, 1, 2, 3
-DDNM_FLAG_LS_FAIL, DDNM_FLAG_WS_FALLBACK, DDNM_FLAG_FLOOR = 1, 2, 4
+DDNM_FLAG_LS_FAIL, DDNM_FLAG_WS_FALLBACK, DDNM_FLAG_STEP = 1, 2, 4
 
 _ip = C.POINTER(C.c_int)
 _dp = C.POINTER(C.c_double)
@@ -43,7 +43,7 @@ class ddnm_problem(C.Structure):
 
 class ddnm_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("armijo_c1", C.c_double),
-                ("beta", C.c_double), ("max_backtracks", C.c_int), ("floor_stop", C.c_int)]
+                ("beta", C.c_double), ("max_backtracks", C.c_int), ("step_tol", C.c_double)]
 
 
 class ddnm_decoder(C.Structure):
@@ -216,8 +216,8 @@ def ddnm_set_test_matrix(ctx, Cmat):
     _check(ctx, _lib.ddnm_set_test_matrix(ctx, Cm.ctypes.data))
 
 
-def ddnm_set_options(ctx, tol=1e-4, max_iter=15, armijo_c1=1e-4, beta=0.5, max_backtracks=20, floor_stop=0):
-    o = ddnm_options(tol, max_iter, armijo_c1, beta, max_backtracks, int(floor_stop))
+def ddnm_set_options(ctx, tol=1e-4, max_iter=15, armijo_c1=1e-4, beta=0.5, max_backtracks=20, step_tol=0.0):
+    o = ddnm_options(tol, max_iter, armijo_c1, beta, max_backtracks, float(step_tol))
     _check(ctx, _lib.ddnm_set_options(ctx, C.byref(o)))
 
 

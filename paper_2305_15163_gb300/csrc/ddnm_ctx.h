@@ -63,7 +63,7 @@ struct ddnm_ctx {
     int nx = 0, ny = 0, kx = 0, ky = 0, n_sub = 0, N = 0, n_C = 0, N_A = 0;
     int precision = DDNM_MIXED, device = 0;
     double nu = 0.1, box[4] = {-1, 1, -1, 1}, hx = 0, hy = 0;
-    ddnm_options opt{1e-4, 15, 1e-4, 0.5, 20, 0};
+    ddnm_options opt{1e-4, 15, 1e-4, 0.5, 20, 0.0};
     std::vector<int> xb, yb;
     std::vector<SubHost> subs;
     std::vector<int> con_var, con_lo, con_hi, con_lo_flat, con_hi_flat;

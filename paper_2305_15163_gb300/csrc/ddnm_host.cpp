@@ -314,8 +314,8 @@ extern "C" int ddnm_set_test_matrix(ddnm_ctx* ctx, const double* C) {
 extern "C" int ddnm_set_options(ddnm_ctx* ctx, const ddnm_options* o) {
     if (!ctx || !o) return DDNM_E_INVALID;
     if (!(o->tol >= 0) || o->max_iter < 0 || !(o->armijo_c1 >= 0 && o->armijo_c1 < 0.5) || !(o->beta > 0 && o->beta < 1) ||
-        o->max_backtracks < 0 || o->max_iter > 100000 || o->max_backtracks > 60 || o->floor_stop < 0 ||
-        o->floor_stop > 1)
+        o->max_backtracks < 0 || o->max_iter > 100000 || o->max_backtracks > 60 || !(o->step_tol >= 0.0 &&
+        o->step_tol < 1.0))
         return ddnm_fail(ctx, DDNM_E_INVALID, "options out of range");
     ctx->opt = *o;
     return DDNM_OK;
@@ -550,9 +550,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     ctx->hsub.assign(ns, SubDev{});
     ctx->hchunk.clear();
     ctx->htiles.clear();
-    // an instance's block area: the n_sub merits ||rho_i||^2, the n_sub squared rounding bounds of rho_i (mixed
-    // path; zero in FP64), padded to an even count, then the blocks
-    int xoff = 0, hr_off = 0, blk = (2 * ctx->n_sub + 1) & ~1;
+    // an instance's block area: the n_sub merits ||rho_i||^2, then per subdomain ||s_i||^2 and ||x_i||^2 of the
+    // last Gauss-Newton step (the step test), padded to an even count, then the blocks
+    int xoff = 0, hr_off = 0, blk = (3 * ctx->n_sub + 1) & ~1;
     long long pg_stride = 0;
     std::vector<float> qtc;        // mixed path: every Q_i split and tiled for the tensor-core D_i GEMM
     ctx->max_nG = 1;
@@ -587,7 +587,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 chunk_rows(sd, cand, cn, nullptr);
                 SubDev T{};
                 T.nO = sd.nO; T.nG = sd.nG; T.ni = sd.nO + sd.nG; T.hO = hO[s]; T.hG = hG[s];
-                T.NG = (int)sd.interface.size(); T.NGn = (int)sd.needG.size(); T.hr_chunk = cand;
+                T.NG = (int)sd.interface.size(); T.NGn = (int)sd.needG.size(); T.hr_chunk = cand; T.nr = sd.nr;
                 for (const auto& c : cn) T.mmax = std::max(T.mmax, (int)c.size());
                 const int b = eval_smem(T, nC, (int)tsize).bytes;
                 bytes = std::max(bytes, b);

@@ -161,7 +161,7 @@ struct ProbDev {
     double tol, c1, beta;
     double piv_eps;                // block pivots d_j <= piv_eps max_k H_kk count as zero (rank test)
     int max_iter, max_bt;
-    int floor_stop;                // mixed path: accept and stop at the FP32 rounding floor of the merit
+    double step_tol;               // mixed path: stop on a first trial whose step is below step_tol of the iterate
     int blk_stride;                // doubles per instance of the block area
     const SubDev* sub;
     const ChunkDev* chunk;
@@ -234,9 +234,9 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     e.hidG = o; o = align16(o + round4(s.hG) * rG * tsize);
     e.outGn = o; o = align16(o + s.NGn * rG * tsize);        // [y, Jacobian row] per interface output the stencils use
     e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
-    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 2) * tsize); // [R row, r, rabs] per collocation row (chunk)
+    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
     e.red = o; o = align16(o + (eval_threads(tsize, rO, rG) / nC) * nC * s.nG * tsize);   // D_i partials per thread group
-    e.Rt = o; o = align16(o + s.nr * (s.ni + 2) * tsize);  // gappy POD: (Z Phi)^+ [R, r, rabs] over the rows
+    e.Rt = o; o = align16(o + s.nr * (s.ni + 1) * tsize);  // gappy POD: (Z Phi)^+ [R, r] over the rows
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
     e.dt = o; o = align16(o + s.ni * 8);

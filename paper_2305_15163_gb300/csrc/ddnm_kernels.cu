@@ -424,6 +424,15 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, 
         }
         gsync<NT>(bar);
         if (tid < ni) xt[tid] = x[tid] + s[tid];
+        if (tid < 32) {          // ||s_i||^2 and ||x_i||^2 after the merits in the header (the step test)
+            const double a = warp_sum(tid < ni ? s[tid] * s[tid] : 0.0);
+            const double c = warp_sum(tid < ni ? x[tid] * x[tid] : 0.0);
+            if (tid == 0) {
+                double* hdr = P.blk + (size_t)b * P.blk_stride + P.n_sub + 2 * S.phio;
+                hdr[0] = a;
+                hdr[1] = c;
+            }
+        }
     } else {
         const double alpha = P.dst[(size_t)b * INST_DBLS + D_ALPHA];
         if (tid < ni) xt[tid] = x[tid] + alpha * s[tid];
@@ -451,13 +460,13 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     double* dt = (double*)(smem + L.dt);
     double* dD = (double*)(smem + L.dD);
     T* red = (T*)(smem + L.red);
-    T* Rt = (T*)(smem + L.Rt);                 // gappy POD: (Z_i Phi_i^r)^+ [R, r, rabs], nr x (n_i + 2)
+    T* Rt = (T*)(smem + L.Rt);                 // gappy POD: (Z_i Phi_i^r)^+ [R, r], nr x (n_i + 1)
 
     const T* V = (const T*)P.vpool;
     const int* IP = P.ipool;
     const int nth = NT;
     const int nO = S.nO, nG = S.nG, ni = S.ni, nC = P.n_C, NG = S.NG;
-    const int ld = ni + 2;                 // Rr rows: [R row (n_i), r, sum of |terms of r|]
+    const int ld = ni + 1;                 // Rr rows: [R row (n_i), r]
     constexpr int WO = RO - 1 > 0 ? ((RO - 1 + 3) & ~3) : 4;   // padded W1 row width of the interior subnet
     constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
@@ -646,9 +655,6 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     } else if (tid < npair + ni) {
         pa = tid - npair;
         pc = ni;
-    } else if (tid < npair + 2 * ni) {          // rounding bound of (R^T r)_a: sum_k |R_ka| rabs_k
-        pa = tid - npair - ni;
-        pc = ni + 1;
     }
     T hacc = T(0);
     const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
@@ -712,31 +718,20 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int k = 0; k < RG - 1; ++k)
                 if (k < nG) row[nO + k] = RG_[k];
             row[ni] = r;
-            // magnitudes of r's terms: its FP32 rounding is about 2^-24 times this (cancellation in the stencil)
-            row[ni + 1] = fabs(up * dxf * ax) + fabs(vp * dyf * ay) +
-                          cx * (fabs(f[1]) + T(2) * fabs(f[0]) + fabs(f[2])) +
-                          cy * (fabs(f[3]) + T(2) * fabs(f[0]) + fabs(f[4]));
             if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
         }
         gsync<NT>(bar);
         if (S.nr) {
             // gappy-POD HR (B_i = (Z_i Phi_i^r)^+ Z_i, Sec. 3.1): the projector's columns of this chunk's rows
-            // applied to [R, r] (and its magnitudes to rabs), summed over the chunks; entry e of Rt is one thread's
+            // applied to [R, r], summed over the chunks; entry e of Rt is one thread's
             const T* Pg = V + S.gp + Cq.q0;
             for (int e = tid; e < S.nr * ld; e += nth) {
                 const int a = e / ld, j = e - a * ld;
                 const T* pr = Pg + (size_t)a * S.NB;
                 T acc = T(0);
-                if (j <= ni)
-                    for (int ql = 0; ql < Cq.nq; ++ql) acc += pr[ql] * Rr[(size_t)ql * ld + j];
-                else
-                    for (int ql = 0; ql < Cq.nq; ++ql) acc += fabs(pr[ql]) * Rr[(size_t)ql * ld + j];
+                for (int ql = 0; ql < Cq.nq; ++ql) acc += pr[ql] * Rr[(size_t)ql * ld + j];
                 Rt[e] += acc;
             }
-        } else if (tid >= npair + ni && tid < npair + 2 * ni) {
-            T h0 = T(0);
-            for (int ql = 0; ql < Cq.nq; ++ql) h0 += fabs(Rr[(size_t)ql * ld + pa]) * Rr[(size_t)ql * ld + pc];
-            hacc += h0;
         } else if (tid < npair + ni) {
             T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
             int ql = 0;
@@ -751,15 +746,11 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         }
         if (q + 1 < S.n_chunks) gsync<NT>(bar);   // outO / Rr reused by the next chunk
     }
-    if (S.nr) {                                  // H_i, R_i^T r_i and the rounding bound from the projected rows
+    if (S.nr) {                                  // H_i and R_i^T r_i from the projected rows
         gsync<NT>(bar);
         if (tid < npair + ni) {
             T h0 = T(0);
             for (int a = 0; a < S.nr; ++a) h0 += Rt[(size_t)a * ld + pa] * Rt[(size_t)a * ld + pc];
-            hacc = h0;
-        } else if (tid < npair + 2 * ni) {
-            T h0 = T(0);
-            for (int a = 0; a < S.nr; ++a) h0 += fabs(Rt[(size_t)a * ld + pa]) * Rt[(size_t)a * ld + pc];
             hacc = h0;
         }
     }
@@ -768,18 +759,8 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         dH[pc * ni + pa] = (double)hacc;
     } else if (tid < npair + ni) {
         drho[pa] = (double)hacc;
-    } else if (tid < npair + 2 * ni) {
-        dt[pa] = (double)hacc;                 // dt (the trial-point scratch) is free by now
     }
     gsync<NT>(bar);
-    // squared rounding bound of rho_i in the mixed path, 2^-24 ||sum_k |R_k| rabs_k||, into the header after the
-    // merits (zero in FP64)
-    if (tid < 32) {
-        const double u = sizeof(T) == 4 ? 5.9604644775390625e-08 : 0.0;
-        const double e = tid < ni ? u * dt[tid] : 0.0;
-        const double en = warp_sum(e * e);
-        if (tid == 0) P.blk[(size_t)b * P.blk_stride + P.n_sub + S.phio] = en;
-    }
 
     // H_i and rho_i = R_i^T r + E_i^T lambda (E_i = [0, D_i]) with phi_i = ||rho_i||^2 (in FP64: warp k forms
     // entry n^O + k, lanes over the multipliers), or R_i^T r alone when k_dgemm forms D_i and the rest
@@ -1540,10 +1521,11 @@ __device__ __forceinline__ int kkt_decide(const ProbDev& P, int b, const double*
     const int mode = ist[I_MODE];
     const int iters0 = ist[I_ITERS], nbt = ist[I_NBT];
     const double alpha = dst[D_ALPHA], phi0 = dst[D_PHI0];
-    double acc = 0.0, accn = 0.0;
+    double acc = 0.0, ss = 0.0, xx = 0.0;
     for (int i = t; i < ns; i += n) {
         acc += blk[i];
-        accn += blk[ns + i];
+        ss += blk[ns + 2 * i];
+        xx += blk[ns + 2 * i + 1];
     }
     for (int c = t; c < nC; c += n) {
         const double a = tree_sum(P.Atil + (size_t)b * P.n_split * nC + c, P.n_split, nC);
@@ -1552,15 +1534,20 @@ __device__ __forceinline__ int kkt_decide(const ProbDev& P, int b, const double*
     }
     const double phi2 = range_sum(acc, scratch, t, n, bar);   // barriers inside: the range has read ist and dst
     const double phi = sqrt(phi2);
-    // the FP32 rounding floor of the merit (mixed path with floor_stop): a trial at or below it is accepted and
-    // ends the solve; its Armijo comparison would only compare rounding noise
-    const bool at_floor = P.floor_stop && phi <= sqrt(range_sum(accn, scratch, t, n, bar));
+    // the step test (mixed path with step_tol > 0): the first trial of a step whose Gauss-Newton step is below
+    // step_tol of the iterate is accepted and ends the solve (near the solution the FP32 evaluation's merit
+    // stalls at its rounding level, where an Armijo comparison would only compare rounding noise)
+    bool small = false;
+    if (P.step_tol > 0.0 && mode == MODE_LS && nbt == 0) {
+        const double s2 = range_sum(ss, scratch, t, n, bar), x2 = range_sum(xx, scratch, t, n, bar);
+        small = s2 <= P.step_tol * P.step_tol * x2 && x2 > 0.0;
+    }
     if (mode == MODE_INIT0) {
         if (t == 0) ist[I_NEVALS] += 1;
         return DEC_INIT0;
     }
     bool accept = true, lsfail = false;
-    if (mode == MODE_LS && !(phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0) && !at_floor) {
+    if (mode == MODE_LS && !(phi2 <= (1.0 - 2.0 * P.c1 * alpha) * phi0 * phi0) && !small) {
         if (nbt < P.max_bt) accept = false;
         else lsfail = true;
     }
@@ -1584,7 +1571,7 @@ __device__ __forceinline__ int kkt_decide(const ProbDev& P, int b, const double*
     int status = ST_RUNNING;
     if (!isfinite(phi)) status = DDNM_NONFINITE;
     else if (phi < P.tol) status = DDNM_CONVERGED;
-    else if (at_floor) status = DDNM_CONVERGED;
+    else if (small) status = DDNM_CONVERGED;
     else if (iters >= P.max_iter) status = DDNM_MAX_ITER;
     if (copy_x || status != ST_RUNNING) {
         double* x = P.x + (size_t)b * nD;
@@ -1598,7 +1585,7 @@ __device__ __forceinline__ int kkt_decide(const ProbDev& P, int b, const double*
         dst[D_PHI] = phi;
         if (mode == MODE_LS) dst[D_ALPHA_LAST] = alpha;
         if (lsfail) ist[I_FLAGS] |= DDNM_FLAG_LS_FAIL;
-        if (at_floor && !(phi < P.tol)) ist[I_FLAGS] |= DDNM_FLAG_FLOOR;
+        if (small && !(phi < P.tol)) ist[I_FLAGS] |= DDNM_FLAG_STEP;
         if (status != ST_RUNNING) ist[I_STATUS] = status;
     }
     return status == ST_RUNNING ? DEC_STEP : DEC_DONE;
@@ -2473,7 +2460,7 @@ int solve_graph(ddnm_ctx* ctx, const ProbDev& P, int B, int Bw, bool ws, bool ha
     };
     const ddnm_options& o = ctx->opt;
     const std::vector<long long> key{ctx->gen, B, Bw, ws, has_x0, has_lam0, (long long)sizeof(T), max_passes,
-                                     bits(o.tol), bits(o.armijo_c1), bits(o.beta), o.max_iter, o.max_backtracks, P.floor_stop,
+                                     bits(o.tol), bits(o.armijo_c1), bits(o.beta), o.max_iter, o.max_backtracks, bits(P.step_tol),
                                      ctx->tune.chains, ctx->tune.con_split, ctx->tune.eval_persist, ctx->n_sm,
                                      P.d_gemm, ctx->tune.eval_groups, P.atil_df};
     if (!ctx->gexec || key != ctx->gkey) {
@@ -2529,7 +2516,7 @@ extern "C" int ddnm_solve_batch(ddnm_ctx* ctx, int B, const double* mu, const do
     P.beta = ctx->opt.beta;
     P.max_iter = ctx->opt.max_iter;
     P.max_bt = ctx->opt.max_backtracks;
-    P.floor_stop = fp64 ? 0 : ctx->opt.floor_stop;
+    P.step_tol = fp64 ? 0.0 : ctx->opt.step_tol;
     P.con_split = ctx->tune.con_split;
     P.n_split = (P.N_A + P.con_split - 1) / P.con_split;
     P.d_gemm = resolved_dgemm(ctx);
