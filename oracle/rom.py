@@ -82,9 +82,11 @@ class DDROM:
     hr: per subdomain local residual-row ids (None = all rows, i.e. B_i = I);
     C: n_C x N_A test matrix;
     hr_proj: per subdomain (Z_i Phi_i^r)^+ (n_r x N_B, columns in the order of hr[i]) for gappy-POD HR,
-    or None (collocation)."""
+    or None (collocation);
+    Ahat: per subdomain A^_i (n_A x n_i^G) for the SRPC formulation (Sec. 3.2, Eq. dd_lspg_NLP_rom_port:
+    linear constraints sum_i A^_i xh_i^G = 0, D_i = A^_i; see ``oracle.srpc``), or None (WFPC with C)."""
 
-    def __init__(self, fom: Burgers, dd: Decomposition, decoders_O, decoders_G, hr, C, hr_proj=None):
+    def __init__(self, fom: Burgers, dd: Decomposition, decoders_O, decoders_G, hr, C, hr_proj=None, Ahat=None):
         self.fom, self.dd = fom, dd
         self.dO, self.dG = list(decoders_O), list(decoders_G)
         self.C = np.asarray(C, dtype=np.float64).reshape(-1, dd.N_A) if dd.N_A else np.zeros((0, 0))
@@ -92,6 +94,9 @@ class DDROM:
         # C A_i (n_C x N_i^G) through the sparse A_i
         self.CA = [np.asarray((A.T @ self.C.T).T) for A in dd.A] if dd.N_A else \
             [np.zeros((0, sd.interface.size)) for sd in dd.subs]
+        self.Ahat = None if Ahat is None else [np.asarray(a, dtype=np.float64) for a in Ahat]
+        if self.Ahat is not None:
+            self.n_C = self.Ahat[0].shape[0]
         self.proj = [None] * len(dd.subs) if hr_proj is None else \
             [None if p is None else np.asarray(p, dtype=np.float64) for p in hr_proj]
         self.rows = []
@@ -144,7 +149,7 @@ class DDROM:
             x[sd.interior[need]] = 0.0
             x[sd.interface] = 0.0
             R = np.hstack([J[:, sd.interior[need]] @ JO, J[:, sd.interface] @ JG])
-            D = self.CA[i] @ JG
+            D = self.CA[i] @ JG if self.Ahat is None else self.Ahat[i]
             Pg = self.proj[i]
             Rb, rb = (R, r) if Pg is None else (Pg @ R, Pg @ r)      # B_i applied (gappy POD) or Z_i alone
             grad = Rb.T @ rb
@@ -152,7 +157,7 @@ class DDROM:
             rho[self.nO[i]:] += D.T @ lam
             ev.r.append(r); ev.R.append(R); ev.H.append(Rb.T @ Rb); ev.grad.append(grad)
             ev.D.append(D); ev.rho.append(rho); ev.gO.append(gO); ev.gG.append(gG)
-            ev.Atil = ev.Atil + self.CA[i] @ gG
+            ev.Atil = ev.Atil + (self.CA[i] @ gG if self.Ahat is None else self.Ahat[i] @ xg)
         ev.F = np.concatenate(ev.rho + [ev.Atil])
         ev.phi = float(np.linalg.norm(ev.F))
         return ev
@@ -174,7 +179,7 @@ class DDROM:
             r = fom.residual(x, mu, bvec)[rows]
             J = fom.jacobian(x, mu, bvec)[rows]
             R = np.hstack([J[:, sd.interior] @ JO, J[:, sd.interface] @ JG])
-            D = self.CA[i] @ JG
+            D = self.CA[i] @ JG if self.Ahat is None else self.Ahat[i]
             Pg = self.proj[i]
             Rb, rb = (R, r) if Pg is None else (Pg @ R, Pg @ r)      # B_i applied (gappy POD) or Z_i alone
             grad = Rb.T @ rb
@@ -182,7 +187,7 @@ class DDROM:
             rho[self.nO[i]:] += D.T @ lam
             ev.r.append(r); ev.R.append(R); ev.H.append(Rb.T @ Rb); ev.grad.append(grad)
             ev.D.append(D); ev.rho.append(rho); ev.gO.append(gO); ev.gG.append(gG)
-            ev.Atil = ev.Atil + self.CA[i] @ gG
+            ev.Atil = ev.Atil + (self.CA[i] @ gG if self.Ahat is None else self.Ahat[i] @ xg)
         ev.F = np.concatenate(ev.rho + [ev.Atil])
         ev.phi = float(np.linalg.norm(ev.F))
         return ev
