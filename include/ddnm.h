@@ -93,7 +93,7 @@ typedef struct ddnm_problem {
     const int* xb;          /* kx+1 node breakpoints, 0 .. nx */
     const int* yb;          /* ky+1 node breakpoints, 0 .. ny */
     const int* n_omega;     /* kx*ky interior latent dims n_i^O (1..16) */
-    const int* n_gamma;     /* kx*ky interface latent dims n_i^G (1..8, n_i^O + n_i^G <= 16) */
+    const int* n_gamma;     /* kx*ky interface latent dims n_i^G (1..11, n_i^O + n_i^G <= 16) */
     const int* hr_count;    /* kx*ky collocation row counts N_i^B (>= n_i^O + n_i^G) */
     const int* hr_rows;     /* sum(hr_count) local residual-row ids, sorted ascending per subdomain */
     int n_c;                /* rows of the test matrix C (weak constraints), 1..128 */
@@ -246,6 +246,32 @@ int ddnm_set_hr_projection(ddnm_ctx* ctx, int sub, int nr, const double* proj);
  * Host computation (no device); 1 <= nr[i] <= min(64, n_snap), nr[i] <= n_samples[i] <= N_i^r. */
 int ddnm_hr_select(ddnm_ctx* ctx, int n_snap, const double* snaps, const int* nr, const int* n_samples, int* rows_out,
                    double* proj_out);
+
+/* ---- SRPC formulation (Sec. 3.2, Eq. dd_lspg_NLP_rom_port; Sec. 5.2, Eq. interface_decoder_rom_port_blocks) ----
+ * Ports: the interface variables grouped by the set P(j) of subdomains sharing them, in ascending
+ * lexicographic order of P(j), each port's variables in ascending global order.  Port j has a decoder g_j^p
+ * with n_j^p = max(min(N_j^p - 1, n~), 1) latents (Sec. 7.5); subdomain i's interface latents are its ports'
+ * latents stacked in port order, so n_i^G = sum over its ports of n_j^p, and its interface decoder is the
+ * block-diagonal assembly of its ports' decoders.  The constraints become linear, sum_i A^_i x^_i^G = 0: for
+ * every port, latent component c and consecutive pair s_k < s_{k+1} of P(j), the row x^_{s_k}[c] -
+ * x^_{s_{k+1}}[c] (rows by port, then component, then pair); n_A rows in all.  The SQP then has D_i = A^_i and
+ * Atil = sum_i A^_i x^_i^G (no test matrix).
+ *
+ * ddnm_get_ports: the ports of ctx's decomposition under n~ (host bookkeeping, on any context of the same
+ * grid and partition): n_ports; when cap >= n_ports, per port its subdomains (port_subs, 4 per port, -1
+ * padded), N_j^p and n_j^p; n_gamma[n_sub] the interface latent sizes to pass to ddnm_setup, whose n_c must
+ * be n_A = sum_j (|P(j)| - 1) n_j^p. */
+int ddnm_get_ports(const ddnm_ctx* ctx, int n_tilde, int cap, int* n_ports, int* port_subs, int* port_N, int* port_n,
+                   int* n_gamma);
+/* Switch ctx to SRPC under n~: checks n_gamma and n_c against the ports, builds A^_i; every interface decoder is
+ * then assembled from port decoders (ddnm_load_port_decoder) and ddnm_set_test_matrix is not needed.
+ * DDNM_E_INVALID on a size mismatch (the message gives the expected sizes). */
+int ddnm_set_srpc(ddnm_ctx* ctx, int n_tilde);
+/* Port decoder g_j^p (N = N_j^p outputs in the port's variable order, n = n_j^p), copied; once all ports of a
+ * subdomain are loaded its interface decoder is assembled and loaded. */
+int ddnm_load_port_decoder(ddnm_ctx* ctx, int port, const ddnm_decoder* d);
+/* A^_i of subdomain `sub` (n_C x n_i^G row-major) of an SRPC context. */
+int ddnm_get_port_matrix(const ddnm_ctx* ctx, int sub, double* out);
 
 /* Replace the SQP options. */
 int ddnm_set_options(ddnm_ctx* ctx, const ddnm_options* opt);

@@ -124,6 +124,10 @@ _sig = {
     "ddnm_fom_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, C.c_int, _vp]),
     "ddnm_set_hr_projection": (C.c_int, [_vp, C.c_int, C.c_int, _vp]),
     "ddnm_hr_select": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "ddnm_get_ports": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "ddnm_set_srpc": (C.c_int, [_vp, C.c_int]),
+    "ddnm_load_port_decoder": (C.c_int, [_vp, C.c_int, C.POINTER(ddnm_decoder)]),
+    "ddnm_get_port_matrix": (C.c_int, [_vp, C.c_int, _vp]),
     "ddnm_timing_enable": (C.c_int, [_vp, C.c_int]),
     "ddnm_get_timing": (C.c_int, [_vp, C.POINTER(ddnm_timing)]),
     "ddnm_get_work": (C.c_int, [_vp, C.POINTER(ddnm_work)]),
@@ -404,6 +408,41 @@ def ddnm_hr_select(ctx, snaps, nr, n_samples):
     return out_r, out_p
 
 
+def ddnm_get_ports(ctx, n_tilde):
+    """Ports under n~: (list of (subdomains, N_j^p, n_j^p), n_gamma per subdomain)."""
+    n = C.c_int()
+    n_sub = ddnm_get_sizes(ctx).n_sub
+    ng = np.zeros(n_sub, dtype=np.int32)
+    _check(ctx, _lib.ddnm_get_ports(ctx, int(n_tilde), 0, C.byref(n), None, None, None, ng.ctypes.data))
+    m = n.value
+    subs = np.zeros(4 * m, dtype=np.int32)
+    pN, pn = np.zeros(m, dtype=np.int32), np.zeros(m, dtype=np.int32)
+    _check(ctx, _lib.ddnm_get_ports(ctx, int(n_tilde), m, C.byref(n), subs.ctypes.data, pN.ctypes.data,
+                                    pn.ctypes.data, ng.ctypes.data))
+    return [(tuple(int(v) for v in subs[4 * j:4 * j + 4] if v >= 0), int(pN[j]), int(pn[j])) for j in range(m)], ng
+
+
+def ddnm_set_srpc(ctx, n_tilde):
+    _check(ctx, _lib.ddnm_set_srpc(ctx, int(n_tilde)))
+
+
+def ddnm_load_port_decoder(ctx, port, spec: dict):
+    """spec: a decoder dict (N = N_j^p rows in the port's variable order, n = n_j^p)."""
+    W1, b1 = _f64(spec["W1"]), _f64(spec["b1"])
+    cols, vals = _i32(spec["cols"]), _f64(spec["vals"])
+    sc, off = _f64(spec["scale"]), _f64(spec["offset"])
+    d = ddnm_decoder(spec["N"], spec["w"], spec["n"], DDNM_ACT[spec.get("act", "swish")], cols.shape[1],
+                     W1.ctypes.data_as(_dp), b1.ctypes.data_as(_dp), cols.ctypes.data_as(_ip),
+                     vals.ctypes.data_as(_dp), sc.ctypes.data_as(_dp), off.ctypes.data_as(_dp))
+    _check(ctx, _lib.ddnm_load_port_decoder(ctx, int(port), C.byref(d)))
+
+
+def ddnm_get_port_matrix(ctx, sub, n_gamma):
+    out = np.zeros((ddnm_get_sizes(ctx).n_C, int(n_gamma)))
+    _check(ctx, _lib.ddnm_get_port_matrix(ctx, int(sub), out.ctypes.data))
+    return out
+
+
 def mlp_param_count(n_in, H, n_out):
     return H * n_in + H + H * H + H + n_out * H + n_out
 
@@ -512,7 +551,9 @@ def ddnm_autotune(ctx, mu, max_iter=0, reps=3, stream=None):
 class Solver:
     """One library context for a workload (``inputs.Workload``-like object)."""
 
-    def __init__(self, wl, precision=None, device=0):
+    def __init__(self, wl, precision=None, device=0, n_gamma=None, n_c=None):
+        """n_gamma / n_c override the workload's interface latent sizes and constraint count (the SRPC
+        formulation takes them from the ports: ddnm_get_ports)."""
         prec = precision if precision is not None else (DDNM_MIXED if wl.mixed else DDNM_FP64)
         self.wl = wl
         hr = getattr(wl, "hr_override", None)
@@ -520,8 +561,9 @@ class Solver:
             import inputs   # seeded generator (not method code)
             hr = inputs.hr_sets(wl)
         self.hr = hr
-        self.ctx = ddnm_setup(wl.nx, wl.ny, wl.xb, wl.yb, wl.n_omega, wl.n_gamma, [len(h) for h in hr],
-                              np.concatenate(hr), wl.n_c(), prec, wl.nu, device=device)
+        self.ctx = ddnm_setup(wl.nx, wl.ny, wl.xb, wl.yb, wl.n_omega, wl.n_gamma if n_gamma is None else n_gamma,
+                              [len(h) for h in hr], np.concatenate(hr), wl.n_c() if n_c is None else n_c, prec,
+                              wl.nu, device=device)
         self.sizes = ddnm_get_sizes(self.ctx)
         self.subs = [ddnm_get_subdomain(self.ctx, i) for i in range(self.sizes.n_sub)]
 
@@ -541,6 +583,14 @@ class Solver:
             ddnm_load_decoders(self.ctx, i, DDNM_DECODER_INTERIOR, a)
             ddnm_load_decoders(self.ctx, i, DDNM_DECODER_INTERFACE, b)
         ddnm_set_test_matrix(self.ctx, Cmat)
+
+    def load_srpc(self, n_tilde, dec_o, port_decs):
+        """SRPC formulation: interior decoders per subdomain and one decoder per port (ddnm_get_ports order)."""
+        ddnm_set_srpc(self.ctx, n_tilde)
+        for i, a in enumerate(dec_o):
+            ddnm_load_decoders(self.ctx, i, DDNM_DECODER_INTERIOR, a)
+        for j, d in enumerate(port_decs):
+            ddnm_load_port_decoder(self.ctx, j, d)
 
     def options(self, **kw):
         ddnm_set_options(self.ctx, **kw)

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddnm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ddnm_host.cpp", "ddnm_kernels.cu", "ddnm_mlp.cu", "ddnm_fom.cu", "ddnm_ae.cu", "ddnm_tc.cu", "ddnm_hr.cpp"]
+SOURCES = ["ddnm_host.cpp", "ddnm_kernels.cu", "ddnm_mlp.cu", "ddnm_fom.cu", "ddnm_ae.cu", "ddnm_tc.cu", "ddnm_hr.cpp", "ddnm_srpc.cpp"]
 
 
 def nvcc() -> str:

@@ -16,6 +16,12 @@ struct DecoderHost {
     std::vector<int> cols;
 };
 
+// one port of the SRPC formulation: the sorted subdomains P(j) sharing it, its variables (ascending global ids)
+struct PortHost {
+    std::vector<int> subs, vars;
+    int N = 0, n = 0;            // variables, latents n_j^p
+};
+
 struct SubHost {
     std::vector<int> owned;      // owned node ids, ascending
     std::vector<int> interior;   // global variable ids, ascending
@@ -72,6 +78,11 @@ struct ddnm_ctx {
     std::vector<double> C;
     bool have_C = false;
     std::vector<DecoderHost> decO, decG;
+    // SRPC formulation (ddnm_srpc.cpp): ports, their decoders, A^_i (n_C x n_i^G each)
+    bool srpc = false;
+    std::vector<PortHost> ports;
+    std::vector<DecoderHost> port_dec;
+    std::vector<std::vector<double>> Ahat;
     int n_D = 0, sum_NG = 0, sum_NB = 0;
 
     // device side (valid once finalized)
@@ -89,6 +100,7 @@ struct ddnm_ctx {
     float* d_Ct = nullptr;             // mixed path: C transposed, split into FP32 hi and lo parts (2 N_A ldct)
     float* d_Qtc = nullptr;            // mixed path: Q_i split into TF32 hi / lo, tiled for k_dgemm_tc
     int* d_err = nullptr;              // device error word (ddnm::DDNM_TC_TIMEOUT)
+    double* d_Ahat = nullptr;          // SRPC: every A^_i, n_C x n_i^G, at SubDev::ahat
     int* d_bnd_ij = nullptr;
     ddnm::SubDev* d_sub = nullptr;
     ddnm::ChunkDev* d_chunk = nullptr;

@@ -140,7 +140,7 @@ extern "C" int ddnm_setup(const ddnm_problem* p, ddnm_ctx** out) {
         sd.nO = p->n_omega[s];
         sd.nG = p->n_gamma[s];
         if (sd.nO < 1 || sd.nG < 0 || sd.nO + sd.nG > MAX_NI || sd.nG > MAX_NG)
-            return bail(DDNM_E_UNSUPPORTED, "latent dims must satisfy 1 <= n^O, n^G <= 8, n^O + n^G <= 16");
+            return bail(DDNM_E_UNSUPPORTED, "latent dims must satisfy 1 <= n^O, n^G <= 11, n^O + n^G <= 16");
         if (ns > 1 && sd.nG < 1) return bail(DDNM_E_INVALID, "n^G must be >= 1 with more than one subdomain");
     }
     // compatibility rows
@@ -245,6 +245,7 @@ extern "C" void ddnm_destroy(ddnm_ctx* ctx) {
     cudaFree(ctx->d_C);
     cudaFree(ctx->d_Ct);
     cudaFree(ctx->d_Qtc);
+    cudaFree(ctx->d_Ahat);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_bnd_ij);
     cudaFree(ctx->d_sub);
@@ -416,6 +417,17 @@ void subnet_hidden(const DecoderHost& d, const std::vector<int>& Io, Pools& P, l
     b1 = P.addv(b1s.data(), b1s.size());
 }
 
+// d's row-major ELL W2 widened to K slots a row (the extra slots column -1, value 0)
+void pad_ell(const DecoderHost& d, int K, std::vector<int>& cols, std::vector<double>& vals) {
+    cols.assign((size_t)d.N * K, -1);
+    vals.assign((size_t)d.N * K, 0.0);
+    for (int r = 0; r < d.N; ++r)
+        for (int t = 0; t < d.K; ++t) {
+            cols[(size_t)r * K + t] = d.cols[(size_t)r * d.K + t];
+            vals[(size_t)r * K + t] = d.vals[(size_t)r * d.K + t];
+        }
+}
+
 // Output rows `rows` of the subnet W2~ (Eq. subnet) in slot-major ELL (Kp slots; padding column 0 value 0),
 // columns renumbered into I_h, followed by their scale and offset.
 void subnet_rows(const DecoderHost& d, const std::vector<int>& rows, const std::vector<int>& pos, int Kp, Pools& P,
@@ -555,6 +567,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     int xoff = 0, hr_off = 0, blk = (3 * ctx->n_sub + 1) & ~1;
     long long pg_stride = 0;
     std::vector<float> qtc;        // mixed path: every Q_i split and tiled for the tensor-core D_i GEMM
+    std::vector<double> ahat_all;  // SRPC: every A^_i
     ctx->max_nG = 1;
     const size_t tsize = ctx->precision == DDNM_FP64 ? 8 : 4;
     ctx->eval_smem = 0;
@@ -613,13 +626,18 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     for (int s = 0; s < ns; ++s) {
         const SubHost& sd = ctx->subs[s];
         const DecoderHost &dO = ctx->decO[s], &dG = ctx->decG[s];
-        if (dO.K != dG.K) return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "interior and interface decoders must share K");
         SubDev& S = ctx->hsub[s];
         S.nO = sd.nO; S.nG = sd.nG; S.ni = sd.nO + sd.nG; S.xoff = xoff; xoff += S.ni;
         S.NB = (int)sd.hr_rows.size(); S.hr_off = hr_off; hr_off += S.NB;
         S.nr = sd.nr;
+        S.ahat = 0;
+        if (ctx->srpc) {
+            S.ahat = (long long)ahat_all.size();
+            ahat_all.insert(ahat_all.end(), ctx->Ahat[s].begin(), ctx->Ahat[s].end());
+        }
         S.gp = sd.nr ? P.addv(sd.proj.data(), sd.proj.size()) : 0;
-        S.K = dO.K; S.Kp = (dO.K + 7) & ~7; S.actO = dO.act; S.actG = dG.act;
+        // one ELL row length per subdomain (the shorter decoder's rows padded with -1 slots)
+        S.K = std::max(dO.K, dG.K); S.Kp = (S.K + 7) & ~7; S.actO = dO.act; S.actG = dG.act;
         S.goff = ctx->goff[s];
         S.NG = (int)sd.interface.size();
         // interior subnet over I_o = all outputs the stencils need; one slot-major table per HR chunk
@@ -691,16 +709,20 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         so.insert(so.end(), dO.offset.begin(), dO.offset.end());
         S.fw1O = P.addv(dO.W1.data(), dO.W1.size());
         S.fb1O = P.addv(dO.b1.data(), dO.b1.size());
-        S.fw2O = P.addv(dO.vals.data(), dO.vals.size());
+        std::vector<int> pcol;
+        std::vector<double> pval;
+        pad_ell(dO, S.K, pcol, pval);
+        S.fw2O = P.addv(pval.data(), pval.size());
         S.foutO = P.addv(so.data(), so.size());
-        S.fcolO = P.addi(dO.cols.data(), dO.cols.size());
+        S.fcolO = P.addi(pcol.data(), pcol.size());
         std::vector<double> sg(dG.scale);
         sg.insert(sg.end(), dG.offset.begin(), dG.offset.end());
         S.fw1G = P.addv(dG.W1.data(), dG.W1.size());
         S.fb1G = P.addv(dG.b1.data(), dG.b1.size());
-        S.fw2G = P.addv(dG.vals.data(), dG.vals.size());
+        pad_ell(dG, S.K, pcol, pval);
+        S.fw2G = P.addv(pval.data(), pval.size());
         S.foutG = P.addv(sg.data(), sg.size());
-        S.fcolG = P.addi(dG.cols.data(), dG.cols.size());
+        S.fcolG = P.addi(pcol.data(), pcol.size());
         std::vector<int> own, ids;
         for (int v : sd.interior) { own.push_back(std::binary_search(sd.owned.begin(), sd.owned.end(), v % ctx->N) ? 1 : 0); ids.push_back(v); }
         for (int v : sd.interface) { own.push_back(std::binary_search(sd.owned.begin(), sd.owned.end(), v % ctx->N) ? 1 : 0); ids.push_back(v); }
@@ -799,6 +821,12 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     CK(cudaMemcpy(ctx->d_con, con.data(), con.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_C, std::max<size_t>(ctx->C.size(), 1) * 8));
     CK(cudaMemcpy(ctx->d_C, ctx->C.data(), ctx->C.size() * 8, cudaMemcpyHostToDevice));
+    cudaFree(ctx->d_Ahat);
+    ctx->d_Ahat = nullptr;
+    if (!ahat_all.empty()) {
+        CK(cudaMalloc(&ctx->d_Ahat, ahat_all.size() * 8));
+        CK(cudaMemcpy(ctx->d_Ahat, ahat_all.data(), ahat_all.size() * 8, cudaMemcpyHostToDevice));
+    }
     cudaFree(ctx->d_Qtc);
     ctx->d_Qtc = nullptr;
     if (!qtc.empty()) {
@@ -892,6 +920,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     pd.Ctlo = ctx->d_Ct ? ctx->d_Ct + (size_t)ctx->N_A * ldct : nullptr;
     pd.atil_df = 0;
     pd.Qtc = ctx->d_Qtc;
+    pd.srpc = ctx->srpc ? 1 : 0;
+    pd.Ahat = ctx->d_Ahat;
     pd.err = ctx->d_err;
     pd.pg_stride = std::max(pg_stride, 1LL);
     pd.sub = ctx->d_sub; pd.chunk = ctx->d_chunk; pd.tiles = ctx->d_tiles; pd.vpool = ctx->d_vpool; pd.ipool = ctx->d_ipool;

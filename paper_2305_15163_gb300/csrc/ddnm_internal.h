@@ -9,7 +9,8 @@ namespace ddnm {
 
 constexpr int MAX_NI = 16;     // n_i^O + n_i^G per subdomain
 constexpr int MAX_TRI = MAX_NI * (MAX_NI - 1) / 2;   // entries of the largest trailing triangle of an H_i
-constexpr int MAX_NG = 8;      // n_i^G
+constexpr int MAX_NG = 11;     // n_i^G (round4(n_i^G + 1) <= 12: the interface width classes of the evaluation)
+constexpr int NG_SMALL = 8;    // the factorisation variant register-sized for n_i^G <= 8
 constexpr int MAX_K = 64;      // ELL slots of a decoder output row
 constexpr int MAX_NC = 128;    // weak constraints
 constexpr int MAX_SUB = 256;   // subdomains
@@ -108,6 +109,7 @@ struct SubDev {
     long long Qt;                  // value pool: Q_i^T = (C A_i diag(scale) W2~)^T, h_G x n_C
     int nr, pad_nr;                // gappy-POD HR: rows of (Z_i Phi_i^r)^+ (0: collocation, B_i = Z_i)
     long long gp;                  // value pool: (Z_i Phi_i^r)^+, nr x N_B row-major
+    long long ahat;                // SRPC: offset of A^_i (n_C x n_i^G, FP64) in P.Ahat
     long long qtc;                 // mixed path: Q_i split into TF32 hi / lo in k_dgemm_tc's order (floats into
     int hGp, pad_tc;               // P.Qtc); h_G rounded up to the tensor-core K chunk
     long long pgoff;               // offset of this subdomain's P_G (h_G x n^G) in an instance's P_G area
@@ -177,6 +179,8 @@ struct ProbDev {
     int ldct;                      // row stride of Cthi / Ctlo: n_C rounded up to 32, 64 or a multiple of 128
     const float* Qtc;              // mixed path: every Q_i split and tiled for k_dgemm_tc (SubDev::qtc)
     int* err;                      // device error word (DDNM_TC_TIMEOUT: a bounded tensor-core wait ran out)
+    int srpc;                      // SRPC formulation: D_i = A^_i constant, Atil = sum_i A^_i xh_i^G
+    const double* Ahat;            // SRPC: the A^_i (SubDev::ahat)
     int atil_df;                   // 1: Atil by k_atil_df (instance tiles, double-float); 0: FP64 slices
     int qld;                       // row stride of every Q_i^T in the value pool: round4(n_C)
     const int* bnd_ij;             // n_bnd x 2 grid indices of the Dirichlet points the stencils touch

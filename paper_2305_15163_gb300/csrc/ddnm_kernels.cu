@@ -366,7 +366,7 @@ __device__ __forceinline__ void gsync(int bar) {
 // L D L^T factors of the accepted evaluation: s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda]) when H_i is PD,
 // s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G) with s_G from the step kernel when H_i is singular in its G
 // block.  Then xt_i = x_i + alpha s_i (Eq. sqp_update); alpha = 1 on a new step.
-template <int NT>
+template <int NT, int NGM>
 __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, int tid, int bar) {
     const int xm = P.ist[(size_t)b * INST_INTS + I_XTMODE];
     if (xm == XT_KEEP) return;
@@ -386,22 +386,22 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, 
             const double* y = P.slam + (size_t)b * nC;
             int nb;
             if (blk[BL.flag] == FLAG_PD) {
-                double part[MAX_NG];
+                double part[NGM];
 #pragma unroll
-                for (int k = 0; k < MAX_NG; ++k) part[k] = 0.0;
+                for (int k = 0; k < NGM; ++k) part[k] = 0.0;
                 for (int c = lane; c < nC; c += 32) {
                     const double yc = y[c];
 #pragma unroll
-                    for (int k = 0; k < MAX_NG; ++k)
+                    for (int k = 0; k < NGM; ++k)
                         if (k < nG) part[k] += Wi[k * nC + c] * yc;
                 }
 #pragma unroll
-                for (int k = 0; k < MAX_NG; ++k)
+                for (int k = 0; k < NGM; ++k)
                     if (k < nG) part[k] = warp_sum(part[k]);
                 if (lane < ni) {
                     double v = ti[lane];
 #pragma unroll
-                    for (int k = 0; k < MAX_NG; ++k)
+                    for (int k = 0; k < NGM; ++k)
                         if (k < nG && lane == nO + k) v += part[k];
                     z[lane] = v * ri[lane];
                 }
@@ -471,7 +471,7 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
     // latent coordinates and multipliers of the trial point
-    form_trial<NT>(P, S, b, dt, tid, bar);
+    form_trial<NT, RG - 1>(P, S, b, dt, tid, bar);      // n_i^G <= RG - 1
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
     gsync<NT>(bar);
 
@@ -564,7 +564,10 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         // records).  Either here, thread (group, c) summing the hidden units h = group, group + n_grp, ... for
         // row c (eight Q loads in flight) and the groups added in order afterwards, or batched over the
         // instances that share the decoder (k_dgemm), for which P_G is written out.
-        if (P.d_gemm) {
+        if (P.srpc) {                          // SRPC: D_i = A^_i, constant (Sec. 3.2)
+            for (int o = t_; o < nC * nG; o += n_) dD[o] = P.Ahat[S.ahat + o];
+            gsync<NT>(bar);
+        } else if (P.d_gemm) {
             T* pg = (T*)P.PG + (size_t)b * P.pg_stride + S.pgoff;
             for (int e = t_; e < S.hG * nG; e += n_) {
                 const int h = e / nG, k = e - h * nG;
@@ -958,6 +961,7 @@ __global__ void __launch_bounds__(DG_THREADS) k_dgemm(ProbDev P, int B, int TB) 
     }
 }
 
+template <int NGM>
 __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr);
 
 // Partial Atil over one slice of the constraint rows: jump_r = g_lo - g_hi (FP64, once per row), then
@@ -965,17 +969,33 @@ __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr);
 // are split over nrg CTAs (the same sums, more SMs, when the batch alone gives too few CTAs).  CTA (x, b):
 // x < n_split nrg takes slice x % n_split, row group x / n_split; the CTAs after them factor the
 // Gauss-Newton blocks of the evaluated point for the step kernel (factor_cta), side by side in one launch.
-template <typename T>
+template <typename T, int NGM>
 __global__ void __launch_bounds__(CON_THREADS) k_constraint(ProbDev P, int B, int nrg) {
     extern __shared__ double jump[];      // con_split doubles (or the factorisation scratch)
     const int b = blockIdx.y, xi = blockIdx.x, ncon = P.n_split * nrg;
     if (b >= B) return;
     if (P.ist[(size_t)b * INST_INTS + I_STATUS] != ST_RUNNING) return;
     if (xi >= ncon) {
-        factor_cta(P, b, xi - ncon, jump);
+        factor_cta<NGM>(P, b, xi - ncon, jump);
         return;
     }
     const int sp = xi % P.n_split, rg = xi / P.n_split;
+    if (P.srpc) {               // SRPC: Atil = sum_i A^_i xh_i^G (Sec. 3.2) into slice 0, the other slices zero
+        const int rpg0 = (P.n_C + nrg - 1) / nrg;
+        double* o0 = P.Atil + ((size_t)b * P.n_split + sp) * P.n_C;
+        for (int c = rg * rpg0 + threadIdx.x; c < min(P.n_C, (rg + 1) * rpg0); c += blockDim.x) {
+            double a = 0.0;
+            if (sp == 0)
+                for (int i = 0; i < P.n_sub; ++i) {
+                    const SubDev& S = P.sub[i];
+                    const double* Ai = P.Ahat + S.ahat + (size_t)c * S.nG;
+                    const double* xg = P.xt + (size_t)b * P.n_D + S.xoff + S.nO;
+                    for (int k = 0; k < S.nG; ++k) a += Ai[k] * xg[k];
+                }
+            o0[c] = a;
+        }
+        return;
+    }
     const int r0 = sp * P.con_split, nr = min(P.con_split, P.N_A - r0);
     const T* g = (const T*)P.gG + (size_t)b * P.sum_NG;
     for (int r = threadIdx.x; r < nr; r += blockDim.x)
@@ -1173,7 +1193,7 @@ int con_row_groups(const ddnm_ctx* ctx, const ProbDev& P, int B) {
 // exceeds P.piv_eps times the block's largest diagonal entry (below that it is the rounding remainder of a
 // direction the collocation rows miss, and the block takes the second Schur level).
 // Columns are taken two at a time where the lane groups allow (one reciprocal per pair), else one at a time.
-template <int LG>
+template <int LG, int NGM>
 __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, const unsigned char* s_nO,
                              const unsigned char* s_nG, int i_first, int ns, double* scr, int fs, unsigned char* fl,
                              const unsigned short* tri) {
@@ -1191,9 +1211,9 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
     double* G = ucol2 + ni;
     int nmax = 0;
     for (int q = 0; q < 32 / LG && i_first + q < ns; ++q) nmax = max(nmax, (int)s_nO[i_first + q] + s_nG[i_first + q]);
-    double dpre[2][MAX_NG];                     // D_i[c][:] for c = hl, hl + LG, loaded ahead of the pivots
+    double dpre[2][NGM];                        // D_i[c][:] for c = hl, hl + LG, loaded ahead of the pivots
 #pragma unroll
-    for (int q = 0; q < MAX_NG; ++q) dpre[0][q] = dpre[1][q] = 0.0;
+    for (int q = 0; q < NGM; ++q) dpre[0][q] = dpre[1][q] = 0.0;
     if (on) {
         for (int e = hl; e < ni * ni; e += LG) L[e] = bi[BL.H + e];
         for (int e = hl; e < ni; e += LG) t[e] = bi[BL.rho + e];
@@ -1201,7 +1221,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
         for (int u = 0; u < 2; ++u)
             if (hl + u * LG < nC) {
 #pragma unroll
-                for (int q = 0; q < MAX_NG; ++q)
+                for (int q = 0; q < NGM; ++q)
                     if (q < nG) dpre[u][q] = bi[BL.D + (hl + u * LG) * nG + q];
             }
     }
@@ -1326,10 +1346,10 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
             for (int e = hl; e < nG * nG; e += LG) bi[BL.G + e] = G[e];
         if (flag == 0) {
             for (int c = hl; c < nC; c += LG) {
-                double wv[MAX_NG];
+                double wv[NGM];
                 double uc = 0.0;
 #pragma unroll
-                for (int q = 0; q < MAX_NG; ++q) {
+                for (int q = 0; q < NGM; ++q) {
                     if (q < nG) {
                         double v = c == hl ? dpre[0][q] : (c == hl + LG ? dpre[1][q] : bi[BL.D + c * nG + q]);
 #pragma unroll
@@ -1358,6 +1378,7 @@ __device__ void factor_group(const ProbDev& P, double* blk, const int* s_blk, co
 // trial's factors are never read: a backtrack forms its trial point from s).  Then, when the staging fits
 // (P.Spart set), the CTA's share of the Schur sums of the KKT step.  scr: ctx->fac_smem bytes, i.e.
 // 8 fac_stride doubles, or (2 fac_rows + 8) n_C doubles with the shares.
+template <int NGM>
 __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
     constexpr int SPC = 2 * FAC_WARPS;                          // subdomains per CTA
     __shared__ int s_blk[SPC];
@@ -1399,7 +1420,7 @@ __device__ void factor_cta(const ProbDev& P, int b, int f, double* scr) {
     if (s_skip) return;
     double* blk = P.blk + (size_t)b * P.blk_stride;
     if (w < FAC_WARPS && 2 * w < nrel)
-        factor_group<16>(P, blk, s_blk, s_nO, s_nG, 2 * w, nrel, scr + (size_t)w * 2 * P.fac_stride, P.fac_stride,
+        factor_group<16, NGM>(P, blk, s_blk, s_nO, s_nG, 2 * w, nrel, scr + (size_t)w * 2 * P.fac_stride, P.fac_stride,
                          s_fl, tri);
     if (!P.Spart) return;          // the KKT step forms the Schur sums itself
     __syncthreads();               // the CTA's blocks factored: W_i, 1 / D_jj, u_i and the flags written
@@ -2126,7 +2147,9 @@ int set_smem_attrs(ddnm_ctx* ctx) {
         CK(cudaFuncSetAttribute(eval_kernel<T>(g.ro, g.rg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 std::max(g.smem, g.groups * g.stride)));
     CK(cudaFuncSetAttribute(k_kkt, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->kkt_smem));
-    CK(cudaFuncSetAttribute(k_constraint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncSetAttribute(k_constraint<T, NG_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            std::max(MAX_CON_SPLIT * 8, ctx->fac_smem)));
+    CK(cudaFuncSetAttribute(k_constraint<T, MAX_NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             std::max(MAX_CON_SPLIT * 8, ctx->fac_smem)));
     {
         constexpr int CPT = sizeof(T) == 8 ? 16 : 32;
@@ -2198,8 +2221,11 @@ int launch_eval(ddnm_ctx* ctx, const ProbDev& P, int B, cudaStream_t st, bool pe
         const size_t smem = std::max((size_t)P.con_split * 8, nfc ? (size_t)ctx->fac_smem : 0);
         if (smem > (size_t)std::max(MAX_CON_SPLIT * 8, ctx->fac_smem))     // beyond what set_smem_attrs allowed
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "constraint launch: shared memory above its limit");
-        if (P.n_split * nrg + nfc > 0)
-            k_constraint<T><<<dim3(P.n_split * nrg + nfc, B), CON_THREADS, smem, st>>>(P, B, nrg);
+        if (P.n_split * nrg + nfc > 0) {
+            // the factorisation's register arrays sized for the largest n_i^G
+            auto kern = ctx->max_nG <= NG_SMALL ? k_constraint<T, NG_SMALL> : k_constraint<T, MAX_NG>;
+            kern<<<dim3(P.n_split * nrg + nfc, B), CON_THREADS, smem, st>>>(P, B, nrg);
+        }
     }
     CK(cudaGetLastError());
     tstop(ctx, k, st);
@@ -2319,6 +2345,7 @@ void fold_pending(ddnm_ctx* ctx) {
 // the D_i form: 0 in the evaluation, 1 the batched FP32 GEMM, 2 the tensor-core GEMM (mixed path only; the
 // FP64 path and sizes it does not take fall back to 1)
 int resolved_dgemm(const ddnm_ctx* ctx) {
+    if (ctx->srpc) return 0;                    // SRPC: D_i is the constant A^_i
     int d = ctx->tune.d_gemm;
     if (d < 0) d = ctx->dgemm_auto && ddnm_dgemm_tc_ok(ctx) ? 2 : ctx->dgemm_auto;
     return d == 2 && !ddnm_dgemm_tc_ok(ctx) ? 1 : d;
@@ -2328,7 +2355,7 @@ int resolved_dgemm(const ddnm_ctx* ctx) {
 // sets the slices of the constraint rows that the Atil partials cover
 void resolve_atil(const ddnm_ctx* ctx, ProbDev& P) {
     const int want = ctx->tune.atil < 0 ? ctx->atil_auto : ctx->tune.atil;
-    P.atil_df = (ctx->precision == DDNM_MIXED && want == 1 && P.Cthi) ? 1 : 0;
+    P.atil_df = (ctx->precision == DDNM_MIXED && want == 1 && P.Cthi && !ctx->srpc) ? 1 : 0;
     if (P.atil_df) {
         P.con_split = ATIL_KS;
         P.n_split = (P.N_A + ATIL_KS - 1) / ATIL_KS;
@@ -2963,7 +2990,8 @@ int noalloc_eval(ddnm_ctx* ctx, ProbDev& P, int B, double* F_out, cudaStream_t s
     }
     {
         const int nrg = con_row_groups(ctx, P, B);
-        k_constraint<T><<<dim3(P.n_split * nrg, B), CON_THREADS, P.con_split * sizeof(double), st>>>(P, B, nrg);
+        k_constraint<T, NG_SMALL><<<dim3(P.n_split * nrg, B), CON_THREADS, P.con_split * sizeof(double), st>>>(
+            P, B, nrg);        // no factorisation CTAs here
     }
     k_gather<<<B, 128, 0, st>>>(P, B, F_out, nullptr, nullptr, nullptr);
     e = cudaGetLastError();

