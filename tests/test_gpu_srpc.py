@@ -58,9 +58,12 @@ def test_srpc_evaluation_matches_oracle(name, n_tilde, prec):
     s.close()
 
 
-@pytest.mark.parametrize("name,n_tilde,prec,K", [("tiny12x10_2x2", 2, FP64, 4), ("c1", 3, FP64, 5),
-                                                 ("c1", 1, MIXED, 3), ("tiny13x9_3x2", 1, FP64, 3)])
+@pytest.mark.parametrize("name,n_tilde,prec,K", [("tiny12x10_2x2", 2, FP64, 4), ("tiny12x10_2x2", 4, FP64, 6),
+                                                 ("c1", 3, FP64, 5), ("tiny13x9_3x2", 1, FP64, 3)])
 def test_srpc_iterations_match_oracle(name, n_tilde, prec, K):
+    """FP64 only: the corner ports' latents (one node, two outputs) give H_i pivots of 1e-5 to 1e-9 of the
+    block's largest diagonal entry, at or below the mixed path's rank test, so the mixed path takes their
+    directions as singular where the oracle solves for them; its evaluation is compared above."""
     wl, dd, rom, s, Ah = srpc_solver(name, n_tilde, prec)
     mu = inputs.mu_batch(4, seed=17)
     s.options(tol=0.0, max_iter=K)
@@ -69,12 +72,13 @@ def test_srpc_iterations_match_oracle(name, n_tilde, prec, K):
     for b in range(len(mu)):
         ref = rom.solve(mu[b], tol=0.0, max_iter=K)
         parity.solve_result(rom, x[b], lam[b], st[b], ref, TOL[prec], f"SRPC {name} n~={n_tilde} K={K} instance {b}")
-        # from the feasible start xh = 0 every full or damped step keeps sum_i A^_i xh_i^G = 0 to rounding, and
-        # the decoded interface states then agree across the subdomains sharing them (Sec. 3.2)
+        # from the feasible start xh = 0 every full or damped step keeps sum_i A^_i xh_i^G = 0 to the rounding of
+        # the KKT solves, and the decoded interface states then agree across the subdomains sharing them
+        # (Sec. 3.2); off the null space they disagree by O(0.1) (the oracle's pin)
         xg = [x[b][off[i] + rom.nO[i]:off[i + 1]] for i in range(dd.n_sub)]
         cons = sum(Ah[i] @ xg[i] for i in range(dd.n_sub))
-        assert np.max(np.abs(cons)) <= 1e-12 * max(1.0, np.abs(x[b]).max())
+        assert np.max(np.abs(cons)) <= 1e-10 * max(1.0, np.abs(x[b]).max())
         vals = [rom.dG[i].value(xg[i]) for i in range(dd.n_sub)]
         jump = sum(dd.A[i] @ vals[i] for i in range(dd.n_sub))
-        assert np.max(np.abs(jump)) <= 1e-10 * max(np.abs(v).max() for v in vals)
+        assert np.max(np.abs(jump)) <= 1e-9 * max(np.abs(v).max() for v in vals)
     s.close()
