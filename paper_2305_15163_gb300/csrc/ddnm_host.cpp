@@ -578,9 +578,12 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     int dev_max = 0, sm_smem = 0;
     CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-    // collocation rows per chunk, among 128, 64, ..., 8: the largest whose evaluation CTAs per SM (shared
-    // memory against the register budget) come within a factor 1.5 of the best candidate's, since every chunk
-    // adds barriers and a round of table loads; it must fit one CTA
+    // collocation rows per chunk, among 128, 64, ..., 8: one with the most evaluation CTAs per SM (shared
+    // memory against the register budget), preferring 32, then 64, 16, 128, 8.  Resident CTAs hide more of
+    // the evaluation's latency, and a smaller shared-memory share leaves more L1 for the decoder tables,
+    // while every chunk adds barriers and a round of table loads.  On the 1024^2 / 8 x 8 workload (mixed
+    // path, one 1024-instance launch): 32 rows at 3 CTAs per SM 12.1 ms, 16 rows at 3 CTAs 16.0 ms, 64 rows at
+    // 2 CTAs 12.8 ms, 128 rows at 2 CTAs 18.1 ms.  It must fit one CTA.
     int hc = 0, need_bytes = 0;
     {
         std::vector<int> hO(ns), hG(ns);
@@ -612,11 +615,9 @@ int ddnm_finalize(ddnm_ctx* ctx) {
         }
         int best = 0;
         for (const auto& c : cands) best = std::max(best, c.second);
-        for (const auto& c : cands)                 // largest first
-            if (2 * c.second * 3 >= 2 * best * 2) {  // ctas >= best / 1.5
-                hc = c.first;
-                break;
-            }
+        for (int pref : {32, 64, 16, 128, 8})
+            for (const auto& c : cands)
+                if (!hc && c.first == pref && c.second == best) hc = c.first;
         need_bytes = smallest;
         if (!hc)
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain's evaluation needs " + std::to_string(smallest) +

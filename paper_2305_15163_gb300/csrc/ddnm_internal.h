@@ -221,7 +221,7 @@ constexpr int CTL_INTS = MAX_CHAINS * (3 + MAX_CLASSES);
 
 // Shared-memory carve-out (bytes) of one subdomain evaluation; tsize = sizeof(value type).
 struct EvalSmem {
-    int Rt;
+    int Rt, hp, hpair;
     int sx, hidO, hidG, outGn, outO, Rr, red;  // value-type arrays
     int dH, drho, dt, dD;                      // double arrays
     int bytes;
@@ -234,13 +234,23 @@ __host__ __device__ inline EvalSmem eval_smem(const SubDev& s, int nC, int tsize
     const int rO = round4(s.nO + 1), rG = round4(s.nG + 1);
     int o = 0;
     e.sx = o; o = align16(o + MAX_NI * tsize);
-    e.hidO = o; o = align16(o + round4(s.hO) * rO * tsize);  // [sigma, sigma' W1 row] per hidden unit (+ zero rows)
-    e.hidG = o; o = align16(o + round4(s.hG) * rG * tsize);
+    // [sigma, sigma' W1 row] per hidden unit (+ zero rows): the interface records during the interface phase,
+    // then the interior records in the same place for the chunk loop
+    e.hidO = e.hidG = o;
+    const int recO = round4(s.hO) * rO, recG = round4(s.hG) * rG;
+    o = align16(o + (recO > recG ? recO : recG) * tsize);
     e.outGn = o; o = align16(o + s.NGn * rG * tsize);        // [y, Jacobian row] per interface output the stencils use
-    e.outO = o; o = align16(o + s.mmax * rO * tsize);        // [y, Jacobian row] per needed interior output (chunk)
-    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize); // [R row, r] per collocation row (chunk)
-    e.red = o; o = align16(o + (eval_threads(tsize, rO, rG) / nC) * nC * s.nG * tsize);   // D_i partials per thread group
+    // the chunk loop's [y, Jacobian row] per needed interior output and [R row, r] per collocation row; the
+    // D_i partials per thread group of the interface phase in the same place
+    const int o_chunk = o;
+    e.outO = o; o = align16(o + s.mmax * rO * tsize);
+    e.Rr = o; o = align16(o + s.hr_chunk * (s.ni + 1) * tsize);
+    e.red = o_chunk;
+    const int o_red = align16(o_chunk + (eval_threads(tsize, rO, rG) / nC) * nC * s.nG * tsize);
+    o = o > o_red ? o : o_red;
     e.Rt = o; o = align16(o + s.nr * (s.ni + 1) * tsize);  // gappy POD: (Z Phi)^+ [R, r] over the rows
+    e.hp = o; o = align16(o + (eval_threads(tsize, rO, rG) / 32) * (s.ni * (s.ni + 3) / 2) * tsize);  // H_i, R_i^T r partials per warp
+    e.hpair = o; o = align16(o + (s.ni * (s.ni + 3) / 2) * 4);    // (a, c) of each of those entries
     e.dH = o; o = align16(o + s.ni * s.ni * 8);
     e.drho = o; o = align16(o + s.ni * 8);
     e.dt = o; o = align16(o + s.ni * 8);

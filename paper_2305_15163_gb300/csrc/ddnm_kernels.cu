@@ -365,9 +365,10 @@ __device__ __forceinline__ void gsync(int bar) {
 // subdomain back-substitutes its own piece of the KKT solution of Eq. (sqp_system) from s_lambda, with the
 // L D L^T factors of the accepted evaluation: s_i = -L^{-T} D^{-1} (t_i + [0; W_i s_lambda]) when H_i is PD,
 // s_O = -L_OO^{-T} (D_O^{-1} t_O + L_GO^T s_G) with s_G from the step kernel when H_i is singular in its G
-// block.  Then xt_i = x_i + alpha s_i (Eq. sqp_update); alpha = 1 on a new step.
+// block.  Then xt_i = x_i + alpha s_i (Eq. sqp_update); alpha = 1 on a new step.  The whole group stages
+// L_i (n_i x n_i doubles) in shared memory (Ls) first, so the solve's warp reads no global memory in its loop.
 template <int NT, int NGM>
-__device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, int tid, int bar) {
+__device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, double* Ls, int tid, int bar) {
     const int xm = P.ist[(size_t)b * INST_INTS + I_XTMODE];
     if (xm == XT_KEEP) return;
     const int nC = P.n_C, ni = S.ni, nO = S.nO, nG = S.nG;
@@ -375,11 +376,17 @@ __device__ void form_trial(const ProbDev& P, const SubDev& S, int b, double* z, 
     double* xt = P.xt + (size_t)b * P.n_D + S.xoff;
     double* s = P.s + (size_t)b * P.n_D + S.xoff;
     if (xm == XT_NEWSTEP) {
+        {
+            const double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
+            const double* Lg = blk + blk_layout(ni, nG, nC).L;
+            for (int e = tid; e < ni * ni; e += NT) Ls[e] = Lg[e];
+        }
+        gsync<NT>(bar);
         if (tid < 32) {
             const int lane = tid;
             const double* blk = P.blk + (size_t)b * P.blk_stride + S.blk;
             const BlkLayout BL = blk_layout(ni, nG, nC);
-            const double* Li = blk + BL.L;
+            const double* Li = Ls;
             const double* ri = blk + BL.rinv;
             const double* ti = blk + BL.t;
             const double* Wi = blk + BL.W;
@@ -471,17 +478,16 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
     constexpr int WG = RG - 1 > 0 ? ((RG - 1 + 3) & ~3) : 4;
 
     // latent coordinates and multipliers of the trial point
-    form_trial<NT, RG - 1>(P, S, b, dt, tid, bar);      // n_i^G <= RG - 1
+    form_trial<NT, RG - 1>(P, S, b, dt, dH, tid, bar);  // n_i^G <= RG - 1; dH is free until the chunks end
     if (tid < ni) sx[tid] = (T)P.xt[(size_t)b * P.n_D + S.xoff + tid];
     gsync<NT>(bar);
 
-    // hidden layers of both subnets: rows [sigma(z), sigma'(z) W1[c, :], 0...]; the rows that pad each
-    // record array to a multiple of 4 are zero (dense-window tiles may span them with zero values)
-    for (int e = tid; e < (round4(S.hO) - S.hO) * RO; e += nth) hidO[(size_t)S.hO * RO + e] = T(0);
-    for (int e = tid; e < (round4(S.hG) - S.hG) * RG; e += nth) hidG[(size_t)S.hG * RG + e] = T(0);
-    for (int c = tid; c < S.hO + S.hG; c += nth) {
-        const bool g = c >= S.hO;
-        if (!g) {
+    // hidden layers: rows [sigma(z), sigma'(z) W1[c, :], 0...]; the rows that pad each record array to a
+    // multiple of 4 are zero (dense-window tiles may span them with zero values).  The interface subnet's
+    // records serve the interface phase; the interior subnet's then take their place for the chunk loop.
+    auto hidden_interior = [&]() {
+        for (int e = tid; e < (round4(S.hO) - S.hO) * RO; e += nth) hidO[(size_t)S.hO * RO + e] = T(0);
+        for (int c = tid; c < S.hO; c += nth) {
             const T* W1 = V + S.w1O + (size_t)c * round4(nO);
             T w[WO];
 #pragma unroll
@@ -500,27 +506,28 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             for (int k = 1; k < RO; ++k) row[k] = (k - 1 < WO) ? ds * w[k - 1] : T(0);
 #pragma unroll
             for (int k = 0; k < RO; k += 4) st4(hidO + (size_t)c * RO + k, row + k);
-        } else {
-            const int cc = c - S.hO;
-            const T* W1 = V + S.w1G + (size_t)cc * round4(nG);
-            T w[WG];
-#pragma unroll
-            for (int k = 0; k < WG; k += 4) {
-                if (k < round4(nG)) ld4(W1 + k, w + k);
-                else w[k] = w[k + 1] = w[k + 2] = w[k + 3] = T(0);
-            }
-            T z = V[S.b1G + cc];
-#pragma unroll
-            for (int k = 0; k < WG; ++k) z += w[k] * (k < nG ? sx[nO + k] : T(0));
-            T s, ds;
-            activation<T>(S.actG, z, s, ds);
-            T row[RG];
-            row[0] = s;
-#pragma unroll
-            for (int k = 1; k < RG; ++k) row[k] = (k - 1 < WG) ? ds * w[k - 1] : T(0);
-#pragma unroll
-            for (int k = 0; k < RG; k += 4) st4(hidG + (size_t)cc * RG + k, row + k);
         }
+    };
+    for (int e = tid; e < (round4(S.hG) - S.hG) * RG; e += nth) hidG[(size_t)S.hG * RG + e] = T(0);
+    for (int cc = tid; cc < S.hG; cc += nth) {
+        const T* W1 = V + S.w1G + (size_t)cc * round4(nG);
+        T w[WG];
+#pragma unroll
+        for (int k = 0; k < WG; k += 4) {
+            if (k < round4(nG)) ld4(W1 + k, w + k);
+            else w[k] = w[k + 1] = w[k + 2] = w[k + 3] = T(0);
+        }
+        T z = V[S.b1G + cc];
+#pragma unroll
+        for (int k = 0; k < WG; ++k) z += w[k] * (k < nG ? sx[nO + k] : T(0));
+        T s, ds;
+        activation<T>(S.actG, z, s, ds);
+        T row[RG];
+        row[0] = s;
+#pragma unroll
+        for (int k = 1; k < RG; ++k) row[k] = (k - 1 < WG) ? ds * w[k - 1] : T(0);
+#pragma unroll
+        for (int k = 0; k < RG; k += 4) st4(hidG + (size_t)cc * RG + k, row + k);
     }
     gsync<NT>(bar);
 
@@ -645,32 +652,55 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
         }
     }
     };
-    // H_i = R^T R and R^T r: thread p owns one entry (a <= c), running sum over the chunks
-    const int npair = ni * (ni + 1) / 2;
-    int pa = 0, pc = 0;
-    if (tid < npair) {
-        int rem = tid;
-        while (rem >= ni - pa) {
-            rem -= ni - pa;
-            ++pa;
+    // H_i = R^T R and R^T r.  Entry e < npair is the pair (a <= c) of H_i, entry npair + a is (R^T r)_a: the
+    // product of columns a and c of the [R, r] rows.  Warp w sums the chunk rows w, w + nwarp, ... for the
+    // entries lane, lane + 32, ... into its own running sums in shared memory (hp); after the chunks the
+    // warps' sums are added in warp order, thread e taking entry e (gappy HR: thread e forms entry e from the
+    // projected rows instead).
+    const int npair = ni * (ni + 1) / 2, nent = npair + ni;
+    auto entry_pair = [&](int e, int& a, int& c) {
+        a = 0;
+        c = 0;
+        if (e < npair) {
+            int rem = e;
+            while (rem >= ni - a) {
+                rem -= ni - a;
+                ++a;
+            }
+            c = a + rem;
+        } else if (e < nent) {
+            a = e - npair;
+            c = ni;
         }
-        pc = pa + rem;
-    } else if (tid < npair + ni) {
-        pa = tid - npair;
-        pc = ni;
+    };
+    int pa, pc;
+    entry_pair(tid, pa, pc);
+    T* hp = (T*)(smem + L.hp);
+    int* hpair = (int*)(smem + L.hpair);
+    for (int e = tid; e < nent; e += nth) {
+        int a, c;
+        entry_pair(e, a, c);
+        hpair[e] = a | c << 16;
     }
+    for (int e = tid; e < nwarp * nent; e += nth) hp[e] = T(0);   // read after the chunk's barriers
     T hacc = T(0);
     const int* hr = P.hr + (size_t)S.hr_off * HR_INTS;
     for (int e = tid; e < S.nr * ld; e += nth) Rt[e] = T(0);
     interface_phase(tid, nth, w, nwarp);
+    gsync<NT>(bar);                              // the interface records are no longer read
+    hidden_interior();
+    gsync<NT>(bar);
     for (int q = 0; q < S.n_chunks; ++q) {
         const ChunkDev Cq = P.chunk[S.chunk0 + q];
         interior_outputs(Cq, tid, nth, w, nwarp);
         gsync<NT>(bar);
-        // collocation rows of the chunk
+        // collocation rows of the chunk: tpr threads per row, thread `sub` of a row forming entries sub,
+        // sub + tpr, ... of its [R row, r] (each entry sums the row's operands in the same order whatever tpr)
         const T* bnd = (const T*)P.bnd + (size_t)b * P.n_bnd * 2;
         const T ax = cst<T>(P, 0), ay = cst<T>(P, 1), cx = cst<T>(P, 2), cy = cst<T>(P, 3);
-        for (int it = tid; it < Cq.nq; it += nth) {
+        const int tpr = S.hr_chunk < nth ? nth / S.hr_chunk : 1;
+        const int sub = tid % tpr;
+        for (int it = tid / tpr; it < Cq.nq; it += nth / tpr) {
             const int qq = Cq.q0 + it;
             const int comp = hr[qq];
             int code[6];
@@ -695,33 +725,25 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
             d[3] = -vp * ay + cy;
             d[4] = vp * ay + cy;
             d[5] = -(comp == 0 ? dyf * ay : dxf * ax);
-            T RO_[RO - 1 > 0 ? RO - 1 : 1], RG_[RG - 1 > 0 ? RG - 1 : 1];
-#pragma unroll
-            for (int k = 0; k < RO - 1; ++k) RO_[k] = T(0);
-#pragma unroll
-            for (int k = 0; k < RG - 1; ++k) RG_[k] = T(0);
-#pragma unroll
-            for (int o = 0; o < 6; ++o) {
-                const int kind = code[o] >> OP_SHIFT, idx = code[o] & OP_MASK;
-                if (kind == OP_INTERIOR) {
-                    const T* j = outO + (size_t)idx * RO + 1;
-#pragma unroll
-                    for (int k = 0; k < RO - 1; ++k) RO_[k] += d[o] * j[k];
-                } else if (kind == OP_INTERFACE) {
-                    const T* j = outGn + (size_t)idx * RG + 1;
-#pragma unroll
-                    for (int k = 0; k < RG - 1; ++k) RG_[k] += d[o] * j[k];
-                }
-            }
             T* row = Rr + (size_t)it * ld;
+            for (int k = sub; k <= ni; k += tpr) {
+                // interior latents take the interior operands' Jacobian rows, interface latents the interface
+                // operands'; entry n_i is the residual
+                if (k == ni) {
+                    row[k] = r;
+                    continue;
+                }
+                const bool inner = k < nO;
+                const int want = inner ? OP_INTERIOR : OP_INTERFACE;
+                const T* base = inner ? outO + 1 + k : outGn + 1 + (k - nO);
+                const int rs = inner ? RO : RG;
+                T v = T(0);
 #pragma unroll
-            for (int k = 0; k < RO - 1; ++k)
-                if (k < nO) row[k] = RO_[k];
-#pragma unroll
-            for (int k = 0; k < RG - 1; ++k)
-                if (k < nG) row[nO + k] = RG_[k];
-            row[ni] = r;
-            if (P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
+                for (int o = 0; o < 6; ++o)
+                    if ((code[o] >> OP_SHIFT) == want) v += d[o] * base[(size_t)(code[o] & OP_MASK) * rs];
+                row[k] = v;
+            }
+            if (sub == 0 && P.r_hr) P.r_hr[(size_t)b * P.sum_NB + S.hr_off + qq] = (double)r;
         }
         gsync<NT>(bar);
         if (S.nr) {
@@ -735,25 +757,33 @@ __device__ void eval_item(const ProbDev& P, const SubDev& S, int b, unsigned cha
                 for (int ql = 0; ql < Cq.nq; ++ql) acc += pr[ql] * Rr[(size_t)ql * ld + j];
                 Rt[e] += acc;
             }
-        } else if (tid < npair + ni) {
-            T h0 = T(0), h1 = T(0), h2 = T(0), h3 = T(0);
-            int ql = 0;
-            for (; ql + 3 < Cq.nq; ql += 4) {
-                h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
-                h1 += Rr[(size_t)(ql + 1) * ld + pa] * Rr[(size_t)(ql + 1) * ld + pc];
-                h2 += Rr[(size_t)(ql + 2) * ld + pa] * Rr[(size_t)(ql + 2) * ld + pc];
-                h3 += Rr[(size_t)(ql + 3) * ld + pa] * Rr[(size_t)(ql + 3) * ld + pc];
+        } else {
+            for (int e = lane; e < nent; e += 32) {
+                const int pk = hpair[e], a = pk & 0xFFFF, c = pk >> 16;
+                T h0 = T(0), h1 = T(0);
+                int ql = w;
+                for (; ql + nwarp < Cq.nq; ql += 2 * nwarp) {
+                    h0 += Rr[(size_t)ql * ld + a] * Rr[(size_t)ql * ld + c];
+                    h1 += Rr[(size_t)(ql + nwarp) * ld + a] * Rr[(size_t)(ql + nwarp) * ld + c];
+                }
+                if (ql < Cq.nq) h0 += Rr[(size_t)ql * ld + a] * Rr[(size_t)ql * ld + c];
+                hp[(size_t)w * nent + e] += h0 + h1;
             }
-            for (; ql < Cq.nq; ++ql) h0 += Rr[(size_t)ql * ld + pa] * Rr[(size_t)ql * ld + pc];
-            hacc += (h0 + h1) + (h2 + h3);
         }
         if (q + 1 < S.n_chunks) gsync<NT>(bar);   // outO / Rr reused by the next chunk
     }
     if (S.nr) {                                  // H_i and R_i^T r_i from the projected rows
         gsync<NT>(bar);
-        if (tid < npair + ni) {
+        if (tid < nent) {
             T h0 = T(0);
             for (int a = 0; a < S.nr; ++a) h0 += Rt[(size_t)a * ld + pa] * Rt[(size_t)a * ld + pc];
+            hacc = h0;
+        }
+    } else {                                     // the warps' sums, added in warp order
+        gsync<NT>(bar);
+        if (tid < nent) {
+            T h0 = T(0);
+            for (int v = 0; v < nwarp; ++v) h0 += hp[(size_t)v * nent + tid];
             hacc = h0;
         }
     }
