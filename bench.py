@@ -136,8 +136,9 @@ def measured_peaks():
 
 
 def traffic_profile(kernel: str, workload: str):
-    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, if it was taken on the
-    current kernel source (same SHA-256), else None."""
+    """DRAM bytes per instance-evaluation of `kernel` on `workload` from the committed ncu summary (a full
+    launch's dram__bytes_read.sum + dram__bytes_write.sum over the instances it evaluated), if it was taken on
+    the current kernel source (same SHA-256), else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     src = os.path.join(ROOT, "paper_2305_15163_gb300", "csrc", "ddnm_kernels.cu")
     try:
@@ -146,7 +147,7 @@ def traffic_profile(kernel: str, workload: str):
     except OSError:
         return None
     m_sha = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
-    m_b = re.search(r"dram bytes per launch: ([0-9]+)", text)
+    m_b = re.search(r"dram bytes per instance-evaluation: ([0-9]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
     return int(m_b.group(1))
@@ -697,10 +698,12 @@ def main():
             "kernel_ms_per_solve": {k: round(v / kb, 3) for k, v in kern.items()},
             "measured_peaks_tflops": {"fp32": f32_peak, "fp64": f64_peak},
             "timed_in": f"{kb} extra headline solves, host-driven loop, one CTA per item, CUDA events around every launch"}
-    prof = traffic_profile(dom, args.config)
+    prof = traffic_profile(dom, args.config) if dom == "k_eval" else None
     if prof is not None:
-        roof["traffic"] = prof
-        roof["traffic_source"] = f"profiles/{dom}_{args.config}.md (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+        # the captured launch's bytes per instance-evaluation times this run's instance-evaluations per launch
+        roof["traffic"] = prof * evals / max(tm["eval_launches"], 1)
+        roof["traffic_source"] = (f"profiles/{dom}_{args.config}.md (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                  "of a full launch, per instance-evaluation, times this run's per launch)")
 
     # ---- end to end through the public API with host (pinned) buffers, copies inside the timed region
     mu_h = torch.from_numpy(mu.copy()).pin_memory()

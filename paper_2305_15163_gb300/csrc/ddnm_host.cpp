@@ -578,12 +578,15 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     int dev_max = 0, sm_smem = 0;
     CK(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-    // collocation rows per chunk, among 128, 64, ..., 8: one with the most evaluation CTAs per SM (shared
-    // memory against the register budget), preferring 32, then 64, 16, 128, 8.  Resident CTAs hide more of
-    // the evaluation's latency, and a smaller shared-memory share leaves more L1 for the decoder tables,
-    // while every chunk adds barriers and a round of table loads.  On the 1024^2 / 8 x 8 workload (mixed
-    // path, one 1024-instance launch): 32 rows at 3 CTAs per SM 12.1 ms, 16 rows at 3 CTAs 16.0 ms, 64 rows at
-    // 2 CTAs 12.8 ms, 128 rows at 2 CTAs 18.1 ms.  It must fit one CTA.
+    // collocation rows per chunk, among 128, 64, ..., 8: among the candidates with the most evaluation CTAs
+    // per SM (shared memory against the register budget), the largest whose CTAs leave the SM at least
+    // L1_KEEP bytes of its unified L1 / shared memory for caching the decoder tables, else the largest.
+    // Resident CTAs hide the evaluation's latency and every chunk adds barriers and a round of table loads,
+    // but the tables are re-read per instance.  Measured (k_eval, one 1024-instance launch): 1024^2 / 8 x 8
+    // mixed, 32 rows at 3 CTAs per SM 12.1 ms, 16 rows at 3 CTAs 16.0 ms, 64 rows at 2 CTAs 12.8 ms, 128 rows
+    // at 2 CTAs (208 kB of shared memory per SM) 18.1 ms; the same in FP64 at one CTA per SM, 32 rows
+    // 161 ms, 128 rows (about 200 kB) 252 ms; 128 x 128 / 4 x 4 mixed at 4 CTAs, 128 rows 0.83 ms, 32 rows
+    // 1.16 ms.  It must fit one CTA.
     int hc = 0, need_bytes = 0;
     {
         std::vector<int> hO(ns), hG(ns);
@@ -594,7 +597,8 @@ int ddnm_finalize(ddnm_ctx* ctx) {
             hG[s] = hidden_count(ctx->decG[s], allG);
         }
         int smallest = 1 << 30;
-        std::vector<std::pair<int, int>> cands;     // (chunk, CTAs per SM) of the candidates that fit
+        struct Cand { int chunk, ctas, bytes; };
+        std::vector<Cand> cands;                    // the candidates that fit, largest first
         for (int cand = HR_CHUNK; cand >= 8; cand /= 2) {
             int bytes = 0, ctas = 1 << 30;
             for (int s = 0; s < ns; ++s) {
@@ -611,13 +615,15 @@ int ddnm_finalize(ddnm_ctx* ctx) {
                 ctas = std::min(ctas, std::min(by_smem, eval_ctas_by_regs((int)tsize, round4(T.nO + 1), round4(T.nG + 1))));
             }
             smallest = std::min(smallest, bytes);
-            if (bytes <= dev_max) cands.push_back({cand, ctas});
+            if (bytes <= dev_max) cands.push_back({cand, ctas, bytes});
         }
         int best = 0;
-        for (const auto& c : cands) best = std::max(best, c.second);
-        for (int pref : {32, 64, 16, 128, 8})
-            for (const auto& c : cands)
-                if (!hc && c.first == pref && c.second == best) hc = c.first;
+        for (const auto& c : cands) best = std::max(best, c.ctas);
+        constexpr int L1_KEEP = 88 * 1024;           // of the 256 kB unified L1 / shared memory of an SM
+        for (const auto& c : cands)
+            if (!hc && c.ctas == best && c.ctas * (c.bytes + 1024) <= 256 * 1024 - L1_KEEP) hc = c.chunk;
+        for (const auto& c : cands)
+            if (!hc && c.ctas == best) hc = c.chunk;
         need_bytes = smallest;
         if (!hc)
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain's evaluation needs " + std::to_string(smallest) +
