@@ -54,9 +54,13 @@ AE_STAGES = ((200, 3e-3), (200, 1e-3), (200, 3e-4), (200, 1e-4))   # (epochs, le
 AE_SIDE, AE_BATCH = 12, 16
 WS_HIDDEN, WS_EPOCHS, WS_TRAIN = 256, 400, 4096
 # the mixed solves: the paper's stopping rule (Sec. 7.1) plus the step test (a Gauss-Newton step below 1e-5 of
-# the iterate ends the solve), and at most 3 halvings per line search (near the solution the FP32 merit's
-# Armijo test compares rounding noise; 20 halvings there only cost evaluations)
+# the iterate ends the solve), and at most LS_DEPTHS[-1] halvings per line search.  Near the solution the FP32
+# merit's Armijo test compares rounding noise, so halvings there only cost evaluations: the benchmark takes the
+# smallest depth of LS_DEPTHS that makes as many instances of the calibration batch accurate as the deepest
+# (within LS_SLACK of them), the way the plain FP64 solve gets its iteration budget.
 HEADLINE_OPTS = dict(tol=1e-4, max_iter=15, step_tol=1e-5, max_backtracks=3)
+LS_DEPTHS = (0, 1, 2, 3)
+LS_SLACK = 0.005
 _T0 = time.perf_counter()
 
 
@@ -544,13 +548,20 @@ def main():
     k64, f64 = smallest_k(lambda K: R.solve(s64, mu_cal, K)[0], x_cal_ref, [8, 10, 12, 14, 16, 18, 20, 22, 24, 28, 32, 40],
                           R.state_errors)
     log(f"calibrated FP64 budget {k64} ({f64:.3f} of the calibration batch accurate)")
-    # the mixed solves stop by themselves: the paper's rule plus the step test
+    # the mixed solves stop by themselves: the paper's rule plus the step test; the line-search depth is the
+    # smallest that loses no accuracy on the calibration batch
     lib.ddnm_ws_enable(s.ctx, True)
-    s.options(**HEADLINE_OPTS)
-    _, _, st_cal = s.solve(mu_cal)
-    x_cal = s.solve(mu_cal)[0]
-    f_cal = float(np.mean(R.state_errors(x_cal, x_cal_ref) <= ACC))
-    log(f"mixed + warm start on the calibration batch: {f_cal:.3f} accurate, {st_cal['iters'].mean():.2f} iterations")
+    ls_cal = {}
+    for depth in LS_DEPTHS:
+        s.options(**dict(HEADLINE_OPTS, max_backtracks=depth))
+        x_cal, _, st_c = s.solve(mu_cal)
+        ls_cal[depth] = (float(np.mean(R.state_errors(x_cal, x_cal_ref) <= ACC)), st_c)
+    depth = min(d for d in LS_DEPTHS if ls_cal[d][0] >= ls_cal[LS_DEPTHS[-1]][0] - LS_SLACK)
+    head_opts = dict(HEADLINE_OPTS, max_backtracks=depth)
+    s.options(**head_opts)
+    f_cal, st_cal = ls_cal[depth]
+    log(f"mixed + warm start on the calibration batch: line-search depth {depth}, {f_cal:.3f} accurate, "
+        f"{st_cal['iters'].mean():.2f} iterations")
 
     # ---- launch plan of the headline solve: autotuned on this batch with its options
     plan, tune_ms = lib.ddnm_autotune(s.ctx, mu, max_iter=0, reps=2)
@@ -587,7 +598,7 @@ def main():
     l_d = torch.zeros((B, R.nC), dtype=torch.float64, device=dev)
     st_d = torch.zeros(B * 32, dtype=torch.uint8, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    s.options(**HEADLINE_OPTS)
+    s.options(**head_opts)
 
     def step():
         lib.ddnm_solve_batch(s.ctx, B, mu_d, None, None, x_d, l_d, None, st_d)
@@ -647,7 +658,7 @@ def main():
     lib.ddnm_ws_enable(s.ctx, False)
     x64, st64, t64 = timed_once(s64, tol=0.0, max_iter=k64)
     e64t = R.state_errors(x64, x_ref)
-    xmp, stmp, tmp_ = timed_once(s, **HEADLINE_OPTS)
+    xmp, stmp, tmp_ = timed_once(s, **head_opts)
     emp_t = R.state_errors(xmp, x_ref)
     xpr, stpr, tpr = timed_once(s64, tol=1e-4, max_iter=15)
     epr = R.state_errors(xpr, x_ref)
@@ -660,7 +671,7 @@ def main():
     # ---- roofline of the dominant kernel: per-kernel device time from the library's CUDA events, in a
     # separate run of the headline solve through the host-driven loop (events around every launch)
     kb = 3
-    s.options(**HEADLINE_OPTS)
+    s.options(**head_opts)
     plan_now = lib.ddnm_get_tune(s.ctx)
     lib.ddnm_set_tune(s.ctx, **dict(plan_now, graph=0, eval_persist=0))
     lib.ddnm_timing_enable(s.ctx, True)
@@ -710,7 +721,7 @@ def main():
     xh_h = torch.zeros((B, R.nD), dtype=torch.float64).pin_memory()
     lh_h = torch.zeros((B, R.nC), dtype=torch.float64).pin_memory()
     st_h = np.zeros(B, dtype=lib.STATS_DTYPE)
-    s.options(**HEADLINE_OPTS)
+    s.options(**head_opts)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
     if dist:
@@ -734,7 +745,8 @@ def main():
     cfg.update({
         "method": "mixed precision (FP32 evaluation, FP64 KKT / merit / constraint residual) + learned warm start; "
                   "stop at ||F||_2 < 1e-4, at a Gauss-Newton step below 1e-5 of the iterate, or after 15 iterations; "
-                  "at most 3 halvings per line search",
+                  f"at most {depth} halvings per line search (the smallest of {list(LS_DEPTHS)} that loses no "
+                  f"accuracy on the calibration batch)",
         "accuracy_criterion": f"relative 2-norm of g(xh) - g(xh_ref) <= {ACC:g}, xh_ref: FP64 ROM solution "
                               f"({K_REF} SQP iterations); only instances that meet it are counted",
         "accurate_fraction": n_ok / B,
@@ -762,6 +774,8 @@ def main():
                                       "solves_per_s": n_ok_fp(emp_t) * 1.0 / tmp_,
                                       "accurate_fraction": n_ok_fp(emp_t) / B},
         "mixed_warm_start_calibration_batch": {"accurate_fraction": f_cal, "mean_iters": float(st_cal["iters"].mean())},
+        "line_search_calibration": {str(d): {"accurate_fraction": ls_cal[d][0],
+                                             "mean_evals": float(ls_cal[d][1]["n_evals"].mean())} for d in LS_DEPTHS},
         "fp64_paper_rule": {"converged_fraction": float(np.mean(stpr["status"] == lib.DDNM_CONVERGED)),
                             "mean_iters": float(stpr["iters"].mean()), "solves_per_s_all": B / tpr,
                             "accurate_fraction": n_ok_fp(epr) / B},
