@@ -35,6 +35,7 @@ constexpr int TC_KC = 32;                       // hidden units per K chunk (4 M
 constexpr int TC_M = 128;
 constexpr int TC_MAXN = 256;
 constexpr int TC_ABYTES = TC_M * TC_KC * 4;     // one part (hi or lo) of a Q chunk
+constexpr int PG_BATCH = 8;                     // P_G loads a staging thread has in flight
 constexpr long long TC_SPIN = 1LL << 22;        // bounded mbarrier waits (try_wait polls)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -165,18 +166,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_dgemm_tc(ProbDev P, int B, in
             bulk_g2s(smem_u32(Ahi(s)), Qhi + (size_t)c * TC_M * TC_KC, TC_ABYTES, bf);
             bulk_g2s(smem_u32(Alo(s)), Qlo + (size_t)c * TC_M * TC_KC, TC_ABYTES, bf);
         }
-        // P_G chunk: column n = t n^G + k of the tile, K = hidden units h0 .. h0 + 31; split into hi + lo
-        const int h0 = c * TC_KC;
-        for (int e = tid; e < TB * TC_KC * nG; e += TC_THREADS) {
-            const int t = e / (TC_KC * nG), rem = e - t * TC_KC * nG;
-            const int hh = rem / nG, k = rem - hh * nG;
-            float v = 0.f;
-            if (h0 + hh < hG && s_run[t])
-                v = PG[(size_t)(b0 + t) * P.pg_stride + S.pgoff + (size_t)(h0 + hh) * nG + k];
-            const float hi = tf32_rna(v), lo = tf32_rna(v - hi);
-            const int idx = kmajor_index(t * nG + k, hh);
-            Bhi(s)[idx] = hi;
-            Blo(s)[idx] = lo;
+        // P_G chunk: column n = t n^G + k of the tile, K = hidden units h0 .. h0 + 31; split into hi + lo.  Each
+        // thread issues PG_BATCH loads before it splits and stores any (P_G is read-only here), so the chunk's
+        // loads are in flight together instead of one memory latency per element.
+        const int h0 = c * TC_KC, tot = TB * TC_KC * nG;
+        for (int e0 = tid; e0 < tot; e0 += PG_BATCH * TC_THREADS) {
+            float v[PG_BATCH];
+#pragma unroll
+            for (int u = 0; u < PG_BATCH; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                v[u] = 0.f;
+                if (e < tot) {
+                    const int t = e / (TC_KC * nG), rem = e - t * TC_KC * nG;
+                    if (h0 + rem / nG < hG && s_run[t])
+                        v[u] = __ldg(PG + (size_t)(b0 + t) * P.pg_stride + S.pgoff + (size_t)h0 * nG + rem);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PG_BATCH; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                if (e < tot) {
+                    const int t = e / (TC_KC * nG), rem = e - t * TC_KC * nG;
+                    const int hh = rem / nG, k = rem - hh * nG;
+                    const float hi = tf32_rna(v[u]), lo = tf32_rna(v[u] - hi);
+                    const int idx = kmajor_index(t * nG + k, hh);
+                    Bhi(s)[idx] = hi;
+                    Blo(s)[idx] = lo;
+                }
+            }
         }
         for (int e = tid; e < (Np - cols) * TC_KC; e += TC_THREADS) {   // padding columns
             const int n = cols + e / TC_KC, hh = e % TC_KC;
