@@ -438,6 +438,12 @@ class Rom:
         return time.perf_counter() - t0, losses
 
 
+def choose_ls_depth(accurate: dict, depths=LS_DEPTHS, slack=LS_SLACK) -> int:
+    """The smallest line-search depth whose calibration accurate fraction is within `slack` of the deepest's."""
+    ref = accurate[depths[-1]]
+    return min(d for d in depths if accurate[d] >= ref - slack)
+
+
 def smallest_k(run, x_ref, Ks, errf, share=CAL_SHARE):
     """The smallest K of the increasing list Ks whose solve meets the accuracy criterion on at least `share` of
     the instances (bisection; the error falls with K; the last K is taken when none does).  run(K) -> x.
@@ -556,7 +562,7 @@ def main():
         s.options(**dict(HEADLINE_OPTS, max_backtracks=depth))
         x_cal, _, st_c = s.solve(mu_cal)
         ls_cal[depth] = (float(np.mean(R.state_errors(x_cal, x_cal_ref) <= ACC)), st_c)
-    depth = min(d for d in LS_DEPTHS if ls_cal[d][0] >= ls_cal[LS_DEPTHS[-1]][0] - LS_SLACK)
+    depth = choose_ls_depth({d: ls_cal[d][0] for d in LS_DEPTHS})
     head_opts = dict(HEADLINE_OPTS, max_backtracks=depth)
     s.options(**head_opts)
     f_cal, st_cal = ls_cal[depth]

@@ -57,3 +57,25 @@ def test_srpc_rejects_mismatched_sizes():
     with pytest.raises(lib.DDNMError):
         lib.ddnm_load_port_decoder(s.ctx, len(pl), port_decs[0])
     s.close()
+
+
+@pytest.mark.parametrize("name,n_tilde,order", [("tiny12x10_2x2", 2, 1), ("tiny12x10_2x2", 4, -1), ("tiny13x9_3x2", 1, -1),
+                                                ("c1", 3, 1)])
+def test_assembled_interface_decoders_match_oracle(name, n_tilde, order):
+    """The library assembles each subdomain's interface decoder from its port decoders once all of them are
+    loaded (Eq. interface_decoder_rom_port_blocks): W1, b1, the masked W2 values, scale and offset identical to
+    the oracle's assembly, whatever order the ports are loaded in."""
+    import inputs
+    wl, dd, pl, n_p, Q, n_gamma, Ah, port_decs, dec_g = srpc_case(name, n_tilde)
+    s = lib.Solver(wl, n_gamma=n_gamma, n_c=Ah[0].shape[0])
+    lib.ddnm_set_srpc(s.ctx, n_tilde)
+    dec_o = inputs.decoders_for(wl, [sd.interior for sd in dd.subs], [sd.interface for sd in dd.subs])[0]
+    for i, d in enumerate(dec_o):
+        lib.ddnm_load_decoders(s.ctx, i, lib.DDNM_DECODER_INTERIOR, d)
+    for j in list(range(len(pl)))[::order]:
+        lib.ddnm_load_port_decoder(s.ctx, j, port_decs[j])
+    for i in range(wl.n_sub):
+        got = lib.ddnm_get_decoder(s.ctx, i, lib.DDNM_DECODER_INTERFACE, dec_g[i])
+        for k in ("W1", "b1", "vals", "scale", "offset"):
+            assert np.array_equal(got[k], dec_g[i][k]), f"subdomain {i}: {k}"
+    s.close()
