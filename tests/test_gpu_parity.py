@@ -154,15 +154,17 @@ def test_c3_uneven_iterations(prec, K):
     s.options()
 
 
-@pytest.mark.parametrize("prec,max_iter,max_bt", [(FP64, 30, 20), (FP64, 15, 3), (MIXED, 15, 3)])
+@pytest.mark.parametrize("prec,max_iter,max_bt", [(FP64, 30, 20), (FP64, 15, 3), (MIXED, 15, 3), (FP64, 15, 0),
+                                                  (MIXED, 8, 0)])
 def test_line_search_failure_flags(prec, max_iter, max_bt):
     """Line searches that run out of halvings: on the 12x10 2x2 workload, 30 iterations with the paper's 20
     halvings leave two of four instances stalled (every trial fails Armijo, the last one is taken and the
-    instance is flagged LS_FAIL), and 3 halvings flag most instances within 15 iterations.  The flag, the
-    counts and the iterates match the oracle's."""
+    instance is flagged LS_FAIL), and 3 halvings flag most instances within 15 iterations; with no halvings
+    (the benchmark's calibrated depth) every step is the full Gauss-Newton step.  The flag, the counts and the
+    iterates match the oracle's."""
     wl, fom, dd, rom, raw, s = case("tiny12x10_2x2", prec)
     s.options(tol=0.0, max_iter=max_iter, max_backtracks=max_bt)
-    mu = inputs.mu_batch(6 if max_bt == 3 else 4)
+    mu = inputs.mu_batch(6 if max_bt in (0, 3) else 4)
     x, lam, st = s.solve(mu)
     flagged = 0
     for b in range(len(mu)):
