@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__``).
 
-The paper starts its SQP from RBF interpolants of snapshot latents (Sec. 7.2); this build replaces them by
+The paper starts its SQP from RBF interpolants of snapshot latents (Sec. 7.2); the library replaces them by
 a small MLP trained on solutions the SQP itself produces.  Model (flat parameter order W1, b1, W2, b2, W3, b3):
     a1 = tanh(W1 z + b1),  a2 = tanh(W2 a1 + b2),  y = W3 a2 + b3,
 with input z = (mu - mu_c) / mu_s and output xh0 = out_mean + out_std * y (standardisation fixed from the
