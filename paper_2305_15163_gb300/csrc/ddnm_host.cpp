@@ -587,7 +587,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     // at 2 CTAs (208 kB of shared memory per SM) 18.1 ms; the same in FP64 at one CTA per SM, 32 rows
     // 161 ms, 128 rows (about 200 kB) 252 ms; 128 x 128 / 4 x 4 mixed at 4 CTAs, 128 rows 0.83 ms, 32 rows
     // 1.16 ms.  It must fit one CTA.
-    int hc = 0, need_bytes = 0;
+    int hc = 0;
     {
         std::vector<int> hO(ns), hG(ns);
         for (int s = 0; s < ns; ++s) {
@@ -624,7 +624,6 @@ int ddnm_finalize(ddnm_ctx* ctx) {
             if (!hc && c.ctas == best && c.ctas * (c.bytes + 1024) <= 256 * 1024 - L1_KEEP) hc = c.chunk;
         for (const auto& c : cands)
             if (!hc && c.ctas == best) hc = c.chunk;
-        need_bytes = smallest;
         if (!hc)
             return ddnm_fail(ctx, DDNM_E_UNSUPPORTED, "a subdomain's evaluation needs " + std::to_string(smallest) +
                                                           " bytes of shared memory (device limit " +
@@ -749,7 +748,7 @@ int ddnm_finalize(ddnm_ctx* ctx) {
     std::vector<int> cls;
     for (int ro = 4; ro <= 16; ro += 4)
         for (int rg = 4; rg <= 12; rg += 4) {
-            EvalClass c{ro, rg, (int)cls.size(), 0, 0, 0, 1};
+            EvalClass c{ro, rg, (int)cls.size(), 0, 0, 0, 1, 0};
             for (int s = 0; s < ns; ++s) {
                 const SubDev& S = ctx->hsub[s];
                 if (round4(S.nO + 1) == ro && round4(S.nG + 1) == rg) {
